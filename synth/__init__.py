@@ -1,0 +1,188 @@
+"""Seeded synthetic point sets shaped like the paper's workloads (§4, "Datasets").
+
+The paper measures on HACC cosmology particles, GPS traces and generated
+uniform / normal clouds.  None of those files exist here, so these generators
+stand in for them with the same dimension, size and kind of structure:
+
+* ``uniform``      -- i.i.d. uniform in [0,1)^d (the Uniform* sets).
+* ``blobs``        -- isotropic Gaussian blobs plus a uniform background
+                      (VisualVar / trajectory-like clustered 2D data).
+* ``halos``        -- NFW-profile halos with a power-law mass function plus a
+                      uniform background (stands in for Hacc37M / Hacc497M).
+* ``lattice_ties`` -- points of the integer lattice {0..199}^3 / 200 with 4 %
+                      duplicates: a tie-stress set (massive equal weights).
+* ``batched_sizes`` / ``batched_instances`` -- many independent instances of
+                      uneven size.
+
+This module holds no arithmetic of the EMST method: it only draws numbers.
+Everything is generated in FP64 from ``numpy.random.Generator(PCG64(seed))``
+and cast to FP32 C-contiguous (n, d) arrays.  Points that leave the unit box
+are wrapped modulo 1 (a periodic box, as in a cosmology volume).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "uniform",
+    "blobs",
+    "halos",
+    "lattice_ties",
+    "batched_sizes",
+    "batched_instances",
+    "config_points",
+]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _wrap_f32(x: np.ndarray) -> np.ndarray:
+    x = np.mod(x, 1.0)
+    out = x.astype(np.float32)
+    # FP32 rounding of a value just below 1 can land on 1.0; keep [0,1).
+    out[out >= np.float32(1.0)] = np.float32(0.0)
+    return np.ascontiguousarray(out)
+
+
+def uniform(n: int, dim: int, seed: int) -> np.ndarray:
+    """n points i.i.d. uniform in [0,1)^dim."""
+    g = _rng(seed)
+    return _wrap_f32(g.random((n, dim)))
+
+
+def blobs(n: int, dim: int, seed: int, n_blobs: int = 50, frac_background: float = 0.10,
+          sigma_range=(1e-3, 5e-2)) -> np.ndarray:
+    """Gaussian blobs + uniform background.
+
+    (1 - frac_background)·n points come from ``n_blobs`` isotropic Gaussians with
+    centres uniform in the unit box, sigma log-uniform in ``sigma_range`` and
+    mixture weights Dirichlet(1); the rest are uniform.  Rows are shuffled.
+    """
+    g = _rng(seed)
+    n_bg = int(round(frac_background * n))
+    n_cl = n - n_bg
+    centres = g.random((n_blobs, dim))
+    lo, hi = np.log(sigma_range[0]), np.log(sigma_range[1])
+    sigmas = np.exp(g.uniform(lo, hi, n_blobs))
+    weights = g.dirichlet(np.ones(n_blobs))
+    counts = g.multinomial(n_cl, weights)
+    which = np.repeat(np.arange(n_blobs), counts)
+    pts = centres[which] + sigmas[which, None] * g.standard_normal((n_cl, dim))
+    bg = g.random((n_bg, dim))
+    allp = np.concatenate([pts, bg], axis=0)
+    allp = allp[g.permutation(n)]
+    return _wrap_f32(allp)
+
+
+def _nfw_mass(x):
+    return np.log1p(x) - x / (1.0 + x)
+
+
+def _nfw_inverse(y: np.ndarray, c: float) -> np.ndarray:
+    """Solve ln(1+x) - x/(1+x) = y for x in [0, c] (table guess + Newton)."""
+    grid = np.linspace(0.0, c, 8193)
+    mg = _nfw_mass(grid)
+    x = np.interp(y, mg, grid)
+    for _ in range(4):
+        f = _nfw_mass(x) - y
+        fp = x / (1.0 + x) ** 2
+        step = np.where(fp > 1e-300, f / np.maximum(fp, 1e-300), 0.0)
+        x = np.clip(x - step, 0.0, c)
+    return x
+
+
+def halos(n: int, seed: int, frac_background: float = 0.20, alpha: float = 1.9,
+          m_min: float = 10.0, m_max: float = 1e5, concentration: float = 5.0,
+          r_vir_max: float = 0.01) -> np.ndarray:
+    """3D cosmology-shaped clustering.
+
+    (1 - frac_background)·n points are placed in halos.  Halo member counts m
+    follow p(m) ∝ m^-alpha on [m_min, m_max] (inverse-CDF draws, floored), drawn
+    until the budget is used (the last halo is truncated).  Centres are uniform,
+    the radial profile is NFW with the given concentration and
+    r_vir = r_vir_max·(m/m_max)^(1/3); the radius comes from inverting the
+    enclosed-mass profile, the direction is isotropic.  The rest is uniform.
+    """
+    g = _rng(seed)
+    n_bg = int(round(frac_background * n))
+    n_cl = n - n_bg
+    a1 = 1.0 - alpha
+    lo_p, hi_p = m_min ** a1, m_max ** a1
+    sizes = []
+    used = 0
+    while used < n_cl:
+        u = g.random(4096)
+        m = np.floor((lo_p + u * (hi_p - lo_p)) ** (1.0 / a1)).astype(np.int64)
+        m = np.maximum(m, 1)
+        for mi in m:
+            take = int(min(mi, n_cl - used))
+            sizes.append(take)
+            used += take
+            if used >= n_cl:
+                break
+    sizes = np.asarray(sizes, dtype=np.int64)
+    masses = sizes.astype(np.float64)
+    n_h = len(sizes)
+    centres = g.random((n_h, 3))
+    r_vir = r_vir_max * (masses / m_max) ** (1.0 / 3.0)
+    which = np.repeat(np.arange(n_h), sizes)
+    y = g.random(n_cl) * _nfw_mass(concentration)
+    x = _nfw_inverse(y, concentration)
+    r = x / concentration * r_vir[which]
+    v = g.standard_normal((n_cl, 3))
+    v /= np.maximum(np.linalg.norm(v, axis=1, keepdims=True), 1e-300)
+    pts = centres[which] + r[:, None] * v
+    bg = g.random((n_bg, 3))
+    allp = np.concatenate([pts, bg], axis=0)
+    allp = allp[g.permutation(n)]
+    return _wrap_f32(allp)
+
+
+def lattice_ties(n_sites: int = 7_680_000, n_dup: int = 320_000, side: int = 200,
+                 seed: int = 3) -> np.ndarray:
+    """Tie-stress set: distinct lattice sites of {0..side-1}^3 (without
+    replacement) plus ``n_dup`` repeats of drawn sites, shuffled, scaled by 1/side."""
+    g = _rng(seed)
+    total = side ** 3
+    sites = g.choice(total, size=n_sites, replace=False)
+    dups = sites[g.integers(0, n_sites, n_dup)]
+    allsites = np.concatenate([sites, dups])
+    allsites = allsites[g.permutation(len(allsites))]
+    k = np.stack([allsites // (side * side), (allsites // side) % side, allsites % side], axis=1)
+    pts = k.astype(np.float64) / float(side)
+    return np.ascontiguousarray(pts.astype(np.float32))
+
+
+def batched_sizes(num_instances: int, seed: int, lo: int = 100, hi: int = 1_000_000) -> np.ndarray:
+    """Instance sizes log-uniform in [lo, hi] (integers)."""
+    g = _rng(seed)
+    s = np.exp(g.uniform(np.log(lo), np.log(hi), num_instances))
+    return np.floor(s).astype(np.int64)
+
+
+def batched_instances(sizes, seed: int, n_blobs: int = 20, frac_background: float = 0.10):
+    """Concatenated 3D instances (blobs generator, 20 blobs, 10 % uniform) and
+    the int64 offsets array of length len(sizes)+1."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    offsets = np.zeros(len(sizes) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(sizes)
+    out = np.empty((int(offsets[-1]), 3), dtype=np.float32)
+    for k, s in enumerate(sizes):
+        out[offsets[k]:offsets[k + 1]] = blobs(int(s), 3, seed * 1_000_003 + k, n_blobs=n_blobs,
+                                               frac_background=frac_background)
+    return out, offsets
+
+
+def config_points(config: int, n: int | None = None, seed: int | None = None) -> np.ndarray:
+    """The five workload shapes, optionally resized (same generator, other n)."""
+    if config == 1:
+        return uniform(10_000 if n is None else n, 3, 0 if seed is None else seed)
+    if config == 2:
+        return blobs(1_000_000 if n is None else n, 2, 1 if seed is None else seed)
+    if config == 3:
+        return halos(37_000_000 if n is None else n, 2 if seed is None else seed)
+    if config == 5:
+        return halos(100_000_000 if n is None else n, 3 if seed is None else seed)
+    raise ValueError(f"no single point set for config {config}")
