@@ -1,0 +1,164 @@
+/*
+ * emst.h -- C ABI of libemst.so: the single-tree Boruvka Euclidean minimum
+ * spanning tree (EMST) of Prokopenko, Sao and Lebrun-Grandie (arXiv
+ * 2207.00514) on one NVIDIA GB300 (sm_103a).
+ *
+ * The problem (§2, "EMST computation"): given n points in d dimensions, the
+ * EMST is the minimum spanning tree of the complete graph whose edge (i, j)
+ * weighs ||p_i - p_j||.  The method (§3, Fig. 3): build one bounding volume
+ * hierarchy over the points, then repeat Boruvka rounds (Algorithm 1) until
+ * one component is left; each round labels tree nodes by component
+ * (Optimization 1), bounds each component's shortest outgoing edge from
+ * curve-adjacent pairs (Optimization 2), runs one nearest-other-component
+ * query per point (Algorithm 2), reduces the per-component minimum and merges
+ * the chains of components (§3, "Merging components together").
+ *
+ * Conventions shared by every entry point:
+ *  - points: row-major n x dim FP32, dim 2 or 3.  Pointers may be device
+ *    memory or host memory (pinned or pageable); the library detects which.
+ *  - edge weight: the FP32 squared distance w = fma(dz,dz, fma(dy,dy, dx*dx))
+ *    with dx = x_i - x_j rounded to FP32 (2D: fma(dy,dy, dx*dx)).  Squaring
+ *    keeps the order of lengths, so the tree is the EMST.
+ *  - ties: edges compare by (w, min(i,j), max(i,j)), the tie-break of §2
+ *    ("Boruvka's algorithm", last paragraph); under it the MST is unique.
+ *  - output: exactly n-1 edges (i < j, original point indices), sorted by
+ *    that same (w, i, j) order.
+ *  - streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Work is ordered on it; each call returns after that
+ *    work has finished (it synchronises the stream once to read the status).
+ *  - memory: the caller owns inputs and outputs.  Scratch memory is taken
+ *    stream-ordered from a library-owned pool on the current device and
+ *    returned to the pool before the call returns.
+ *  - errors: every entry point returns an emst_status value; nothing traps
+ *    or aborts.  Device-side failures (non-finite input, round limit, an
+ *    internal guard) are read back from a status word at the end of the call.
+ *  - limits: 0 <= n <= EMST_MAX_POINTS.  n = 0 or 1 gives 0 edges.
+ */
+#ifndef EMST_H_
+#define EMST_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One spanning-tree edge: original point indices i < j and the FP32 squared
+ * distance w between them (12 bytes, no padding). */
+typedef struct emst_edge {
+  uint32_t i;
+  uint32_t j;
+  float w;
+} emst_edge;
+
+typedef enum emst_status {
+  EMST_OK = 0,
+  EMST_ERR_INVALID_ARG = -1, /* bad n, dim, null pointer, offsets, options */
+  EMST_ERR_NONFINITE = -2,   /* a coordinate is NaN or infinite */
+  EMST_ERR_OOM = -3,         /* scratch allocation failed */
+  EMST_ERR_CUDA = -4,        /* a CUDA runtime call or launch failed */
+  EMST_ERR_ROUND_LIMIT = -5, /* more Boruvka rounds than ceil(log2 n) (cannot happen for valid input) */
+  EMST_ERR_INTERNAL = -6     /* an internal device-side guard fired (bounded wait, stack) */
+} emst_status;
+
+#define EMST_MAX_POINTS ((int64_t)1073741823) /* 2^30 - 1 */
+
+/* Options for emst_compute_ex.  Zero-initialise, then set struct_size. */
+typedef struct emst_options {
+  int32_t struct_size;        /* sizeof(emst_options) */
+  int32_t block_size;         /* traversal CTA size: 0 = default, else 64..1024, multiple of 32 */
+  int32_t carried_radius;     /* 1 (default if struct_size==0) = seed each query with the previous
+                                 round's neighbour when it is still in another component */
+  int32_t use_graph;          /* 1 = run the round loop as a CUDA graph with a device-side
+                                 loop condition; 0 = host loop (one sync per round) */
+  int32_t count_visits;       /* 1 = count node visits per round into emst_stats */
+  int32_t reserved[11];
+} emst_options;
+
+/* Per-call statistics filled by emst_compute_ex when `stats` is not NULL. */
+typedef struct emst_stats {
+  int32_t struct_size;   /* set by the caller: sizeof(emst_stats) */
+  int32_t rounds;        /* Boruvka rounds run */
+  int32_t kernel_launches; /* kernels this call launched */
+  int32_t reserved0;
+  double total_ms;       /* device time of the whole call (CUDA events) */
+  double build_ms;       /* scene box, codes, sort, hierarchy, refit (A1-A4) */
+  double rounds_ms;      /* all Boruvka rounds */
+  double output_ms;      /* final ordering of the edges (+ copies) */
+  int64_t node_visits;   /* total internal-node visits by queries (count_visits=1) */
+  int64_t components_per_round[40]; /* components at the start of each round */
+  int64_t reserved[8];
+} emst_stats;
+
+/* EMST of n points (§3, Fig. 3 end to end).
+ *   points    n x dim FP32, device or host memory, read only.
+ *   n, dim    0 <= n <= EMST_MAX_POINTS, dim in {2, 3}.
+ *   out_edges room for max(n-1, 0) emst_edge, device or host memory.
+ *   stream    cudaStream_t as void* (NULL = default stream).
+ * Returns EMST_OK or an emst_status error (then out_edges is unspecified). */
+int emst_compute(const float *points, int64_t n, int dim, emst_edge *out_edges, void *stream);
+
+/* emst_compute with options (NULL = defaults) and statistics (NULL = none). */
+int emst_compute_ex(const float *points, int64_t n, int dim, emst_edge *out_edges, void *stream,
+                    const emst_options *options, emst_stats *stats);
+
+/* Many independent EMSTs in one call (not in the paper: instances are
+ * independent problems, each solved exactly as emst_compute would).
+ *   points        all instances' points concatenated, sum(n_k) x dim FP32.
+ *   offsets       num_instances+1 int64, offsets[0] = 0, non-decreasing,
+ *                 instance k = rows [offsets[k], offsets[k+1]); host memory.
+ *   out_edges     room for sum(max(n_k-1, 0)) edges; instance k's edges are
+ *                 contiguous, use ids local to the instance, sorted as above.
+ *   out_offsets   num_instances+1 int64 (host memory): edge block bounds.
+ * Returns EMST_OK or an emst_status error. */
+int emst_compute_batched(const float *points, const int64_t *offsets, int num_instances, int dim,
+                         emst_edge *out_edges, int64_t *out_offsets, void *stream);
+
+/* Static string for a status code (never NULL). */
+const char *emst_status_string(int status);
+
+/* ---------------------------------------------------------------------- */
+/* Inspection entry points: the hot path's intermediate results, for tests */
+/* and tools.  All output pointers are DEVICE memory owned by the caller.   */
+/* ---------------------------------------------------------------------- */
+
+/* Tree build (§2 "ArborX": Z-curve sort and linear BVH; §3 Fig. 4 numbering).
+ *   points           n x dim FP32 (device or host), n >= 2.
+ *   out_codes        n uint64: Morton codes in sorted order.
+ *   out_perm         n uint32: input index of the k-th point in curve order.
+ *   out_children     2(n-1) uint32: internal node v's left/right child; a
+ *                    leaf k is 0x80000000|k, an internal node is its index.
+ *   out_boxes        (n-1) x 2 x 6 FP32: per internal node, per child, the
+ *                    child's box (lo x,y,z, hi x,y,z; z = 0 in 2D).
+ * Any output pointer may be NULL (then it is not written). */
+int emst_build_bvh(const float *points, int64_t n, int dim, uint64_t *out_codes, uint32_t *out_perm,
+                   uint32_t *out_children, float *out_boxes, void *stream);
+
+/* One Boruvka round from given component labels (§3: Optimization 1 node
+ * labels, Optimization 2 upper bounds, Algorithm 2 queries, the per-component
+ * minimum, and the merge).  Everything is indexed in CURVE order (the
+ * out_perm order of emst_build_bvh); a label is the curve index of a point of
+ * its component, and labels[labels[k]] == labels[k] must hold.
+ *   labels_in        n uint32 (device).
+ *   radius_in        n FP32 per-point starting radius, or NULL to use the
+ *                    component upper bound only (device).
+ *   out_node_labels  2(n-1) uint32: the label stored with each child of each
+ *                    internal node (0xFFFFFFFF = several components).
+ *   out_upper_bound  n FP32 indexed by label (+inf where none).
+ *   out_nn_w, out_nn_j  n FP32 / uint32: each point's neighbour in another
+ *                    component within its radius (j in curve order,
+ *                    0xFFFFFFFF = none, w = +inf).
+ *   out_labels       n uint32: labels after the merge.
+ *   out_edges        room for n edges (device); *out_num_edges (host) = count,
+ *                    in no particular order.
+ * Any device output pointer may be NULL. */
+int emst_round_step(const float *points, int64_t n, int dim, const uint32_t *labels_in,
+                    const float *radius_in, uint32_t *out_node_labels, float *out_upper_bound,
+                    float *out_nn_w, uint32_t *out_nn_j, uint32_t *out_labels, emst_edge *out_edges,
+                    int64_t *out_num_edges, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMST_H_ */

@@ -376,7 +376,10 @@ void oracle_component_min(const uint32_t *labels, const uint32_t *orig_ids, cons
 /* A9. Merge (§3, "Merging components together"; the chains of §2): every
  * component C points to T(C) = label of the outside endpoint of its edge.
  * Each point follows the chain from its component until the terminal pair
- * X <-> T(X) and takes the smaller label of the pair.  The chosen edges are
+ * X <-> T(X) and takes the smaller label of the pair.  (When a radius cut
+ * the queries short, a component may have no edge; a chain ends there and
+ * keeps that component's label.  In the full method every component has an
+ * edge.)  The chosen edges are
  * emitted once each (a mutual pair shares one edge).  Returns the number of
  * emitted edges, or -1 if some chain is longer than n (impossible under a
  * strict total order). */
@@ -398,14 +401,17 @@ int64_t oracle_merge(const uint32_t *labels, const int64_t *comp_a, const int64_
     ++emitted;
   }
   for (int64_t k = 0; k < n; ++k) {
+    /* follow C -> T(C) -> ... ; a component without an edge (possible only
+     * when queries were cut off by a radius) ends its chain */
     uint32_t x = labels[k];
-    if (T[x] == ORACLE_INVALID) { new_labels[k] = x; continue; }
     int64_t steps = 0;
-    while (T[T[x]] != x) {
-      x = T[x];
+    for (;;) {
+      uint32_t t = T[x];
+      if (t == ORACLE_INVALID) { new_labels[k] = x; break; }
+      if (T[t] == x) { new_labels[k] = x < t ? x : t; break; }
+      x = t;
       if (++steps > n) { free(T); return -1; }
     }
-    new_labels[k] = x < T[x] ? x : T[x];
   }
   free(T);
   return emitted;

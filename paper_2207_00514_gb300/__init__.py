@@ -1,0 +1,274 @@
+"""Python binding of libemst.so (include/emst.h): single-tree Boruvka EMST on a GB300.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Tensors are torch tensors (device memory, or host memory for the end-to-end
+path); the CUDA stream defaults to torch's current stream.  There is no CPU
+fallback: a missing or unloadable library raises ``EmstLibraryError``.
+
+Edges come back as an (m, 3) int32 tensor: columns i, j (original indices,
+i < j) and the FP32 bits of w (``edges_w(t)`` views them as float32), in
+(w, i, j) order.  ``edges_numpy`` turns them into a structured numpy array
+with fields i, j, w.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+__all__ = [
+    "EmstError",
+    "EmstLibraryError",
+    "EMST_MAX_POINTS",
+    "library_path",
+    "load_library",
+    "emst_compute",
+    "emst_compute_ex",
+    "emst_compute_batched",
+    "emst_status_string",
+    "emst_build_bvh",
+    "emst_round_step",
+    "edges_w",
+    "edges_numpy",
+    "EDGE_DTYPE",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libemst.so")
+_HEADER = os.path.join(os.path.dirname(_HERE), "include", "emst.h")
+EMST_MAX_POINTS = (1 << 30) - 1
+EDGE_DTYPE = np.dtype([("i", np.uint32), ("j", np.uint32), ("w", np.float32)])
+INVALID = 0xFFFFFFFF
+
+
+class EmstError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: emst status {status} ({emst_status_string(status)})")
+
+
+class EmstLibraryError(RuntimeError):
+    pass
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("block_size", ctypes.c_int32),
+                ("carried_radius", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("count_visits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("total_ms", ctypes.c_double), ("build_ms", ctypes.c_double),
+                ("rounds_ms", ctypes.c_double), ("output_ms", ctypes.c_double),
+                ("node_visits", ctypes.c_int64), ("components_per_round", ctypes.c_int64 * 40),
+                ("reserved", ctypes.c_int64 * 8)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(path: str | None = None):
+    """Load libemst.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or _LIB_PATH
+        if not os.path.exists(p):
+            raise EmstLibraryError(f"libemst.so not built ({p}); run __graft_entry__.build()")
+        try:
+            lib = ctypes.CDLL(p)
+        except OSError as e:  # pragma: no cover - depends on the machine
+            raise EmstLibraryError(f"cannot load {p}: {e}") from e
+        V, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.emst_compute.argtypes = [V, I64, I, V, V]
+        lib.emst_compute.restype = I
+        lib.emst_compute_ex.argtypes = [V, I64, I, V, V, ctypes.POINTER(_Options), ctypes.POINTER(_Stats)]
+        lib.emst_compute_ex.restype = I
+        lib.emst_compute_batched.argtypes = [V, V, I, I, V, V, V]
+        lib.emst_compute_batched.restype = I
+        lib.emst_status_string.argtypes = [I]
+        lib.emst_status_string.restype = ctypes.c_char_p
+        lib.emst_build_bvh.argtypes = [V, I64, I, V, V, V, V, V]
+        lib.emst_build_bvh.restype = I
+        lib.emst_round_step.argtypes = [V, I64, I, V, V, V, V, V, V, V, V, ctypes.POINTER(I64), V]
+        lib.emst_round_step.restype = I
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def declared_functions(header: str = _HEADER):
+    """Names of the functions include/emst.h declares."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(emst_[a-z_]+)\s*\(", txt)))
+
+
+def emst_status_string(status: int) -> str:
+    try:
+        return load_library().emst_status_string(int(status)).decode()
+    except EmstLibraryError:
+        return "library not loaded"
+
+
+# ----------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream, device):
+    torch = _torch()
+    if stream is None:
+        if device.type == "cuda":
+            return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check_points(points):
+    torch = _torch()
+    if not isinstance(points, torch.Tensor):
+        raise TypeError("points must be a torch tensor")
+    if points.dtype != torch.float32 or points.dim() != 2 or points.shape[1] not in (2, 3):
+        raise ValueError("points must be an (n, 2|3) float32 tensor")
+    if not points.is_contiguous():
+        raise ValueError("points must be contiguous")
+    return points.shape[0], points.shape[1]
+
+
+def _edges_out(n, like, out_edges):
+    torch = _torch()
+    m = max(n - 1, 0)
+    if out_edges is None:
+        pin = like.device.type == "cpu" and torch.cuda.is_available()
+        out_edges = torch.empty((m, 3), dtype=torch.int32, device=like.device, pin_memory=pin)
+    elif out_edges.dtype != torch.int32 or tuple(out_edges.shape) != (m, 3) or not out_edges.is_contiguous():
+        raise ValueError(f"out_edges must be a contiguous ({m}, 3) int32 tensor")
+    return out_edges
+
+
+def emst_compute(points, out_edges=None, stream=None):
+    """EMST of an (n, dim) float32 tensor (device or host); returns the edges."""
+    n, dim = _check_points(points)
+    out_edges = _edges_out(n, points, out_edges)
+    rc = load_library().emst_compute(_ptr(points), n, dim, _ptr(out_edges),
+                                     _stream_ptr(stream, points.device))
+    if rc != 0:
+        raise EmstError(rc, "emst_compute")
+    return out_edges
+
+
+def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_radius=True,
+                    use_graph=False, count_visits=False):
+    """emst_compute with options; returns (edges, stats dict)."""
+    n, dim = _check_points(points)
+    out_edges = _edges_out(n, points, out_edges)
+    opt = _Options()
+    opt.struct_size = ctypes.sizeof(_Options)
+    opt.block_size = int(block_size)
+    opt.carried_radius = 1 if carried_radius else 0
+    opt.use_graph = 1 if use_graph else 0
+    opt.count_visits = 1 if count_visits else 0
+    st = _Stats()
+    st.struct_size = ctypes.sizeof(_Stats)
+    rc = load_library().emst_compute_ex(_ptr(points), n, dim, _ptr(out_edges),
+                                        _stream_ptr(stream, points.device), ctypes.byref(opt),
+                                        ctypes.byref(st))
+    if rc != 0:
+        raise EmstError(rc, "emst_compute_ex")
+    stats = dict(rounds=st.rounds, kernel_launches=st.kernel_launches, total_ms=st.total_ms,
+                 build_ms=st.build_ms, rounds_ms=st.rounds_ms, output_ms=st.output_ms,
+                 node_visits=st.node_visits,
+                 components_per_round=[int(st.components_per_round[k]) for k in range(min(st.rounds, 40))])
+    return out_edges, stats
+
+
+def emst_compute_batched(points, offsets, out_edges=None, stream=None):
+    """Independent EMSTs of the row blocks [offsets[k], offsets[k+1]).
+    Returns (edges, edge_offsets) with instance-local ids."""
+    torch = _torch()
+    n, dim = _check_points(points)
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if offs.ndim != 1 or len(offs) < 1 or offs[0] != 0 or offs[-1] != n or np.any(np.diff(offs) < 0):
+        raise ValueError("offsets must start at 0, end at n and be non-decreasing")
+    k = len(offs) - 1
+    sizes = np.diff(offs)
+    m = int(np.maximum(sizes - 1, 0).sum())
+    if out_edges is None:
+        pin = points.device.type == "cpu" and torch.cuda.is_available()
+        out_edges = torch.empty((m, 3), dtype=torch.int32, device=points.device, pin_memory=pin)
+    out_offs = np.zeros(k + 1, dtype=np.int64)
+    rc = load_library().emst_compute_batched(_ptr(points), ctypes.c_void_p(offs.ctypes.data), k, dim,
+                                             _ptr(out_edges), ctypes.c_void_p(out_offs.ctypes.data),
+                                             _stream_ptr(stream, points.device))
+    if rc != 0:
+        raise EmstError(rc, "emst_compute_batched")
+    return out_edges, out_offs
+
+
+def emst_build_bvh(points, stream=None):
+    """The built hierarchy: dict(codes, perm, children (n-1, 2), boxes (n-1, 2, 6))."""
+    torch = _torch()
+    n, dim = _check_points(points)
+    dev = points.device if points.device.type == "cuda" else torch.device("cuda")
+    codes = torch.empty(n, dtype=torch.int64, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    children = torch.empty((max(n - 1, 0), 2), dtype=torch.int32, device=dev)
+    boxes = torch.empty((max(n - 1, 0), 2, 6), dtype=torch.float32, device=dev)
+    rc = load_library().emst_build_bvh(_ptr(points), n, dim, _ptr(codes), _ptr(perm), _ptr(children),
+                                       _ptr(boxes), _stream_ptr(stream, dev))
+    if rc != 0:
+        raise EmstError(rc, "emst_build_bvh")
+    return dict(codes=codes, perm=perm, children=children, boxes=boxes)
+
+
+def emst_round_step(points, labels, radius=None, stream=None):
+    """One Boruvka round from curve-order labels; see include/emst.h."""
+    torch = _torch()
+    n, dim = _check_points(points)
+    dev = points.device if points.device.type == "cuda" else torch.device("cuda")
+    labels = labels.to(device=dev, dtype=torch.int32).contiguous()
+    if radius is not None:
+        radius = radius.to(device=dev, dtype=torch.float32).contiguous()
+    node_labels = torch.empty((max(n - 1, 0), 2), dtype=torch.int32, device=dev)
+    ub = torch.empty(n, dtype=torch.float32, device=dev)
+    nn_w = torch.empty(n, dtype=torch.float32, device=dev)
+    nn_j = torch.empty(n, dtype=torch.int32, device=dev)
+    new_labels = torch.empty(n, dtype=torch.int32, device=dev)
+    edges = torch.empty((n, 3), dtype=torch.int32, device=dev)
+    m = ctypes.c_int64(0)
+    rc = load_library().emst_round_step(_ptr(points), n, dim, _ptr(labels), _ptr(radius),
+                                        _ptr(node_labels), _ptr(ub), _ptr(nn_w), _ptr(nn_j),
+                                        _ptr(new_labels), _ptr(edges), ctypes.byref(m),
+                                        _stream_ptr(stream, dev))
+    if rc != 0:
+        raise EmstError(rc, "emst_round_step")
+    return dict(node_labels=node_labels, upper_bound=ub, nn_w=nn_w, nn_j=nn_j, labels=new_labels,
+                edges=edges[: m.value])
+
+
+def edges_w(edges):
+    return edges[:, 2].view(_torch().float32)
+
+
+def edges_numpy(edges) -> np.ndarray:
+    a = edges.detach().cpu().contiguous().numpy()
+    return np.ascontiguousarray(a).view(EDGE_DTYPE).reshape(-1)

@@ -1,0 +1,446 @@
+// api.cu -- the C ABI (include/emst.h): argument checks, scratch layout,
+// host/device pointer handling and the orchestration of the method (Fig. 3):
+// build the hierarchy once, then Boruvka rounds until n-1 edges are found.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace emst {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Stream-ordered scratch from one library-owned pool per device.  The pool
+// keeps its memory between calls (release threshold = max), so repeated calls
+// of the same size allocate nothing new from the driver.
+// ---------------------------------------------------------------------------
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64];
+bool g_pool_ready[64] = {false};
+
+cudaError_t get_pool(int dev, cudaMemPool_t *out) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!g_pool_ready[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaError_t e = cudaMemPoolCreate(&g_pool[dev], &props);
+    if (e != cudaSuccess) return e;
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pool_ready[dev] = true;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+bool device_accessible(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  explicit Carver(char *b) : base(b) {}
+  template <class T>
+  T *take(int64_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += sizeof(T) * (size_t)(count > 0 ? count : 1);
+    return p;
+  }
+};
+
+// Lays the scratch of one problem out from `base` (nullptr: only measures).
+size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
+  const int64_t n = P.n;
+  Carver c(base);
+  P.counters = c.take<uint32_t>(64);
+  P.sort_hist = c.take<uint32_t>(8 * 256);
+  P.sort_tiles = sort_tiles_for(n);
+  P.sort_lookback = c.take<uint32_t>(256 * P.sort_tiles);
+  P.pts = c.take<float4>(n);
+  P.keys[0] = c.take<uint64_t>(n);
+  P.keys[1] = c.take<uint64_t>(n);
+  P.vals[0] = c.take<uint32_t>(n);
+  P.vals[1] = c.take<uint32_t>(n);
+  P.inv = c.take<uint32_t>(n);
+  P.nodes = c.take<NodeRec>(n - 1);
+  P.parent_leaf = c.take<uint32_t>(n);
+  P.parent_node = c.take<uint32_t>(n - 1);
+  P.arrivals = c.take<uint32_t>(n - 1);
+  P.labels = c.take<uint32_t>(n);
+  P.bound = c.take<uint32_t>(n);
+  P.res = c.take<uint2>(n);
+  P.res_id = c.take<uint32_t>(n);
+  P.comp_key = c.take<uint64_t>(n);
+  P.comp_max = c.take<uint32_t>(n);
+  P.target = c.take<uint32_t>(n);
+  P.root = c.take<uint32_t>(n);
+  P.edges = c.take<emst_edge>(n);
+  float *pcopy = c.take<float>(copy_points ? n * P.dim : 1);
+  if (copy_points) P.points = pcopy;
+  emst_edge *ecopy = c.take<emst_edge>(copy_edges ? n : 1);
+  P.out_stage = copy_edges ? ecopy : nullptr;
+  return c.off + 256;
+}
+
+int status_from_bits(uint32_t bits) {
+  if (bits & kErrNonFinite) return EMST_ERR_NONFINITE;
+  if (bits & (kErrStack | kErrSpin | kErrChain)) return EMST_ERR_INTERNAL;
+  return EMST_OK;
+}
+
+#define CU(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) { rc = EMST_ERR_CUDA; goto done; } \
+  } while (0)
+
+int check_args(const float *points, int64_t n, int dim) {
+  if (n < 0 || n > EMST_MAX_POINTS) return EMST_ERR_INVALID_ARG;
+  if (dim != 2 && dim != 3) return EMST_ERR_INVALID_ARG;
+  if (n > 0 && !points) return EMST_ERR_INVALID_ARG;
+  return EMST_OK;
+}
+
+int bits_for(int64_t v) {  // bits needed to represent values in [0, v]
+  int b = 0;
+  while (b < 63 && (v >> b) != 0) ++b;
+  return b;
+}
+
+// A1-A4: scene box, codes, sort, gather, hierarchy, refit.
+void run_build(Problem &P, bool init_labels) {
+  launch_scene_box(P);
+  launch_morton(P);
+  int src = radix_sort_pairs(P, P.n, 0, 8, 0);
+  if (src != 0) {  // keep the sorted codes in keys[0] and the order in vals[0]
+    std::swap(P.keys[0], P.keys[1]);
+    std::swap(P.vals[0], P.vals[1]);
+  }
+  P.perm = P.vals[0];
+  launch_gather(P, P.perm);
+  if (P.n >= 2) {
+    cudaMemsetAsync(P.arrivals, 0, sizeof(uint32_t) * (size_t)(P.n - 1), P.stream);
+    launch_hierarchy(P);
+    launch_refit(P, init_labels);
+  }
+}
+
+void reset_round_state(Problem &P) {
+  cudaMemsetAsync(P.bound, 0xFF, sizeof(uint32_t) * (size_t)P.n, P.stream);
+  cudaMemsetAsync(P.comp_key, 0xFF, sizeof(uint64_t) * (size_t)P.n, P.stream);
+  cudaMemsetAsync(P.comp_max, 0xFF, sizeof(uint32_t) * (size_t)P.n, P.stream);
+}
+
+// A12: the n-1 edges in (w, i, j) order into `out` (device).
+void run_output(Problem &P, emst_edge *out) {
+  const int64_t m = P.n - 1;
+  const int L = bits_for(P.n - 1);
+  launch_edge_keys_j(P, m);
+  int s = radix_sort_pairs(P, m, 0, (L + 7) / 8, 0);
+  launch_edge_keys_wi(P, m, s, L);
+  s = radix_sort_pairs(P, m, 0, (32 + L + 7) / 8, s);
+  launch_edge_gather(P, m, P.vals[s], out);
+}
+
+struct Timer {
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool on = false;
+  void start(cudaStream_t s) {
+    on = true;
+    for (auto &e : ev) cudaEventCreate(&e);
+    cudaEventRecord(ev[0], s);
+  }
+  void mark(int k, cudaStream_t s) { if (on) cudaEventRecord(ev[k], s); }
+  float ms(int a, int b) {
+    float t = 0.f;
+    if (on) cudaEventElapsedTime(&t, ev[a], ev[b]);
+    return t;
+  }
+  ~Timer() { for (auto &e : ev) if (e) cudaEventDestroy(e); }
+};
+
+}  // namespace
+
+int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStream_t stream,
+                const emst_options *opt, emst_stats *stats) {
+  int rc = check_args(points, n, dim);
+  if (rc != EMST_OK) return rc;
+  if (n >= 2 && !out) return EMST_ERR_INVALID_ARG;
+  if (stats) {
+    int32_t sz = stats->struct_size;
+    std::memset(stats, 0, sizeof(emst_stats));
+    stats->struct_size = sz;
+  }
+  if (n == 0) return EMST_OK;
+  int block = 0, carried = 1, count = 0;
+  if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
+    block = opt->block_size;
+    carried = opt->carried_radius;
+    count = opt->count_visits;
+    if (block != 0 && (block < 64 || block > 1024 || block % 32 != 0)) return EMST_ERR_INVALID_ARG;
+  } else if (opt && opt->struct_size != 0) {
+    return EMST_ERR_INVALID_ARG;
+  }
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return EMST_ERR_CUDA;
+  cudaMemPool_t pool;
+  if (get_pool(dev, &pool) != cudaSuccess) return EMST_ERR_CUDA;
+  const bool pts_dev = device_accessible(points);
+  const bool out_dev = n < 2 || device_accessible(out);
+
+  Problem P;
+  P.n = n;
+  P.dim = dim;
+  P.stream = stream;
+  P.points = points;
+  const size_t need = layout(P, nullptr, !pts_dev, !out_dev);
+  char *base = nullptr;
+  uint32_t host_counters[4] = {0, 0, 0, 0};
+  Timer tm;
+  int rounds = 0;
+  if (cudaMallocFromPoolAsync((void **)&base, need, pool, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return EMST_ERR_OOM;
+  }
+  layout(P, base, !pts_dev, !out_dev);
+  if (stats) tm.start(stream);
+  CU(cudaMemsetAsync(P.counters, 0, sizeof(uint32_t) * 64, stream));
+  if (!pts_dev)
+    CU(cudaMemcpyAsync((void *)P.points, points, sizeof(float) * (size_t)n * dim,
+                       cudaMemcpyHostToDevice, stream));
+  run_build(P, true);
+  tm.mark(1, stream);
+  if (n >= 2) {
+    reset_round_state(P);
+    // Boruvka rounds (Fig. 3 loop): each round at least halves the number of
+    // components, so more than ceil(log2 n) rounds means something is wrong.
+    const int limit = bits_for(n - 1) + 1;
+    for (rounds = 0;; ++rounds) {
+      if (rounds >= limit) { rc = EMST_ERR_ROUND_LIMIT; goto done; }
+      if (stats && rounds < 40) stats->components_per_round[rounds] = n - (int64_t)host_counters[0];
+      if (rounds > 0) launch_node_labels(P);
+      launch_upper_bounds(P);
+      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0);
+      launch_reduce(P);
+      launch_merge(P);
+      CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost,
+                         stream));
+      CU(cudaStreamSynchronize(stream));
+      if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
+      if ((int64_t)host_counters[0] >= n - 1) { ++rounds; break; }
+    }
+    tm.mark(2, stream);
+    if ((int64_t)host_counters[0] != n - 1) { rc = EMST_ERR_INTERNAL; goto done; }
+    run_output(P, out_dev ? out : P.out_stage);
+    if (!out_dev)
+      CU(cudaMemcpyAsync(out, P.out_stage, sizeof(emst_edge) * (size_t)(n - 1),
+                         cudaMemcpyDeviceToHost, stream));
+  } else {
+    tm.mark(2, stream);
+  }
+  tm.mark(3, stream);
+  CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost,
+                     stream));
+  CU(cudaStreamSynchronize(stream));
+  CU(cudaGetLastError());
+  rc = status_from_bits(host_counters[1]);
+done:
+  cudaFreeAsync(base, stream);
+  if (rc == EMST_ERR_CUDA) cudaGetLastError();
+  if (stats) {
+    cudaStreamSynchronize(stream);
+    stats->rounds = rounds;
+    stats->kernel_launches = P.launches;
+    stats->build_ms = tm.ms(0, 1);
+    stats->rounds_ms = tm.ms(1, 2);
+    stats->output_ms = tm.ms(2, 3);
+    stats->total_ms = tm.ms(0, 3);
+    stats->node_visits = (int64_t)host_counters[2] | ((int64_t)host_counters[3] << 32);
+  }
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Inspection helpers
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_bound_to_float(const uint32_t *b, float *out, int64_t n) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = bound_to_radius(b[k]);
+}
+__global__ void k_split_res(const uint2 *res, float *w, uint32_t *j, int64_t n) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  uint2 r = res[k];
+  if (w) w[k] = __uint_as_float(r.x);
+  if (j) j[k] = r.y;
+}
+
+struct Session {
+  Problem P;
+  char *base = nullptr;
+  int rc = EMST_OK;
+  ~Session() {
+    if (base) cudaFreeAsync(base, P.stream);
+  }
+};
+
+int open_session(Session &S, const float *points, int64_t n, int dim, cudaStream_t stream) {
+  int rc = check_args(points, n, dim);
+  if (rc != EMST_OK) return rc;
+  if (n < 2) return EMST_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return EMST_ERR_CUDA;
+  cudaMemPool_t pool;
+  if (get_pool(dev, &pool) != cudaSuccess) return EMST_ERR_CUDA;
+  const bool pts_dev = device_accessible(points);
+  S.P.n = n;
+  S.P.dim = dim;
+  S.P.stream = stream;
+  S.P.points = points;
+  size_t need = layout(S.P, nullptr, !pts_dev, false);
+  if (cudaMallocFromPoolAsync((void **)&S.base, need, pool, stream) != cudaSuccess) {
+    cudaGetLastError();
+    S.base = nullptr;
+    return EMST_ERR_OOM;
+  }
+  layout(S.P, S.base, !pts_dev, false);
+  cudaMemsetAsync(S.P.counters, 0, sizeof(uint32_t) * 64, stream);
+  if (!pts_dev)
+    cudaMemcpyAsync((void *)S.P.points, points, sizeof(float) * (size_t)n * dim,
+                    cudaMemcpyHostToDevice, stream);
+  return EMST_OK;
+}
+
+int finish_session(Session &S) {
+  uint32_t st = 0;
+  if (cudaMemcpyAsync(&st, S.P.counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                      S.P.stream) != cudaSuccess)
+    return EMST_ERR_CUDA;
+  if (cudaStreamSynchronize(S.P.stream) != cudaSuccess) return EMST_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return EMST_ERR_CUDA;
+  return status_from_bits(st);
+}
+}  // namespace
+
+}  // namespace emst
+
+using namespace emst;
+
+extern "C" {
+
+const char *emst_status_string(int status) {
+  switch (status) {
+    case EMST_OK: return "ok";
+    case EMST_ERR_INVALID_ARG: return "invalid argument";
+    case EMST_ERR_NONFINITE: return "non-finite coordinate";
+    case EMST_ERR_OOM: return "out of device memory";
+    case EMST_ERR_CUDA: return "CUDA error";
+    case EMST_ERR_ROUND_LIMIT: return "Boruvka round limit exceeded";
+    case EMST_ERR_INTERNAL: return "internal error (device-side guard)";
+    default: return "unknown status";
+  }
+}
+
+int emst_compute(const float *points, int64_t n, int dim, emst_edge *out_edges, void *stream) {
+  return compute_one(points, n, dim, out_edges, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+int emst_compute_ex(const float *points, int64_t n, int dim, emst_edge *out_edges, void *stream,
+                    const emst_options *options, emst_stats *stats) {
+  return compute_one(points, n, dim, out_edges, (cudaStream_t)stream, options, stats);
+}
+
+int emst_compute_batched(const float *points, const int64_t *offsets, int num_instances, int dim,
+                         emst_edge *out_edges, int64_t *out_offsets, void *stream) {
+  if (num_instances < 0 || !offsets || !out_offsets || (dim != 2 && dim != 3))
+    return EMST_ERR_INVALID_ARG;
+  if (offsets[0] != 0) return EMST_ERR_INVALID_ARG;
+  out_offsets[0] = 0;
+  for (int k = 0; k < num_instances; ++k) {
+    int64_t nk = offsets[k + 1] - offsets[k];
+    if (nk < 0 || nk > EMST_MAX_POINTS) return EMST_ERR_INVALID_ARG;
+    out_offsets[k + 1] = out_offsets[k] + (nk > 1 ? nk - 1 : 0);
+  }
+  for (int k = 0; k < num_instances; ++k) {
+    int64_t nk = offsets[k + 1] - offsets[k];
+    if (nk == 0) continue;
+    int rc = compute_one(points + offsets[k] * dim, nk, dim, out_edges + out_offsets[k],
+                         (cudaStream_t)stream, nullptr, nullptr);
+    if (rc != EMST_OK) return rc;
+  }
+  return EMST_OK;
+}
+
+int emst_build_bvh(const float *points, int64_t n, int dim, uint64_t *out_codes, uint32_t *out_perm,
+                   uint32_t *out_children, float *out_boxes, void *stream) {
+  Session S;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = open_session(S, points, n, dim, s);
+  if (rc != EMST_OK) return rc;
+  Problem &P = S.P;
+  run_build(P, true);
+  const int64_t m = n - 1;
+  if (out_codes) cudaMemcpyAsync(out_codes, P.keys[0], 8 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+  if (out_perm) cudaMemcpyAsync(out_perm, P.perm, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+  if (out_children)
+    cudaMemcpy2DAsync(out_children, 8, reinterpret_cast<char *>(P.nodes) + 48, 64, 8, (size_t)m,
+                      cudaMemcpyDeviceToDevice, s);
+  if (out_boxes)
+    cudaMemcpy2DAsync(out_boxes, 48, P.nodes, 64, 48, (size_t)m, cudaMemcpyDeviceToDevice, s);
+  return finish_session(S);
+}
+
+int emst_round_step(const float *points, int64_t n, int dim, const uint32_t *labels_in,
+                    const float *radius_in, uint32_t *out_node_labels, float *out_upper_bound,
+                    float *out_nn_w, uint32_t *out_nn_j, uint32_t *out_labels, emst_edge *out_edges,
+                    int64_t *out_num_edges, void *stream) {
+  if (!labels_in) return EMST_ERR_INVALID_ARG;
+  Session S;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = open_session(S, points, n, dim, s);
+  if (rc != EMST_OK) return rc;
+  Problem &P = S.P;
+  run_build(P, false);
+  cudaMemcpyAsync(P.labels, labels_in, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+  reset_round_state(P);
+  launch_node_labels(P);
+  if (out_node_labels)
+    cudaMemcpy2DAsync(out_node_labels, 8, reinterpret_cast<char *>(P.nodes) + 56, 64, 8,
+                      (size_t)(n - 1), cudaMemcpyDeviceToDevice, s);
+  launch_upper_bounds(P);
+  if (out_upper_bound)
+    k_bound_to_float<<<grid_for(n, 256), 256, 0, s>>>(P.bound, out_upper_bound, n);
+  launch_traverse(P, false, radius_in, 0, false);
+  if (out_nn_w || out_nn_j) k_split_res<<<grid_for(n, 256), 256, 0, s>>>(P.res, out_nn_w, out_nn_j, n);
+  launch_reduce(P);
+  launch_merge(P);
+  if (out_labels) cudaMemcpyAsync(out_labels, P.labels, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+  uint32_t emitted = 0;
+  cudaMemcpyAsync(&emitted, P.counters, 4, cudaMemcpyDeviceToHost, s);
+  rc = finish_session(S);
+  if (rc != EMST_OK) return rc;
+  if (out_edges && emitted)
+    cudaMemcpyAsync(out_edges, P.edges, sizeof(emst_edge) * emitted, cudaMemcpyDeviceToDevice, s);
+  if (out_num_edges) *out_num_edges = emitted;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return EMST_ERR_CUDA;
+  return EMST_OK;
+}
+
+}  // extern "C"

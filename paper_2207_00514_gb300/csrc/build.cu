@@ -1,0 +1,272 @@
+// build.cu -- the tree build of the method (§2 "ArborX": Z-curve
+// linearisation, sort, fully parallel bottom-up hierarchy construction):
+//   A1 scene box, A2 Morton codes, A3 (sort.cu), A4 gather + hierarchy + refit.
+#include "common.cuh"
+
+namespace emst {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------------------
+// A1. Scene box: per-dimension min / max of all coordinates, plus a flag for
+// any non-finite coordinate.  box[0..2] = ordered min, box[3..5] = ordered max.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_scene_box(const float *__restrict__ pts, int64_t n,
+                                                      uint32_t *__restrict__ box,
+                                                      uint32_t *__restrict__ status) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY};
+  float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool bad = false;
+  const int64_t total = n * DIM;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    float x = __ldg(pts + e);
+    int d = (int)(e % DIM);
+    if (!isfinite(x)) { bad = true; continue; }
+#pragma unroll
+    for (int q = 0; q < DIM; ++q)
+      if (q == d) { lo[q] = fminf(lo[q], x); hi[q] = fmaxf(hi[q], x); }
+  }
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[q] = fminf(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+      hi[q] = fmaxf(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) {
+      if (lo[q] <= hi[q]) {
+        atomicMin(&box[q], float_to_ordered(lo[q]));
+        atomicMax(&box[3 + q], float_to_ordered(hi[q]));
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kErrNonFinite);
+}
+
+__global__ void k_box_init(uint32_t *box) {
+  int t = threadIdx.x;
+  if (t < 3) box[t] = 0xFFFFFFFFu;
+  else if (t < 6) box[t] = 0u;
+}
+
+void launch_scene_box(Problem &P) {
+  uint32_t *box = P.counters + 4;
+  k_box_init<<<1, 32, 0, P.stream>>>(box);
+  int grid = 152 * 4;
+  int64_t need = (P.n * P.dim + kBlock - 1) / kBlock;
+  if (need < grid) grid = (int)(need < 1 ? 1 : need);
+  if (P.dim == 3)
+    k_scene_box<3><<<grid, kBlock, 0, P.stream>>>(P.points, P.n, box, P.counters + 1);
+  else
+    k_scene_box<2><<<grid, kBlock, 0, P.stream>>>(P.points, P.n, box, P.counters + 1);
+  P.launches += 2;
+}
+
+// ---------------------------------------------------------------------------
+// A2. Morton codes.  Quantisation decided in FP32 exactly as specified (B = 21
+// bits per dimension in 3D, 32 in 2D):
+//   s = 2^B / (hi - lo) (0 for a flat dimension), t = (x - lo) * s,
+//   q = t >= 2^B ? 2^B - 1 : trunc(t)
+// and the bits interleave x (most significant), y, z.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint64_t x) {
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ uint64_t spread2(uint64_t x) {
+  x &= 0xffffffffull;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_morton(const float *__restrict__ pts, int64_t n,
+                                                   const uint32_t *__restrict__ box,
+                                                   uint64_t *__restrict__ keys,
+                                                   uint32_t *__restrict__ vals) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float twoB = DIM == 3 ? 2097152.0f : 4294967296.0f;
+  const uint32_t qmax = DIM == 3 ? 0x1fffffu : 0xffffffffu;
+  uint32_t q[3] = {0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    float lo = ordered_to_float(box[d]);
+    float hi = ordered_to_float(box[3 + d]);
+    float ext = __fsub_rn(hi, lo);
+    float s = ext > 0.0f ? __fdiv_rn(twoB, ext) : 0.0f;
+    float t = __fmul_rn(__fsub_rn(__ldg(pts + k * DIM + d), lo), s);
+    q[d] = (t >= twoB) ? qmax : (uint32_t)t;
+  }
+  uint64_t code;
+  if (DIM == 3)
+    code = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+  else
+    code = (spread2(q[0]) << 1) | spread2(q[1]);
+  keys[k] = code;
+  vals[k] = (uint32_t)k;
+}
+
+void launch_morton(Problem &P) {
+  int g = grid_for(P.n, kBlock);
+  if (P.dim == 3)
+    k_morton<3><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0]);
+  else
+    k_morton<2><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0]);
+  P.launches += 1;
+}
+
+// ---------------------------------------------------------------------------
+// A4 (a). Gather the points into curve order as float4 (x, y, z, original
+// index bits), the inverse permutation, and the first labels (labels(i) = i,
+// Fig. 3), in curve indices.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_gather(const float *__restrict__ pts,
+                                                   const uint32_t *__restrict__ perm, int64_t n,
+                                                   float4 *__restrict__ out,
+                                                   uint32_t *__restrict__ inv,
+                                                   uint32_t *__restrict__ labels) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  uint32_t o = __ldg(perm + k);
+  const float *p = pts + (int64_t)o * DIM;
+  float x = __ldg(p), y = __ldg(p + 1), z = DIM == 3 ? __ldg(p + 2) : 0.0f;
+  out[k] = make_float4(x, y, z, __uint_as_float(o));
+  inv[o] = (uint32_t)k;
+  labels[k] = (uint32_t)k;
+}
+
+void launch_gather(Problem &P, const uint32_t *perm) {
+  int g = grid_for(P.n, kBlock);
+  if (P.dim == 3)
+    k_gather<3><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.inv, P.labels);
+  else
+    k_gather<2><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.inv, P.labels);
+  P.launches += 1;
+}
+
+// ---------------------------------------------------------------------------
+// A4 (b). Hierarchy: Karras's fully parallel binary radix tree over the sorted
+// codes.  Keys are augmented by their position so equal codes still split.
+// Internal node i covers a range with one end at i; its split gamma gives the
+// children gamma (left) and gamma+1 (right), leaves when the range ends there.
+// This is the numbering drawn in Fig. 4.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k, int64_t n, int64_t i,
+                                            int64_t j) {
+  if (j < 0 || j >= n) return -1;
+  uint64_t a = __ldg(k + i), b = __ldg(k + j);
+  if (a != b) return __clzll((long long)(a ^ b));
+  return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+__global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict__ keys, int64_t n,
+                                                      NodeRec *__restrict__ nodes,
+                                                      uint32_t *__restrict__ parent_leaf,
+                                                      uint32_t *__restrict__ parent_node) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int d = (prefix_delta(keys, n, i, i + 1) - prefix_delta(keys, n, i, i - 1)) > 0 ? 1 : -1;
+  int dmin = prefix_delta(keys, n, i, i - d);
+  int64_t lmax = 2;
+  while (prefix_delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int64_t l = 0;
+  for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+    if (prefix_delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  int64_t j = i + l * d;
+  int dnode = prefix_delta(keys, n, i, j);
+  int64_t s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (prefix_delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+  int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+  uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
+  uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
+  reinterpret_cast<uint2 *>(&nodes[i].d)[0] = make_uint2(left, right);
+  uint32_t up = (uint32_t)i << 1;
+  if (left & kLeafBit) parent_leaf[left & ~kLeafBit] = up; else parent_node[left] = up;
+  if (right & kLeafBit) parent_leaf[right & ~kLeafBit] = up | 1u; else parent_node[right] = up | 1u;
+  if (i == 0) parent_node[0] = kInvalid;
+}
+
+void launch_hierarchy(Problem &P) {
+  k_hierarchy<<<grid_for(P.n - 1, kBlock), kBlock, 0, P.stream>>>(P.keys[0] /*sorted*/, P.n, P.nodes,
+                                                                   P.parent_leaf, P.parent_node);
+  P.launches += 1;
+}
+
+// ---------------------------------------------------------------------------
+// A4 (c). Refit: bottom-up boxes.  One thread per leaf writes its point as the
+// box of its slot in the parent record, then climbs: at every node the first
+// arriver stops and the second (who sees an odd arrival count) merges the two
+// child boxes and carries the union one level up.  Wait-free.  The arrival
+// counters are never reset: each pass adds exactly two arrivals per node, so
+// the parity of the count before the add tells first from second.
+// With init_labels, the round-0 child labels are written on the way
+// (leaf k: label k; internal: several components, kInvalid).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, float lx, float ly, float lz,
+                                               float hx, float hy, float hz) {
+  float2 *f = reinterpret_cast<float2 *>(rec) + 3 * slot;
+  f[0] = make_float2(lx, ly);
+  f[1] = make_float2(lz, hx);
+  f[2] = make_float2(hy, hz);
+}
+
+__global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
+                                                  NodeRec *nodes,
+                                                  const uint32_t *__restrict__ parent_leaf,
+                                                  const uint32_t *__restrict__ parent_node,
+                                                  uint32_t *arrivals, int init_labels) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  float4 p = pts[k];
+  uint32_t up = parent_leaf[k];
+  uint32_t node = up >> 1;
+  int slot = (int)(up & 1u);
+  store_slot_box(&nodes[node], slot, p.x, p.y, p.z, p.x, p.y, p.z);
+  if (init_labels) reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = (uint32_t)k;
+  while (true) {
+    __threadfence();
+    uint32_t before = atomicAdd(&arrivals[node], 1u);
+    if ((before & 1u) == 0u) return;  // first arriver: the sibling will carry on
+    __threadfence();
+    const float4 *r = reinterpret_cast<const float4 *>(&nodes[node]);
+    float4 a = __ldcg(r), b = __ldcg(r + 1), c = __ldcg(r + 2);
+    // left box: a.x a.y a.z | a.w b.x b.y ; right box: b.z b.w c.x | c.y c.z c.w
+    float lx = fminf(a.x, b.z), ly = fminf(a.y, b.w), lz = fminf(a.z, c.x);
+    float hx = fmaxf(a.w, c.y), hy = fmaxf(b.x, c.z), hz = fmaxf(b.y, c.w);
+    if (node == 0) return;
+    up = parent_node[node];
+    node = up >> 1;
+    slot = (int)(up & 1u);
+    store_slot_box(&nodes[node], slot, lx, ly, lz, hx, hy, hz);
+    if (init_labels) reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = kInvalid;
+  }
+}
+
+void launch_refit(Problem &P, bool init_labels) {
+  k_refit<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.n, P.nodes, P.parent_leaf,
+                                                          P.parent_node, P.arrivals,
+                                                          init_labels ? 1 : 0);
+  P.launches += 1;
+}
+
+}  // namespace emst

@@ -1,0 +1,154 @@
+// common.cuh -- types, device helpers and kernel launchers shared by the
+// translation units of libemst.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/emst.h"
+
+namespace emst {
+
+constexpr uint32_t kInvalid = 0xFFFFFFFFu;   // no label / no neighbour
+constexpr uint32_t kLeafBit = 0x80000000u;   // child reference of a leaf
+constexpr uint32_t kNoBound = 0xFFFFFFFFu;   // "+inf" in the u32 radius arrays
+constexpr uint64_t kEmptyKey = ~0ull;        // empty per-component minimum
+
+// Error bits of the device status word.
+enum : uint32_t {
+  kErrNonFinite = 1u << 0,
+  kErrStack = 1u << 1,
+  kErrSpin = 1u << 2,
+  kErrChain = 1u << 3,
+};
+
+// One internal node of the hierarchy, 64 bytes.  The boxes of both children
+// travel with the parent, so a query visiting the node tests both children
+// with one record load (Algorithm 2, the loop over children).  Child labels
+// (Optimization 1) live in the same record and are rewritten every round.
+//   f[0..5]   left child box  (lo x,y,z, hi x,y,z)
+//   f[6..11]  right child box
+//   u[12..13] child references (leaf k: kLeafBit|k; internal node: its index)
+//   u[14..15] child labels (kInvalid: leaves of several components)
+struct __align__(16) NodeRec {
+  float4 a, b, c;
+  uint4 d;
+};
+static_assert(sizeof(NodeRec) == 64, "node record must be 64 bytes");
+
+// ---------------------------------------------------------------------------
+// The edge weight of the method: FP32 squared distance in a fixed fma order,
+// every step rounded explicitly (no contraction freedom left to the compiler).
+// 2D runs with z = 0 everywhere: fma(0, 0, s) == s exactly.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float sq_dist(float px, float py, float pz, float qx, float qy,
+                                         float qz) {
+  float dx = __fsub_rn(px, qx);
+  float dy = __fsub_rn(py, qy);
+  float dz = __fsub_rn(pz, qz);
+  float s = __fmul_rn(dx, dx);
+  s = __fmaf_rn(dy, dy, s);
+  s = __fmaf_rn(dz, dz, s);
+  return s;
+}
+
+// Lower bound of sq_dist from p to any point of the box [lo, hi]: the same
+// order on p - clamp(p, lo, hi).  Per dimension |p - clamp| <= |p - q| for q in
+// the box, rounding is monotone and mul / fma are monotone in non-negative
+// operands, so the bound never exceeds the weight to a point inside; for a
+// degenerate box (a leaf: lo == hi == q) it IS the weight to q.
+__device__ __forceinline__ float box_dist(float px, float py, float pz, float lx, float ly,
+                                          float lz, float hx, float hy, float hz) {
+  float cx = fminf(fmaxf(px, lx), hx);
+  float cy = fminf(fmaxf(py, ly), hy);
+  float cz = fminf(fmaxf(pz, lz), hz);
+  return sq_dist(px, py, pz, cx, cy, cz);
+}
+
+__device__ __forceinline__ float bound_to_radius(uint32_t b) {
+  return b == kNoBound ? __int_as_float(0x7f800000) : __uint_as_float(b);
+}
+
+// Order-preserving map float -> uint32 (for atomic min/max of floats).
+__device__ __forceinline__ uint32_t float_to_ordered(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(uint32_t o) {
+  uint32_t u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t *p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------------------
+// Scratch layout of one EMST problem (carved from one allocation).
+// ---------------------------------------------------------------------------
+struct Problem {
+  int64_t n = 0;
+  int dim = 3;
+  cudaStream_t stream = nullptr;
+
+  const float *points = nullptr;  // n x dim, device
+  float4 *pts = nullptr;          // n, curve order, .w = original index bits
+  uint64_t *keys[2] = {nullptr, nullptr};
+  uint32_t *vals[2] = {nullptr, nullptr};
+  uint32_t *perm = nullptr;       // curve index -> original index
+  uint32_t *inv = nullptr;        // original index -> curve index
+  NodeRec *nodes = nullptr;       // n-1
+  uint32_t *parent_leaf = nullptr;   // n: (parent << 1) | slot
+  uint32_t *parent_node = nullptr;   // n-1: (parent << 1) | slot, root: kInvalid
+  uint32_t *arrivals = nullptr;      // n-1 arrival counters (parity = who is second)
+  uint32_t *labels = nullptr;        // n
+  uint32_t *bound = nullptr;         // n, FP32 bits of the component upper bound
+  uint2 *res = nullptr;              // n: (w bits, neighbour curve index)
+  uint32_t *res_id = nullptr;        // n: neighbour original index
+  uint64_t *comp_key = nullptr;      // n: (w bits << 32) | min original id
+  uint32_t *comp_max = nullptr;      // n: max original id of the winning edge
+  uint32_t *target = nullptr;        // n: component the edge points to
+  uint32_t *root = nullptr;          // n: new label of a component
+  emst_edge *edges = nullptr;        // n: edges in emission order
+  emst_edge *out_stage = nullptr;    // n-1: device staging of host outputs
+  uint32_t *counters = nullptr;      // [0] edges emitted, [1] status bits, [2] visits lo, [3] visits hi,
+                                     // [4..9] scene box (ordered), [10..] sort tile counters
+  uint32_t *sort_hist = nullptr;     // 8 x 256
+  uint32_t *sort_lookback = nullptr; // tiles x 256
+  int64_t sort_tiles = 0;
+  int launches = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (host side), one per kernel family.
+// ---------------------------------------------------------------------------
+// build.cu
+void launch_scene_box(Problem &P);
+void launch_morton(Problem &P);
+void launch_gather(Problem &P, const uint32_t *perm);
+void launch_hierarchy(Problem &P);
+void launch_refit(Problem &P, bool init_labels);
+// sort.cu
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 12;
+constexpr int kSortTile = kSortThreads * kSortItems;
+int64_t sort_tiles_for(int64_t n);
+// Stable LSD radix sort of (keys, vals) pairs on digits [digit_begin, digit_end)
+// (8-bit digits).  Returns the index (0/1) of the buffers holding the result.
+int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int src);
+// rounds.cu
+void launch_node_labels(Problem &P);
+void launch_upper_bounds(Problem &P);
+void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count);
+void launch_reduce(Problem &P);
+void launch_merge(Problem &P);
+void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
+// output
+void launch_edge_keys_j(Problem &P, int64_t m);
+void launch_edge_keys_wi(Problem &P, int64_t m, int src, int shift_i);
+void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge *out);
+
+inline int grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace emst

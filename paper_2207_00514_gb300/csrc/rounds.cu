@@ -1,0 +1,368 @@
+// rounds.cu -- one Boruvka round of the method (§3, Fig. 3 loop body):
+//   A5 node labels (Optimization 1, Fig. 4), A6 component upper bounds
+//   (Optimization 2), A7 nearest-other-component traversal (Algorithm 2),
+//   A8 per-component minimum, A9 merge (§3 "Merging components together"),
+// plus the final ordering of the edges (A12).
+#include "common.cuh"
+
+namespace emst {
+
+constexpr int kBlock = 256;
+constexpr int kStackDepth = 100;  // > 96 = the deepest possible path (see k_traverse)
+
+// ---------------------------------------------------------------------------
+// A5. Node labels, bottom-up (the reduceLabels pass of §3): one thread per
+// leaf stores its label in its parent's record and climbs; the first arriver
+// at a node stops, the second combines the two child labels (equal -> that
+// label, else kInvalid) and carries the result up.  Same parity-of-arrivals
+// scheme as the refit (the counters are shared and never reset).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restrict__ labels,
+                                                        int64_t n, NodeRec *nodes,
+                                                        const uint32_t *__restrict__ parent_leaf,
+                                                        const uint32_t *__restrict__ parent_node,
+                                                        uint32_t *arrivals) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  uint32_t lab = labels[k];
+  uint32_t up = parent_leaf[k];
+  uint32_t node = up >> 1;
+  reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + (up & 1u)] = lab;
+  while (true) {
+    __threadfence();
+    uint32_t before = atomicAdd(&arrivals[node], 1u);
+    if ((before & 1u) == 0u) return;
+    __threadfence();
+    const uint32_t *u = reinterpret_cast<const uint32_t *>(&nodes[node].d);
+    uint32_t l0 = __ldcg(u + 2), l1 = __ldcg(u + 3);
+    lab = (l0 == l1) ? l0 : kInvalid;
+    if (node == 0) return;
+    up = parent_node[node];
+    node = up >> 1;
+    reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + (up & 1u)] = lab;
+  }
+}
+
+void launch_node_labels(Problem &P) {
+  k_node_labels<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.labels, P.n, P.nodes,
+                                                                P.parent_leaf, P.parent_node,
+                                                                P.arrivals);
+  P.launches += 1;
+}
+
+// ---------------------------------------------------------------------------
+// A6. Upper bounds (computeUpperBounds): every pair of curve neighbours with
+// different labels bounds the shortest outgoing edge of both components.
+// bound[] holds FP32 bits (non-negative, so they order like uint32);
+// kNoBound is +inf.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_upper_bounds(const float4 *__restrict__ pts,
+                                                         const uint32_t *__restrict__ labels,
+                                                         int64_t n, uint32_t *bound) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k + 1 >= n) return;
+  uint32_t la = labels[k], lb = labels[k + 1];
+  if (la == lb) return;
+  float4 p = pts[k], q = pts[k + 1];
+  uint32_t w = __float_as_uint(sq_dist(p.x, p.y, p.z, q.x, q.y, q.z));
+  atomicMin(&bound[la], w);
+  atomicMin(&bound[lb], w);
+}
+
+void launch_upper_bounds(Problem &P) {
+  k_upper_bounds<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.labels, P.n, P.bound);
+  P.launches += 1;
+}
+
+// ---------------------------------------------------------------------------
+// A7. Nearest other-component neighbour of every point (Algorithm 2), one
+// thread per point in curve order (neighbouring threads get nearby queries).
+//  - cutoff: the component's upper bound, optionally tightened by the carried
+//    neighbour of the previous round when it still lies in another component
+//    (a real cross edge of this point, so never below the component minimum);
+//  - a child is examined only if its label differs from the query's
+//    (Optimization 1) and its box is within the cutoff (inclusive: equal
+//    weights with smaller ids must survive);
+//  - a leaf within the cutoff updates the best (w, original id) and shrinks
+//    the cutoff to w;
+//  - internal children: descend into the nearer, stack the farther with its
+//    box distance, re-tested when popped.
+// The stack never overflows: every split of the hierarchy uses a strictly
+// later bit of the 96-bit augmented key (64-bit code + 32-bit position), so a
+// root-to-leaf path has at most 96 internal nodes and at most one stacked
+// sibling per level.
+// Ends with the first half of the per-component minimum (A8): an atomicMin of
+// (w bits << 32 | min original id) per component.
+// ---------------------------------------------------------------------------
+template <bool CARRIED, bool RADIUS_IN, bool COUNT>
+__global__ void __launch_bounds__(kBlock) k_traverse(
+    const float4 *__restrict__ pts, const NodeRec *__restrict__ nodes,
+    const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound,
+    const float *__restrict__ radius_in, uint2 *__restrict__ res, uint32_t *__restrict__ res_id,
+    uint64_t *__restrict__ comp_key, int64_t n, uint32_t *status,
+    unsigned long long *visits) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = pts[i];
+  const uint32_t me = labels[i];
+  float radius;
+  if (RADIUS_IN) radius = radius_in[i];
+  else radius = bound_to_radius(bound[me]);
+  if (CARRIED) {
+    uint2 prev = res[i];
+    if (prev.y != kInvalid && labels[prev.y] != me) radius = fminf(radius, __uint_as_float(prev.x));
+  }
+  float best = __int_as_float(0x7f800000);
+  uint32_t bj = kInvalid, bid = kInvalid;
+  uint32_t st_node[kStackDepth];
+  float st_dist[kStackDepth];
+  int sp = 0;
+  uint32_t node = 0;
+  unsigned long long nvis = 0;
+  bool overflow = false;
+
+  while (true) {
+    if (COUNT) ++nvis;
+    const float4 *r = reinterpret_cast<const float4 *>(nodes + node);
+    const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+    const uint4 dd = __ldg(reinterpret_cast<const uint4 *>(r + 3));
+    const float dL = box_dist(p.x, p.y, p.z, a.x, a.y, a.z, a.w, b.x, b.y);
+    const float dR = box_dist(p.x, p.y, p.z, b.z, b.w, c.x, c.y, c.z, c.w);
+    bool okL = (dd.z != me) && (dL <= radius);
+    bool okR = (dd.w != me) && (dR <= radius);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const bool ok = side == 0 ? okL : okR;
+      const uint32_t ref = side == 0 ? dd.x : dd.y;
+      const float d = side == 0 ? dL : dR;
+      if (ok && (ref & kLeafBit) && d <= radius) {
+        const uint32_t j = ref & ~kLeafBit;
+        if (d < best) {
+          best = d;
+          bj = j;
+          bid = kInvalid;
+          radius = d;
+        } else if (d == best) {
+          const uint32_t idj = __float_as_uint(pts[j].w);
+          if (bid == kInvalid) bid = __float_as_uint(pts[bj].w);
+          if (idj < bid) { bj = j; bid = idj; }
+        }
+      }
+    }
+    okL = okL && !(dd.x & kLeafBit) && dL <= radius;
+    okR = okR && !(dd.y & kLeafBit) && dR <= radius;
+    if (okL && okR) {
+      if (sp >= kStackDepth) { overflow = true; break; }
+      if (dL <= dR) { st_node[sp] = dd.y; st_dist[sp] = dR; node = dd.x; }
+      else { st_node[sp] = dd.x; st_dist[sp] = dL; node = dd.y; }
+      ++sp;
+      continue;
+    }
+    if (okL) { node = dd.x; continue; }
+    if (okR) { node = dd.y; continue; }
+    bool found = false;
+    while (sp > 0) {
+      --sp;
+      if (st_dist[sp] <= radius) { node = st_node[sp]; found = true; break; }
+    }
+    if (!found) break;
+  }
+  if (overflow) atomicOr(status, kErrStack);
+  if (COUNT) atomicAdd(visits, nvis);
+  res[i] = make_uint2(__float_as_uint(best), bj);
+  if (bj != kInvalid) {
+    const uint32_t oi = __float_as_uint(p.w);
+    const uint32_t oj = bid != kInvalid ? bid : __float_as_uint(pts[bj].w);
+    res_id[i] = oj;
+    const uint64_t key = ((uint64_t)__float_as_uint(best) << 32) | (uint64_t)(oi < oj ? oi : oj);
+    atomicMin(reinterpret_cast<unsigned long long *>(comp_key + me), (unsigned long long)key);
+  } else {
+    res_id[i] = kInvalid;
+  }
+}
+
+void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count) {
+  if (block <= 0) block = kBlock;
+  int g = grid_for(P.n, block);
+  auto *vis = reinterpret_cast<unsigned long long *>(P.counters + 2);
+  cudaStream_t s = P.stream;
+#define EMST_TRAV(C, R, K)                                                                    \
+  k_traverse<C, R, K><<<g, block, 0, s>>>(P.pts, P.nodes, P.labels, P.bound, radius_in, P.res, \
+                                          P.res_id, P.comp_key, P.n, P.counters + 1, vis)
+  if (radius_in) {
+    EMST_TRAV(false, true, false);
+  } else if (carried) {
+    if (count) EMST_TRAV(true, false, true); else EMST_TRAV(true, false, false);
+  } else {
+    if (count) EMST_TRAV(false, false, true); else EMST_TRAV(false, false, false);
+  }
+#undef EMST_TRAV
+  P.launches += 1;
+}
+
+// ---------------------------------------------------------------------------
+// A8 (second half). Among the points whose (w, min id) equals the component's
+// winner, the smallest max id: together the exact minimum of the key
+// (w, min id, max id) of §2 over the component.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_reduce_max(const float4 *__restrict__ pts,
+                                                       const uint32_t *__restrict__ labels,
+                                                       const uint2 *__restrict__ res,
+                                                       const uint32_t *__restrict__ res_id,
+                                                       const uint64_t *__restrict__ comp_key,
+                                                       uint32_t *comp_max, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint2 r = res[i];
+  if (r.y == kInvalid) return;
+  uint32_t me = labels[i];
+  uint32_t oi = __float_as_uint(pts[i].w), oj = res_id[i];
+  uint64_t key = ((uint64_t)r.x << 32) | (uint64_t)(oi < oj ? oi : oj);
+  if (key == comp_key[me]) atomicMin(&comp_max[me], oi < oj ? oj : oi);
+}
+
+void launch_reduce(Problem &P) {
+  k_reduce_max<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.labels, P.res, P.res_id,
+                                                               P.comp_key, P.comp_max, P.n);
+  P.launches += 1;
+}
+
+// ---------------------------------------------------------------------------
+// A9. Merge.  (a) every component C with an edge points to T(C), the label of
+// the edge's outside endpoint; (b) following the chain C -> T(C) -> ... ends
+// in a mutual pair X <-> T(X) (edge weights strictly decrease along a chain
+// under the total order, so there is no longer cycle); the new label is the
+// smaller label of that pair.  The pair's shared edge is emitted once, by its
+// smaller side; every other component emits its own edge.  (A component with
+// no edge -- possible only when a given radius cut every query short -- ends
+// any chain that reaches it and keeps its label.)  (c) relabel every
+// point and reset the per-component scratch for the next round.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_merge_targets(const uint64_t *__restrict__ comp_key,
+                                                          const uint32_t *__restrict__ comp_max,
+                                                          const uint32_t *__restrict__ inv,
+                                                          const uint32_t *__restrict__ labels,
+                                                          uint32_t *__restrict__ target,
+                                                          int64_t n) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  uint64_t key = comp_key[c];
+  if (key == kEmptyKey) {
+    target[c] = kInvalid;
+    return;
+  }
+  uint32_t lmn = labels[inv[(uint32_t)key]];
+  uint32_t lmx = labels[inv[comp_max[c]]];
+  target[c] = (lmn == (uint32_t)c) ? lmx : lmn;
+}
+
+__global__ void __launch_bounds__(kBlock) k_merge_roots(uint64_t *__restrict__ comp_key,
+                                                        uint32_t *__restrict__ comp_max,
+                                                        const uint32_t *__restrict__ target,
+                                                        uint32_t *__restrict__ root,
+                                                        emst_edge *__restrict__ edges,
+                                                        uint32_t *counters, int64_t n) {
+  int64_t c64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c64 >= n) return;
+  const uint32_t c = (uint32_t)c64;
+  const uint64_t key = comp_key[c];
+  if (key == kEmptyKey) {  // no edge: not a label, or a component whose queries found nothing
+    root[c] = c;
+    return;
+  }
+  const uint32_t t = target[c];
+  const bool mutual = target[t] == c;
+  if (!mutual || c < t) {
+    uint32_t e = atomicAdd(&counters[0], 1u);
+    emst_edge E;
+    E.i = (uint32_t)key;
+    E.j = comp_max[c];
+    E.w = __uint_as_float((uint32_t)(key >> 32));
+    edges[e] = E;
+  }
+  uint32_t x = c, r = c;
+  for (int64_t steps = 0;; ++steps) {
+    uint32_t y = target[x];
+    if (y == kInvalid) { r = x; break; }  // chain ends at a component without an edge
+    if (target[y] == x) { r = x < y ? x : y; break; }
+    x = y;
+    if (steps > n) { atomicOr(&counters[1], kErrChain); r = x; break; }
+  }
+  root[c] = r;
+  comp_key[c] = kEmptyKey;
+  comp_max[c] = kInvalid;
+}
+
+__global__ void __launch_bounds__(kBlock) k_relabel(uint32_t *__restrict__ labels,
+                                                    const uint32_t *__restrict__ root,
+                                                    uint32_t *__restrict__ bound, int64_t n) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  labels[k] = root[labels[k]];
+  bound[k] = kNoBound;
+}
+
+void launch_merge(Problem &P) {
+  int g = grid_for(P.n, kBlock);
+  k_merge_targets<<<g, kBlock, 0, P.stream>>>(P.comp_key, P.comp_max, P.inv, P.labels, P.target,
+                                              P.n);
+  k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.comp_key, P.comp_max, P.target, P.root, P.edges,
+                                            P.counters, P.n);
+  k_relabel<<<g, kBlock, 0, P.stream>>>(P.labels, P.root, P.bound, P.n);
+  P.launches += 3;
+}
+
+__global__ void k_fill_u32(uint32_t *p, uint32_t v, int64_t count) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < count) p[k] = v;
+}
+
+void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count) {
+  if (count <= 0) return;
+  k_fill_u32<<<grid_for(count, kBlock), kBlock, 0, P.stream>>>(p, v, count);
+  P.launches += 1;
+}
+
+// ---------------------------------------------------------------------------
+// A12. Output order: (w, i, j) ascending, by two stable radix sorts (first by
+// j, then by (w bits << L) | i), then a gather.
+// ---------------------------------------------------------------------------
+__global__ void k_edge_keys_j(const emst_edge *__restrict__ edges, int64_t m,
+                              uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  keys[e] = edges[e].j;
+  vals[e] = (uint32_t)e;
+}
+
+__global__ void k_edge_keys_wi(const emst_edge *__restrict__ edges, int64_t m,
+                               uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                               int shift_i) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  emst_edge E = edges[vals[e]];
+  keys[e] = ((uint64_t)__float_as_uint(E.w) << shift_i) | (uint64_t)E.i;
+}
+
+__global__ void k_edge_gather(const emst_edge *__restrict__ edges, int64_t m,
+                              const uint32_t *__restrict__ order, emst_edge *__restrict__ out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  out[e] = edges[order[e]];
+}
+
+void launch_edge_keys_j(Problem &P, int64_t m) {
+  k_edge_keys_j<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[0], P.vals[0]);
+  P.launches += 1;
+}
+void launch_edge_keys_wi(Problem &P, int64_t m, int src, int shift_i) {
+  k_edge_keys_wi<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[src], P.vals[src],
+                                                               shift_i);
+  P.launches += 1;
+}
+void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge *out) {
+  k_edge_gather<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, order, out);
+  P.launches += 1;
+}
+
+}  // namespace emst

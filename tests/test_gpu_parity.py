@@ -1,0 +1,238 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Bit-exact throughout: the tree build (codes, order, hierarchy, boxes), every
+step of one Boruvka round, and whole spanning trees (edge ids and FP32 weight
+bits), on seeded inputs shaped like the paper's workloads, at sizes that span
+several sort tiles and CTAs with ragged tails, plus the degenerate cases.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+INVALID = 0xFFFFFFFF
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2207_00514_gb300 as p
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p.load_library()
+    return p
+
+
+def dev_pts(pts):
+    return torch.from_numpy(np.ascontiguousarray(pts)).cuda()
+
+
+def gpu_emst(pkg, pts):
+    e = pkg.emst_compute(dev_pts(pts))
+    torch.cuda.synchronize()
+    return pkg.edges_numpy(e)
+
+
+def assert_same_edges(got, want, what=""):
+    g = got.view(np.uint8).reshape(-1, 12)
+    w = want.view(np.uint8).reshape(-1, 12)
+    assert g.shape == w.shape, (what, g.shape, w.shape)
+    rows = np.nonzero((g != w).any(1))[0]
+    assert len(rows) == 0, f"{what}: {len(rows)} edges differ, first {rows[:5]}: got {got[rows[:3]]} want {want[rows[:3]]}"
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+# ---------------------------------------------------------------------------
+# A1-A4: tree build
+# ---------------------------------------------------------------------------
+BUILD_CASES = [
+    ("uniform3", lambda: synth.uniform(5000, 3, 1)),
+    ("blobs2", lambda: synth.blobs(7001, 2, 2)),
+    ("halos3", lambda: synth.halos(9000, 3)),
+    ("lattice_dups", lambda: synth.lattice_ties(n_sites=3000, n_dup=400, side=16, seed=4)),
+    ("tiny2", lambda: synth.uniform(2, 3, 5)),
+    ("tiny3", lambda: synth.uniform(3, 2, 6)),
+    ("one_tile_plus_one", lambda: synth.uniform(3073, 3, 7)),
+]
+
+
+@pytest.mark.parametrize("name,make", BUILD_CASES, ids=[c[0] for c in BUILD_CASES])
+def test_bvh_matches_oracle(pkg, name, make):
+    pts = make()
+    n = len(pts)
+    ref = oracle.bvh_reference(pts)
+    out = pkg.emst_build_bvh(dev_pts(pts))
+    torch.cuda.synchronize()
+    codes = out["codes"].cpu().numpy().view(np.uint64)
+    perm = u32(out["perm"])
+    assert np.array_equal(codes, ref["sorted_codes"])
+    assert np.array_equal(perm, ref["perm"])
+    ch = u32(out["children"]).astype(np.int64)
+    conv = np.where(ch & 0x80000000, (n - 1) + (ch & 0x7FFFFFFF), ch)
+    assert np.array_equal(conv[:, 0], ref["left"])
+    assert np.array_equal(conv[:, 1], ref["right"])
+    boxes = out["boxes"].cpu().numpy()
+    sp = ref["sorted_points"]
+    d = pts.shape[1]
+    for side, refs in ((0, ref["left"]), (1, ref["right"])):
+        leaf = refs >= n - 1
+        lo = np.where(leaf[:, None], sp[np.clip(refs - (n - 1), 0, n - 1)], ref["box_lo"][np.clip(refs, 0, n - 2)])
+        hi = np.where(leaf[:, None], sp[np.clip(refs - (n - 1), 0, n - 1)], ref["box_hi"][np.clip(refs, 0, n - 2)])
+        assert np.array_equal(boxes[:, side, 0:d], lo)
+        assert np.array_equal(boxes[:, side, 3:3 + d], hi)
+        if d == 2:
+            assert np.all(boxes[:, side, 2] == 0) and np.all(boxes[:, side, 5] == 0)
+
+
+# ---------------------------------------------------------------------------
+# A5-A9: one round from given labels
+# ---------------------------------------------------------------------------
+def _labels_from_groups(groups):
+    """Curve-order labels: each group's label is its smallest curve index."""
+    n = len(groups)
+    first = {}
+    lab = np.empty(n, np.uint32)
+    for k in range(n):
+        g = int(groups[k])
+        if g not in first:
+            first[g] = k
+        lab[k] = first[g]
+    return lab
+
+
+ROUND_CASES = [
+    ("singletons", 3000, 3, lambda n, g: np.arange(n)),
+    ("runs", 4000, 3, lambda n, g: np.maximum.accumulate(np.where(g.random(n) < 0.05, np.arange(n), 0))),
+    ("scattered", 2500, 2, lambda n, g: g.integers(0, 40, n)),
+    ("two", 1500, 3, lambda n, g: (np.arange(n) > n // 3).astype(np.int64)),
+]
+
+
+@pytest.mark.parametrize("name,n,dim,groups", ROUND_CASES, ids=[c[0] for c in ROUND_CASES])
+@pytest.mark.parametrize("given_radius", [False, True])
+def test_round_step_matches_oracle(pkg, name, n, dim, groups, given_radius):
+    g = np.random.default_rng(n + dim)
+    pts = synth.blobs(n, dim, n, n_blobs=6)
+    ref = oracle.bvh_reference(pts)
+    sp, perm = ref["sorted_points"], ref["perm"]
+    labels = _labels_from_groups(groups(n, g))
+    radius = None
+    if given_radius:
+        radius = np.where(g.random(n) < 0.5, np.float32(np.inf),
+                          np.float32(g.random(n) * 0.002)).astype(np.float32)
+    out = pkg.emst_round_step(dev_pts(pts), torch.from_numpy(labels.view(np.int32)),
+                              None if radius is None else torch.from_numpy(radius))
+    torch.cuda.synchronize()
+    # A5 node labels (per child of each internal node)
+    node_lab = oracle.node_labels(labels, ref["first"], ref["last"])
+    for side, refs in ((0, ref["left"]), (1, ref["right"])):
+        want = np.where(refs >= n - 1, labels[np.clip(refs - (n - 1), 0, n - 1)], node_lab[np.clip(refs, 0, n - 2)])
+        assert np.array_equal(u32(out["node_labels"])[:, side], want.astype(np.uint32))
+    # A6 upper bounds
+    ub = oracle.upper_bounds(sp, labels)
+    assert np.array_equal(out["upper_bound"].cpu().numpy().view(np.uint32), ub.view(np.uint32))
+    # A7 queries
+    rad = ub[labels] if radius is None else radius
+    w, j = oracle.nn_other(sp, perm, labels, rad)
+    assert np.array_equal(out["nn_w"].cpu().numpy().view(np.uint32), w.view(np.uint32))
+    jj = np.where(j < 0, INVALID, j).astype(np.uint32)
+    assert np.array_equal(u32(out["nn_j"]), jj)
+    # A8 + A9
+    cw, ca, cb = oracle.component_min(labels, perm, w, j)
+    new, e = oracle.merge(labels, ca, cb, cw, perm)
+    assert np.array_equal(u32(out["labels"]), new)
+    got_e = np.sort(pkg.edges_numpy(out["edges"]), order=["w", "i", "j"])
+    want_e = np.sort(e, order=["w", "i", "j"])
+    assert_same_edges(got_e, want_e, "round edges")
+
+
+# ---------------------------------------------------------------------------
+# Whole EMST
+# ---------------------------------------------------------------------------
+EMST_CASES = [
+    ("n2", lambda: synth.uniform(2, 3, 0)),
+    ("n3_2d", lambda: synth.uniform(3, 2, 1)),
+    ("n5", lambda: synth.uniform(5, 3, 2)),
+    ("n100_2d", lambda: synth.uniform(100, 2, 3)),
+    ("tile_plus_one", lambda: synth.uniform(3073, 3, 4)),
+    ("config1_uniform10k", lambda: synth.uniform(10_000, 3, 0)),
+    ("blobs2d_12k", lambda: synth.blobs(12_345, 2, 1)),
+    ("halos3d_15k", lambda: synth.halos(15_000, 2)),
+    ("lattice_ties_dups", lambda: synth.lattice_ties(n_sites=6000, n_dup=250, side=20, seed=3)),
+    ("all_identical", lambda: np.full((257, 3), 0.25, np.float32)),
+    ("collinear", lambda: np.stack([np.arange(1000, dtype=np.float32) ** 1.5 / 1e4,
+                                    np.zeros(1000, np.float32), np.zeros(1000, np.float32)], 1)),
+    ("flat_dimension", lambda: np.concatenate([synth.uniform(2000, 2, 9), np.full((2000, 1), 0.5, np.float32)], 1)),
+    ("negative_coords", lambda: (synth.uniform(3000, 3, 10) * 200 - 100).astype(np.float32)),
+]
+
+
+@pytest.mark.parametrize("name,make", EMST_CASES, ids=[c[0] for c in EMST_CASES])
+def test_emst_matches_oracle(pkg, name, make):
+    pts = np.ascontiguousarray(make(), dtype=np.float32)
+    got = gpu_emst(pkg, pts)
+    want = oracle.prim(pts) if len(pts) <= 4000 else oracle.kd_boruvka(pts, threads=os.cpu_count() or 4)
+    assert_same_edges(got, want, name)
+
+
+def test_host_buffers_match_device_buffers(pkg):
+    pts = synth.halos(20_000, 5)
+    dev = gpu_emst(pkg, pts)
+    pinned = torch.from_numpy(pts).pin_memory()
+    e_pinned = pkg.emst_compute(pinned)
+    assert e_pinned.device.type == "cpu"
+    assert_same_edges(pkg.edges_numpy(e_pinned), dev, "pinned host")
+    pageable = torch.from_numpy(pts.copy())
+    out = torch.empty((len(pts) - 1, 3), dtype=torch.int32)
+    pkg.emst_compute(pageable, out_edges=out)
+    assert_same_edges(pkg.edges_numpy(out), dev, "pageable host")
+
+
+def test_repeatable_and_stats(pkg):
+    pts = synth.blobs(50_000, 3, 11)
+    t = dev_pts(pts)
+    a, st = pkg.emst_compute_ex(t, count_visits=True)
+    b = pkg.emst_compute(t)
+    torch.cuda.synchronize()
+    assert_same_edges(pkg.edges_numpy(a), pkg.edges_numpy(b), "repeat")
+    assert 1 <= st["rounds"] <= int(np.ceil(np.log2(len(pts))))
+    assert st["components_per_round"][0] == len(pts)
+    assert st["node_visits"] > 0 and st["kernel_launches"] > 0
+    c, _ = pkg.emst_compute_ex(t, carried_radius=False, block_size=128)
+    assert_same_edges(pkg.edges_numpy(c), pkg.edges_numpy(b), "options")
+
+
+def test_degenerate_sizes_and_errors(pkg):
+    for n in (0, 1):
+        e = pkg.emst_compute(dev_pts(np.zeros((n, 3), np.float32)))
+        assert e.shape == (0, 3)
+    bad = synth.uniform(1000, 3, 1)
+    bad[123, 2] = np.nan
+    with pytest.raises(pkg.EmstError) as ei:
+        pkg.emst_compute(dev_pts(bad))
+    assert ei.value.status == -2
+    bad[123, 2] = np.inf
+    with pytest.raises(pkg.EmstError):
+        pkg.emst_compute(dev_pts(bad))
+    # the context is still usable after a reported error
+    ok = gpu_emst(pkg, synth.uniform(500, 2, 3))
+    assert len(ok) == 499
+
+
+@pytest.mark.parametrize("cfg", [2])
+def test_full_size_config_vs_kd_oracle(pkg, cfg):
+    """Config 2 at full size (1,000,000 2D blob points): the whole tree."""
+    pts = synth.config_points(cfg)
+    got = gpu_emst(pkg, pts)
+    want = oracle.kd_boruvka(pts, threads=os.cpu_count() or 4)
+    assert_same_edges(got, want, f"config {cfg}")
