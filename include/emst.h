@@ -87,7 +87,11 @@ typedef struct emst_stats {
   double output_ms;      /* final ordering of the edges (+ copies) */
   int64_t node_visits;   /* total internal-node visits by queries (count_visits=1) */
   int64_t components_per_round[40]; /* components at the start of each round */
-  int64_t reserved[8];
+  double traverse_ms;    /* device time of the traversal kernels (Algorithm 2) alone */
+  int32_t traverse_launches; /* traversal kernels timed in traverse_ms */
+  int32_t reserved1;
+  double round_traverse_ms[40]; /* traversal time of each round */
+  int64_t reserved[6];
 } emst_stats;
 
 /* EMST of n points (§3, Fig. 3 end to end).

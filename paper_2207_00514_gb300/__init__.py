@@ -66,7 +66,9 @@ class _Stats(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("build_ms", ctypes.c_double),
                 ("rounds_ms", ctypes.c_double), ("output_ms", ctypes.c_double),
                 ("node_visits", ctypes.c_int64), ("components_per_round", ctypes.c_int64 * 40),
-                ("reserved", ctypes.c_int64 * 8)]
+                ("traverse_ms", ctypes.c_double), ("traverse_launches", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32), ("round_traverse_ms", ctypes.c_double * 40),
+                ("reserved", ctypes.c_int64 * 6)]
 
 
 _lock = threading.Lock()
@@ -196,7 +198,9 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
         raise EmstError(rc, "emst_compute_ex")
     stats = dict(rounds=st.rounds, kernel_launches=st.kernel_launches, total_ms=st.total_ms,
                  build_ms=st.build_ms, rounds_ms=st.rounds_ms, output_ms=st.output_ms,
-                 node_visits=st.node_visits,
+                 node_visits=st.node_visits, traverse_ms=st.traverse_ms,
+                 traverse_launches=st.traverse_launches,
+                 round_traverse_ms=[float(st.round_traverse_ms[k]) for k in range(min(st.rounds, 40))],
                  components_per_round=[int(st.components_per_round[k]) for k in range(min(st.rounds, 40))])
     return out_edges, stats
 

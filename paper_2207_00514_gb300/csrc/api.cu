@@ -214,6 +214,8 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
   uint32_t host_counters[4] = {0, 0, 0, 0};
   Timer tm;
   int rounds = 0;
+  cudaEvent_t tev[2 * 40];
+  int n_tev = 0;
   if (cudaMallocFromPoolAsync((void **)&base, need, pool, stream) != cudaSuccess) {
     cudaGetLastError();
     return EMST_ERR_OOM;
@@ -226,6 +228,11 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
                        cudaMemcpyHostToDevice, stream));
   run_build(P, true);
   tm.mark(1, stream);
+  // Non-finite input is reported before any round runs.
+  CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost,
+                     stream));
+  CU(cudaStreamSynchronize(stream));
+  if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
   if (n >= 2) {
     reset_round_state(P);
     // Boruvka rounds (Fig. 3 loop): each round at least halves the number of
@@ -236,7 +243,16 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
       if (stats && rounds < 40) stats->components_per_round[rounds] = n - (int64_t)host_counters[0];
       if (rounds > 0) launch_node_labels(P);
       launch_upper_bounds(P);
+      if (stats && rounds < 40) {
+        cudaEventCreate(&tev[2 * rounds]);
+        cudaEventCreate(&tev[2 * rounds + 1]);
+        cudaEventRecord(tev[2 * rounds], stream);
+      }
       launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0);
+      if (stats && rounds < 40) {
+        cudaEventRecord(tev[2 * rounds + 1], stream);
+        n_tev = rounds + 1;
+      }
       launch_reduce(P);
       launch_merge(P);
       CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost,
@@ -272,6 +288,17 @@ done:
     stats->output_ms = tm.ms(2, 3);
     stats->total_ms = tm.ms(0, 3);
     stats->node_visits = (int64_t)host_counters[2] | ((int64_t)host_counters[3] << 32);
+    for (int r = 0; r < n_tev; ++r) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, tev[2 * r], tev[2 * r + 1]);
+      stats->round_traverse_ms[r] = t;
+      stats->traverse_ms += t;
+    }
+    stats->traverse_launches = n_tev;
+  }
+  for (int r = 0; r < n_tev; ++r) {
+    cudaEventDestroy(tev[2 * r]);
+    cudaEventDestroy(tev[2 * r + 1]);
   }
   return rc;
 }

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
       const float d = side == 0 ? dL : dR;
       if (ok && (ref & kLeafBit) && d <= radius) {
         const uint32_t j = ref & ~kLeafBit;
-        if (d < best) {
+        if (bj == kInvalid || d < best) {  // first candidate, or strictly closer
           best = d;
           bj = j;
           bid = kInvalid;
@@ -243,16 +243,20 @@ __global__ void __launch_bounds__(kBlock) k_merge_targets(const uint64_t *__rest
                                                           const uint32_t *__restrict__ inv,
                                                           const uint32_t *__restrict__ labels,
                                                           uint32_t *__restrict__ target,
-                                                          int64_t n) {
+                                                          uint32_t *status, int64_t n) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   uint64_t key = comp_key[c];
-  if (key == kEmptyKey) {
+  const uint32_t mx = comp_max[c];
+  if (key == kEmptyKey || mx == kInvalid) {
+    // (the second case cannot happen: the winner of the first half always
+    // matches its own key in the second; guarded so no index is ever wild)
+    if (key != kEmptyKey) atomicOr(status, kErrChain);
     target[c] = kInvalid;
     return;
   }
   uint32_t lmn = labels[inv[(uint32_t)key]];
-  uint32_t lmx = labels[inv[comp_max[c]]];
+  uint32_t lmx = labels[inv[mx]];
   target[c] = (lmn == (uint32_t)c) ? lmx : lmn;
 }
 
@@ -271,6 +275,12 @@ __global__ void __launch_bounds__(kBlock) k_merge_roots(uint64_t *__restrict__ c
     return;
   }
   const uint32_t t = target[c];
+  if (t == kInvalid) {  // guarded above; keeps the component as it is
+    root[c] = c;
+    comp_key[c] = kEmptyKey;
+    comp_max[c] = kInvalid;
+    return;
+  }
   const bool mutual = target[t] == c;
   if (!mutual || c < t) {
     uint32_t e = atomicAdd(&counters[0], 1u);
@@ -305,7 +315,7 @@ __global__ void __launch_bounds__(kBlock) k_relabel(uint32_t *__restrict__ label
 void launch_merge(Problem &P) {
   int g = grid_for(P.n, kBlock);
   k_merge_targets<<<g, kBlock, 0, P.stream>>>(P.comp_key, P.comp_max, P.inv, P.labels, P.target,
-                                              P.n);
+                                              P.counters + 1, P.n);
   k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.comp_key, P.comp_max, P.target, P.root, P.edges,
                                             P.counters, P.n);
   k_relabel<<<g, kBlock, 0, P.stream>>>(P.labels, P.root, P.bound, P.n);
