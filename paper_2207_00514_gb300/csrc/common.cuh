@@ -146,6 +146,18 @@ void launch_edge_keys_j(Problem &P, int64_t m);
 void launch_edge_keys_wi(Problem &P, int64_t m, int src, int shift_i);
 void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge *out);
 
+// api.cu: helpers of the orchestration
+bool device_accessible(const void *p);
+// Lays the scratch of one problem out from `base` (nullptr: only measures);
+// returns the bytes needed.
+size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges);
+int status_from_bits(uint32_t bits);
+int check_args(const float *points, int64_t n, int dim);
+int bits_for(int64_t v);
+void run_build(Problem &P, bool init_labels);
+void reset_round_state(Problem &P);
+void run_output(Problem &P, emst_edge *out);
+
 inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   return (int)(g < 1 ? 1 : g);
