@@ -58,7 +58,8 @@ typedef enum emst_status {
   EMST_ERR_OOM = -3,         /* scratch allocation failed */
   EMST_ERR_CUDA = -4,        /* a CUDA runtime call or launch failed */
   EMST_ERR_ROUND_LIMIT = -5, /* more Boruvka rounds than ceil(log2 n) (cannot happen for valid input) */
-  EMST_ERR_INTERNAL = -6     /* an internal device-side guard fired (bounded wait, stack) */
+  EMST_ERR_INTERNAL = -6,    /* an internal device-side guard fired (bounded wait, stack) */
+  EMST_ERR_TOO_LARGE = -7    /* n above EMST_NOALLOC_MAX_POINTS in emst_compute_noalloc */
 } emst_status;
 
 #define EMST_MAX_POINTS ((int64_t)1073741823) /* 2^30 - 1 */
@@ -117,6 +118,28 @@ int emst_compute_ex(const float *points, int64_t n, int dim, emst_edge *out_edge
  * Returns EMST_OK or an emst_status error. */
 int emst_compute_batched(const float *points, const int64_t *offsets, int num_instances, int dim,
                          emst_edge *out_edges, int64_t *out_offsets, void *stream);
+
+/* EMST with no device allocation (the paper has no counterpart: this is a
+ * deployment variant of emst_compute).  For callers that cannot allocate
+ * device memory where they need the tree -- an execute hook that must not
+ * allocate, a process under a device-memory budget it does not own, or a
+ * latency-critical loop that cannot take an allocator's implicit
+ * synchronisation.  Same arguments, result and output order as emst_compute.
+ *   - Scratch: one fixed 13 MiB array in the library's device memory, held by
+ *     every GPU that loads the library until the process exits; no cudaMalloc,
+ *     cudaFree or pool allocation happens in the call.
+ *   - Limit: n <= EMST_NOALLOC_MAX_POINTS, else EMST_ERR_TOO_LARGE (nothing
+ *     launched).
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture on the device.
+ *   - Every call on a device shares the array and it keeps the last call's
+ *     contents (each call clears what must start at zero).  Calls whose GPU
+ *     work overlaps (other streams or threads, same device) race on it and
+ *     give undefined results: serialise them. */
+#define EMST_NOALLOC_MAX_POINTS ((int64_t)65536)
+int emst_compute_noalloc(const float *points, int64_t n, int dim, emst_edge *out_edges,
+                         void *stream);
 
 /* Static string for a status code (never NULL). */
 const char *emst_status_string(int status);

@@ -28,6 +28,8 @@ __all__ = [
     "emst_compute",
     "emst_compute_ex",
     "emst_compute_batched",
+    "emst_compute_noalloc",
+    "EMST_NOALLOC_MAX_POINTS",
     "emst_status_string",
     "emst_build_bvh",
     "emst_round_step",
@@ -105,6 +107,8 @@ def load_library(path: str | None = None):
         lib.emst_build_bvh.restype = I
         lib.emst_round_step.argtypes = [V, I64, I, V, V, V, V, V, V, V, V, ctypes.POINTER(I64), V]
         lib.emst_round_step.restype = I
+        lib.emst_compute_noalloc.argtypes = [V, I64, I, V, V]
+        lib.emst_compute_noalloc.restype = I
         if path is None:
             _lib = lib
         return lib
@@ -175,6 +179,24 @@ def emst_compute(points, out_edges=None, stream=None):
                                      _stream_ptr(stream, points.device))
     if rc != 0:
         raise EmstError(rc, "emst_compute")
+    return out_edges
+
+
+EMST_NOALLOC_MAX_POINTS = 65536
+
+
+def emst_compute_noalloc(points, out_edges=None, stream=None):
+    """emst_compute without any device allocation inside the call: scratch is
+    the library's fixed device array (n <= EMST_NOALLOC_MAX_POINTS).  For
+    callers that cannot allocate device memory where they need the tree.
+    Calls that overlap on one GPU share that array and race: serialise them.
+    (Passing out_edges=None still lets this binding allocate the result.)"""
+    n, dim = _check_points(points)
+    out_edges = _edges_out(n, points, out_edges)
+    rc = load_library().emst_compute_noalloc(_ptr(points), n, dim, _ptr(out_edges),
+                                             _stream_ptr(stream, points.device))
+    if rc != 0:
+        raise EmstError(rc, "emst_compute_noalloc")
     return out_edges
 
 

@@ -40,6 +40,10 @@ cudaError_t get_pool(int dev, cudaMemPool_t *out) {
   return cudaSuccess;
 }
 
+}  // namespace
+
+// Helpers shared with the other entry points of the library (declared in
+// common.cuh).
 bool device_accessible(const void *p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -156,6 +160,8 @@ void run_output(Problem &P, emst_edge *out) {
   s = radix_sort_pairs(P, m, 0, (32 + L + 7) / 8, s);
   launch_edge_gather(P, m, P.vals[s], out);
 }
+
+namespace {
 
 struct Timer {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -381,6 +387,7 @@ const char *emst_status_string(int status) {
     case EMST_ERR_CUDA: return "CUDA error";
     case EMST_ERR_ROUND_LIMIT: return "Boruvka round limit exceeded";
     case EMST_ERR_INTERNAL: return "internal error (device-side guard)";
+    case EMST_ERR_TOO_LARGE: return "too many points for the fixed scratch of emst_compute_noalloc";
     default: return "unknown status";
   }
 }

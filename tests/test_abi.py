@@ -25,7 +25,7 @@ def test_exports_every_declared_function(lib):
 
 def test_status_strings(lib):
     assert pkg.emst_status_string(0) == "ok"
-    for code in range(-6, 0):
+    for code in range(-7, 0):
         s = pkg.emst_status_string(code)
         assert s and s != "unknown status"
     assert pkg.emst_status_string(42) == "unknown status"
