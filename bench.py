@@ -217,12 +217,18 @@ def main():
     ev0.record(stream)
     launches = 0
     trav_ms, trav_launches, rounds = 0.0, 0, []
+    phases = {"build": 0.0, "rounds": 0.0, "output": 0.0, "traverse": 0.0}
+    round_trav = None
     for _ in range(args.steps):
         st = step(stats=True)
         launches += st["kernel_launches"]
         trav_ms += st["traverse_ms"]
         trav_launches += st["traverse_launches"]
         rounds.append(st["rounds"])
+        for k in ("build", "rounds", "output", "traverse"):
+            phases[k] += st[k + "_ms"] / args.steps
+        round_trav = st["round_traverse_ms"]
+        comps = st["components_per_round"]
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     if pg:
@@ -300,6 +306,9 @@ def main():
                        "inputs": "resident in HBM; working set ~6 GB and input 444 MB, both larger than L2 (no flush)",
                        "parallelism": f"{world} independent replica(s)" if world > 1 else "1 GPU",
                        "rounds": rounds[-1] if rounds else None,
+                       "phases_ms": {k: round(v, 3) for k, v in phases.items()},
+                       "round_traverse_ms": [round(x, 3) for x in (round_trav or [])],
+                       "components_per_round": comps,
                        "mfeatures_per_s": value * 3},
             "roofline": roofline,
             "cpu_baseline": cpu,
