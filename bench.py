@@ -267,6 +267,11 @@ def main():
                "h2d_bytes_per_step": int(n * 3 * 4), "d2h_bytes_per_step": int((n - 1) * 12),
                "ms_per_step": ems}
 
+    # node visits per query (one extra, untimed call with counting on)
+    vis = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, count_visits=True)[1]
+    torch.cuda.synchronize(dev)
+    visits_per_query_round = vis["node_visits"] / float(n * max(vis["rounds"], 1))
+
     peak, peak_kind = measured_peaks()
     avg_trav = trav_ms / max(trav_launches, 1)
     alg = traversal_algorithmic_bytes(n)
@@ -309,6 +314,7 @@ def main():
                        "phases_ms": {k: round(v, 3) for k, v in phases.items()},
                        "round_traverse_ms": [round(x, 3) for x in (round_trav or [])],
                        "components_per_round": comps,
+                       "node_visits_per_query_per_round": round(visits_per_query_round, 2),
                        "mfeatures_per_s": value * 3},
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -85,6 +85,8 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.parent_leaf = c.take<uint32_t>(n);
   P.parent_node = c.take<uint32_t>(n - 1);
   P.arrivals = c.take<uint32_t>(n - 1);
+  P.range = c.take<uint2>(n - 1);
+  P.runs = c.take<uint32_t>(n);
   P.labels = c.take<uint32_t>(n);
   P.bound = c.take<uint32_t>(n);
   P.res = c.take<uint2>(n);

@@ -178,7 +178,8 @@ __device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k, int6
 __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict__ keys, int64_t n,
                                                       NodeRec *__restrict__ nodes,
                                                       uint32_t *__restrict__ parent_leaf,
-                                                      uint32_t *__restrict__ parent_node) {
+                                                      uint32_t *__restrict__ parent_node,
+                                                      uint2 *__restrict__ range) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   int d = (prefix_delta(keys, n, i, i + 1) - prefix_delta(keys, n, i, i - 1)) > 0 ? 1 : -1;
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
   uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
   uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
   reinterpret_cast<uint2 *>(&nodes[i].d)[0] = make_uint2(left, right);
+  range[i] = make_uint2((uint32_t)lo, (uint32_t)hi);
   uint32_t up = (uint32_t)i << 1;
   if (left & kLeafBit) parent_leaf[left & ~kLeafBit] = up; else parent_node[left] = up;
   if (right & kLeafBit) parent_leaf[right & ~kLeafBit] = up | 1u; else parent_node[right] = up | 1u;
@@ -208,7 +210,8 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
 
 void launch_hierarchy(Problem &P) {
   k_hierarchy<<<grid_for(P.n - 1, kBlock), kBlock, 0, P.stream>>>(P.keys[0] /*sorted*/, P.n, P.nodes,
-                                                                   P.parent_leaf, P.parent_node);
+                                                                   P.parent_leaf, P.parent_node,
+                                                                   P.range);
   P.launches += 1;
 }
 

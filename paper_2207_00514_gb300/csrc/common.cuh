@@ -99,6 +99,8 @@ struct Problem {
   uint32_t *parent_leaf = nullptr;   // n: (parent << 1) | slot
   uint32_t *parent_node = nullptr;   // n-1: (parent << 1) | slot, root: kInvalid
   uint32_t *arrivals = nullptr;      // n-1 arrival counters (parity = who is second)
+  uint2 *range = nullptr;            // n-1: leaf range [first, last] of each internal node
+  uint32_t *runs = nullptr;          // n: label boundaries before each curve position
   uint32_t *labels = nullptr;        // n
   uint32_t *bound = nullptr;         // n, FP32 bits of the component upper bound
   uint2 *res = nullptr;              // n: (w bits, neighbour curve index)

@@ -9,45 +9,132 @@ namespace emst {
 
 constexpr int kBlock = 256;
 constexpr int kStackDepth = 100;  // > 96 = the deepest possible path (see k_traverse)
+constexpr int kWindow = 4;        // curve neighbours on each side that seed a query
 
 // ---------------------------------------------------------------------------
-// A5. Node labels, bottom-up (the reduceLabels pass of §3): one thread per
-// leaf stores its label in its parent's record and climbs; the first arriver
-// at a node stops, the second combines the two child labels (equal -> that
-// label, else kInvalid) and carries the result up.  Same parity-of-arrivals
-// scheme as the refit (the counters are shared and never reset).
+// A5. Node labels (the reduceLabels step of §3, Optimization 1; Fig. 4): a
+// node's label is the label shared by all of its leaves, else kInvalid.  The
+// leaves of a node are a contiguous range [a, b] of curve positions, so the
+// node is single-component iff no label boundary lies inside the range.  With
+// runs[k] = number of positions m < k where labels[m] != labels[m+1] (one
+// prefix scan), that is runs[b] == runs[a], and the label is labels[a].  The
+// result equals the bottom-up combination of the paper (equal child labels ->
+// that label, else invalid) without its atomics and climbing threads.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restrict__ labels,
-                                                        int64_t n, NodeRec *nodes,
-                                                        const uint32_t *__restrict__ parent_leaf,
-                                                        const uint32_t *__restrict__ parent_node,
-                                                        uint32_t *arrivals) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  uint32_t lab = labels[k];
-  uint32_t up = parent_leaf[k];
-  uint32_t node = up >> 1;
-  reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + (up & 1u)] = lab;
-  while (true) {
-    __threadfence();
-    uint32_t before = atomicAdd(&arrivals[node], 1u);
-    if ((before & 1u) == 0u) return;
-    __threadfence();
-    const uint32_t *u = reinterpret_cast<const uint32_t *>(&nodes[node].d);
-    uint32_t l0 = __ldcg(u + 2), l1 = __ldcg(u + 3);
-    lab = (l0 == l1) ? l0 : kInvalid;
-    if (node == 0) return;
-    up = parent_node[node];
-    node = up >> 1;
-    reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + (up & 1u)] = lab;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr uint32_t kScanAggregate = 1u << 30;
+constexpr uint32_t kScanPrefix = 2u << 30;
+constexpr uint32_t kScanMask = (1u << 30) - 1u;
+
+// Single-pass exclusive scan of the boundary flags with decoupled look-back.
+__global__ void __launch_bounds__(kScanThreads) k_label_runs(const uint32_t *__restrict__ labels,
+                                                             int64_t n, uint32_t *__restrict__ runs,
+                                                             uint32_t *lookback,
+                                                             uint32_t *tile_counter,
+                                                             uint32_t *status) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_warp[kScanThreads / 32];
+  __shared__ uint32_t s_prefix;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t first = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
+  uint32_t flags = 0;  // bit q: boundary after position first+q
+  uint32_t lab[kScanItems + 1];
+#pragma unroll
+  for (int q = 0; q <= kScanItems; ++q) {
+    int64_t k = first + q;
+    lab[q] = k < n ? __ldg(labels + k) : kInvalid;
+  }
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t k = first + q;
+    if (k + 1 < n && lab[q] != lab[q + 1]) flags |= 1u << q;
+  }
+  const uint32_t mine = __popc(flags);
+  uint32_t x = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
+    uint32_t z = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
+    }
+    if (lane < kScanThreads / 32) s_warp[lane] = z - w;  // exclusive per warp
+    const uint32_t total = __shfl_sync(0xffffffffu, z, kScanThreads / 32 - 1);
+    if (lane == 0) {
+      volatile uint32_t *lb = lookback + tile;
+      *lb = (tile == 0 ? kScanPrefix : kScanAggregate) | total;
+      uint32_t excl = 0;
+      if (tile > 0) {
+        for (int64_t j = (int64_t)tile - 1; j >= 0; --j) {
+          const volatile uint32_t *pj = lookback + j;
+          uint32_t wv = *pj;
+          int spins = 0;
+          while ((wv & ~kScanMask) == 0u) {
+            if (++spins > (1 << 22)) { atomicOr(status, kErrSpin); wv = kScanPrefix; break; }
+            __nanosleep(32);
+            wv = *pj;
+          }
+          excl += wv & kScanMask;
+          if ((wv & ~kScanMask) == kScanPrefix) break;
+        }
+        *lb = kScanPrefix | ((excl + total) & kScanMask);
+      }
+      s_prefix = excl;
+    }
+  }
+  __syncthreads();
+  uint32_t run = s_prefix + s_warp[warp] + x - mine;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t k = first + q;
+    if (k < n) runs[k] = run;
+    run += (flags >> q) & 1u;
   }
 }
 
+__global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restrict__ labels,
+                                                        const uint32_t *__restrict__ runs,
+                                                        const uint2 *__restrict__ range,
+                                                        int64_t n, NodeRec *__restrict__ nodes) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const uint2 ch = *reinterpret_cast<const uint2 *>(&nodes[i].d);
+  uint32_t lab[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const uint32_t c = s == 0 ? ch.x : ch.y;
+    if (c & kLeafBit) {
+      lab[s] = __ldg(labels + (c & ~kLeafBit));
+    } else {
+      const uint2 r = __ldg(range + c);
+      lab[s] = (__ldg(runs + r.y) == __ldg(runs + r.x)) ? __ldg(labels + r.x) : kInvalid;
+    }
+  }
+  reinterpret_cast<uint2 *>(&nodes[i].d)[1] = make_uint2(lab[0], lab[1]);
+}
+
 void launch_node_labels(Problem &P) {
-  k_node_labels<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.labels, P.n, P.nodes,
-                                                                P.parent_leaf, P.parent_node,
-                                                                P.arrivals);
-  P.launches += 1;
+  const int64_t tiles = (P.n + kScanTile - 1) / kScanTile;
+  uint32_t *ctr = P.counters + 24;
+  cudaMemsetAsync(ctr, 0, sizeof(uint32_t), P.stream);
+  cudaMemsetAsync(P.sort_lookback, 0, sizeof(uint32_t) * (size_t)tiles, P.stream);
+  k_label_runs<<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(P.labels, P.n, P.runs,
+                                                               P.sort_lookback, ctr,
+                                                               P.counters + 1);
+  k_node_labels<<<grid_for(P.n - 1, kBlock), kBlock, 0, P.stream>>>(P.labels, P.runs, P.range,
+                                                                    P.n, P.nodes);
+  P.launches += 2;
 }
 
 // ---------------------------------------------------------------------------
@@ -114,6 +201,26 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   }
   float best = __int_as_float(0x7f800000);
   uint32_t bj = kInvalid, bid = kInvalid;
+  if (!RADIUS_IN) {
+    // Seed with the curve neighbours within kWindow positions that lie in
+    // other components: real candidates, so their best weight is a valid
+    // (inclusive) cutoff.  Ties keep the smaller original id.
+#pragma unroll
+    for (int o = -kWindow; o <= kWindow; ++o) {
+      const int64_t j = i + o;
+      if (o == 0 || j < 0 || j >= n) continue;
+      if (__ldg(labels + j) == me) continue;
+      const float4 q = __ldg(pts + j);
+      const float d = sq_dist(p.x, p.y, p.z, q.x, q.y, q.z);
+      const uint32_t idj = __float_as_uint(q.w);
+      if (d < best || (d == best && idj < bid)) { best = d; bj = (uint32_t)j; bid = idj; }
+    }
+    radius = fminf(radius, best);
+    // The component's best weight found so far this round (a real cross edge
+    // of the component, so never below its minimum) tightens the cutoff.
+    const uint32_t cw = (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(comp_key + me)) >> 32);
+    radius = fminf(radius, bound_to_radius(cw));
+  }
   uint32_t st_node[kStackDepth];
   float st_dist[kStackDepth];
   int sp = 0;
