@@ -256,7 +256,7 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
         cudaEventCreate(&tev[2 * rounds + 1]);
         cudaEventRecord(tev[2 * rounds], stream);
       }
-      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0);
+      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true);
       if (stats && rounds < 40) {
         cudaEventRecord(tev[2 * rounds + 1], stream);
         n_tev = rounds + 1;
@@ -463,7 +463,7 @@ int emst_round_step(const float *points, int64_t n, int dim, const uint32_t *lab
   launch_upper_bounds(P);
   if (out_upper_bound)
     k_bound_to_float<<<grid_for(n, 256), 256, 0, s>>>(P.bound, out_upper_bound, n);
-  launch_traverse(P, false, radius_in, 0, false);
+  launch_traverse(P, false, radius_in, 0, false, false);
   if (out_nn_w || out_nn_j) k_split_res<<<grid_for(n, 256), 256, 0, s>>>(P.res, out_nn_w, out_nn_j, n);
   launch_reduce(P);
   launch_merge(P);

@@ -98,7 +98,7 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
       if (round >= limit) return EMST_ERR_ROUND_LIMIT;
       if (round > 0) launch_node_labels(P);
       launch_upper_bounds(P);
-      launch_traverse(P, round > 0, nullptr, 0, false);
+      launch_traverse(P, round > 0, nullptr, 0, false, true);
       launch_reduce(P);
       launch_merge(P);
       if (!sync_counters()) return EMST_ERR_CUDA;

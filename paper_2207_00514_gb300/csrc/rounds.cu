@@ -180,8 +180,14 @@ void launch_upper_bounds(Problem &P) {
 // sibling per level.
 // Ends with the first half of the per-component minimum (A8): an atomicMin of
 // (w bits << 32 | min original id) per component.
+// SEEDED (the emst_compute path) also starts each query from its best curve
+// neighbour in another component and from the component's best weight found
+// so far; both are real cross edges, so the component minimum is unchanged,
+// but a point may then report a neighbour outside its own bound, or none.
+// Unseeded, each point reports exactly its nearest other-component point
+// within its cutoff (what the inspection entry point exposes).
 // ---------------------------------------------------------------------------
-template <bool CARRIED, bool RADIUS_IN, bool COUNT>
+template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED>
 __global__ void __launch_bounds__(kBlock) k_traverse(
     const float4 *__restrict__ pts, const NodeRec *__restrict__ nodes,
     const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound,
@@ -201,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   }
   float best = __int_as_float(0x7f800000);
   uint32_t bj = kInvalid, bid = kInvalid;
-  if (!RADIUS_IN) {
+  if (SEEDED) {
     // Seed with the curve neighbours within kWindow positions that lie in
     // other components: real candidates, so their best weight is a valid
     // (inclusive) cutoff.  Ties keep the smaller original id.
@@ -288,20 +294,23 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   }
 }
 
-void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count) {
+void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
+                     bool seeded) {
   if (block <= 0) block = kBlock;
   int g = grid_for(P.n, block);
   auto *vis = reinterpret_cast<unsigned long long *>(P.counters + 2);
   cudaStream_t s = P.stream;
-#define EMST_TRAV(C, R, K)                                                                    \
-  k_traverse<C, R, K><<<g, block, 0, s>>>(P.pts, P.nodes, P.labels, P.bound, radius_in, P.res, \
-                                          P.res_id, P.comp_key, P.n, P.counters + 1, vis)
+#define EMST_TRAV(C, R, K, S)                                                                    \
+  k_traverse<C, R, K, S><<<g, block, 0, s>>>(P.pts, P.nodes, P.labels, P.bound, radius_in, P.res, \
+                                             P.res_id, P.comp_key, P.n, P.counters + 1, vis)
   if (radius_in) {
-    EMST_TRAV(false, true, false);
+    EMST_TRAV(false, true, false, false);
+  } else if (!seeded) {
+    EMST_TRAV(false, false, false, false);
   } else if (carried) {
-    if (count) EMST_TRAV(true, false, true); else EMST_TRAV(true, false, false);
+    if (count) EMST_TRAV(true, false, true, true); else EMST_TRAV(true, false, false, true);
   } else {
-    if (count) EMST_TRAV(false, false, true); else EMST_TRAV(false, false, false);
+    if (count) EMST_TRAV(false, false, true, true); else EMST_TRAV(false, false, false, true);
   }
 #undef EMST_TRAV
   P.launches += 1;
