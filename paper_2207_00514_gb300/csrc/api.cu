@@ -86,6 +86,7 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.parent_node = c.take<uint32_t>(n - 1);
   P.arrivals = c.take<uint32_t>(n - 1);
   P.range = c.take<uint2>(n - 1);
+  P.delta = c.take<uint8_t>(n - 1);
   P.runs = c.take<uint32_t>(n);
   P.labels = c.take<uint32_t>(n);
   P.bound = c.take<uint32_t>(n);
@@ -195,11 +196,12 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
     stats->struct_size = sz;
   }
   if (n == 0) return EMST_OK;
-  int block = 0, carried = 1, count = 0;
+  int block = 0, carried = 1, count = 0, top_down = 0;
   if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
     block = opt->block_size;
     carried = opt->carried_radius;
     count = opt->count_visits;
+    top_down = opt->top_down;
     if (block != 0 && (block < 64 || block > 1024 || block % 32 != 0)) return EMST_ERR_INVALID_ARG;
   } else if (opt && opt->struct_size != 0) {
     return EMST_ERR_INVALID_ARG;
@@ -256,7 +258,7 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
         cudaEventCreate(&tev[2 * rounds + 1]);
         cudaEventRecord(tev[2 * rounds], stream);
       }
-      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true);
+      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, !top_down);
       if (stats && rounds < 40) {
         cudaEventRecord(tev[2 * rounds + 1], stream);
         n_tev = rounds + 1;

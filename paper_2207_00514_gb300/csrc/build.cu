@@ -73,26 +73,6 @@ void launch_scene_box(Problem &P) {
 //   q = t >= 2^B ? 2^B - 1 : trunc(t)
 // and the bits interleave x (most significant), y, z.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t spread3(uint64_t x) {
-  x &= 0x1fffffull;
-  x = (x | (x << 32)) & 0x1f00000000ffffull;
-  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
-  x = (x | (x << 8)) & 0x100f00f00f00f00full;
-  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-  x = (x | (x << 2)) & 0x1249249249249249ull;
-  return x;
-}
-
-__device__ __forceinline__ uint64_t spread2(uint64_t x) {
-  x &= 0xffffffffull;
-  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
-  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
-  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
-  x = (x | (x << 2)) & 0x3333333333333333ull;
-  x = (x | (x << 1)) & 0x5555555555555555ull;
-  return x;
-}
-
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_morton(const float *__restrict__ pts, int64_t n,
                                                    const uint32_t *__restrict__ box,
@@ -100,24 +80,11 @@ __global__ void __launch_bounds__(kBlock) k_morton(const float *__restrict__ pts
                                                    uint32_t *__restrict__ vals) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const float twoB = DIM == 3 ? 2097152.0f : 4294967296.0f;
-  const uint32_t qmax = DIM == 3 ? 0x1fffffu : 0xffffffffu;
+  const Quantizer Q = make_quantizer(box, DIM);
   uint32_t q[3] = {0, 0, 0};
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    float lo = ordered_to_float(box[d]);
-    float hi = ordered_to_float(box[3 + d]);
-    float ext = __fsub_rn(hi, lo);
-    float s = ext > 0.0f ? __fdiv_rn(twoB, ext) : 0.0f;
-    float t = __fmul_rn(__fsub_rn(__ldg(pts + k * DIM + d), lo), s);
-    q[d] = (t >= twoB) ? qmax : (uint32_t)t;
-  }
-  uint64_t code;
-  if (DIM == 3)
-    code = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
-  else
-    code = (spread2(q[0]) << 1) | spread2(q[1]);
-  keys[k] = code;
+  for (int d = 0; d < DIM; ++d) q[d] = quantize(Q, d, __ldg(pts + k * DIM + d));
+  keys[k] = interleave(q[0], q[1], q[2], DIM);
   vals[k] = (uint32_t)k;
 }
 
@@ -179,7 +146,8 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
                                                       NodeRec *__restrict__ nodes,
                                                       uint32_t *__restrict__ parent_leaf,
                                                       uint32_t *__restrict__ parent_node,
-                                                      uint2 *__restrict__ range) {
+                                                      uint2 *__restrict__ range,
+                                                      uint8_t *__restrict__ delta) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   int d = (prefix_delta(keys, n, i, i + 1) - prefix_delta(keys, n, i, i - 1)) > 0 ? 1 : -1;
@@ -202,6 +170,7 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
   uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
   reinterpret_cast<uint2 *>(&nodes[i].d)[0] = make_uint2(left, right);
   range[i] = make_uint2((uint32_t)lo, (uint32_t)hi);
+  delta[i] = (uint8_t)(dnode < 255 ? dnode : 255);
   uint32_t up = (uint32_t)i << 1;
   if (left & kLeafBit) parent_leaf[left & ~kLeafBit] = up; else parent_node[left] = up;
   if (right & kLeafBit) parent_leaf[right & ~kLeafBit] = up | 1u; else parent_node[right] = up | 1u;
@@ -211,7 +180,7 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
 void launch_hierarchy(Problem &P) {
   k_hierarchy<<<grid_for(P.n - 1, kBlock), kBlock, 0, P.stream>>>(P.keys[0] /*sorted*/, P.n, P.nodes,
                                                                    P.parent_leaf, P.parent_node,
-                                                                   P.range);
+                                                                   P.range, P.delta);
   P.launches += 1;
 }
 

@@ -82,6 +82,69 @@ __device__ __forceinline__ float ordered_to_float(uint32_t o) {
 __device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t *p) { return __ldcg(p); }
 
 // ---------------------------------------------------------------------------
+// Z-curve quantisation (decided in FP32, the same everywhere it is used):
+// B = 21 bits per dimension in 3D, 32 in 2D; s = 2^B / (hi - lo) (0 for a
+// flat dimension); t = (x - lo) * s; q = t >= 2^B ? 2^B - 1 : max(t, 0)
+// truncated.  Monotone non-decreasing in x.  Bits interleave x (most
+// significant), y, z.
+// ---------------------------------------------------------------------------
+struct Quantizer {
+  float lo[3];
+  float s[3];
+  float twoB;
+  uint32_t qmax;
+};
+
+__device__ __forceinline__ Quantizer make_quantizer(const uint32_t *box, int dim) {
+  Quantizer Q;
+  Q.twoB = dim == 3 ? 2097152.0f : 4294967296.0f;
+  Q.qmax = dim == 3 ? 0x1fffffu : 0xffffffffu;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Q.lo[d] = 0.f;
+    Q.s[d] = 0.f;
+    if (d < dim) {
+      float lo = ordered_to_float(box[d]);
+      float hi = ordered_to_float(box[3 + d]);
+      float ext = __fsub_rn(hi, lo);
+      Q.lo[d] = lo;
+      Q.s[d] = ext > 0.0f ? __fdiv_rn(Q.twoB, ext) : 0.0f;
+    }
+  }
+  return Q;
+}
+
+__device__ __forceinline__ uint32_t quantize(const Quantizer &Q, int d, float x) {
+  float t = __fmul_rn(__fsub_rn(x, Q.lo[d]), Q.s[d]);
+  return (t >= Q.twoB) ? Q.qmax : (t > 0.0f ? (uint32_t)t : 0u);
+}
+
+__device__ __forceinline__ uint64_t spread3(uint64_t x) {
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ uint64_t spread2(uint64_t x) {
+  x &= 0xffffffffull;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+__device__ __forceinline__ uint64_t interleave(uint32_t qx, uint32_t qy, uint32_t qz, int dim) {
+  return dim == 3 ? ((spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz))
+                  : ((spread2(qx) << 1) | spread2(qy));
+}
+
+// ---------------------------------------------------------------------------
 // Scratch layout of one EMST problem (carved from one allocation).
 // ---------------------------------------------------------------------------
 struct Problem {
@@ -100,6 +163,9 @@ struct Problem {
   uint32_t *parent_node = nullptr;   // n-1: (parent << 1) | slot, root: kInvalid
   uint32_t *arrivals = nullptr;      // n-1 arrival counters (parity = who is second)
   uint2 *range = nullptr;            // n-1: leaf range [first, last] of each internal node
+  uint8_t *delta = nullptr;          // n-1: leading bits shared by the node's (code, position)
+                                     //      keys, capped at 255; < 64 means the node holds
+                                     //      exactly the points of one Morton cell
   uint32_t *runs = nullptr;          // n: label boundaries before each curve position
   uint32_t *labels = nullptr;        // n
   uint32_t *bound = nullptr;         // n, FP32 bits of the component upper bound
@@ -140,7 +206,7 @@ int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int 
 void launch_node_labels(Problem &P);
 void launch_upper_bounds(Problem &P);
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded);
+                     bool seeded, bool climb = true);
 void launch_reduce(Problem &P);
 void launch_merge(Problem &P);
 void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);

@@ -187,85 +187,58 @@ void launch_upper_bounds(Problem &P) {
 // Unseeded, each point reports exactly its nearest other-component point
 // within its cutoff (what the inspection entry point exposes).
 // ---------------------------------------------------------------------------
-template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED>
-__global__ void __launch_bounds__(kBlock) k_traverse(
-    const float4 *__restrict__ pts, const NodeRec *__restrict__ nodes,
-    const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound,
-    const float *__restrict__ radius_in, uint2 *__restrict__ res, uint32_t *__restrict__ res_id,
-    uint64_t *__restrict__ comp_key, int64_t n, uint32_t *status,
-    unsigned long long *visits) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float4 p = pts[i];
-  const uint32_t me = labels[i];
-  float radius;
-  if (RADIUS_IN) radius = radius_in[i];
-  else radius = bound_to_radius(bound[me]);
-  if (CARRIED) {
-    uint2 prev = res[i];
-    if (prev.y != kInvalid && labels[prev.y] != me) radius = fminf(radius, __uint_as_float(prev.x));
-  }
-  float best = __int_as_float(0x7f800000);
-  uint32_t bj = kInvalid, bid = kInvalid;
-  if (SEEDED) {
-    // Seed with the curve neighbours within kWindow positions that lie in
-    // other components: real candidates, so their best weight is a valid
-    // (inclusive) cutoff.  Ties keep the smaller original id.
-#pragma unroll
-    for (int o = -kWindow; o <= kWindow; ++o) {
-      const int64_t j = i + o;
-      if (o == 0 || j < 0 || j >= n) continue;
-      if (__ldg(labels + j) == me) continue;
-      const float4 q = __ldg(pts + j);
-      const float d = sq_dist(p.x, p.y, p.z, q.x, q.y, q.z);
-      const uint32_t idj = __float_as_uint(q.w);
-      if (d < best || (d == best && idj < bid)) { best = d; bj = (uint32_t)j; bid = idj; }
-    }
-    radius = fminf(radius, best);
-    // The component's best weight found so far this round (a real cross edge
-    // of the component, so never below its minimum) tightens the cutoff.
-    const uint32_t cw = (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(comp_key + me)) >> 32);
-    radius = fminf(radius, bound_to_radius(cw));
-  }
-  uint32_t st_node[kStackDepth];
-  float st_dist[kStackDepth];
-  int sp = 0;
-  uint32_t node = 0;
-  unsigned long long nvis = 0;
-  bool overflow = false;
+// Per-query state of Algorithm 2.
+struct Query {
+  float px, py, pz;
+  uint32_t me;     // the query's component label
+  float radius;    // cutoff (inclusive)
+  float best;      // best weight found
+  uint32_t bj;     // its curve index (kInvalid: none yet)
+  uint32_t bid;    // its original index (kInvalid: not loaded yet)
+};
 
+// A leaf j at weight d <= radius: keep the smaller (w, original id).
+__device__ __forceinline__ void take_leaf(Query &q, const float4 *__restrict__ pts, uint32_t j,
+                                          float d) {
+  if (q.bj == kInvalid || d < q.best) {  // first candidate, or strictly closer
+    q.best = d;
+    q.bj = j;
+    q.bid = kInvalid;
+    q.radius = d;
+  } else if (d == q.best) {
+    const uint32_t idj = __float_as_uint(pts[j].w);
+    if (q.bid == kInvalid) q.bid = __float_as_uint(pts[q.bj].w);
+    if (idj < q.bid) { q.bj = j; q.bid = idj; }
+  }
+}
+
+// Depth-first search of the subtree of internal node `node`, whose own box
+// the caller has already accepted: test both children of every visited
+// record, take leaves, descend into the nearer accepted internal child and
+// stack the farther one with its box distance (re-tested when popped).
+template <bool COUNT>
+__device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
+                                        const float4 *__restrict__ pts, uint32_t *st_node,
+                                        float *st_dist, unsigned long long &nvis) {
+  int sp = 0;
   while (true) {
     if (COUNT) ++nvis;
     const float4 *r = reinterpret_cast<const float4 *>(nodes + node);
     const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
     const uint4 dd = __ldg(reinterpret_cast<const uint4 *>(r + 3));
-    const float dL = box_dist(p.x, p.y, p.z, a.x, a.y, a.z, a.w, b.x, b.y);
-    const float dR = box_dist(p.x, p.y, p.z, b.z, b.w, c.x, c.y, c.z, c.w);
-    bool okL = (dd.z != me) && (dL <= radius);
-    bool okR = (dd.w != me) && (dR <= radius);
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const bool ok = side == 0 ? okL : okR;
-      const uint32_t ref = side == 0 ? dd.x : dd.y;
-      const float d = side == 0 ? dL : dR;
-      if (ok && (ref & kLeafBit) && d <= radius) {
-        const uint32_t j = ref & ~kLeafBit;
-        if (bj == kInvalid || d < best) {  // first candidate, or strictly closer
-          best = d;
-          bj = j;
-          bid = kInvalid;
-          radius = d;
-        } else if (d == best) {
-          const uint32_t idj = __float_as_uint(pts[j].w);
-          if (bid == kInvalid) bid = __float_as_uint(pts[bj].w);
-          if (idj < bid) { bj = j; bid = idj; }
-        }
-      }
+    const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
+    const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
+    bool okL = (dd.z != q.me) && (dL <= q.radius);
+    bool okR = (dd.w != q.me) && (dR <= q.radius);
+    if (okL && (dd.x & kLeafBit)) { take_leaf(q, pts, dd.x & ~kLeafBit, dL); okL = false; }
+    if (okR && (dd.y & kLeafBit)) {
+      if (dR <= q.radius) take_leaf(q, pts, dd.y & ~kLeafBit, dR);
+      okR = false;
     }
-    okL = okL && !(dd.x & kLeafBit) && dL <= radius;
-    okR = okR && !(dd.y & kLeafBit) && dR <= radius;
+    okL = okL && dL <= q.radius;
+    okR = okR && dR <= q.radius;
     if (okL && okR) {
-      if (sp >= kStackDepth) { overflow = true; break; }
+      if (sp >= kStackDepth) return false;
       if (dL <= dR) { st_node[sp] = dd.y; st_dist[sp] = dR; node = dd.x; }
       else { st_node[sp] = dd.x; st_dist[sp] = dL; node = dd.y; }
       ++sp;
@@ -276,41 +249,190 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
     bool found = false;
     while (sp > 0) {
       --sp;
-      if (st_dist[sp] <= radius) { node = st_node[sp]; found = true; break; }
+      if (st_dist[sp] <= q.radius) { node = st_node[sp]; found = true; break; }
     }
-    if (!found) break;
+    if (!found) return true;
   }
-  if (overflow) atomicOr(status, kErrStack);
+}
+
+// Morton codes of the two corners of the quantised box that holds every point
+// within the cutoff of the query.  If the FP32 weight w(p, y) <= r then, per
+// dimension, |p - y| <= sqrt(r) (1 - 2^-24)^(-5/2) < sqrt(r) (1 + 2^-21): each
+// of the five roundings on the way (difference, square, two fma) shrinks the
+// exact value by at most a factor (1 - 2^-24).  R rounds up, the corners round
+// outwards, and the quantiser is monotone, so every such y quantises inside.
+__device__ __forceinline__ void ball_corners(const Quantizer &Q, int dim, const Query &q,
+                                             uint64_t &clo, uint64_t &chi) {
+  const float R = __fmul_ru(__fsqrt_ru(q.radius), 1.00000047683715820312f);
+  const float pc[3] = {q.px, q.py, q.pz};
+  uint32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d < dim) {
+      lo[d] = quantize(Q, d, __fsub_rd(pc[d], R));
+      hi[d] = quantize(Q, d, __fadd_ru(pc[d], R));
+    }
+  }
+  clo = interleave(lo[0], lo[1], lo[2], dim);
+  chi = interleave(hi[0], hi[1], hi[2], dim);
+}
+
+// ---------------------------------------------------------------------------
+// A7. Nearest other-component neighbour of every point (Algorithm 2), one
+// thread per point in curve order (neighbouring threads get nearby queries).
+//  - cutoff: the component's upper bound (Optimization 2), optionally
+//    tightened by the previous round's neighbour when it still lies in
+//    another component (a real cross edge of this point, so never below the
+//    component minimum);
+//  - a child is examined only if its label differs from the query's
+//    (Optimization 1) and its box is within the cutoff (inclusive: equal
+//    weights with smaller ids must survive); a leaf updates the best
+//    (w, original id) and shrinks the cutoff to w.
+// Order of the search (CLIMB): instead of descending from the root, the query
+// climbs from its own leaf.  At each ancestor A it searches the subtree of the
+// sibling of the child it came from, so A's whole subtree has then been
+// searched.  A node whose two end codes differ (delta < 64) holds exactly the
+// points of one aligned Morton cell; when the quantised box around the cutoff
+// ball (ball_corners) lies inside A's cell, every point within the cutoff is
+// in A's subtree and the query ends.  Otherwise it climbs on, at worst to the
+// root.  Without CLIMB the search starts at the root (the paper's order).
+// The stack never overflows: every split of the hierarchy uses a strictly
+// later bit of the 96-bit augmented key (64-bit code + 32-bit position), so a
+// root-to-leaf path has at most 96 internal nodes and at most one stacked
+// sibling per level.
+// Ends with the first half of the per-component minimum (A8): an atomicMin of
+// (w bits << 32 | min original id) per component.
+// SEEDED (the emst_compute path) also starts each query from its best curve
+// neighbour in another component and from the component's best weight found
+// so far; both are real cross edges, so the component minimum is unchanged,
+// but a point may then report a neighbour outside its own bound, or none.
+// Unseeded, each point reports exactly its nearest other-component point
+// within its cutoff (what the inspection entry point exposes).
+// ---------------------------------------------------------------------------
+template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CLIMB>
+__global__ void __launch_bounds__(kBlock) k_traverse(
+    const float4 *__restrict__ pts, const NodeRec *__restrict__ nodes,
+    const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound,
+    const float *__restrict__ radius_in, const uint64_t *__restrict__ codes,
+    const uint32_t *__restrict__ parent_leaf, const uint32_t *__restrict__ parent_node,
+    const uint8_t *__restrict__ delta, const uint32_t *__restrict__ box, int dim,
+    uint2 *__restrict__ res, uint32_t *__restrict__ res_id, uint64_t *__restrict__ comp_key,
+    int64_t n, uint32_t *status, unsigned long long *visits) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = pts[i];
+  Query q;
+  q.px = p.x;
+  q.py = p.y;
+  q.pz = p.z;
+  q.me = labels[i];
+  q.best = __int_as_float(0x7f800000);
+  q.bj = kInvalid;
+  q.bid = kInvalid;
+  if (RADIUS_IN) q.radius = radius_in[i];
+  else q.radius = bound_to_radius(bound[q.me]);
+  if (CARRIED) {
+    uint2 prev = res[i];
+    if (prev.y != kInvalid && labels[prev.y] != q.me)
+      q.radius = fminf(q.radius, __uint_as_float(prev.x));
+  }
+  if (SEEDED) {
+    // Curve neighbours within kWindow positions in other components: real
+    // candidates, so their best weight is a valid (inclusive) cutoff.
+#pragma unroll
+    for (int o = -kWindow; o <= kWindow; ++o) {
+      const int64_t j = i + o;
+      if (o == 0 || j < 0 || j >= n) continue;
+      if (__ldg(labels + j) == q.me) continue;
+      const float4 c = __ldg(pts + j);
+      const float d = sq_dist(q.px, q.py, q.pz, c.x, c.y, c.z);
+      const uint32_t idj = __float_as_uint(c.w);
+      if (d < q.best || (d == q.best && idj < q.bid)) { q.best = d; q.bj = (uint32_t)j; q.bid = idj; }
+    }
+    q.radius = fminf(q.radius, q.best);
+    // The component's best weight found so far this round (a real cross edge
+    // of the component, so never below its minimum).
+    const uint32_t cw =
+        (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(comp_key + q.me)) >> 32);
+    q.radius = fminf(q.radius, bound_to_radius(cw));
+  }
+  uint32_t st_node[kStackDepth];
+  float st_dist[kStackDepth];
+  unsigned long long nvis = 0;
+  bool ok = true;
+
+  if (!CLIMB) {
+    ok = explore<COUNT>(q, 0u, nodes, pts, st_node, st_dist, nvis);
+  } else {
+    const Quantizer Q = make_quantizer(box, dim);
+    const uint64_t code_p = __ldg(codes + i);
+    float corner_r = -1.0f;
+    uint64_t clo = 0, chi = 0;
+    uint32_t up = __ldg(parent_leaf + i);
+    while (ok) {
+      const uint32_t A = up >> 1;
+      const int side = 1 - (int)(up & 1u);  // the sibling of the child we came from
+      if (COUNT) ++nvis;
+      const float *f = reinterpret_cast<const float *>(nodes + A) + 6 * side;
+      const float2 b0 = __ldg(reinterpret_cast<const float2 *>(f));
+      const float2 b1 = __ldg(reinterpret_cast<const float2 *>(f) + 1);
+      const float2 b2 = __ldg(reinterpret_cast<const float2 *>(f) + 2);
+      const uint4 dd = __ldg(reinterpret_cast<const uint4 *>(nodes + A) + 3);
+      const uint32_t ref = side ? dd.y : dd.x;
+      const uint32_t lab = side ? dd.w : dd.z;
+      if (lab != q.me) {
+        const float d = box_dist(q.px, q.py, q.pz, b0.x, b0.y, b1.x, b1.y, b2.x, b2.y);
+        if (d <= q.radius) {
+          if (ref & kLeafBit) take_leaf(q, pts, ref & ~kLeafBit, d);
+          else ok = explore<COUNT>(q, ref, nodes, pts, st_node, st_dist, nvis);
+        }
+      }
+      if (A == 0) break;
+      const uint32_t dl = __ldg(delta + A);
+      if (dl < 64 && q.radius < __int_as_float(0x7f800000)) {
+        if (q.radius != corner_r) {
+          ball_corners(Q, dim, q, clo, chi);
+          corner_r = q.radius;
+        }
+        if (dl == 0 || (((clo ^ code_p) | (chi ^ code_p)) >> (64 - dl)) == 0) break;
+      }
+      up = __ldg(parent_node + A);
+    }
+  }
+  if (!ok) atomicOr(status, kErrStack);
   if (COUNT) atomicAdd(visits, nvis);
-  res[i] = make_uint2(__float_as_uint(best), bj);
-  if (bj != kInvalid) {
+  res[i] = make_uint2(__float_as_uint(q.best), q.bj);
+  if (q.bj != kInvalid) {
     const uint32_t oi = __float_as_uint(p.w);
-    const uint32_t oj = bid != kInvalid ? bid : __float_as_uint(pts[bj].w);
+    const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(pts[q.bj].w);
     res_id[i] = oj;
-    const uint64_t key = ((uint64_t)__float_as_uint(best) << 32) | (uint64_t)(oi < oj ? oi : oj);
-    atomicMin(reinterpret_cast<unsigned long long *>(comp_key + me), (unsigned long long)key);
+    const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
+    atomicMin(reinterpret_cast<unsigned long long *>(comp_key + q.me), (unsigned long long)key);
   } else {
     res_id[i] = kInvalid;
   }
 }
 
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded) {
+                     bool seeded, bool climb) {
   if (block <= 0) block = kBlock;
   int g = grid_for(P.n, block);
   auto *vis = reinterpret_cast<unsigned long long *>(P.counters + 2);
   cudaStream_t s = P.stream;
-#define EMST_TRAV(C, R, K, S)                                                                    \
-  k_traverse<C, R, K, S><<<g, block, 0, s>>>(P.pts, P.nodes, P.labels, P.bound, radius_in, P.res, \
-                                             P.res_id, P.comp_key, P.n, P.counters + 1, vis)
+#define EMST_TRAV(C, R, K, S, L)                                                              \
+  k_traverse<C, R, K, S, L><<<g, block, 0, s>>>(                                               \
+      P.pts, P.nodes, P.labels, P.bound, radius_in, P.keys[0], P.parent_leaf, P.parent_node,   \
+      P.delta, P.counters + 4, P.dim, P.res, P.res_id, P.comp_key, P.n, P.counters + 1, vis)
   if (radius_in) {
-    EMST_TRAV(false, true, false, false);
+    EMST_TRAV(false, true, false, false, true);
   } else if (!seeded) {
-    EMST_TRAV(false, false, false, false);
+    EMST_TRAV(false, false, false, false, true);
+  } else if (!climb) {
+    if (count) EMST_TRAV(true, false, true, true, false); else EMST_TRAV(true, false, false, true, false);
   } else if (carried) {
-    if (count) EMST_TRAV(true, false, true, true); else EMST_TRAV(true, false, false, true);
+    if (count) EMST_TRAV(true, false, true, true, true); else EMST_TRAV(true, false, false, true, true);
   } else {
-    if (count) EMST_TRAV(false, false, true, true); else EMST_TRAV(false, false, false, true);
+    if (count) EMST_TRAV(false, false, true, true, true); else EMST_TRAV(false, false, false, true, true);
   }
 #undef EMST_TRAV
   P.launches += 1;
