@@ -372,6 +372,9 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
     while (ok) {
       const uint32_t A = up >> 1;
       const int side = 1 - (int)(up & 1u);  // the sibling of the child we came from
+      // everything this step needs is addressed by A alone: one round trip
+      const uint32_t next_up = A != 0 ? __ldg(parent_node + A) : kInvalid;
+      const uint32_t dl = __ldg(delta + A);
       if (COUNT) ++nvis;
       const float *f = reinterpret_cast<const float *>(nodes + A) + 6 * side;
       const float2 b0 = __ldg(reinterpret_cast<const float2 *>(f));
@@ -388,7 +391,6 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
         }
       }
       if (A == 0) break;
-      const uint32_t dl = __ldg(delta + A);
       if (dl < 64 && q.radius < __int_as_float(0x7f800000)) {
         if (q.radius != corner_r) {
           ball_corners(Q, dim, q, clo, chi);
@@ -396,11 +398,16 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
         }
         if (dl == 0 || (((clo ^ code_p) | (chi ^ code_p)) >> (64 - dl)) == 0) break;
       }
-      up = __ldg(parent_node + A);
+      up = next_up;
     }
   }
   if (!ok) atomicOr(status, kErrStack);
-  if (COUNT) atomicAdd(visits, nvis);
+  if (COUNT) {
+    // one atomic per warp: sum the active lanes' counts first
+    const unsigned mask = __activemask();
+    const unsigned v = __reduce_add_sync(mask, (unsigned)nvis);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) atomicAdd(visits, (unsigned long long)v);
+  }
   res[i] = make_uint2(__float_as_uint(q.best), q.bj);
   if (q.bj != kInvalid) {
     const uint32_t oi = __float_as_uint(p.w);
