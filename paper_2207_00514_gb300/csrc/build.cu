@@ -77,10 +77,12 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_morton(const float *__restrict__ pts, int64_t n,
                                                    const uint32_t *__restrict__ box,
                                                    uint64_t *__restrict__ keys,
-                                                   uint32_t *__restrict__ vals) {
+                                                   uint32_t *__restrict__ vals,
+                                                   float *__restrict__ quant_out) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const Quantizer Q = make_quantizer(box, DIM);
+  if (k == 0) store_quantizer(Q, quant_out);  // reused by the queries of every round
   uint32_t q[3] = {0, 0, 0};
 #pragma unroll
   for (int d = 0; d < DIM; ++d) q[d] = quantize(Q, d, __ldg(pts + k * DIM + d));
@@ -91,9 +93,11 @@ __global__ void __launch_bounds__(kBlock) k_morton(const float *__restrict__ pts
 void launch_morton(Problem &P) {
   int g = grid_for(P.n, kBlock);
   if (P.dim == 3)
-    k_morton<3><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0]);
+    k_morton<3><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0],
+                                            reinterpret_cast<float *>(P.counters + 32));
   else
-    k_morton<2><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0]);
+    k_morton<2><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0],
+                                            reinterpret_cast<float *>(P.counters + 32));
   P.launches += 1;
 }
 

@@ -114,6 +114,28 @@ __device__ __forceinline__ Quantizer make_quantizer(const uint32_t *box, int dim
   return Q;
 }
 
+// The quantiser as 7 floats (lo x,y,z, s x,y,z, 2^B) in device memory, written
+// once per call after the scene box (counters + 32).
+__device__ __forceinline__ void store_quantizer(const Quantizer &Q, float *out) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    out[d] = Q.lo[d];
+    out[3 + d] = Q.s[d];
+  }
+  out[6] = Q.twoB;
+}
+__device__ __forceinline__ Quantizer load_quantizer(const float *in, int dim) {
+  Quantizer Q;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Q.lo[d] = __ldg(in + d);
+    Q.s[d] = __ldg(in + 3 + d);
+  }
+  Q.twoB = __ldg(in + 6);
+  Q.qmax = dim == 3 ? 0x1fffffu : 0xffffffffu;
+  return Q;
+}
+
 __device__ __forceinline__ uint32_t quantize(const Quantizer &Q, int d, float x) {
   float t = __fmul_rn(__fsub_rn(x, Q.lo[d]), Q.s[d]);
   return (t >= Q.twoB) ? Q.qmax : (t > 0.0f ? (uint32_t)t : 0u);
@@ -177,8 +199,9 @@ struct Problem {
   uint32_t *root = nullptr;          // n: new label of a component
   emst_edge *edges = nullptr;        // n: edges in emission order
   emst_edge *out_stage = nullptr;    // n-1: device staging of host outputs
-  uint32_t *counters = nullptr;      // [0] edges emitted, [1] status bits, [2] visits lo, [3] visits hi,
-                                     // [4..9] scene box (ordered), [10..] sort tile counters
+  uint32_t *counters = nullptr;      // [0] edges emitted, [1] status bits, [2..3] node visits (u64),
+                                     // [4..9] scene box (ordered), [16..23] sort tile counters,
+                                     // [24] scan tile counter, [32..38] quantiser (floats)
   uint32_t *sort_hist = nullptr;     // 8 x 256
   uint32_t *sort_lookback = nullptr; // tiles x 256
   int64_t sort_tiles = 0;

@@ -161,32 +161,6 @@ void launch_upper_bounds(Problem &P) {
   P.launches += 1;
 }
 
-// ---------------------------------------------------------------------------
-// A7. Nearest other-component neighbour of every point (Algorithm 2), one
-// thread per point in curve order (neighbouring threads get nearby queries).
-//  - cutoff: the component's upper bound, optionally tightened by the carried
-//    neighbour of the previous round when it still lies in another component
-//    (a real cross edge of this point, so never below the component minimum);
-//  - a child is examined only if its label differs from the query's
-//    (Optimization 1) and its box is within the cutoff (inclusive: equal
-//    weights with smaller ids must survive);
-//  - a leaf within the cutoff updates the best (w, original id) and shrinks
-//    the cutoff to w;
-//  - internal children: descend into the nearer, stack the farther with its
-//    box distance, re-tested when popped.
-// The stack never overflows: every split of the hierarchy uses a strictly
-// later bit of the 96-bit augmented key (64-bit code + 32-bit position), so a
-// root-to-leaf path has at most 96 internal nodes and at most one stacked
-// sibling per level.
-// Ends with the first half of the per-component minimum (A8): an atomicMin of
-// (w bits << 32 | min original id) per component.
-// SEEDED (the emst_compute path) also starts each query from its best curve
-// neighbour in another component and from the component's best weight found
-// so far; both are real cross edges, so the component minimum is unchanged,
-// but a point may then report a neighbour outside its own bound, or none.
-// Unseeded, each point reports exactly its nearest other-component point
-// within its cutoff (what the inspection entry point exposes).
-// ---------------------------------------------------------------------------
 // Per-query state of Algorithm 2.
 struct Query {
   float px, py, pz;
@@ -255,26 +229,43 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
   }
 }
 
-// Morton codes of the two corners of the quantised box that holds every point
-// within the cutoff of the query.  If the FP32 weight w(p, y) <= r then, per
-// dimension, |p - y| <= sqrt(r) (1 - 2^-24)^(-5/2) < sqrt(r) (1 + 2^-21): each
-// of the five roundings on the way (difference, square, two fma) shrinks the
-// exact value by at most a factor (1 - 2^-24).  R rounds up, the corners round
-// outwards, and the quantiser is monotone, so every such y quantises inside.
-__device__ __forceinline__ void ball_corners(const Quantizer &Q, int dim, const Query &q,
-                                             uint64_t &clo, uint64_t &chi) {
+// Quantised box that holds every point within the cutoff of the query.  If
+// the FP32 weight w(p, y) <= r then, per dimension, |p - y| <= sqrt(r)
+// (1 - 2^-24)^(-5/2) < sqrt(r) (1 + 2^-21): each of the five roundings on the
+// way (difference, square, two fma) shrinks the exact value by at most a
+// factor (1 - 2^-24).  R rounds up, the box edges round outwards and the
+// quantiser is monotone, so every such y quantises inside [lo, hi].
+__device__ __forceinline__ void ball_box(const Quantizer &Q, int dim, const Query &q,
+                                         uint32_t *lo, uint32_t *hi) {
   const float R = __fmul_ru(__fsqrt_ru(q.radius), 1.00000047683715820312f);
   const float pc[3] = {q.px, q.py, q.pz};
-  uint32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = d < dim ? quantize(Q, d, __fsub_rd(pc[d], R)) : 0u;
+    hi[d] = d < dim ? quantize(Q, d, __fadd_ru(pc[d], R)) : 0u;
+  }
+}
+
+// Is the quantised box [lo, hi] inside the Morton cell of the query's
+// ancestor whose keys share their first `dl` bits (dl < 64)?  A prefix of dl
+// code bits fixes the top (dl+1)/3, dl/3, (dl-1)/3 bits of x, y, z in 3D (bit
+// 63 is unused) and the top (dl+1)/2, dl/2 bits of x, y in 2D; the cell is the
+// aligned box of coordinates sharing those bits with the query's own.
+__device__ __forceinline__ bool box_in_cell(int dim, uint32_t dl, const uint32_t *qp,
+                                            const uint32_t *lo, const uint32_t *hi) {
+  const int B = dim == 3 ? 21 : 32;
+  const int nb[3] = {dim == 3 ? (int)(dl + 1) / 3 : (int)(dl + 1) / 2,
+                     dim == 3 ? (int)dl / 3 : (int)dl / 2,
+                     dim == 3 ? ((int)dl - 1) / 3 : 0};
+  bool in = true;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (d < dim) {
-      lo[d] = quantize(Q, d, __fsub_rd(pc[d], R));
-      hi[d] = quantize(Q, d, __fadd_ru(pc[d], R));
+      const int sh = B - nb[d];
+      in = in && ((((uint64_t)(lo[d] ^ qp[d])) >> sh) == 0) && ((((uint64_t)(hi[d] ^ qp[d])) >> sh) == 0);
     }
   }
-  clo = interleave(lo[0], lo[1], lo[2], dim);
-  chi = interleave(hi[0], hi[1], hi[2], dim);
+  return in;
 }
 
 // ---------------------------------------------------------------------------
@@ -293,7 +284,7 @@ __device__ __forceinline__ void ball_corners(const Quantizer &Q, int dim, const 
 // sibling of the child it came from, so A's whole subtree has then been
 // searched.  A node whose two end codes differ (delta < 64) holds exactly the
 // points of one aligned Morton cell; when the quantised box around the cutoff
-// ball (ball_corners) lies inside A's cell, every point within the cutoff is
+// ball (ball_box) lies inside A's cell, every point within the cutoff is
 // in A's subtree and the query ends.  Otherwise it climbs on, at worst to the
 // root.  Without CLIMB the search starts at the root (the paper's order).
 // The stack never overflows: every split of the hierarchy uses a strictly
@@ -315,7 +306,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
     const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound,
     const float *__restrict__ radius_in, const uint64_t *__restrict__ codes,
     const uint32_t *__restrict__ parent_leaf, const uint32_t *__restrict__ parent_node,
-    const uint8_t *__restrict__ delta, const uint32_t *__restrict__ box, int dim,
+    const uint8_t *__restrict__ delta, const float *__restrict__ quant, int dim,
     uint2 *__restrict__ res, uint32_t *__restrict__ res_id, uint64_t *__restrict__ comp_key,
     int64_t n, uint32_t *status, unsigned long long *visits) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -364,10 +355,13 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   if (!CLIMB) {
     ok = explore<COUNT>(q, 0u, nodes, pts, st_node, st_dist, nvis);
   } else {
-    const Quantizer Q = make_quantizer(box, dim);
-    const uint64_t code_p = __ldg(codes + i);
-    float corner_r = -1.0f;
-    uint64_t clo = 0, chi = 0;
+    const Quantizer Q = load_quantizer(quant, dim);
+    uint32_t qp[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (d < dim) qp[d] = quantize(Q, d, d == 0 ? q.px : (d == 1 ? q.py : q.pz));
+    float box_r = __int_as_float(0x7f800000);  // radius the box was computed for
+    uint32_t blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
     uint32_t up = __ldg(parent_leaf + i);
     while (ok) {
       const uint32_t A = up >> 1;
@@ -392,11 +386,15 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
       }
       if (A == 0) break;
       if (dl < 64 && q.radius < __int_as_float(0x7f800000)) {
-        if (q.radius != corner_r) {
-          ball_corners(Q, dim, q, clo, chi);
-          corner_r = q.radius;
+        // a box computed for a larger radius is still a valid (looser) test;
+        // recompute only when that test fails and the radius has shrunk
+        bool in = box_r < __int_as_float(0x7f800000) && box_in_cell(dim, dl, qp, blo, bhi);
+        if (!in && q.radius < box_r) {
+          ball_box(Q, dim, q, blo, bhi);
+          box_r = q.radius;
+          in = box_in_cell(dim, dl, qp, blo, bhi);
         }
-        if (dl == 0 || (((clo ^ code_p) | (chi ^ code_p)) >> (64 - dl)) == 0) break;
+        if (in) break;
       }
       up = next_up;
     }
@@ -429,7 +427,8 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
 #define EMST_TRAV(C, R, K, S, L)                                                              \
   k_traverse<C, R, K, S, L><<<g, block, 0, s>>>(                                               \
       P.pts, P.nodes, P.labels, P.bound, radius_in, P.keys[0], P.parent_leaf, P.parent_node,   \
-      P.delta, P.counters + 4, P.dim, P.res, P.res_id, P.comp_key, P.n, P.counters + 1, vis)
+      P.delta, reinterpret_cast<const float *>(P.counters + 32), P.dim, P.res, P.res_id,         \
+      P.comp_key, P.n, P.counters + 1, vis)
   if (radius_in) {
     EMST_TRAV(false, true, false, false, true);
   } else if (!seeded) {
