@@ -355,48 +355,76 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   if (!CLIMB) {
     ok = explore<COUNT>(q, 0u, nodes, pts, st_node, st_dist, nvis);
   } else {
+    // One loop, one record per iteration, so the lanes of a warp stay in step
+    // whether they are climbing or searching a sibling subtree.  `anc` is the
+    // ancestor being completed; its child on the path is masked out (its
+    // subtree is already done); when the depth-first stack runs dry, anc's
+    // whole subtree has been searched and the containment test decides
+    // whether to stop or climb one level.
     const Quantizer Q = load_quantizer(quant, dim);
     uint32_t qp[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (d < dim) qp[d] = quantize(Q, d, d == 0 ? q.px : (d == 1 ? q.py : q.pz));
-    float box_r = __int_as_float(0x7f800000);  // radius the box was computed for
+    float box_r = __int_as_float(0x7f800000);  // radius the ball box was computed for
     uint32_t blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
-    uint32_t up = __ldg(parent_leaf + i);
-    while (ok) {
-      const uint32_t A = up >> 1;
-      const int side = 1 - (int)(up & 1u);  // the sibling of the child we came from
-      // everything this step needs is addressed by A alone: one round trip
-      const uint32_t next_up = A != 0 ? __ldg(parent_node + A) : kInvalid;
-      const uint32_t dl = __ldg(delta + A);
+    const uint32_t up0 = __ldg(parent_leaf + i);
+    uint32_t anc = up0 >> 1;
+    uint32_t anc_up = anc != 0 ? __ldg(parent_node + anc) : kInvalid;
+    uint32_t anc_dl = __ldg(delta + anc);
+    uint32_t node = anc;
+    int masked = (int)(up0 & 1u);  // child of `node` not to test (-1: none)
+    int sp = 0;
+    while (true) {
       if (COUNT) ++nvis;
-      const float *f = reinterpret_cast<const float *>(nodes + A) + 6 * side;
-      const float2 b0 = __ldg(reinterpret_cast<const float2 *>(f));
-      const float2 b1 = __ldg(reinterpret_cast<const float2 *>(f) + 1);
-      const float2 b2 = __ldg(reinterpret_cast<const float2 *>(f) + 2);
-      const uint4 dd = __ldg(reinterpret_cast<const uint4 *>(nodes + A) + 3);
-      const uint32_t ref = side ? dd.y : dd.x;
-      const uint32_t lab = side ? dd.w : dd.z;
-      if (lab != q.me) {
-        const float d = box_dist(q.px, q.py, q.pz, b0.x, b0.y, b1.x, b1.y, b2.x, b2.y);
-        if (d <= q.radius) {
-          if (ref & kLeafBit) take_leaf(q, pts, ref & ~kLeafBit, d);
-          else ok = explore<COUNT>(q, ref, nodes, pts, st_node, st_dist, nvis);
-        }
+      const float4 *r = reinterpret_cast<const float4 *>(nodes + node);
+      const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+      const uint4 dd = __ldg(reinterpret_cast<const uint4 *>(r + 3));
+      const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
+      const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
+      bool okL = masked != 0 && (dd.z != q.me) && (dL <= q.radius);
+      bool okR = masked != 1 && (dd.w != q.me) && (dR <= q.radius);
+      if (okL && (dd.x & kLeafBit)) { take_leaf(q, pts, dd.x & ~kLeafBit, dL); okL = false; }
+      if (okR && (dd.y & kLeafBit)) {
+        if (dR <= q.radius) take_leaf(q, pts, dd.y & ~kLeafBit, dR);
+        okR = false;
       }
-      if (A == 0) break;
-      if (dl < 64 && q.radius < __int_as_float(0x7f800000)) {
+      okL = okL && dL <= q.radius;
+      okR = okR && dR <= q.radius;
+      masked = -1;
+      if (okL && okR) {
+        if (sp >= kStackDepth) { ok = false; break; }
+        if (dL <= dR) { st_node[sp] = dd.y; st_dist[sp] = dR; node = dd.x; }
+        else { st_node[sp] = dd.x; st_dist[sp] = dL; node = dd.y; }
+        ++sp;
+        continue;
+      }
+      if (okL) { node = dd.x; continue; }
+      if (okR) { node = dd.y; continue; }
+      bool found = false;
+      while (sp > 0) {
+        --sp;
+        if (st_dist[sp] <= q.radius) { node = st_node[sp]; found = true; break; }
+      }
+      if (found) continue;
+      // anc's subtree is complete: stop if the cutoff ball lies in its cell
+      if (anc == 0) break;
+      if (anc_dl < 64 && q.radius < __int_as_float(0x7f800000)) {
         // a box computed for a larger radius is still a valid (looser) test;
         // recompute only when that test fails and the radius has shrunk
-        bool in = box_r < __int_as_float(0x7f800000) && box_in_cell(dim, dl, qp, blo, bhi);
+        bool in = box_r < __int_as_float(0x7f800000) && box_in_cell(dim, anc_dl, qp, blo, bhi);
         if (!in && q.radius < box_r) {
           ball_box(Q, dim, q, blo, bhi);
           box_r = q.radius;
-          in = box_in_cell(dim, dl, qp, blo, bhi);
+          in = box_in_cell(dim, anc_dl, qp, blo, bhi);
         }
         if (in) break;
       }
-      up = next_up;
+      masked = (int)(anc_up & 1u);
+      anc = anc_up >> 1;
+      node = anc;
+      anc_up = anc != 0 ? __ldg(parent_node + anc) : kInvalid;
+      anc_dl = __ldg(delta + anc);
     }
   }
   if (!ok) atomicOr(status, kErrStack);
