@@ -73,8 +73,9 @@ typedef struct emst_options {
   int32_t use_graph;          /* 1 = run the round loop as a CUDA graph with a device-side
                                  loop condition; 0 = host loop (one sync per round) */
   int32_t count_visits;       /* 1 = count node visits per round into emst_stats */
-  int32_t top_down;           /* 1 = queries descend from the root (the paper's order) instead
-                                 of climbing from their own leaf with early termination */
+  int32_t climb;              /* 1 = queries climb from their own leaf and stop early once the
+                                 cutoff ball lies in an ancestor's Morton cell; 0 (default) =
+                                 they descend from the root (the paper's order) */
   int32_t reserved[10];
 } emst_options;
 

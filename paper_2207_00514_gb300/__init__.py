@@ -59,7 +59,7 @@ class EmstLibraryError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("carried_radius", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("count_visits", ctypes.c_int32), ("top_down", ctypes.c_int32),
+                ("count_visits", ctypes.c_int32), ("climb", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 10)]
 
 
@@ -202,7 +202,7 @@ def emst_compute_noalloc(points, out_edges=None, stream=None):
 
 
 def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_radius=True,
-                    use_graph=False, count_visits=False, top_down=False):
+                    use_graph=False, count_visits=False, climb=False):
     """emst_compute with options; returns (edges, stats dict)."""
     n, dim = _check_points(points)
     out_edges = _edges_out(n, points, out_edges)
@@ -212,7 +212,7 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
     opt.carried_radius = 1 if carried_radius else 0
     opt.use_graph = 1 if use_graph else 0
     opt.count_visits = 1 if count_visits else 0
-    opt.top_down = 1 if top_down else 0
+    opt.climb = 1 if climb else 0
     st = _Stats()
     st.struct_size = ctypes.sizeof(_Stats)
     rc = load_library().emst_compute_ex(_ptr(points), n, dim, _ptr(out_edges),

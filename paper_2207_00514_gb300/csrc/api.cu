@@ -196,12 +196,12 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
     stats->struct_size = sz;
   }
   if (n == 0) return EMST_OK;
-  int block = 0, carried = 1, count = 0, top_down = 0;
+  int block = 0, carried = 1, count = 0, climb = 0;
   if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
     block = opt->block_size;
     carried = opt->carried_radius;
     count = opt->count_visits;
-    top_down = opt->top_down;
+    climb = opt->climb;
     if (block != 0 && (block < 64 || block > 1024 || block % 32 != 0)) return EMST_ERR_INVALID_ARG;
   } else if (opt && opt->struct_size != 0) {
     return EMST_ERR_INVALID_ARG;
@@ -258,7 +258,7 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
         cudaEventCreate(&tev[2 * rounds + 1]);
         cudaEventRecord(tev[2 * rounds], stream);
       }
-      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, !top_down);
+      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, climb != 0);
       if (stats && rounds < 40) {
         cudaEventRecord(tev[2 * rounds + 1], stream);
         n_tev = rounds + 1;

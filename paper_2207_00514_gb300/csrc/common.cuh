@@ -229,7 +229,7 @@ int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int 
 void launch_node_labels(Problem &P);
 void launch_upper_bounds(Problem &P);
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded, bool climb = true);
+                     bool seeded, bool climb = false);
 void launch_reduce(Problem &P);
 void launch_merge(Problem &P);
 void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);

@@ -293,10 +293,14 @@ __device__ __forceinline__ bool box_in_cell(int dim, uint32_t dl, const uint32_t
 // sibling per level.
 // Ends with the first half of the per-component minimum (A8): an atomicMin of
 // (w bits << 32 | min original id) per component.
-// SEEDED (the emst_compute path) also starts each query from its best curve
-// neighbour in another component and from the component's best weight found
-// so far; both are real cross edges, so the component minimum is unchanged,
-// but a point may then report a neighbour outside its own bound, or none.
+// SEEDED (the emst_compute path) also tightens each cutoff with the
+// component's best weight found so far and with the point's best curve
+// neighbour in another component (both real cross edges, so never below the
+// component minimum), reports the exact nearest neighbour within that cutoff
+// (or none), and keeps a per-point lower bound for the next round (res.x):
+// a point whose bound exceeds its component's cutoff skips its query.  The
+// endpoint of every component's minimum edge still finds it, so the minima
+// (and the tree) are unchanged; which other points report differs.
 // Unseeded, each point reports exactly its nearest other-component point
 // within its cutoff (what the inspection entry point exposes).
 // ---------------------------------------------------------------------------
@@ -322,11 +326,28 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   q.bid = kInvalid;
   if (RADIUS_IN) q.radius = radius_in[i];
   else q.radius = bound_to_radius(bound[q.me]);
-  if (CARRIED) {
-    uint2 prev = res[i];
-    if (prev.y != kInvalid && labels[prev.y] != q.me)
-      q.radius = fminf(q.radius, __uint_as_float(prev.x));
+  uint2 prev = make_uint2(0u, kInvalid);
+  if (CARRIED) prev = res[i];
+  if (SEEDED) {
+    // The component's best weight found so far this round: a real cross edge
+    // of the component, so never below its minimum.
+    const uint32_t cw =
+        (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(comp_key + q.me)) >> 32);
+    q.radius = fminf(q.radius, bound_to_radius(cw));
+    // prev.x is a lower bound of this point's nearest other-component weight
+    // (components only grow, so that weight never decreases).  Above the
+    // component-level cutoff, this point cannot be an endpoint of the
+    // component's minimum edge: skip the query.
+    if (CARRIED && __uint_as_float(prev.x) > q.radius) {
+      res[i] = make_uint2(prev.x, kInvalid);
+      res_id[i] = kInvalid;
+      return;
+    }
   }
+  // The previous round's neighbour, if still in another component, is a real
+  // cross edge of this point: a per-point cutoff.
+  if (CARRIED && prev.y != kInvalid && labels[prev.y] != q.me)
+    q.radius = fminf(q.radius, __uint_as_float(prev.x));
   if (SEEDED) {
     // Curve neighbours within kWindow positions in other components: real
     // candidates, so their best weight is a valid (inclusive) cutoff.
@@ -341,12 +362,8 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
       if (d < q.best || (d == q.best && idj < q.bid)) { q.best = d; q.bj = (uint32_t)j; q.bid = idj; }
     }
     q.radius = fminf(q.radius, q.best);
-    // The component's best weight found so far this round (a real cross edge
-    // of the component, so never below its minimum).
-    const uint32_t cw =
-        (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(comp_key + q.me)) >> 32);
-    q.radius = fminf(q.radius, bound_to_radius(cw));
   }
+  const float r0 = q.radius;  // the search is exact within this cutoff
   uint32_t st_node[kStackDepth];
   float st_dist[kStackDepth];
   unsigned long long nvis = 0;
@@ -434,7 +451,17 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
     const unsigned v = __reduce_add_sync(mask, (unsigned)nvis);
     if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) atomicAdd(visits, (unsigned long long)v);
   }
-  res[i] = make_uint2(__float_as_uint(q.best), q.bj);
+  if (SEEDED) {
+    // Report only the exact nearest neighbour within r0 (a seed beyond r0 is
+    // dropped); keep in res.x a lower bound for the next round: the found
+    // weight, or r0 when nothing lies within it.
+    const bool found = q.bj != kInvalid && q.best <= r0;
+    if (!found) q.bj = kInvalid;
+    const float lb = found ? q.best : (r0 < __int_as_float(0x7f800000) ? r0 : 0.0f);
+    res[i] = make_uint2(__float_as_uint(lb), q.bj);
+  } else {
+    res[i] = make_uint2(__float_as_uint(q.best), q.bj);
+  }
   if (q.bj != kInvalid) {
     const uint32_t oi = __float_as_uint(p.w);
     const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(pts[q.bj].w);
@@ -458,15 +485,15 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
       P.delta, reinterpret_cast<const float *>(P.counters + 32), P.dim, P.res, P.res_id,         \
       P.comp_key, P.n, P.counters + 1, vis)
   if (radius_in) {
-    EMST_TRAV(false, true, false, false, true);
+    EMST_TRAV(false, true, false, false, false);
   } else if (!seeded) {
-    EMST_TRAV(false, false, false, false, true);
-  } else if (!climb) {
-    if (count) EMST_TRAV(true, false, true, true, false); else EMST_TRAV(true, false, false, true, false);
+    EMST_TRAV(false, false, false, false, false);
+  } else if (climb) {
+    if (carried) EMST_TRAV(true, false, false, true, true); else EMST_TRAV(false, false, false, true, true);
   } else if (carried) {
-    if (count) EMST_TRAV(true, false, true, true, true); else EMST_TRAV(true, false, false, true, true);
+    if (count) EMST_TRAV(true, false, true, true, false); else EMST_TRAV(true, false, false, true, false);
   } else {
-    if (count) EMST_TRAV(false, false, true, true, true); else EMST_TRAV(false, false, false, true, true);
+    if (count) EMST_TRAV(false, false, true, true, false); else EMST_TRAV(false, false, false, true, false);
   }
 #undef EMST_TRAV
   P.launches += 1;

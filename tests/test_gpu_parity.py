@@ -210,8 +210,8 @@ def test_repeatable_and_stats(pkg):
     assert st["node_visits"] > 0 and st["kernel_launches"] > 0
     c, _ = pkg.emst_compute_ex(t, carried_radius=False, block_size=128)
     assert_same_edges(pkg.edges_numpy(c), pkg.edges_numpy(b), "options")
-    d, st_td = pkg.emst_compute_ex(t, top_down=True, count_visits=True)
-    assert_same_edges(pkg.edges_numpy(d), pkg.edges_numpy(b), "top-down order")
+    d, _ = pkg.emst_compute_ex(t, climb=True)
+    assert_same_edges(pkg.edges_numpy(d), pkg.edges_numpy(b), "climbing search order")
 
 
 def test_degenerate_sizes_and_errors(pkg):
