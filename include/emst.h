@@ -128,7 +128,7 @@ int emst_compute_batched(const float *points, const int64_t *offsets, int num_in
  * allocate, a process under a device-memory budget it does not own, or a
  * latency-critical loop that cannot take an allocator's implicit
  * synchronisation.  Same arguments, result and output order as emst_compute.
- *   - Scratch: one fixed 13 MiB array in the library's device memory, held by
+ *   - Scratch: one fixed 16 MiB array in the library's device memory, held by
  *     every GPU that loads the library until the process exits; no cudaMalloc,
  *     cudaFree or pool allocation happens in the call.
  *   - Limit: n <= EMST_NOALLOC_MAX_POINTS, else EMST_ERR_TOO_LARGE (nothing

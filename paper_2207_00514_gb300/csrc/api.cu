@@ -88,8 +88,18 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.range = c.take<uint2>(n - 1);
   P.delta = c.take<uint8_t>(n - 1);
   P.runs = c.take<uint32_t>(n);
-  P.labels = c.take<uint32_t>(n);
-  P.bound = c.take<uint32_t>(n);
+  P.labels_buf[0] = c.take<uint32_t>(n);
+  P.labels_buf[1] = c.take<uint32_t>(n);
+  P.bound_buf[0] = c.take<uint32_t>(n);
+  P.bound_buf[1] = c.take<uint32_t>(n);
+  P.list_buf[0] = c.take<uint32_t>(n);
+  P.list_buf[1] = c.take<uint32_t>(n);
+  P.cur = 0;
+  P.labels = P.labels_buf[0];
+  P.bound = P.bound_buf[0];
+  P.active_list = nullptr;
+  P.next_list = P.list_buf[0];
+  P.n_active = n;
   P.res = c.take<uint2>(n);
   P.res_id = c.take<uint32_t>(n);
   P.comp_key = c.take<uint64_t>(n);
@@ -145,6 +155,17 @@ void run_build(Problem &P, bool init_labels) {
     launch_hierarchy(P);
     launch_refit(P, init_labels);
   }
+}
+
+// One Boruvka round (the loop body of Fig. 3).  Round 0 takes its node labels
+// from the refit and computes its curve-pair bounds here; later rounds use
+// what the previous round's relabel pass prepared.
+void run_round(Problem &P, int round, bool carried, int block, bool count, bool climb) {
+  if (round > 0) launch_node_labels(P);
+  else launch_upper_bounds(P);
+  launch_traverse(P, round > 0 && carried, nullptr, block, count, true, climb);
+  launch_reduce(P);
+  launch_merge(P);
 }
 
 void reset_round_state(Problem &P) {
@@ -221,7 +242,7 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
   P.points = points;
   const size_t need = layout(P, nullptr, !pts_dev, !out_dev);
   char *base = nullptr;
-  uint32_t host_counters[4] = {0, 0, 0, 0};
+  uint32_t host_counters[16] = {0};
   Timer tm;
   int rounds = 0;
   cudaEvent_t tev[2 * 40];
@@ -239,7 +260,7 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
   run_build(P, true);
   tm.mark(1, stream);
   // Non-finite input is reported before any round runs.
-  CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost,
+  CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(host_counters), cudaMemcpyDeviceToHost,
                      stream));
   CU(cudaStreamSynchronize(stream));
   if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
@@ -252,7 +273,7 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
       if (rounds >= limit) { rc = EMST_ERR_ROUND_LIMIT; goto done; }
       if (stats && rounds < 40) stats->components_per_round[rounds] = n - (int64_t)host_counters[0];
       if (rounds > 0) launch_node_labels(P);
-      launch_upper_bounds(P);
+      else launch_upper_bounds(P);
       if (stats && rounds < 40) {
         cudaEventCreate(&tev[2 * rounds]);
         cudaEventCreate(&tev[2 * rounds + 1]);
@@ -265,10 +286,11 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
       }
       launch_reduce(P);
       launch_merge(P);
-      CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost,
+      CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(host_counters), cudaMemcpyDeviceToHost,
                          stream));
       CU(cudaStreamSynchronize(stream));
       if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
+      advance_round(P, (int64_t)host_counters[12]);
       if ((int64_t)host_counters[0] >= n - 1) { ++rounds; break; }
     }
     tm.mark(2, stream);
@@ -281,7 +303,7 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
     tm.mark(2, stream);
   }
   tm.mark(3, stream);
-  CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost,
+  CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(host_counters), cudaMemcpyDeviceToHost,
                      stream));
   CU(cudaStreamSynchronize(stream));
   CU(cudaGetLastError());
@@ -458,6 +480,7 @@ int emst_round_step(const float *points, int64_t n, int dim, const uint32_t *lab
   run_build(P, false);
   cudaMemcpyAsync(P.labels, labels_in, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
   reset_round_state(P);
+  launch_label_runs(P);
   launch_node_labels(P);
   if (out_node_labels)
     cudaMemcpy2DAsync(out_node_labels, 8, reinterpret_cast<char *>(P.nodes) + 56, 64, 8,
@@ -469,7 +492,8 @@ int emst_round_step(const float *points, int64_t n, int dim, const uint32_t *lab
   if (out_nn_w || out_nn_j) k_split_res<<<grid_for(n, 256), 256, 0, s>>>(P.res, out_nn_w, out_nn_j, n);
   launch_reduce(P);
   launch_merge(P);
-  if (out_labels) cudaMemcpyAsync(out_labels, P.labels, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+  if (out_labels)
+    cudaMemcpyAsync(out_labels, P.labels_buf[P.cur ^ 1], 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
   uint32_t emitted = 0;
   cudaMemcpyAsync(&emitted, P.counters, 4, cudaMemcpyDeviceToHost, s);
   rc = finish_session(S);

@@ -191,10 +191,14 @@ void launch_hierarchy(Problem &P) {
 // ---------------------------------------------------------------------------
 // A4 (c). Refit: bottom-up boxes.  One thread per leaf writes its point as the
 // box of its slot in the parent record, then climbs: at every node the first
-// arriver stops and the second (who sees an odd arrival count) merges the two
-// child boxes and carries the union one level up.  Wait-free.  The arrival
-// counters are never reset: each pass adds exactly two arrivals per node, so
-// the parity of the count before the add tells first from second.
+// arriver stops and the second merges the two child boxes and carries the
+// union one level up.  Wait-free.
+// A node whose leaf range lies inside this CTA's 256 leaves has both arrivals
+// from this CTA, so it is counted in shared memory with block-scope fences;
+// only nodes spanning CTAs use the global counters (about 2 per 256 leaves
+// per level above the CTA).  The global counters are never reset: each pass
+// adds exactly two arrivals per node, so the parity of the count before the
+// add tells first from second.
 // With init_labels, the round-0 child labels are written on the way
 // (leaf k: label k; internal: several components, kInvalid).
 // ---------------------------------------------------------------------------
@@ -210,8 +214,14 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
                                                   NodeRec *nodes,
                                                   const uint32_t *__restrict__ parent_leaf,
                                                   const uint32_t *__restrict__ parent_node,
+                                                  const uint2 *__restrict__ range,
                                                   uint32_t *arrivals, int init_labels) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ uint32_t s_arrive[kBlock];
+  const int64_t first = (int64_t)blockIdx.x * kBlock;
+  const int64_t last = first + kBlock - 1;
+  s_arrive[threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t k = first + threadIdx.x;
   if (k >= n) return;
   float4 p = pts[k];
   uint32_t up = parent_leaf[k];
@@ -220,15 +230,31 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
   store_slot_box(&nodes[node], slot, p.x, p.y, p.z, p.x, p.y, p.z);
   if (init_labels) reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = (uint32_t)k;
   while (true) {
-    __threadfence();
-    uint32_t before = atomicAdd(&arrivals[node], 1u);
-    if ((before & 1u) == 0u) return;  // first arriver: the sibling will carry on
-    __threadfence();
-    const float4 *r = reinterpret_cast<const float4 *>(&nodes[node]);
-    float4 a = __ldcg(r), b = __ldcg(r + 1), c = __ldcg(r + 2);
+    const uint2 r = __ldg(range + node);
+    const bool local = (int64_t)r.x >= first && (int64_t)r.y <= last;
+    float4 a, b, c;
+    if (local) {
+      __threadfence_block();
+      const uint32_t before = atomicAdd(&s_arrive[node - first], 1u);
+      if (before == 0u) return;  // first arriver: the sibling will carry on
+      __threadfence_block();
+      const float4 *rec = reinterpret_cast<const float4 *>(&nodes[node]);
+      a = rec[0];
+      b = rec[1];
+      c = rec[2];
+    } else {
+      __threadfence();
+      const uint32_t before = atomicAdd(&arrivals[node], 1u);
+      if ((before & 1u) == 0u) return;
+      __threadfence();
+      const float4 *rec = reinterpret_cast<const float4 *>(&nodes[node]);
+      a = __ldcg(rec);
+      b = __ldcg(rec + 1);
+      c = __ldcg(rec + 2);
+    }
     // left box: a.x a.y a.z | a.w b.x b.y ; right box: b.z b.w c.x | c.y c.z c.w
-    float lx = fminf(a.x, b.z), ly = fminf(a.y, b.w), lz = fminf(a.z, c.x);
-    float hx = fmaxf(a.w, c.y), hy = fmaxf(b.x, c.z), hz = fmaxf(b.y, c.w);
+    const float lx = fminf(a.x, b.z), ly = fminf(a.y, b.w), lz = fminf(a.z, c.x);
+    const float hx = fmaxf(a.w, c.y), hy = fmaxf(b.x, c.z), hz = fmaxf(b.y, c.w);
     if (node == 0) return;
     up = parent_node[node];
     node = up >> 1;
@@ -240,7 +266,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
 
 void launch_refit(Problem &P, bool init_labels) {
   k_refit<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.n, P.nodes, P.parent_leaf,
-                                                          P.parent_node, P.arrivals,
+                                                          P.parent_node, P.range, P.arrivals,
                                                           init_labels ? 1 : 0);
   P.launches += 1;
 }

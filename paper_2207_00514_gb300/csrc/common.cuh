@@ -189,8 +189,15 @@ struct Problem {
                                      //      keys, capped at 255; < 64 means the node holds
                                      //      exactly the points of one Morton cell
   uint32_t *runs = nullptr;          // n: label boundaries before each curve position
-  uint32_t *labels = nullptr;        // n
-  uint32_t *bound = nullptr;         // n, FP32 bits of the component upper bound
+  uint32_t *labels = nullptr;        // n, current round (= labels_buf[cur])
+  uint32_t *bound = nullptr;         // n, FP32 bits of the component upper bound (= bound_buf[cur])
+  uint32_t *labels_buf[2] = {nullptr, nullptr};
+  uint32_t *bound_buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint32_t *list_buf[2] = {nullptr, nullptr};  // active component labels, ping-pong
+  uint32_t *active_list = nullptr;   // this round's active labels (nullptr: all n)
+  uint32_t *next_list = nullptr;     // roots appended by the merge
+  int64_t n_active = 0;
   uint2 *res = nullptr;              // n: (w bits, neighbour curve index)
   uint32_t *res_id = nullptr;        // n: neighbour original index
   uint64_t *comp_key = nullptr;      // n: (w bits << 32) | min original id
@@ -201,6 +208,7 @@ struct Problem {
   emst_edge *out_stage = nullptr;    // n-1: device staging of host outputs
   uint32_t *counters = nullptr;      // [0] edges emitted, [1] status bits, [2..3] node visits (u64),
                                      // [4..9] scene box (ordered), [16..23] sort tile counters,
+                                     // [12] next round's active components,
                                      // [24] scan tile counter, [32..38] quantiser (floats)
   uint32_t *sort_hist = nullptr;     // 8 x 256
   uint32_t *sort_lookback = nullptr; // tiles x 256
@@ -219,14 +227,16 @@ void launch_hierarchy(Problem &P);
 void launch_refit(Problem &P, bool init_labels);
 // sort.cu
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 12;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 int64_t sort_tiles_for(int64_t n);
 // Stable LSD radix sort of (keys, vals) pairs on digits [digit_begin, digit_end)
 // (8-bit digits).  Returns the index (0/1) of the buffers holding the result.
 int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int src);
 // rounds.cu
+void launch_label_runs(Problem &P);
 void launch_node_labels(Problem &P);
+void advance_round(Problem &P, int64_t n_active);
 void launch_upper_bounds(Problem &P);
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
                      bool seeded, bool climb = false);
@@ -248,6 +258,7 @@ int check_args(const float *points, int64_t n, int dim);
 int bits_for(int64_t v);
 void run_build(Problem &P, bool init_labels);
 void reset_round_state(Problem &P);
+void run_round(Problem &P, int round, bool carried, int block, bool count, bool climb);
 void run_output(Problem &P, emst_edge *out);
 
 inline int grid_for(int64_t n, int block) {

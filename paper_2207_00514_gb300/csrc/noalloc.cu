@@ -23,9 +23,9 @@
 namespace emst {
 namespace {
 
-// Fixed scratch: 13 MiB, enough for EMST_NOALLOC_MAX_POINTS points of either
+// Fixed scratch: 16 MiB, enough for EMST_NOALLOC_MAX_POINTS points of either
 // dimension including host-copy staging (checked per call against the layout).
-constexpr size_t kNoallocScratchBytes = size_t(13) << 20;
+constexpr size_t kNoallocScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 // Device address of the array, looked up once per device.  In host code the
@@ -76,7 +76,7 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
   if (layout(P, nullptr, !pts_dev, !out_dev) > kNoallocScratchBytes) return EMST_ERR_TOO_LARGE;
   layout(P, base, !pts_dev, !out_dev);
 
-  uint32_t host_counters[4] = {0, 0, 0, 0};
+  uint32_t host_counters[16] = {0};
   auto sync_counters = [&]() -> bool {
     if (cudaMemcpyAsync(host_counters, P.counters, sizeof(host_counters), cudaMemcpyDeviceToHost,
                         stream) != cudaSuccess)
@@ -96,13 +96,10 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
     const int limit = bits_for(n - 1) + 1;
     for (int round = 0;; ++round) {
       if (round >= limit) return EMST_ERR_ROUND_LIMIT;
-      if (round > 0) launch_node_labels(P);
-      launch_upper_bounds(P);
-      launch_traverse(P, round > 0, nullptr, 0, false, true);
-      launch_reduce(P);
-      launch_merge(P);
+      run_round(P, round, true, 0, false, false);
       if (!sync_counters()) return EMST_ERR_CUDA;
       if (host_counters[1] != 0) return status_from_bits(host_counters[1]);
+      advance_round(P, (int64_t)host_counters[12]);
       if ((int64_t)host_counters[0] >= n - 1) break;
     }
     if ((int64_t)host_counters[0] != n - 1) return EMST_ERR_INTERNAL;

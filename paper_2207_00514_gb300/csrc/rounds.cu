@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restri
   reinterpret_cast<uint2 *>(&nodes[i].d)[1] = make_uint2(lab[0], lab[1]);
 }
 
-void launch_node_labels(Problem &P) {
+void launch_label_runs(Problem &P) {
   const int64_t tiles = (P.n + kScanTile - 1) / kScanTile;
   uint32_t *ctr = P.counters + 24;
   cudaMemsetAsync(ctr, 0, sizeof(uint32_t), P.stream);
@@ -132,9 +132,13 @@ void launch_node_labels(Problem &P) {
   k_label_runs<<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(P.labels, P.n, P.runs,
                                                                P.sort_lookback, ctr,
                                                                P.counters + 1);
+  P.launches += 1;
+}
+
+void launch_node_labels(Problem &P) {
   k_node_labels<<<grid_for(P.n - 1, kBlock), kBlock, 0, P.stream>>>(P.labels, P.runs, P.range,
                                                                     P.n, P.nodes);
-  P.launches += 2;
+  P.launches += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -502,16 +506,20 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
 // ---------------------------------------------------------------------------
 // A8 (second half). Among the points whose (w, min id) equals the component's
 // winner, the smallest max id: together the exact minimum of the key
-// (w, min id, max id) of §2 over the component.
+// (w, min id, max id) of §2 over the component.  Also clears the other
+// round's bound buffer (bound_next) for the relabel pass that fills it.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_reduce_max(const float4 *__restrict__ pts,
                                                        const uint32_t *__restrict__ labels,
                                                        const uint2 *__restrict__ res,
                                                        const uint32_t *__restrict__ res_id,
                                                        const uint64_t *__restrict__ comp_key,
-                                                       uint32_t *comp_max, int64_t n) {
+                                                       uint32_t *comp_max,
+                                                       uint32_t *__restrict__ bound_next,
+                                                       int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (bound_next) bound_next[i] = kNoBound;
   uint2 r = res[i];
   if (r.y == kInvalid) return;
   uint32_t me = labels[i];
@@ -521,8 +529,8 @@ __global__ void __launch_bounds__(kBlock) k_reduce_max(const float4 *__restrict_
 }
 
 void launch_reduce(Problem &P) {
-  k_reduce_max<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.labels, P.res, P.res_id,
-                                                               P.comp_key, P.comp_max, P.n);
+  k_reduce_max<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(
+      P.pts, P.labels, P.res, P.res_id, P.comp_key, P.comp_max, P.bound_buf[P.cur ^ 1], P.n);
   P.launches += 1;
 }
 
@@ -534,17 +542,23 @@ void launch_reduce(Problem &P) {
 // smaller label of that pair.  The pair's shared edge is emitted once, by its
 // smaller side; every other component emits its own edge.  (A component with
 // no edge -- possible only when a given radius cut every query short -- ends
-// any chain that reaches it and keeps its label.)  (c) relabel every
-// point and reset the per-component scratch for the next round.
+// any chain that reaches it and keeps its label.)  Components are visited
+// through the list of active labels (all n in the first round); each new root
+// appends itself to the next round's list.  (c) relabel every point (A9) and,
+// in the same pass, prepare the next round: its curve-pair upper bounds (A6)
+// and the label-boundary prefix scan the node labels (A5) need.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_merge_targets(const uint64_t *__restrict__ comp_key,
+__global__ void __launch_bounds__(kBlock) k_merge_targets(const uint32_t *__restrict__ list,
+                                                          int64_t count,
+                                                          const uint64_t *__restrict__ comp_key,
                                                           const uint32_t *__restrict__ comp_max,
                                                           const uint32_t *__restrict__ inv,
                                                           const uint32_t *__restrict__ labels,
                                                           uint32_t *__restrict__ target,
-                                                          uint32_t *status, int64_t n) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
+                                                          uint32_t *status) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const uint32_t c = list ? list[t] : (uint32_t)t;
   uint64_t key = comp_key[c];
   const uint32_t mx = comp_max[c];
   if (key == kEmptyKey || mx == kInvalid) {
@@ -556,69 +570,161 @@ __global__ void __launch_bounds__(kBlock) k_merge_targets(const uint64_t *__rest
   }
   uint32_t lmn = labels[inv[(uint32_t)key]];
   uint32_t lmx = labels[inv[mx]];
-  target[c] = (lmn == (uint32_t)c) ? lmx : lmn;
+  target[c] = (lmn == c) ? lmx : lmn;
 }
 
-__global__ void __launch_bounds__(kBlock) k_merge_roots(uint64_t *__restrict__ comp_key,
+__global__ void __launch_bounds__(kBlock) k_merge_roots(const uint32_t *__restrict__ list,
+                                                        int64_t count,
+                                                        uint64_t *__restrict__ comp_key,
                                                         uint32_t *__restrict__ comp_max,
                                                         const uint32_t *__restrict__ target,
                                                         uint32_t *__restrict__ root,
                                                         emst_edge *__restrict__ edges,
+                                                        uint32_t *__restrict__ next_list,
                                                         uint32_t *counters, int64_t n) {
-  int64_t c64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c64 >= n) return;
-  const uint32_t c = (uint32_t)c64;
+  int64_t t64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t64 >= count) return;
+  const uint32_t c = list ? list[t64] : (uint32_t)t64;
   const uint64_t key = comp_key[c];
-  if (key == kEmptyKey) {  // no edge: not a label, or a component whose queries found nothing
-    root[c] = c;
-    return;
-  }
-  const uint32_t t = target[c];
-  if (t == kInvalid) {  // guarded above; keeps the component as it is
-    root[c] = c;
+  const uint32_t t = key == kEmptyKey ? kInvalid : target[c];
+  uint32_t r = c;
+  if (t != kInvalid) {
+    const bool mutual = target[t] == c;
+    if (!mutual || c < t) {
+      uint32_t e = atomicAdd(&counters[0], 1u);
+      emst_edge E;
+      E.i = (uint32_t)key;
+      E.j = comp_max[c];
+      E.w = __uint_as_float((uint32_t)(key >> 32));
+      edges[e] = E;
+    }
+    uint32_t x = c;
+    for (int64_t steps = 0;; ++steps) {
+      uint32_t y = target[x];
+      if (y == kInvalid) { r = x; break; }  // chain ends at a component without an edge
+      if (target[y] == x) { r = x < y ? x : y; break; }
+      x = y;
+      if (steps > n) { atomicOr(&counters[1], kErrChain); r = x; break; }
+    }
     comp_key[c] = kEmptyKey;
     comp_max[c] = kInvalid;
-    return;
-  }
-  const bool mutual = target[t] == c;
-  if (!mutual || c < t) {
-    uint32_t e = atomicAdd(&counters[0], 1u);
-    emst_edge E;
-    E.i = (uint32_t)key;
-    E.j = comp_max[c];
-    E.w = __uint_as_float((uint32_t)(key >> 32));
-    edges[e] = E;
-  }
-  uint32_t x = c, r = c;
-  for (int64_t steps = 0;; ++steps) {
-    uint32_t y = target[x];
-    if (y == kInvalid) { r = x; break; }  // chain ends at a component without an edge
-    if (target[y] == x) { r = x < y ? x : y; break; }
-    x = y;
-    if (steps > n) { atomicOr(&counters[1], kErrChain); r = x; break; }
   }
   root[c] = r;
-  comp_key[c] = kEmptyKey;
-  comp_max[c] = kInvalid;
+  if (r == c) next_list[atomicAdd(&counters[12], 1u)] = c;
 }
 
-__global__ void __launch_bounds__(kBlock) k_relabel(uint32_t *__restrict__ labels,
-                                                    const uint32_t *__restrict__ root,
-                                                    uint32_t *__restrict__ bound, int64_t n) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  labels[k] = root[labels[k]];
-  bound[k] = kNoBound;
+// Relabel + next round's bounds + label-boundary scan, one tile of positions
+// per CTA, decoupled look-back for the scan.  New labels go to a second
+// buffer (neighbouring tiles still read the old ones).
+__global__ void __launch_bounds__(kScanThreads) k_relabel_runs(
+    const uint32_t *__restrict__ labels_old, const uint32_t *__restrict__ root,
+    const float4 *__restrict__ pts, int64_t n, uint32_t *__restrict__ labels_new,
+    uint32_t *__restrict__ bound_next, uint32_t *__restrict__ runs, uint32_t *lookback,
+    uint32_t *tile_counter, uint32_t *status) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_warp[kScanThreads / 32];
+  __shared__ uint32_t s_prefix;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t first = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
+  uint32_t lab[kScanItems + 1];
+#pragma unroll
+  for (int q = 0; q <= kScanItems; ++q) {
+    int64_t k = first + q;
+    lab[q] = k < n ? __ldg(root + __ldg(labels_old + k)) : kInvalid;
+  }
+  uint32_t flags = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t k = first + q;
+    if (k < n) labels_new[k] = lab[q];
+    if (k + 1 < n && lab[q] != lab[q + 1]) {
+      flags |= 1u << q;
+      const float4 p = __ldg(pts + k), r = __ldg(pts + k + 1);
+      const uint32_t w = __float_as_uint(sq_dist(p.x, p.y, p.z, r.x, r.y, r.z));
+      atomicMin(&bound_next[lab[q]], w);
+      atomicMin(&bound_next[lab[q + 1]], w);
+    }
+  }
+  const uint32_t mine = __popc(flags);
+  uint32_t x = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
+    uint32_t z = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
+    }
+    if (lane < kScanThreads / 32) s_warp[lane] = z - w;
+    const uint32_t total = __shfl_sync(0xffffffffu, z, kScanThreads / 32 - 1);
+    if (lane == 0) {
+      volatile uint32_t *lb = lookback + tile;
+      *lb = (tile == 0 ? kScanPrefix : kScanAggregate) | total;
+      uint32_t excl = 0;
+      if (tile > 0) {
+        for (int64_t j = (int64_t)tile - 1; j >= 0; --j) {
+          const volatile uint32_t *pj = lookback + j;
+          uint32_t wv = *pj;
+          int spins = 0;
+          while ((wv & ~kScanMask) == 0u) {
+            if (++spins > (1 << 22)) { atomicOr(status, kErrSpin); wv = kScanPrefix; break; }
+            __nanosleep(32);
+            wv = *pj;
+          }
+          excl += wv & kScanMask;
+          if ((wv & ~kScanMask) == kScanPrefix) break;
+        }
+        *lb = kScanPrefix | ((excl + total) & kScanMask);
+      }
+      s_prefix = excl;
+    }
+  }
+  __syncthreads();
+  uint32_t run = s_prefix + s_warp[warp] + x - mine;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t k = first + q;
+    if (k < n) runs[k] = run;
+    run += (flags >> q) & 1u;
+  }
 }
 
 void launch_merge(Problem &P) {
-  int g = grid_for(P.n, kBlock);
-  k_merge_targets<<<g, kBlock, 0, P.stream>>>(P.comp_key, P.comp_max, P.inv, P.labels, P.target,
-                                              P.counters + 1, P.n);
-  k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.comp_key, P.comp_max, P.target, P.root, P.edges,
-                                            P.counters, P.n);
-  k_relabel<<<g, kBlock, 0, P.stream>>>(P.labels, P.root, P.bound, P.n);
+  const int64_t count = P.active_list ? P.n_active : P.n;
+  const int g = grid_for(count, kBlock);
+  cudaMemsetAsync(P.counters + 12, 0, sizeof(uint32_t), P.stream);
+  k_merge_targets<<<g, kBlock, 0, P.stream>>>(P.active_list, count, P.comp_key, P.comp_max, P.inv,
+                                              P.labels, P.target, P.counters + 1);
+  k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.active_list, count, P.comp_key, P.comp_max, P.target,
+                                            P.root, P.edges, P.next_list, P.counters, P.n);
+  const int64_t tiles = (P.n + kScanTile - 1) / kScanTile;
+  uint32_t *ctr = P.counters + 24;
+  cudaMemsetAsync(ctr, 0, sizeof(uint32_t), P.stream);
+  cudaMemsetAsync(P.sort_lookback, 0, sizeof(uint32_t) * (size_t)tiles, P.stream);
+  k_relabel_runs<<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(
+      P.labels, P.root, P.pts, P.n, P.labels_buf[P.cur ^ 1], P.bound_buf[P.cur ^ 1], P.runs,
+      P.sort_lookback, ctr, P.counters + 1);
   P.launches += 3;
+}
+
+// After the host has seen a round finish: the next round's labels, bounds and
+// active list become current.
+void advance_round(Problem &P, int64_t n_active) {
+  P.cur ^= 1;
+  P.labels = P.labels_buf[P.cur];
+  P.bound = P.bound_buf[P.cur];
+  uint32_t *t = P.list_buf[0] == P.next_list ? P.list_buf[1] : P.list_buf[0];
+  P.active_list = P.next_list;
+  P.next_list = t;
+  P.n_active = n_active;
 }
 
 __global__ void k_fill_u32(uint32_t *p, uint32_t v, int64_t count) {

@@ -74,7 +74,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_pass(
+__global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n, int shift,
     const uint32_t *__restrict__ digit_offset, uint32_t *lookback, uint32_t *tile_counter,
