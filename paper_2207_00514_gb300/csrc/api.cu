@@ -83,10 +83,9 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.inv = c.take<uint32_t>(n);
   P.nodes = c.take<NodeRec>(n - 1);
   P.parent_leaf = c.take<uint32_t>(n);
-  P.parent_node = c.take<uint32_t>(n - 1);
+  P.up_delta = c.take<uint2>(n - 1);
   P.arrivals = c.take<uint32_t>(n - 1);
   P.range = c.take<uint2>(n - 1);
-  P.delta = c.take<uint8_t>(n - 1);
   P.runs = c.take<uint32_t>(n);
   P.labels_buf[0] = c.take<uint32_t>(n);
   P.labels_buf[1] = c.take<uint32_t>(n);

@@ -149,9 +149,8 @@ __device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k, int6
 __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict__ keys, int64_t n,
                                                       NodeRec *__restrict__ nodes,
                                                       uint32_t *__restrict__ parent_leaf,
-                                                      uint32_t *__restrict__ parent_node,
-                                                      uint2 *__restrict__ range,
-                                                      uint8_t *__restrict__ delta) {
+                                                      uint2 *__restrict__ up_delta,
+                                                      uint2 *__restrict__ range) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   int d = (prefix_delta(keys, n, i, i + 1) - prefix_delta(keys, n, i, i - 1)) > 0 ? 1 : -1;
@@ -174,17 +173,19 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
   uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
   reinterpret_cast<uint2 *>(&nodes[i].d)[0] = make_uint2(left, right);
   range[i] = make_uint2((uint32_t)lo, (uint32_t)hi);
-  delta[i] = (uint8_t)(dnode < 255 ? dnode : 255);
+  reinterpret_cast<uint32_t *>(up_delta + i)[1] = (uint32_t)dnode;
   uint32_t up = (uint32_t)i << 1;
-  if (left & kLeafBit) parent_leaf[left & ~kLeafBit] = up; else parent_node[left] = up;
-  if (right & kLeafBit) parent_leaf[right & ~kLeafBit] = up | 1u; else parent_node[right] = up | 1u;
-  if (i == 0) parent_node[0] = kInvalid;
+  if (left & kLeafBit) parent_leaf[left & ~kLeafBit] = up;
+  else reinterpret_cast<uint32_t *>(up_delta + left)[0] = up;
+  if (right & kLeafBit) parent_leaf[right & ~kLeafBit] = up | 1u;
+  else reinterpret_cast<uint32_t *>(up_delta + right)[0] = up | 1u;
+  if (i == 0) reinterpret_cast<uint32_t *>(up_delta)[0] = kInvalid;
 }
 
 void launch_hierarchy(Problem &P) {
   k_hierarchy<<<grid_for(P.n - 1, kBlock), kBlock, 0, P.stream>>>(P.keys[0] /*sorted*/, P.n, P.nodes,
-                                                                   P.parent_leaf, P.parent_node,
-                                                                   P.range, P.delta);
+                                                                   P.parent_leaf, P.up_delta,
+                                                                   P.range);
   P.launches += 1;
 }
 
@@ -213,7 +214,7 @@ __device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, float lx,
 __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
                                                   NodeRec *nodes,
                                                   const uint32_t *__restrict__ parent_leaf,
-                                                  const uint32_t *__restrict__ parent_node,
+                                                  const uint2 *__restrict__ up_delta,
                                                   const uint2 *__restrict__ range,
                                                   uint32_t *arrivals, int init_labels) {
   __shared__ uint32_t s_arrive[kBlock];
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
     const float lx = fminf(a.x, b.z), ly = fminf(a.y, b.w), lz = fminf(a.z, c.x);
     const float hx = fmaxf(a.w, c.y), hy = fmaxf(b.x, c.z), hz = fmaxf(b.y, c.w);
     if (node == 0) return;
-    up = parent_node[node];
+    up = up_delta[node].x;
     node = up >> 1;
     slot = (int)(up & 1u);
     store_slot_box(&nodes[node], slot, lx, ly, lz, hx, hy, hz);
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
 
 void launch_refit(Problem &P, bool init_labels) {
   k_refit<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.n, P.nodes, P.parent_leaf,
-                                                          P.parent_node, P.range, P.arrivals,
+                                                          P.up_delta, P.range, P.arrivals,
                                                           init_labels ? 1 : 0);
   P.launches += 1;
 }

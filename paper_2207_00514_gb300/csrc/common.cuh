@@ -182,12 +182,12 @@ struct Problem {
   uint32_t *inv = nullptr;        // original index -> curve index
   NodeRec *nodes = nullptr;       // n-1
   uint32_t *parent_leaf = nullptr;   // n: (parent << 1) | slot
-  uint32_t *parent_node = nullptr;   // n-1: (parent << 1) | slot, root: kInvalid
+  uint2 *up_delta = nullptr;         // n-1: x = (parent << 1) | slot (root: kInvalid),
+                                     //      y = leading bits shared by the node's (code,
+                                     //      position) keys; y < 64 means the node holds
+                                     //      exactly the points of one Morton cell
   uint32_t *arrivals = nullptr;      // n-1 arrival counters (parity = who is second)
   uint2 *range = nullptr;            // n-1: leaf range [first, last] of each internal node
-  uint8_t *delta = nullptr;          // n-1: leading bits shared by the node's (code, position)
-                                     //      keys, capped at 255; < 64 means the node holds
-                                     //      exactly the points of one Morton cell
   uint32_t *runs = nullptr;          // n: label boundaries before each curve position
   uint32_t *labels = nullptr;        // n, current round (= labels_buf[cur])
   uint32_t *bound = nullptr;         // n, FP32 bits of the component upper bound (= bound_buf[cur])

@@ -283,14 +283,12 @@ __device__ __forceinline__ bool box_in_cell(int dim, uint32_t dl, const uint32_t
 //    (Optimization 1) and its box is within the cutoff (inclusive: equal
 //    weights with smaller ids must survive); a leaf updates the best
 //    (w, original id) and shrinks the cutoff to w.
-// Order of the search (CLIMB): instead of descending from the root, the query
-// climbs from its own leaf.  At each ancestor A it searches the subtree of the
-// sibling of the child it came from, so A's whole subtree has then been
-// searched.  A node whose two end codes differ (delta < 64) holds exactly the
-// points of one aligned Morton cell; when the quantised box around the cutoff
-// ball (ball_box) lies inside A's cell, every point within the cutoff is
-// in A's subtree and the query ends.  Otherwise it climbs on, at worst to the
-// root.  Without CLIMB the search starts at the root (the paper's order).
+// Where the search starts (CLIMB): the paper's search starts at the root.  A
+// node whose two end codes differ holds exactly the points of one aligned
+// Morton cell, so with CLIMB the query first climbs parent pointers from its
+// leaf to the lowest ancestor whose cell contains the quantised box around its
+// cutoff ball (ball_box, box_in_cell) and searches only that subtree: every
+// point within the cutoff is in it.
 // The stack never overflows: every split of the hierarchy uses a strictly
 // later bit of the 96-bit augmented key (64-bit code + 32-bit position), so a
 // root-to-leaf path has at most 96 internal nodes and at most one stacked
@@ -313,8 +311,8 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
     const float4 *__restrict__ pts, const NodeRec *__restrict__ nodes,
     const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound,
     const float *__restrict__ radius_in, const uint64_t *__restrict__ codes,
-    const uint32_t *__restrict__ parent_leaf, const uint32_t *__restrict__ parent_node,
-    const uint8_t *__restrict__ delta, const float *__restrict__ quant, int dim,
+    const uint32_t *__restrict__ parent_leaf, const uint2 *__restrict__ up_delta,
+    const float *__restrict__ quant, int dim,
     uint2 *__restrict__ res, uint32_t *__restrict__ res_id, uint64_t *__restrict__ comp_key,
     int64_t n, uint32_t *status, unsigned long long *visits) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -373,81 +371,28 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   unsigned long long nvis = 0;
   bool ok = true;
 
-  if (!CLIMB) {
-    ok = explore<COUNT>(q, 0u, nodes, pts, st_node, st_dist, nvis);
-  } else {
-    // One loop, one record per iteration, so the lanes of a warp stay in step
-    // whether they are climbing or searching a sibling subtree.  `anc` is the
-    // ancestor being completed; its child on the path is masked out (its
-    // subtree is already done); when the depth-first stack runs dry, anc's
-    // whole subtree has been searched and the containment test decides
-    // whether to stop or climb one level.
+  uint32_t start = 0u;  // the search starts at the root ...
+  if (CLIMB && q.radius < __int_as_float(0x7f800000)) {
+    // ... or, with CLIMB, at the lowest ancestor of the query's leaf whose
+    // Morton cell contains the quantised box around the cutoff ball: every
+    // point within the cutoff lies in that ancestor's subtree.  The climb only
+    // follows parent pointers (one 8-byte load per level); the search below is
+    // the same depth-first loop for every lane.
     const Quantizer Q = load_quantizer(quant, dim);
-    uint32_t qp[3] = {0, 0, 0};
+    uint32_t qp[3] = {0, 0, 0}, blo[3], bhi[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (d < dim) qp[d] = quantize(Q, d, d == 0 ? q.px : (d == 1 ? q.py : q.pz));
-    float box_r = __int_as_float(0x7f800000);  // radius the ball box was computed for
-    uint32_t blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
-    const uint32_t up0 = __ldg(parent_leaf + i);
-    uint32_t anc = up0 >> 1;
-    uint32_t anc_up = anc != 0 ? __ldg(parent_node + anc) : kInvalid;
-    uint32_t anc_dl = __ldg(delta + anc);
-    uint32_t node = anc;
-    int masked = (int)(up0 & 1u);  // child of `node` not to test (-1: none)
-    int sp = 0;
+    ball_box(Q, dim, q, blo, bhi);
+    uint32_t x = __ldg(parent_leaf + i) >> 1;
     while (true) {
-      if (COUNT) ++nvis;
-      const float4 *r = reinterpret_cast<const float4 *>(nodes + node);
-      const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
-      const uint4 dd = __ldg(reinterpret_cast<const uint4 *>(r + 3));
-      const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
-      const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
-      bool okL = masked != 0 && (dd.z != q.me) && (dL <= q.radius);
-      bool okR = masked != 1 && (dd.w != q.me) && (dR <= q.radius);
-      if (okL && (dd.x & kLeafBit)) { take_leaf(q, pts, dd.x & ~kLeafBit, dL); okL = false; }
-      if (okR && (dd.y & kLeafBit)) {
-        if (dR <= q.radius) take_leaf(q, pts, dd.y & ~kLeafBit, dR);
-        okR = false;
-      }
-      okL = okL && dL <= q.radius;
-      okR = okR && dR <= q.radius;
-      masked = -1;
-      if (okL && okR) {
-        if (sp >= kStackDepth) { ok = false; break; }
-        if (dL <= dR) { st_node[sp] = dd.y; st_dist[sp] = dR; node = dd.x; }
-        else { st_node[sp] = dd.x; st_dist[sp] = dL; node = dd.y; }
-        ++sp;
-        continue;
-      }
-      if (okL) { node = dd.x; continue; }
-      if (okR) { node = dd.y; continue; }
-      bool found = false;
-      while (sp > 0) {
-        --sp;
-        if (st_dist[sp] <= q.radius) { node = st_node[sp]; found = true; break; }
-      }
-      if (found) continue;
-      // anc's subtree is complete: stop if the cutoff ball lies in its cell
-      if (anc == 0) break;
-      if (anc_dl < 64 && q.radius < __int_as_float(0x7f800000)) {
-        // a box computed for a larger radius is still a valid (looser) test;
-        // recompute only when that test fails and the radius has shrunk
-        bool in = box_r < __int_as_float(0x7f800000) && box_in_cell(dim, anc_dl, qp, blo, bhi);
-        if (!in && q.radius < box_r) {
-          ball_box(Q, dim, q, blo, bhi);
-          box_r = q.radius;
-          in = box_in_cell(dim, anc_dl, qp, blo, bhi);
-        }
-        if (in) break;
-      }
-      masked = (int)(anc_up & 1u);
-      anc = anc_up >> 1;
-      node = anc;
-      anc_up = anc != 0 ? __ldg(parent_node + anc) : kInvalid;
-      anc_dl = __ldg(delta + anc);
+      const uint2 ud = __ldg(up_delta + x);
+      if (x == 0 || (ud.y < 64 && box_in_cell(dim, ud.y, qp, blo, bhi))) break;
+      x = ud.x >> 1;
     }
+    start = x;
   }
+  ok = explore<COUNT>(q, start, nodes, pts, st_node, st_dist, nvis);
   if (!ok) atomicOr(status, kErrStack);
   if (COUNT) {
     // one atomic per warp: sum the active lanes' counts first
@@ -485,8 +430,8 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   cudaStream_t s = P.stream;
 #define EMST_TRAV(C, R, K, S, L)                                                              \
   k_traverse<C, R, K, S, L><<<g, block, 0, s>>>(                                               \
-      P.pts, P.nodes, P.labels, P.bound, radius_in, P.keys[0], P.parent_leaf, P.parent_node,   \
-      P.delta, reinterpret_cast<const float *>(P.counters + 32), P.dim, P.res, P.res_id,         \
+      P.pts, P.nodes, P.labels, P.bound, radius_in, P.keys[0], P.parent_leaf, P.up_delta,      \
+      reinterpret_cast<const float *>(P.counters + 32), P.dim, P.res, P.res_id,                 \
       P.comp_key, P.n, P.counters + 1, vis)
   if (radius_in) {
     EMST_TRAV(false, true, false, false, false);
