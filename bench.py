@@ -271,10 +271,12 @@ def main():
     vis = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, count_visits=True)[1]
     torch.cuda.synchronize(dev)
     visits_per_query_round = vis["node_visits"] / float(n * max(vis["rounds"], 1))
-    # the alternative search order (climb from the leaf), untimed, for comparison
-    cl = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, climb=True)[1]
-    torch.cuda.synchronize(dev)
-    climb = {"total_ms": round(cl["total_ms"], 3), "traverse_ms": round(cl["traverse_ms"], 3)}
+    # other leaf chunk sizes, untimed, for comparison
+    leaf_sweep = {}
+    for leaf in (1, 2, 8):
+        lv = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, leaf_size=leaf)[1]
+        torch.cuda.synchronize(dev)
+        leaf_sweep[str(leaf)] = {"total_ms": round(lv["total_ms"], 3), "traverse_ms": round(lv["traverse_ms"], 3)}
 
     peak, peak_kind = measured_peaks()
     avg_trav = trav_ms / max(trav_launches, 1)
@@ -319,7 +321,8 @@ def main():
                        "round_traverse_ms": [round(x, 3) for x in (round_trav or [])],
                        "components_per_round": comps,
                        "node_visits_per_query_per_round": round(visits_per_query_round, 2),
-                       "climb_search_order_for_comparison": climb,
+                       "leaf_size": 4,
+                       "other_leaf_sizes_untimed": leaf_sweep,
                        "mfeatures_per_s": value * 3},
             "roofline": roofline,
             "cpu_baseline": cpu,

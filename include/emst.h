@@ -73,9 +73,8 @@ typedef struct emst_options {
   int32_t use_graph;          /* 1 = run the round loop as a CUDA graph with a device-side
                                  loop condition; 0 = host loop (one sync per round) */
   int32_t count_visits;       /* 1 = count node visits per round into emst_stats */
-  int32_t climb;              /* 1 = queries climb from their own leaf and stop early once the
-                                 cutoff ball lies in an ancestor's Morton cell; 0 (default) =
-                                 they descend from the root (the paper's order) */
+  int32_t leaf_size;          /* points per leaf chunk of the hierarchy: 0 = default (4), else
+                                 1, 2, 4, 8 or 16 (halved while fewer than 2 chunks remain) */
   int32_t reserved[10];
 } emst_options;
 
@@ -153,26 +152,32 @@ const char *emst_status_string(int status);
 /* ---------------------------------------------------------------------- */
 
 /* Tree build (§2 "ArborX": Z-curve sort and linear BVH; §3 Fig. 4 numbering).
+ * The hierarchy's leaves are chunks of leaf_size consecutive points in curve
+ * order (chunk c = curve positions [c*leaf_size, (c+1)*leaf_size), the last
+ * one shorter); with leaf_size = 1 every point is a leaf, as in the paper.
  *   points           n x dim FP32 (device or host), n >= 2.
+ *   leaf_size        1, 2, 4, 8 or 16, with ceil(n / leaf_size) >= 2.
  *   out_codes        n uint64: Morton codes in sorted order.
  *   out_perm         n uint32: input index of the k-th point in curve order.
- *   out_children     2(n-1) uint32: internal node v's left/right child; a
- *                    leaf k is 0x80000000|k, an internal node is its index.
- *   out_boxes        (n-1) x 2 x 6 FP32: per internal node, per child, the
+ *   out_children     2(m-1) uint32, m = ceil(n / leaf_size): internal node v's
+ *                    left/right child; leaf chunk c is 0x80000000|c, an
+ *                    internal node is its index.
+ *   out_boxes        (m-1) x 2 x 6 FP32: per internal node, per child, the
  *                    child's box (lo x,y,z, hi x,y,z; z = 0 in 2D).
  * Any output pointer may be NULL (then it is not written). */
-int emst_build_bvh(const float *points, int64_t n, int dim, uint64_t *out_codes, uint32_t *out_perm,
-                   uint32_t *out_children, float *out_boxes, void *stream);
+int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint64_t *out_codes,
+                   uint32_t *out_perm, uint32_t *out_children, float *out_boxes, void *stream);
 
 /* One Boruvka round from given component labels (§3: Optimization 1 node
  * labels, Optimization 2 upper bounds, Algorithm 2 queries, the per-component
- * minimum, and the merge).  Everything is indexed in CURVE order (the
- * out_perm order of emst_build_bvh); a label is the curve index of a point of
- * its component, and labels[labels[k]] == labels[k] must hold.
+ * minimum, and the merge), on the hierarchy emst_build_bvh builds with the
+ * same leaf_size.  Everything is indexed in CURVE order (the out_perm order of
+ * emst_build_bvh); a label is the curve index of a point of its component,
+ * and labels[labels[k]] == labels[k] must hold.
  *   labels_in        n uint32 (device).
  *   radius_in        n FP32 per-point starting radius, or NULL to use the
  *                    component upper bound only (device).
- *   out_node_labels  2(n-1) uint32: the label stored with each child of each
+ *   out_node_labels  2(m-1) uint32: the label stored with each child of each
  *                    internal node (0xFFFFFFFF = several components).
  *   out_upper_bound  n FP32 indexed by label (+inf where none).
  *   out_nn_w, out_nn_j  n FP32 / uint32: each point's neighbour in another
@@ -182,10 +187,11 @@ int emst_build_bvh(const float *points, int64_t n, int dim, uint64_t *out_codes,
  *   out_edges        room for n edges (device); *out_num_edges (host) = count,
  *                    in no particular order.
  * Any device output pointer may be NULL. */
-int emst_round_step(const float *points, int64_t n, int dim, const uint32_t *labels_in,
-                    const float *radius_in, uint32_t *out_node_labels, float *out_upper_bound,
-                    float *out_nn_w, uint32_t *out_nn_j, uint32_t *out_labels, emst_edge *out_edges,
-                    int64_t *out_num_edges, void *stream);
+int emst_round_step(const float *points, int64_t n, int dim, int leaf_size,
+                    const uint32_t *labels_in, const float *radius_in, uint32_t *out_node_labels,
+                    float *out_upper_bound, float *out_nn_w, uint32_t *out_nn_j,
+                    uint32_t *out_labels, emst_edge *out_edges, int64_t *out_num_edges,
+                    void *stream);
 
 #ifdef __cplusplus
 }

@@ -59,7 +59,7 @@ class EmstLibraryError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("carried_radius", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("count_visits", ctypes.c_int32), ("climb", ctypes.c_int32),
+                ("count_visits", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 10)]
 
 
@@ -104,9 +104,9 @@ def load_library(path: str | None = None):
         lib.emst_compute_batched.restype = I
         lib.emst_status_string.argtypes = [I]
         lib.emst_status_string.restype = ctypes.c_char_p
-        lib.emst_build_bvh.argtypes = [V, I64, I, V, V, V, V, V]
+        lib.emst_build_bvh.argtypes = [V, I64, I, I, V, V, V, V, V]
         lib.emst_build_bvh.restype = I
-        lib.emst_round_step.argtypes = [V, I64, I, V, V, V, V, V, V, V, V, ctypes.POINTER(I64), V]
+        lib.emst_round_step.argtypes = [V, I64, I, I, V, V, V, V, V, V, V, V, ctypes.POINTER(I64), V]
         lib.emst_round_step.restype = I
         lib.emst_compute_noalloc.argtypes = [V, I64, I, V, V]
         lib.emst_compute_noalloc.restype = I
@@ -202,7 +202,7 @@ def emst_compute_noalloc(points, out_edges=None, stream=None):
 
 
 def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_radius=True,
-                    use_graph=False, count_visits=False, climb=False):
+                    use_graph=False, count_visits=False, leaf_size=0):
     """emst_compute with options; returns (edges, stats dict)."""
     n, dim = _check_points(points)
     out_edges = _edges_out(n, points, out_edges)
@@ -212,7 +212,7 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
     opt.carried_radius = 1 if carried_radius else 0
     opt.use_graph = 1 if use_graph else 0
     opt.count_visits = 1 if count_visits else 0
-    opt.climb = 1 if climb else 0
+    opt.leaf_size = int(leaf_size)
     st = _Stats()
     st.struct_size = ctypes.sizeof(_Stats)
     rc = load_library().emst_compute_ex(_ptr(points), n, dim, _ptr(out_edges),
@@ -252,23 +252,25 @@ def emst_compute_batched(points, offsets, out_edges=None, stream=None):
     return out_edges, out_offs
 
 
-def emst_build_bvh(points, stream=None):
-    """The built hierarchy: dict(codes, perm, children (n-1, 2), boxes (n-1, 2, 6))."""
+def emst_build_bvh(points, leaf_size=1, stream=None):
+    """The built hierarchy over leaf chunks of `leaf_size` curve positions:
+    dict(codes, perm, children (m-1, 2), boxes (m-1, 2, 6)), m = ceil(n/leaf_size)."""
     torch = _torch()
     n, dim = _check_points(points)
     dev = points.device if points.device.type == "cuda" else torch.device("cuda")
+    m = max((n + leaf_size - 1) // leaf_size, 1)
     codes = torch.empty(n, dtype=torch.int64, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
-    children = torch.empty((max(n - 1, 0), 2), dtype=torch.int32, device=dev)
-    boxes = torch.empty((max(n - 1, 0), 2, 6), dtype=torch.float32, device=dev)
-    rc = load_library().emst_build_bvh(_ptr(points), n, dim, _ptr(codes), _ptr(perm), _ptr(children),
-                                       _ptr(boxes), _stream_ptr(stream, dev))
+    children = torch.empty((m - 1, 2), dtype=torch.int32, device=dev)
+    boxes = torch.empty((m - 1, 2, 6), dtype=torch.float32, device=dev)
+    rc = load_library().emst_build_bvh(_ptr(points), n, dim, int(leaf_size), _ptr(codes), _ptr(perm),
+                                       _ptr(children), _ptr(boxes), _stream_ptr(stream, dev))
     if rc != 0:
         raise EmstError(rc, "emst_build_bvh")
     return dict(codes=codes, perm=perm, children=children, boxes=boxes)
 
 
-def emst_round_step(points, labels, radius=None, stream=None):
+def emst_round_step(points, labels, radius=None, leaf_size=1, stream=None):
     """One Boruvka round from curve-order labels; see include/emst.h."""
     torch = _torch()
     n, dim = _check_points(points)
@@ -276,14 +278,15 @@ def emst_round_step(points, labels, radius=None, stream=None):
     labels = labels.to(device=dev, dtype=torch.int32).contiguous()
     if radius is not None:
         radius = radius.to(device=dev, dtype=torch.float32).contiguous()
-    node_labels = torch.empty((max(n - 1, 0), 2), dtype=torch.int32, device=dev)
+    m = max((n + leaf_size - 1) // leaf_size, 1)
+    node_labels = torch.empty((m - 1, 2), dtype=torch.int32, device=dev)
     ub = torch.empty(n, dtype=torch.float32, device=dev)
     nn_w = torch.empty(n, dtype=torch.float32, device=dev)
     nn_j = torch.empty(n, dtype=torch.int32, device=dev)
     new_labels = torch.empty(n, dtype=torch.int32, device=dev)
     edges = torch.empty((n, 3), dtype=torch.int32, device=dev)
     m = ctypes.c_int64(0)
-    rc = load_library().emst_round_step(_ptr(points), n, dim, _ptr(labels), _ptr(radius),
+    rc = load_library().emst_round_step(_ptr(points), n, dim, int(leaf_size), _ptr(labels), _ptr(radius),
                                         _ptr(node_labels), _ptr(ub), _ptr(nn_w), _ptr(nn_j),
                                         _ptr(new_labels), _ptr(edges), ctypes.byref(m),
                                         _stream_ptr(stream, dev))

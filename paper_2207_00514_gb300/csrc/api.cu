@@ -68,8 +68,20 @@ struct Carver {
 };
 
 // Lays the scratch of one problem out from `base` (nullptr: only measures).
+int effective_leaf(int64_t n, int requested) {
+  int k = requested > 0 ? requested : 4;
+  if (k > 16) k = 16;
+  int p = 1;
+  while (p * 2 <= k) p *= 2;
+  while (p > 1 && (n + p - 1) / p < 2) p /= 2;
+  return p;
+}
+
 size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   const int64_t n = P.n;
+  if (P.leaf < 1) P.leaf = 1;
+  P.nc = (n + P.leaf - 1) / P.leaf;
+  const int64_t nc = P.nc;
   Carver c(base);
   P.counters = c.take<uint32_t>(64);
   P.sort_hist = c.take<uint32_t>(8 * 256);
@@ -81,11 +93,11 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.vals[0] = c.take<uint32_t>(n);
   P.vals[1] = c.take<uint32_t>(n);
   P.inv = c.take<uint32_t>(n);
-  P.nodes = c.take<NodeRec>(n - 1);
-  P.parent_leaf = c.take<uint32_t>(n);
-  P.up_delta = c.take<uint2>(n - 1);
-  P.arrivals = c.take<uint32_t>(n - 1);
-  P.range = c.take<uint2>(n - 1);
+  P.nodes = c.take<NodeRec>(nc - 1);
+  P.parent_leaf = c.take<uint32_t>(nc);
+  P.up_delta = c.take<uint2>(nc - 1);
+  P.arrivals = c.take<uint32_t>(nc - 1);
+  P.range = c.take<uint2>(nc - 1);
   P.runs = c.take<uint32_t>(n);
   P.labels_buf[0] = c.take<uint32_t>(n);
   P.labels_buf[1] = c.take<uint32_t>(n);
@@ -150,7 +162,7 @@ void run_build(Problem &P, bool init_labels) {
   P.perm = P.vals[0];
   launch_gather(P, P.perm);
   if (P.n >= 2) {
-    cudaMemsetAsync(P.arrivals, 0, sizeof(uint32_t) * (size_t)(P.n - 1), P.stream);
+    cudaMemsetAsync(P.arrivals, 0, sizeof(uint32_t) * (size_t)(P.nc - 1), P.stream);
     launch_hierarchy(P);
     launch_refit(P, init_labels);
   }
@@ -159,10 +171,10 @@ void run_build(Problem &P, bool init_labels) {
 // One Boruvka round (the loop body of Fig. 3).  Round 0 takes its node labels
 // from the refit and computes its curve-pair bounds here; later rounds use
 // what the previous round's relabel pass prepared.
-void run_round(Problem &P, int round, bool carried, int block, bool count, bool climb) {
+void run_round(Problem &P, int round, bool carried, int block, bool count) {
   if (round > 0) launch_node_labels(P);
   else launch_upper_bounds(P);
-  launch_traverse(P, round > 0 && carried, nullptr, block, count, true, climb);
+  launch_traverse(P, round > 0 && carried, nullptr, block, count, true);
   launch_reduce(P);
   launch_merge(P);
 }
@@ -216,12 +228,13 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
     stats->struct_size = sz;
   }
   if (n == 0) return EMST_OK;
-  int block = 0, carried = 1, count = 0, climb = 0;
+  int block = 0, carried = 1, count = 0, leaf_req = 0;
   if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
     block = opt->block_size;
     carried = opt->carried_radius;
     count = opt->count_visits;
-    climb = opt->climb;
+    leaf_req = opt->leaf_size;
+    if (leaf_req < 0 || leaf_req > 16 || (leaf_req & (leaf_req - 1)) != 0) return EMST_ERR_INVALID_ARG;
     if (block != 0 && (block < 64 || block > 1024 || block % 32 != 0)) return EMST_ERR_INVALID_ARG;
   } else if (opt && opt->struct_size != 0) {
     return EMST_ERR_INVALID_ARG;
@@ -239,6 +252,7 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
   P.dim = dim;
   P.stream = stream;
   P.points = points;
+  P.leaf = effective_leaf(n, leaf_req);
   const size_t need = layout(P, nullptr, !pts_dev, !out_dev);
   char *base = nullptr;
   uint32_t host_counters[16] = {0};
@@ -278,7 +292,7 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
         cudaEventCreate(&tev[2 * rounds + 1]);
         cudaEventRecord(tev[2 * rounds], stream);
       }
-      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, climb != 0);
+      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true);
       if (stats && rounds < 40) {
         cudaEventRecord(tev[2 * rounds + 1], stream);
         n_tev = rounds + 1;
@@ -359,10 +373,14 @@ struct Session {
   }
 };
 
-int open_session(Session &S, const float *points, int64_t n, int dim, cudaStream_t stream) {
+int open_session(Session &S, const float *points, int64_t n, int dim, int leaf,
+                 cudaStream_t stream) {
   int rc = check_args(points, n, dim);
   if (rc != EMST_OK) return rc;
   if (n < 2) return EMST_ERR_INVALID_ARG;
+  if (leaf < 1 || leaf > 16 || (leaf & (leaf - 1)) != 0 || (n + leaf - 1) / leaf < 2)
+    return EMST_ERR_INVALID_ARG;
+  S.P.leaf = leaf;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return EMST_ERR_CUDA;
   cudaMemPool_t pool;
@@ -447,15 +465,15 @@ int emst_compute_batched(const float *points, const int64_t *offsets, int num_in
   return EMST_OK;
 }
 
-int emst_build_bvh(const float *points, int64_t n, int dim, uint64_t *out_codes, uint32_t *out_perm,
-                   uint32_t *out_children, float *out_boxes, void *stream) {
+int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint64_t *out_codes,
+                   uint32_t *out_perm, uint32_t *out_children, float *out_boxes, void *stream) {
   Session S;
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = open_session(S, points, n, dim, s);
+  int rc = open_session(S, points, n, dim, leaf_size, s);
   if (rc != EMST_OK) return rc;
   Problem &P = S.P;
   run_build(P, true);
-  const int64_t m = n - 1;
+  const int64_t m = P.nc - 1;
   if (out_codes) cudaMemcpyAsync(out_codes, P.keys[0], 8 * (size_t)n, cudaMemcpyDeviceToDevice, s);
   if (out_perm) cudaMemcpyAsync(out_perm, P.perm, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
   if (out_children)
@@ -466,14 +484,15 @@ int emst_build_bvh(const float *points, int64_t n, int dim, uint64_t *out_codes,
   return finish_session(S);
 }
 
-int emst_round_step(const float *points, int64_t n, int dim, const uint32_t *labels_in,
-                    const float *radius_in, uint32_t *out_node_labels, float *out_upper_bound,
-                    float *out_nn_w, uint32_t *out_nn_j, uint32_t *out_labels, emst_edge *out_edges,
-                    int64_t *out_num_edges, void *stream) {
+int emst_round_step(const float *points, int64_t n, int dim, int leaf_size,
+                    const uint32_t *labels_in, const float *radius_in, uint32_t *out_node_labels,
+                    float *out_upper_bound, float *out_nn_w, uint32_t *out_nn_j,
+                    uint32_t *out_labels, emst_edge *out_edges, int64_t *out_num_edges,
+                    void *stream) {
   if (!labels_in) return EMST_ERR_INVALID_ARG;
   Session S;
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = open_session(S, points, n, dim, s);
+  int rc = open_session(S, points, n, dim, leaf_size, s);
   if (rc != EMST_OK) return rc;
   Problem &P = S.P;
   run_build(P, false);
@@ -483,7 +502,7 @@ int emst_round_step(const float *points, int64_t n, int dim, const uint32_t *lab
   launch_node_labels(P);
   if (out_node_labels)
     cudaMemcpy2DAsync(out_node_labels, 8, reinterpret_cast<char *>(P.nodes) + 56, 64, 8,
-                      (size_t)(n - 1), cudaMemcpyDeviceToDevice, s);
+                      (size_t)(P.nc - 1), cudaMemcpyDeviceToDevice, s);
   launch_upper_bounds(P);
   if (out_upper_bound)
     k_bound_to_float<<<grid_for(n, 256), 256, 0, s>>>(P.bound, out_upper_bound, n);

@@ -77,12 +77,10 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_morton(const float *__restrict__ pts, int64_t n,
                                                    const uint32_t *__restrict__ box,
                                                    uint64_t *__restrict__ keys,
-                                                   uint32_t *__restrict__ vals,
-                                                   float *__restrict__ quant_out) {
+                                                   uint32_t *__restrict__ vals) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const Quantizer Q = make_quantizer(box, DIM);
-  if (k == 0) store_quantizer(Q, quant_out);  // reused by the queries of every round
   uint32_t q[3] = {0, 0, 0};
 #pragma unroll
   for (int d = 0; d < DIM; ++d) q[d] = quantize(Q, d, __ldg(pts + k * DIM + d));
@@ -93,11 +91,9 @@ __global__ void __launch_bounds__(kBlock) k_morton(const float *__restrict__ pts
 void launch_morton(Problem &P) {
   int g = grid_for(P.n, kBlock);
   if (P.dim == 3)
-    k_morton<3><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0],
-                                            reinterpret_cast<float *>(P.counters + 32));
+    k_morton<3><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0]);
   else
-    k_morton<2><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0],
-                                            reinterpret_cast<float *>(P.counters + 32));
+    k_morton<2><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0]);
   P.launches += 1;
 }
 
@@ -132,40 +128,41 @@ void launch_gather(Problem &P, const uint32_t *perm) {
 }
 
 // ---------------------------------------------------------------------------
-// A4 (b). Hierarchy: Karras's fully parallel binary radix tree over the sorted
-// codes.  Keys are augmented by their position so equal codes still split.
-// Internal node i covers a range with one end at i; its split gamma gives the
-// children gamma (left) and gamma+1 (right), leaves when the range ends there.
-// This is the numbering drawn in Fig. 4.
+// A4 (b). Hierarchy: Karras's fully parallel binary radix tree.  Its leaves are
+// chunks of `leaf` consecutive sorted points (leaf = 1: one point per leaf);
+// chunk c's key is the code of its first point, augmented by c so equal codes
+// still split.  Internal node i covers a chunk range with one end at i; its
+// split gamma gives the children gamma (left) and gamma+1 (right), leaves when
+// the range ends there.  This is the numbering drawn in Fig. 4.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k, int64_t n, int64_t i,
-                                            int64_t j) {
-  if (j < 0 || j >= n) return -1;
-  uint64_t a = __ldg(k + i), b = __ldg(k + j);
+__device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k, int64_t nc, int leaf,
+                                            int64_t i, int64_t j) {
+  if (j < 0 || j >= nc) return -1;
+  uint64_t a = __ldg(k + i * leaf), b = __ldg(k + j * leaf);
   if (a != b) return __clzll((long long)(a ^ b));
   return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
 }
 
-__global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict__ keys, int64_t n,
-                                                      NodeRec *__restrict__ nodes,
+__global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict__ keys, int64_t nc,
+                                                      int leaf, NodeRec *__restrict__ nodes,
                                                       uint32_t *__restrict__ parent_leaf,
                                                       uint2 *__restrict__ up_delta,
                                                       uint2 *__restrict__ range) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n - 1) return;
-  int d = (prefix_delta(keys, n, i, i + 1) - prefix_delta(keys, n, i, i - 1)) > 0 ? 1 : -1;
-  int dmin = prefix_delta(keys, n, i, i - d);
+  if (i >= nc - 1) return;
+  int d = (prefix_delta(keys, nc, leaf, i, i + 1) - prefix_delta(keys, nc, leaf, i, i - 1)) > 0 ? 1 : -1;
+  int dmin = prefix_delta(keys, nc, leaf, i, i - d);
   int64_t lmax = 2;
-  while (prefix_delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  while (prefix_delta(keys, nc, leaf, i, i + lmax * d) > dmin) lmax <<= 1;
   int64_t l = 0;
   for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-    if (prefix_delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    if (prefix_delta(keys, nc, leaf, i, i + (l + t) * d) > dmin) l += t;
   int64_t j = i + l * d;
-  int dnode = prefix_delta(keys, n, i, j);
+  int dnode = prefix_delta(keys, nc, leaf, i, j);
   int64_t s = 0, t = l;
   do {
     t = (t + 1) >> 1;
-    if (prefix_delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    if (prefix_delta(keys, nc, leaf, i, i + (s + t) * d) > dnode) s += t;
   } while (t > 1);
   int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
   int64_t lo = i < j ? i : j, hi = i < j ? j : i;
@@ -183,25 +180,24 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
 }
 
 void launch_hierarchy(Problem &P) {
-  k_hierarchy<<<grid_for(P.n - 1, kBlock), kBlock, 0, P.stream>>>(P.keys[0] /*sorted*/, P.n, P.nodes,
-                                                                   P.parent_leaf, P.up_delta,
-                                                                   P.range);
+  k_hierarchy<<<grid_for(P.nc - 1, kBlock), kBlock, 0, P.stream>>>(
+      P.keys[0] /*sorted*/, P.nc, P.leaf, P.nodes, P.parent_leaf, P.up_delta, P.range);
   P.launches += 1;
 }
 
 // ---------------------------------------------------------------------------
-// A4 (c). Refit: bottom-up boxes.  One thread per leaf writes its point as the
-// box of its slot in the parent record, then climbs: at every node the first
+// A4 (c). Refit: bottom-up boxes.  One thread per leaf chunk writes the box of
+// its points into its slot of the parent record, then climbs: at every node the first
 // arriver stops and the second merges the two child boxes and carries the
 // union one level up.  Wait-free.
-// A node whose leaf range lies inside this CTA's 256 leaves has both arrivals
+// A node whose leaf range lies inside this CTA's 256 chunks has both arrivals
 // from this CTA, so it is counted in shared memory with block-scope fences;
 // only nodes spanning CTAs use the global counters (about 2 per 256 leaves
 // per level above the CTA).  The global counters are never reset: each pass
 // adds exactly two arrivals per node, so the parity of the count before the
 // add tells first from second.
 // With init_labels, the round-0 child labels are written on the way
-// (leaf k: label k; internal: several components, kInvalid).
+// (a one-point chunk k: label k; otherwise several components, kInvalid).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, float lx, float ly, float lz,
                                                float hx, float hy, float hz) {
@@ -212,7 +208,7 @@ __device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, float lx,
 }
 
 __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
-                                                  NodeRec *nodes,
+                                                  int64_t nc, int leaf, NodeRec *nodes,
                                                   const uint32_t *__restrict__ parent_leaf,
                                                   const uint2 *__restrict__ up_delta,
                                                   const uint2 *__restrict__ range,
@@ -222,14 +218,22 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
   const int64_t last = first + kBlock - 1;
   s_arrive[threadIdx.x] = 0u;
   __syncthreads();
-  const int64_t k = first + threadIdx.x;
-  if (k >= n) return;
-  float4 p = pts[k];
+  const int64_t k = first + threadIdx.x;  // this thread's chunk
+  if (k >= nc) return;
+  const int64_t p0 = k * leaf, p1 = p0 + leaf < n ? p0 + leaf : n;
+  float4 p = pts[p0];
+  float bx0 = p.x, by0 = p.y, bz0 = p.z, bx1 = p.x, by1 = p.y, bz1 = p.z;
+  for (int64_t m = p0 + 1; m < p1; ++m) {
+    p = pts[m];
+    bx0 = fminf(bx0, p.x); by0 = fminf(by0, p.y); bz0 = fminf(bz0, p.z);
+    bx1 = fmaxf(bx1, p.x); by1 = fmaxf(by1, p.y); bz1 = fmaxf(bz1, p.z);
+  }
   uint32_t up = parent_leaf[k];
   uint32_t node = up >> 1;
   int slot = (int)(up & 1u);
-  store_slot_box(&nodes[node], slot, p.x, p.y, p.z, p.x, p.y, p.z);
-  if (init_labels) reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = (uint32_t)k;
+  store_slot_box(&nodes[node], slot, bx0, by0, bz0, bx1, by1, bz1);
+  if (init_labels)  // round 0: every point is its own component (label = its position)
+    reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = p1 - p0 == 1 ? (uint32_t)p0 : kInvalid;
   while (true) {
     const uint2 r = __ldg(range + node);
     const bool local = (int64_t)r.x >= first && (int64_t)r.y <= last;
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
 }
 
 void launch_refit(Problem &P, bool init_labels) {
-  k_refit<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.n, P.nodes, P.parent_leaf,
+  k_refit<<<grid_for(P.nc, kBlock), kBlock, 0, P.stream>>>(P.pts, P.n, P.nc, P.leaf, P.nodes, P.parent_leaf,
                                                           P.up_delta, P.range, P.arrivals,
                                                           init_labels ? 1 : 0);
   P.launches += 1;

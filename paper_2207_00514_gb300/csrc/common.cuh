@@ -114,28 +114,6 @@ __device__ __forceinline__ Quantizer make_quantizer(const uint32_t *box, int dim
   return Q;
 }
 
-// The quantiser as 7 floats (lo x,y,z, s x,y,z, 2^B) in device memory, written
-// once per call after the scene box (counters + 32).
-__device__ __forceinline__ void store_quantizer(const Quantizer &Q, float *out) {
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    out[d] = Q.lo[d];
-    out[3 + d] = Q.s[d];
-  }
-  out[6] = Q.twoB;
-}
-__device__ __forceinline__ Quantizer load_quantizer(const float *in, int dim) {
-  Quantizer Q;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    Q.lo[d] = __ldg(in + d);
-    Q.s[d] = __ldg(in + 3 + d);
-  }
-  Q.twoB = __ldg(in + 6);
-  Q.qmax = dim == 3 ? 0x1fffffu : 0xffffffffu;
-  return Q;
-}
-
 __device__ __forceinline__ uint32_t quantize(const Quantizer &Q, int d, float x) {
   float t = __fmul_rn(__fsub_rn(x, Q.lo[d]), Q.s[d]);
   return (t >= Q.twoB) ? Q.qmax : (t > 0.0f ? (uint32_t)t : 0u);
@@ -172,6 +150,8 @@ __device__ __forceinline__ uint64_t interleave(uint32_t qx, uint32_t qy, uint32_
 struct Problem {
   int64_t n = 0;
   int dim = 3;
+  int leaf = 1;      // points per leaf chunk of the hierarchy
+  int64_t nc = 0;    // leaf chunks: ceil(n / leaf)
   cudaStream_t stream = nullptr;
 
   const float *points = nullptr;  // n x dim, device
@@ -180,8 +160,8 @@ struct Problem {
   uint32_t *vals[2] = {nullptr, nullptr};
   uint32_t *perm = nullptr;       // curve index -> original index
   uint32_t *inv = nullptr;        // original index -> curve index
-  NodeRec *nodes = nullptr;       // n-1
-  uint32_t *parent_leaf = nullptr;   // n: (parent << 1) | slot
+  NodeRec *nodes = nullptr;       // nc-1 internal nodes
+  uint32_t *parent_leaf = nullptr;   // nc: (parent << 1) | slot of each leaf chunk
   uint2 *up_delta = nullptr;         // n-1: x = (parent << 1) | slot (root: kInvalid),
                                      //      y = leading bits shared by the node's (code,
                                      //      position) keys; y < 64 means the node holds
@@ -209,7 +189,7 @@ struct Problem {
   uint32_t *counters = nullptr;      // [0] edges emitted, [1] status bits, [2..3] node visits (u64),
                                      // [4..9] scene box (ordered), [16..23] sort tile counters,
                                      // [12] next round's active components,
-                                     // [24] scan tile counter, [32..38] quantiser (floats)
+                                     // [24] scan tile counter
   uint32_t *sort_hist = nullptr;     // 8 x 256
   uint32_t *sort_lookback = nullptr; // tiles x 256
   int64_t sort_tiles = 0;
@@ -239,7 +219,7 @@ void launch_node_labels(Problem &P);
 void advance_round(Problem &P, int64_t n_active);
 void launch_upper_bounds(Problem &P);
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded, bool climb = false);
+                     bool seeded);
 void launch_reduce(Problem &P);
 void launch_merge(Problem &P);
 void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
@@ -258,7 +238,10 @@ int check_args(const float *points, int64_t n, int dim);
 int bits_for(int64_t v);
 void run_build(Problem &P, bool init_labels);
 void reset_round_state(Problem &P);
-void run_round(Problem &P, int round, bool carried, int block, bool count, bool climb);
+void run_round(Problem &P, int round, bool carried, int block, bool count);
+// Leaf chunk size actually used for n points and a requested size (0 =
+// default): a power of two, at most the request, leaving at least 2 chunks.
+int effective_leaf(int64_t n, int requested);
 void run_output(Problem &P, emst_edge *out);
 
 inline int grid_for(int64_t n, int block) {

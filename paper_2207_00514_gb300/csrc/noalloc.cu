@@ -73,6 +73,7 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
   P.dim = dim;
   P.stream = stream;
   P.points = points;
+  P.leaf = effective_leaf(n, 0);
   if (layout(P, nullptr, !pts_dev, !out_dev) > kNoallocScratchBytes) return EMST_ERR_TOO_LARGE;
   layout(P, base, !pts_dev, !out_dev);
 
@@ -96,7 +97,7 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
     const int limit = bits_for(n - 1) + 1;
     for (int round = 0;; ++round) {
       if (round >= limit) return EMST_ERR_ROUND_LIMIT;
-      run_round(P, round, true, 0, false, false);
+      run_round(P, round, true, 0, false);
       if (!sync_counters()) return EMST_ERR_CUDA;
       if (host_counters[1] != 0) return status_from_bits(host_counters[1]);
       advance_round(P, (int64_t)host_counters[12]);

@@ -106,20 +106,26 @@ __global__ void __launch_bounds__(kScanThreads) k_label_runs(const uint32_t *__r
 __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restrict__ labels,
                                                         const uint32_t *__restrict__ runs,
                                                         const uint2 *__restrict__ range,
-                                                        int64_t n, NodeRec *__restrict__ nodes) {
+                                                        int64_t n, int64_t nc, int leaf,
+                                                        NodeRec *__restrict__ nodes) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n - 1) return;
+  if (i >= nc - 1) return;
   const uint2 ch = *reinterpret_cast<const uint2 *>(&nodes[i].d);
   uint32_t lab[2];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const uint32_t c = s == 0 ? ch.x : ch.y;
+    int64_t cf, cl;  // chunk range of the child
     if (c & kLeafBit) {
-      lab[s] = __ldg(labels + (c & ~kLeafBit));
+      cf = cl = c & ~kLeafBit;
     } else {
       const uint2 r = __ldg(range + c);
-      lab[s] = (__ldg(runs + r.y) == __ldg(runs + r.x)) ? __ldg(labels + r.x) : kInvalid;
+      cf = r.x;
+      cl = r.y;
     }
+    const int64_t a = cf * leaf;
+    const int64_t b = (cl + 1) * leaf < n ? (cl + 1) * leaf - 1 : n - 1;
+    lab[s] = (__ldg(runs + b) == __ldg(runs + a)) ? __ldg(labels + a) : kInvalid;
   }
   reinterpret_cast<uint2 *>(&nodes[i].d)[1] = make_uint2(lab[0], lab[1]);
 }
@@ -136,8 +142,8 @@ void launch_label_runs(Problem &P) {
 }
 
 void launch_node_labels(Problem &P) {
-  k_node_labels<<<grid_for(P.n - 1, kBlock), kBlock, 0, P.stream>>>(P.labels, P.runs, P.range,
-                                                                    P.n, P.nodes);
+  k_node_labels<<<grid_for(P.nc - 1, kBlock), kBlock, 0, P.stream>>>(
+      P.labels, P.runs, P.range, P.n, P.nc, P.leaf, P.nodes);
   P.launches += 1;
 }
 
@@ -172,32 +178,48 @@ struct Query {
   float radius;    // cutoff (inclusive)
   float best;      // best weight found
   uint32_t bj;     // its curve index (kInvalid: none yet)
-  uint32_t bid;    // its original index (kInvalid: not loaded yet)
+  uint32_t bid;    // its original index
 };
 
-// A leaf j at weight d <= radius: keep the smaller (w, original id).
-__device__ __forceinline__ void take_leaf(Query &q, const float4 *__restrict__ pts, uint32_t j,
-                                          float d) {
+// A candidate j at weight d <= radius: keep the smaller (w, original id).
+__device__ __forceinline__ void take_point(Query &q, uint32_t j, float d, uint32_t idj) {
   if (q.bj == kInvalid || d < q.best) {  // first candidate, or strictly closer
     q.best = d;
     q.bj = j;
-    q.bid = kInvalid;
+    q.bid = idj;
     q.radius = d;
-  } else if (d == q.best) {
-    const uint32_t idj = __float_as_uint(pts[j].w);
-    if (q.bid == kInvalid) q.bid = __float_as_uint(pts[q.bj].w);
-    if (idj < q.bid) { q.bj = j; q.bid = idj; }
+  } else if (d == q.best && idj < q.bid) {
+    q.bj = j;
+    q.bid = idj;
+  }
+}
+
+// A leaf of the hierarchy is a chunk of `leaf` consecutive curve positions
+// (the last one may be shorter); scan it point by point.
+__device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, int leaf, int64_t n,
+                                           const float4 *__restrict__ pts,
+                                           const uint32_t *__restrict__ labels) {
+  const int64_t lo = (int64_t)c * leaf;
+  const int64_t hi = lo + leaf < n ? lo + leaf : n;
+  for (int64_t k = lo; k < hi; ++k) {
+    if (__ldg(labels + k) == q.me) continue;
+    const float4 t = __ldg(pts + k);
+    const float d = sq_dist(q.px, q.py, q.pz, t.x, t.y, t.z);
+    if (d <= q.radius) take_point(q, (uint32_t)k, d, __float_as_uint(t.w));
   }
 }
 
 // Depth-first search of the subtree of internal node `node`, whose own box
 // the caller has already accepted: test both children of every visited
-// record, take leaves, descend into the nearer accepted internal child and
-// stack the farther one with its box distance (re-tested when popped).
+// record, scan accepted leaf chunks, descend into the nearer accepted
+// internal child and stack the farther one with its box distance (re-tested
+// when popped).
 template <bool COUNT>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
-                                        const float4 *__restrict__ pts, uint32_t *st_node,
-                                        float *st_dist, unsigned long long &nvis) {
+                                        const float4 *__restrict__ pts,
+                                        const uint32_t *__restrict__ labels, int leaf, int64_t n,
+                                        uint32_t *st_node, float *st_dist,
+                                        unsigned long long &nvis) {
   int sp = 0;
   while (true) {
     if (COUNT) ++nvis;
@@ -208,9 +230,9 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
     const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
     bool okL = (dd.z != q.me) && (dL <= q.radius);
     bool okR = (dd.w != q.me) && (dR <= q.radius);
-    if (okL && (dd.x & kLeafBit)) { take_leaf(q, pts, dd.x & ~kLeafBit, dL); okL = false; }
+    if (okL && (dd.x & kLeafBit)) { scan_chunk(q, dd.x & ~kLeafBit, leaf, n, pts, labels); okL = false; }
     if (okR && (dd.y & kLeafBit)) {
-      if (dR <= q.radius) take_leaf(q, pts, dd.y & ~kLeafBit, dR);
+      if (dR <= q.radius) scan_chunk(q, dd.y & ~kLeafBit, leaf, n, pts, labels);
       okR = false;
     }
     okL = okL && dL <= q.radius;
@@ -233,45 +255,6 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
   }
 }
 
-// Quantised box that holds every point within the cutoff of the query.  If
-// the FP32 weight w(p, y) <= r then, per dimension, |p - y| <= sqrt(r)
-// (1 - 2^-24)^(-5/2) < sqrt(r) (1 + 2^-21): each of the five roundings on the
-// way (difference, square, two fma) shrinks the exact value by at most a
-// factor (1 - 2^-24).  R rounds up, the box edges round outwards and the
-// quantiser is monotone, so every such y quantises inside [lo, hi].
-__device__ __forceinline__ void ball_box(const Quantizer &Q, int dim, const Query &q,
-                                         uint32_t *lo, uint32_t *hi) {
-  const float R = __fmul_ru(__fsqrt_ru(q.radius), 1.00000047683715820312f);
-  const float pc[3] = {q.px, q.py, q.pz};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    lo[d] = d < dim ? quantize(Q, d, __fsub_rd(pc[d], R)) : 0u;
-    hi[d] = d < dim ? quantize(Q, d, __fadd_ru(pc[d], R)) : 0u;
-  }
-}
-
-// Is the quantised box [lo, hi] inside the Morton cell of the query's
-// ancestor whose keys share their first `dl` bits (dl < 64)?  A prefix of dl
-// code bits fixes the top (dl+1)/3, dl/3, (dl-1)/3 bits of x, y, z in 3D (bit
-// 63 is unused) and the top (dl+1)/2, dl/2 bits of x, y in 2D; the cell is the
-// aligned box of coordinates sharing those bits with the query's own.
-__device__ __forceinline__ bool box_in_cell(int dim, uint32_t dl, const uint32_t *qp,
-                                            const uint32_t *lo, const uint32_t *hi) {
-  const int B = dim == 3 ? 21 : 32;
-  const int nb[3] = {dim == 3 ? (int)(dl + 1) / 3 : (int)(dl + 1) / 2,
-                     dim == 3 ? (int)dl / 3 : (int)dl / 2,
-                     dim == 3 ? ((int)dl - 1) / 3 : 0};
-  bool in = true;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    if (d < dim) {
-      const int sh = B - nb[d];
-      in = in && ((((uint64_t)(lo[d] ^ qp[d])) >> sh) == 0) && ((((uint64_t)(hi[d] ^ qp[d])) >> sh) == 0);
-    }
-  }
-  return in;
-}
-
 // ---------------------------------------------------------------------------
 // A7. Nearest other-component neighbour of every point (Algorithm 2), one
 // thread per point in curve order (neighbouring threads get nearby queries).
@@ -283,14 +266,10 @@ __device__ __forceinline__ bool box_in_cell(int dim, uint32_t dl, const uint32_t
 //    (Optimization 1) and its box is within the cutoff (inclusive: equal
 //    weights with smaller ids must survive); a leaf updates the best
 //    (w, original id) and shrinks the cutoff to w.
-// Where the search starts (CLIMB): the paper's search starts at the root.  A
-// node whose two end codes differ holds exactly the points of one aligned
-// Morton cell, so with CLIMB the query first climbs parent pointers from its
-// leaf to the lowest ancestor whose cell contains the quantised box around its
-// cutoff ball (ball_box, box_in_cell) and searches only that subtree: every
-// point within the cutoff is in it.
+// The leaves of the hierarchy are chunks of `leaf` consecutive curve
+// positions; an accepted chunk is scanned point by point.
 // The stack never overflows: every split of the hierarchy uses a strictly
-// later bit of the 96-bit augmented key (64-bit code + 32-bit position), so a
+// later bit of the 96-bit augmented key (64-bit code + 32-bit index), so a
 // root-to-leaf path has at most 96 internal nodes and at most one stacked
 // sibling per level.
 // Ends with the first half of the per-component minimum (A8): an atomicMin of
@@ -306,14 +285,11 @@ __device__ __forceinline__ bool box_in_cell(int dim, uint32_t dl, const uint32_t
 // Unseeded, each point reports exactly its nearest other-component point
 // within its cutoff (what the inspection entry point exposes).
 // ---------------------------------------------------------------------------
-template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CLIMB>
+template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED>
 __global__ void __launch_bounds__(kBlock) k_traverse(
     const float4 *__restrict__ pts, const NodeRec *__restrict__ nodes,
     const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound,
-    const float *__restrict__ radius_in, const uint64_t *__restrict__ codes,
-    const uint32_t *__restrict__ parent_leaf, const uint2 *__restrict__ up_delta,
-    const float *__restrict__ quant, int dim,
-    uint2 *__restrict__ res, uint32_t *__restrict__ res_id, uint64_t *__restrict__ comp_key,
+    const float *__restrict__ radius_in, int leaf, uint2 *__restrict__ res, uint32_t *__restrict__ res_id, uint64_t *__restrict__ comp_key,
     int64_t n, uint32_t *status, unsigned long long *visits) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -361,7 +337,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
       const float4 c = __ldg(pts + j);
       const float d = sq_dist(q.px, q.py, q.pz, c.x, c.y, c.z);
       const uint32_t idj = __float_as_uint(c.w);
-      if (d < q.best || (d == q.best && idj < q.bid)) { q.best = d; q.bj = (uint32_t)j; q.bid = idj; }
+      if (q.bj == kInvalid || d < q.best || (d == q.best && idj < q.bid)) { q.best = d; q.bj = (uint32_t)j; q.bid = idj; }
     }
     q.radius = fminf(q.radius, q.best);
   }
@@ -371,28 +347,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   unsigned long long nvis = 0;
   bool ok = true;
 
-  uint32_t start = 0u;  // the search starts at the root ...
-  if (CLIMB && q.radius < __int_as_float(0x7f800000)) {
-    // ... or, with CLIMB, at the lowest ancestor of the query's leaf whose
-    // Morton cell contains the quantised box around the cutoff ball: every
-    // point within the cutoff lies in that ancestor's subtree.  The climb only
-    // follows parent pointers (one 8-byte load per level); the search below is
-    // the same depth-first loop for every lane.
-    const Quantizer Q = load_quantizer(quant, dim);
-    uint32_t qp[3] = {0, 0, 0}, blo[3], bhi[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      if (d < dim) qp[d] = quantize(Q, d, d == 0 ? q.px : (d == 1 ? q.py : q.pz));
-    ball_box(Q, dim, q, blo, bhi);
-    uint32_t x = __ldg(parent_leaf + i) >> 1;
-    while (true) {
-      const uint2 ud = __ldg(up_delta + x);
-      if (x == 0 || (ud.y < 64 && box_in_cell(dim, ud.y, qp, blo, bhi))) break;
-      x = ud.x >> 1;
-    }
-    start = x;
-  }
-  ok = explore<COUNT>(q, start, nodes, pts, st_node, st_dist, nvis);
+  ok = explore<COUNT>(q, 0u, nodes, pts, labels, leaf, n, st_node, st_dist, nvis);
   if (!ok) atomicOr(status, kErrStack);
   if (COUNT) {
     // one atomic per warp: sum the active lanes' counts first
@@ -413,7 +368,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   }
   if (q.bj != kInvalid) {
     const uint32_t oi = __float_as_uint(p.w);
-    const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(pts[q.bj].w);
+    const uint32_t oj = q.bid;
     res_id[i] = oj;
     const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
     atomicMin(reinterpret_cast<unsigned long long *>(comp_key + q.me), (unsigned long long)key);
@@ -423,26 +378,22 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
 }
 
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded, bool climb) {
+                     bool seeded) {
   if (block <= 0) block = kBlock;
   int g = grid_for(P.n, block);
   auto *vis = reinterpret_cast<unsigned long long *>(P.counters + 2);
   cudaStream_t s = P.stream;
-#define EMST_TRAV(C, R, K, S, L)                                                              \
-  k_traverse<C, R, K, S, L><<<g, block, 0, s>>>(                                               \
-      P.pts, P.nodes, P.labels, P.bound, radius_in, P.keys[0], P.parent_leaf, P.up_delta,      \
-      reinterpret_cast<const float *>(P.counters + 32), P.dim, P.res, P.res_id,                 \
-      P.comp_key, P.n, P.counters + 1, vis)
+#define EMST_TRAV(C, R, K, S)                                                                   \
+  k_traverse<C, R, K, S><<<g, block, 0, s>>>(P.pts, P.nodes, P.labels, P.bound, radius_in, P.leaf, \
+                                             P.res, P.res_id, P.comp_key, P.n, P.counters + 1, vis)
   if (radius_in) {
-    EMST_TRAV(false, true, false, false, false);
+    EMST_TRAV(false, true, false, false);
   } else if (!seeded) {
-    EMST_TRAV(false, false, false, false, false);
-  } else if (climb) {
-    if (carried) EMST_TRAV(true, false, false, true, true); else EMST_TRAV(false, false, false, true, true);
+    EMST_TRAV(false, false, false, false);
   } else if (carried) {
-    if (count) EMST_TRAV(true, false, true, true, false); else EMST_TRAV(true, false, false, true, false);
+    if (count) EMST_TRAV(true, false, true, true); else EMST_TRAV(true, false, false, true);
   } else {
-    if (count) EMST_TRAV(false, false, true, true, false); else EMST_TRAV(false, false, false, true, false);
+    if (count) EMST_TRAV(false, false, true, true); else EMST_TRAV(false, false, false, true);
   }
 #undef EMST_TRAV
   P.launches += 1;

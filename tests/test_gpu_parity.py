@@ -66,32 +66,54 @@ BUILD_CASES = [
 ]
 
 
+def chunk_ranges(refs, n, nc, leaf, first, last):
+    """Point ranges [a, b] of children given as refs (internal id, or leaf
+    chunk c as nc-1+c) of the oracle's tree over chunk keys."""
+    is_leaf = refs >= nc - 1
+    c = np.clip(refs - (nc - 1), 0, nc - 1)
+    v = np.clip(refs, 0, max(nc - 2, 0))
+    cf = np.where(is_leaf, c, first[v])
+    cl = np.where(is_leaf, c, last[v])
+    return cf * leaf, np.minimum((cl + 1) * leaf, n) - 1
+
+
+@pytest.mark.parametrize("leaf", [1, 4])
 @pytest.mark.parametrize("name,make", BUILD_CASES, ids=[c[0] for c in BUILD_CASES])
-def test_bvh_matches_oracle(pkg, name, make):
+def test_bvh_matches_oracle(pkg, name, make, leaf):
     pts = make()
     n = len(pts)
+    if (n + leaf - 1) // leaf < 2:
+        pytest.skip("fewer than two leaf chunks")
     ref = oracle.bvh_reference(pts)
-    out = pkg.emst_build_bvh(dev_pts(pts))
+    out = pkg.emst_build_bvh(dev_pts(pts), leaf_size=leaf)
     torch.cuda.synchronize()
     codes = out["codes"].cpu().numpy().view(np.uint64)
     perm = u32(out["perm"])
     assert np.array_equal(codes, ref["sorted_codes"])
     assert np.array_equal(perm, ref["perm"])
+    # the hierarchy is the radix tree over the chunks' first codes
+    nc = (n + leaf - 1) // leaf
+    left, right, first, last = oracle.radix_tree(ref["sorted_codes"][::leaf])
     ch = u32(out["children"]).astype(np.int64)
-    conv = np.where(ch & 0x80000000, (n - 1) + (ch & 0x7FFFFFFF), ch)
-    assert np.array_equal(conv[:, 0], ref["left"])
-    assert np.array_equal(conv[:, 1], ref["right"])
+    conv = np.where(ch & 0x80000000, (nc - 1) + (ch & 0x7FFFFFFF), ch)
+    assert np.array_equal(conv[:, 0], left)
+    assert np.array_equal(conv[:, 1], right)
     boxes = out["boxes"].cpu().numpy()
     sp = ref["sorted_points"]
     d = pts.shape[1]
-    for side, refs in ((0, ref["left"]), (1, ref["right"])):
-        leaf = refs >= n - 1
-        lo = np.where(leaf[:, None], sp[np.clip(refs - (n - 1), 0, n - 1)], ref["box_lo"][np.clip(refs, 0, n - 2)])
-        hi = np.where(leaf[:, None], sp[np.clip(refs - (n - 1), 0, n - 1)], ref["box_hi"][np.clip(refs, 0, n - 2)])
+    for side, refs in ((0, left), (1, right)):
+        a, b = chunk_ranges(refs, n, nc, leaf, first, last)
+        lo = np.stack([sp[x:y + 1].min(0) for x, y in zip(a, b)])
+        hi = np.stack([sp[x:y + 1].max(0) for x, y in zip(a, b)])
         assert np.array_equal(boxes[:, side, 0:d], lo)
         assert np.array_equal(boxes[:, side, 3:3 + d], hi)
         if d == 2:
             assert np.all(boxes[:, side, 2] == 0) and np.all(boxes[:, side, 5] == 0)
+    if leaf == 1:  # one point per leaf: the oracle's own node boxes
+        for side, refs in ((0, left), (1, right)):
+            inner = refs < n - 1
+            assert np.array_equal(boxes[inner, side, 0:d], ref["box_lo"][refs[inner]])
+            assert np.array_equal(boxes[inner, side, 3:3 + d], ref["box_hi"][refs[inner]])
 
 
 # ---------------------------------------------------------------------------
@@ -118,9 +140,10 @@ ROUND_CASES = [
 ]
 
 
+@pytest.mark.parametrize("leaf", [1, 4])
 @pytest.mark.parametrize("name,n,dim,groups", ROUND_CASES, ids=[c[0] for c in ROUND_CASES])
 @pytest.mark.parametrize("given_radius", [False, True])
-def test_round_step_matches_oracle(pkg, name, n, dim, groups, given_radius):
+def test_round_step_matches_oracle(pkg, name, n, dim, groups, given_radius, leaf):
     g = np.random.default_rng(n + dim)
     pts = synth.blobs(n, dim, n, n_blobs=6)
     ref = oracle.bvh_reference(pts)
@@ -131,13 +154,24 @@ def test_round_step_matches_oracle(pkg, name, n, dim, groups, given_radius):
         radius = np.where(g.random(n) < 0.5, np.float32(np.inf),
                           np.float32(g.random(n) * 0.002)).astype(np.float32)
     out = pkg.emst_round_step(dev_pts(pts), torch.from_numpy(labels.view(np.int32)),
-                              None if radius is None else torch.from_numpy(radius))
+                              None if radius is None else torch.from_numpy(radius), leaf_size=leaf)
     torch.cuda.synchronize()
-    # A5 node labels (per child of each internal node)
-    node_lab = oracle.node_labels(labels, ref["first"], ref["last"])
-    for side, refs in ((0, ref["left"]), (1, ref["right"])):
-        want = np.where(refs >= n - 1, labels[np.clip(refs - (n - 1), 0, n - 1)], node_lab[np.clip(refs, 0, n - 2)])
-        assert np.array_equal(u32(out["node_labels"])[:, side], want.astype(np.uint32))
+    # A5 node labels (per child of each internal node): the label shared by
+    # every point of the child's range, else invalid
+    if leaf == 1:
+        node_lab = oracle.node_labels(labels, ref["first"], ref["last"])
+        for side, refs in ((0, ref["left"]), (1, ref["right"])):
+            want = np.where(refs >= n - 1, labels[np.clip(refs - (n - 1), 0, n - 1)],
+                            node_lab[np.clip(refs, 0, n - 2)])
+            assert np.array_equal(u32(out["node_labels"])[:, side], want.astype(np.uint32))
+    else:
+        nc = (n + leaf - 1) // leaf
+        left, right, first, last = oracle.radix_tree(ref["sorted_codes"][::leaf])
+        for side, refs in ((0, left), (1, right)):
+            a, b = chunk_ranges(refs, n, nc, leaf, first, last)
+            want = np.array([labels[x] if np.all(labels[x:y + 1] == labels[x]) else INVALID
+                             for x, y in zip(a, b)], dtype=np.uint32)
+            assert np.array_equal(u32(out["node_labels"])[:, side], want)
     # A6 upper bounds
     ub = oracle.upper_bounds(sp, labels)
     assert np.array_equal(out["upper_bound"].cpu().numpy().view(np.uint32), ub.view(np.uint32))
@@ -210,8 +244,9 @@ def test_repeatable_and_stats(pkg):
     assert st["node_visits"] > 0 and st["kernel_launches"] > 0
     c, _ = pkg.emst_compute_ex(t, carried_radius=False, block_size=128)
     assert_same_edges(pkg.edges_numpy(c), pkg.edges_numpy(b), "options")
-    d, _ = pkg.emst_compute_ex(t, climb=True)
-    assert_same_edges(pkg.edges_numpy(d), pkg.edges_numpy(b), "climbing search order")
+    for leaf in (1, 2, 8, 16):
+        d, _ = pkg.emst_compute_ex(t, leaf_size=leaf)
+        assert_same_edges(pkg.edges_numpy(d), pkg.edges_numpy(b), f"leaf size {leaf}")
 
 
 def test_degenerate_sizes_and_errors(pkg):
