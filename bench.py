@@ -273,7 +273,7 @@ def main():
     visits_per_query_round = vis["node_visits"] / float(n * max(vis["rounds"], 1))
     # other leaf chunk sizes, untimed, for comparison
     leaf_sweep = {}
-    for leaf in (1, 2, 8):
+    for leaf in (2, 4, 8):
         lv = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, leaf_size=leaf)[1]
         torch.cuda.synchronize(dev)
         leaf_sweep[str(leaf)] = {"total_ms": round(lv["total_ms"], 3), "traverse_ms": round(lv["traverse_ms"], 3)}
@@ -321,7 +321,7 @@ def main():
                        "round_traverse_ms": [round(x, 3) for x in (round_trav or [])],
                        "components_per_round": comps,
                        "node_visits_per_query_per_round": round(visits_per_query_round, 2),
-                       "leaf_size": 4,
+                       "leaf_size": 1,
                        "other_leaf_sizes_untimed": leaf_sweep,
                        "mfeatures_per_s": value * 3},
             "roofline": roofline,

@@ -73,8 +73,11 @@ typedef struct emst_options {
   int32_t use_graph;          /* 1 = run the round loop as a CUDA graph with a device-side
                                  loop condition; 0 = host loop (one sync per round) */
   int32_t count_visits;       /* 1 = count node visits per round into emst_stats */
-  int32_t leaf_size;          /* points per leaf chunk of the hierarchy: 0 = default (4), else
-                                 1, 2, 4, 8 or 16 (halved while fewer than 2 chunks remain) */
+  int32_t leaf_size;          /* points per leaf chunk of the hierarchy: 0 = default (1, one
+                                 point per leaf as in the paper), else 1, 2, 4, 8 or 16 (halved
+                                 while fewer than 2 chunks remain).  Chunks are runs of
+                                 consecutive curve positions; on clustered data they straddle
+                                 the curve's jumps and search more, so 1 is the fastest there */
   int32_t reserved[10];
 } emst_options;
 

@@ -69,7 +69,7 @@ struct Carver {
 
 // Lays the scratch of one problem out from `base` (nullptr: only measures).
 int effective_leaf(int64_t n, int requested) {
-  int k = requested > 0 ? requested : 4;
+  int k = requested > 0 ? requested : 1;
   if (k > 16) k = 16;
   int p = 1;
   while (p * 2 <= k) p *= 2;

@@ -195,10 +195,27 @@ __device__ __forceinline__ void take_point(Query &q, uint32_t j, float d, uint32
 }
 
 // A leaf of the hierarchy is a chunk of `leaf` consecutive curve positions
-// (the last one may be shorter); scan it point by point.
-__device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, int leaf, int64_t n,
+// (the last one may be shorter).  A one-point leaf's box IS the point, so its
+// box distance d is already the exact weight and its label was tested with
+// the box; its original id is loaded only to break an exact tie.  A longer
+// chunk is scanned point by point.
+__device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, float d1, int leaf, int64_t n,
                                            const float4 *__restrict__ pts,
                                            const uint32_t *__restrict__ labels) {
+  if (leaf == 1) {
+    if (q.bj == kInvalid || d1 < q.best) {
+      q.best = d1;
+      q.bj = c;
+      q.bid = kInvalid;  // loaded lazily
+      q.radius = d1;
+    } else if (d1 == q.best) {
+      const uint32_t idj = __float_as_uint(pts[c].w);
+      if (q.bid == kInvalid) q.bid = __float_as_uint(pts[q.bj].w);
+      if (idj < q.bid) { q.bj = c; q.bid = idj; }
+    }
+    return;
+  }
+  if (q.bid == kInvalid && q.bj != kInvalid) q.bid = __float_as_uint(pts[q.bj].w);
   const int64_t lo = (int64_t)c * leaf;
   const int64_t hi = lo + leaf < n ? lo + leaf : n;
   for (int64_t k = lo; k < hi; ++k) {
@@ -230,9 +247,9 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
     const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
     bool okL = (dd.z != q.me) && (dL <= q.radius);
     bool okR = (dd.w != q.me) && (dR <= q.radius);
-    if (okL && (dd.x & kLeafBit)) { scan_chunk(q, dd.x & ~kLeafBit, leaf, n, pts, labels); okL = false; }
+    if (okL && (dd.x & kLeafBit)) { scan_chunk(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels); okL = false; }
     if (okR && (dd.y & kLeafBit)) {
-      if (dR <= q.radius) scan_chunk(q, dd.y & ~kLeafBit, leaf, n, pts, labels);
+      if (dR <= q.radius) scan_chunk(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels);
       okR = false;
     }
     okL = okL && dL <= q.radius;
@@ -368,7 +385,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   }
   if (q.bj != kInvalid) {
     const uint32_t oi = __float_as_uint(p.w);
-    const uint32_t oj = q.bid;
+    const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(pts[q.bj].w);
     res_id[i] = oj;
     const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
     atomicMin(reinterpret_cast<unsigned long long *>(comp_key + q.me), (unsigned long long)key);
