@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
                                                       int leaf, NodeRec *__restrict__ nodes,
                                                       uint32_t *__restrict__ parent_leaf,
                                                       uint2 *__restrict__ up_delta,
-                                                      uint2 *__restrict__ range) {
+                                                      uint4 *__restrict__ range) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc - 1) return;
   int d = (prefix_delta(keys, nc, leaf, i, i + 1) - prefix_delta(keys, nc, leaf, i, i - 1)) > 0 ? 1 : -1;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
   uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
   uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
   reinterpret_cast<uint2 *>(&nodes[i].d)[0] = make_uint2(left, right);
-  range[i] = make_uint2((uint32_t)lo, (uint32_t)hi);
+  range[i] = make_uint4((uint32_t)lo, (uint32_t)gamma, (uint32_t)hi, 0u);
   reinterpret_cast<uint32_t *>(up_delta + i)[1] = (uint32_t)dnode;
   uint32_t up = (uint32_t)i << 1;
   if (left & kLeafBit) parent_leaf[left & ~kLeafBit] = up;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
                                                   int64_t nc, int leaf, NodeRec *nodes,
                                                   const uint32_t *__restrict__ parent_leaf,
                                                   const uint2 *__restrict__ up_delta,
-                                                  const uint2 *__restrict__ range,
+                                                  const uint4 *__restrict__ range,
                                                   uint32_t *arrivals, int init_labels) {
   __shared__ uint32_t s_arrive[kBlock];
   const int64_t first = (int64_t)blockIdx.x * kBlock;
@@ -235,8 +235,8 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
   if (init_labels)  // round 0: every point is its own component (label = its position)
     reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = p1 - p0 == 1 ? (uint32_t)p0 : kInvalid;
   while (true) {
-    const uint2 r = __ldg(range + node);
-    const bool local = (int64_t)r.x >= first && (int64_t)r.y <= last;
+    const uint4 r = __ldg(range + node);
+    const bool local = (int64_t)r.x >= first && (int64_t)r.z <= last;
     float4 a, b, c;
     if (local) {
       __threadfence_block();

@@ -167,7 +167,8 @@ struct Problem {
                                      //      position) keys; y < 64 means the node holds
                                      //      exactly the points of one Morton cell
   uint32_t *arrivals = nullptr;      // n-1 arrival counters (parity = who is second)
-  uint2 *range = nullptr;            // n-1: leaf range [first, last] of each internal node
+  uint4 *range = nullptr;            // nc-1: (first, split, last, 0) of each internal node: its
+                                     //      leaf-chunk range and the last chunk of its left child
   uint32_t *runs = nullptr;          // n: label boundaries before each curve position
   uint32_t *labels = nullptr;        // n, current round (= labels_buf[cur])
   uint32_t *bound = nullptr;         // n, FP32 bits of the component upper bound (= bound_buf[cur])

@@ -105,29 +105,21 @@ __global__ void __launch_bounds__(kScanThreads) k_label_runs(const uint32_t *__r
 
 __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restrict__ labels,
                                                         const uint32_t *__restrict__ runs,
-                                                        const uint2 *__restrict__ range,
+                                                        const uint4 *__restrict__ range,
                                                         int64_t n, int64_t nc, int leaf,
                                                         NodeRec *__restrict__ nodes) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc - 1) return;
-  const uint2 ch = *reinterpret_cast<const uint2 *>(&nodes[i].d);
-  uint32_t lab[2];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const uint32_t c = s == 0 ? ch.x : ch.y;
-    int64_t cf, cl;  // chunk range of the child
-    if (c & kLeafBit) {
-      cf = cl = c & ~kLeafBit;
-    } else {
-      const uint2 r = __ldg(range + c);
-      cf = r.x;
-      cl = r.y;
-    }
-    const int64_t a = cf * leaf;
-    const int64_t b = (cl + 1) * leaf < n ? (cl + 1) * leaf - 1 : n - 1;
-    lab[s] = (__ldg(runs + b) == __ldg(runs + a)) ? __ldg(labels + a) : kInvalid;
-  }
-  reinterpret_cast<uint2 *>(&nodes[i].d)[1] = make_uint2(lab[0], lab[1]);
+  // the children split the node's chunk range [first, last] after `split`
+  const uint4 r = __ldg(range + i);
+  const int64_t a0 = (int64_t)r.x * leaf;
+  const int64_t b0 = ((int64_t)r.y + 1) * leaf - 1;
+  const int64_t a1 = b0 + 1;
+  const int64_t b1 = ((int64_t)r.z + 1) * leaf < n ? ((int64_t)r.z + 1) * leaf - 1 : n - 1;
+  const uint32_t l0 = __ldg(labels + a0), l1 = __ldg(labels + a1);
+  const uint32_t lab0 = (__ldg(runs + b0) == __ldg(runs + a0)) ? l0 : kInvalid;
+  const uint32_t lab1 = (__ldg(runs + b1) == __ldg(runs + a1)) ? l1 : kInvalid;
+  reinterpret_cast<uint2 *>(&nodes[i].d)[1] = make_uint2(lab0, lab1);
 }
 
 void launch_label_runs(Problem &P) {
@@ -529,7 +521,10 @@ __global__ void __launch_bounds__(kBlock) k_merge_roots(const uint32_t *__restri
 // Relabel + next round's bounds + label-boundary scan, one tile of positions
 // per CTA, decoupled look-back for the scan.  New labels go to a second
 // buffer (neighbouring tiles still read the old ones).
-__global__ void __launch_bounds__(kScanThreads) k_relabel_runs(
+constexpr int kRelabelItems = 8;
+constexpr int kRelabelTile = kScanThreads * kRelabelItems;
+
+__global__ void __launch_bounds__(kScanThreads, 6) k_relabel_runs(
     const uint32_t *__restrict__ labels_old, const uint32_t *__restrict__ root,
     const float4 *__restrict__ pts, int64_t n, uint32_t *__restrict__ labels_new,
     uint32_t *__restrict__ bound_next, uint32_t *__restrict__ runs, uint32_t *lookback,
@@ -541,16 +536,16 @@ __global__ void __launch_bounds__(kScanThreads) k_relabel_runs(
   if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const int64_t first = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
-  uint32_t lab[kScanItems + 1];
+  const int64_t first = (int64_t)tile * kRelabelTile + (int64_t)tid * kRelabelItems;
+  uint32_t lab[kRelabelItems + 1];
 #pragma unroll
-  for (int q = 0; q <= kScanItems; ++q) {
+  for (int q = 0; q <= kRelabelItems; ++q) {
     int64_t k = first + q;
     lab[q] = k < n ? __ldg(root + __ldg(labels_old + k)) : kInvalid;
   }
   uint32_t flags = 0;
 #pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
+  for (int q = 0; q < kRelabelItems; ++q) {
     int64_t k = first + q;
     if (k < n) labels_new[k] = lab[q];
     if (k + 1 < n && lab[q] != lab[q + 1]) {
@@ -603,7 +598,7 @@ __global__ void __launch_bounds__(kScanThreads) k_relabel_runs(
   __syncthreads();
   uint32_t run = s_prefix + s_warp[warp] + x - mine;
 #pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
+  for (int q = 0; q < kRelabelItems; ++q) {
     int64_t k = first + q;
     if (k < n) runs[k] = run;
     run += (flags >> q) & 1u;
@@ -618,7 +613,7 @@ void launch_merge(Problem &P) {
                                               P.labels, P.target, P.counters + 1);
   k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.active_list, count, P.comp_key, P.comp_max, P.target,
                                             P.root, P.edges, P.next_list, P.counters, P.n);
-  const int64_t tiles = (P.n + kScanTile - 1) / kScanTile;
+  const int64_t tiles = (P.n + kRelabelTile - 1) / kRelabelTile;
   uint32_t *ctr = P.counters + 24;
   cudaMemsetAsync(ctr, 0, sizeof(uint32_t), P.stream);
   cudaMemsetAsync(P.sort_lookback, 0, sizeof(uint32_t) * (size_t)tiles, P.stream);
