@@ -191,10 +191,11 @@ __device__ __forceinline__ void take_point(Query &q, uint32_t j, float d, uint32
 // box distance d is already the exact weight and its label was tested with
 // the box; its original id is loaded only to break an exact tie.  A longer
 // chunk is scanned point by point.
+template <bool CHUNKS>
 __device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, float d1, int leaf, int64_t n,
                                            const float4 *__restrict__ pts,
                                            const uint32_t *__restrict__ labels) {
-  if (leaf == 1) {
+  if (!CHUNKS) {
     if (q.bj == kInvalid || d1 < q.best) {
       q.best = d1;
       q.bj = c;
@@ -223,7 +224,7 @@ __device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, float d1, int l
 // record, scan accepted leaf chunks, descend into the nearer accepted
 // internal child and stack the farther one with its box distance (re-tested
 // when popped).
-template <bool COUNT>
+template <bool COUNT, bool CHUNKS>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
                                         const float4 *__restrict__ pts,
                                         const uint32_t *__restrict__ labels, int leaf, int64_t n,
@@ -239,9 +240,9 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
     const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
     bool okL = (dd.z != q.me) && (dL <= q.radius);
     bool okR = (dd.w != q.me) && (dR <= q.radius);
-    if (okL && (dd.x & kLeafBit)) { scan_chunk(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels); okL = false; }
+    if (okL && (dd.x & kLeafBit)) { scan_chunk<CHUNKS>(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels); okL = false; }
     if (okR && (dd.y & kLeafBit)) {
-      if (dR <= q.radius) scan_chunk(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels);
+      if (dR <= q.radius) scan_chunk<CHUNKS>(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels);
       okR = false;
     }
     okL = okL && dL <= q.radius;
@@ -294,7 +295,7 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
 // Unseeded, each point reports exactly its nearest other-component point
 // within its cutoff (what the inspection entry point exposes).
 // ---------------------------------------------------------------------------
-template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED>
+template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS>
 __global__ void __launch_bounds__(kBlock) k_traverse(
     const float4 *__restrict__ pts, const NodeRec *__restrict__ nodes,
     const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound,
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   unsigned long long nvis = 0;
   bool ok = true;
 
-  ok = explore<COUNT>(q, 0u, nodes, pts, labels, leaf, n, st_node, st_dist, nvis);
+  ok = explore<COUNT, CHUNKS>(q, 0u, nodes, pts, labels, leaf, n, st_node, st_dist, nvis);
   if (!ok) atomicOr(status, kErrStack);
   if (COUNT) {
     // one atomic per warp: sum the active lanes' counts first
@@ -392,9 +393,15 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   int g = grid_for(P.n, block);
   auto *vis = reinterpret_cast<unsigned long long *>(P.counters + 2);
   cudaStream_t s = P.stream;
-#define EMST_TRAV(C, R, K, S)                                                                   \
-  k_traverse<C, R, K, S><<<g, block, 0, s>>>(P.pts, P.nodes, P.labels, P.bound, radius_in, P.leaf, \
-                                             P.res, P.res_id, P.comp_key, P.n, P.counters + 1, vis)
+#define EMST_TRAV2(C, R, K, S, H)                                                              \
+  k_traverse<C, R, K, S, H><<<g, block, 0, s>>>(P.pts, P.nodes, P.labels, P.bound, radius_in,   \
+                                                P.leaf, P.res, P.res_id, P.comp_key, P.n,       \
+                                                P.counters + 1, vis)
+#define EMST_TRAV(C, R, K, S)                        \
+  do {                                               \
+    if (P.leaf > 1) EMST_TRAV2(C, R, K, S, true);    \
+    else EMST_TRAV2(C, R, K, S, false);              \
+  } while (0)
   if (radius_in) {
     EMST_TRAV(false, true, false, false);
   } else if (!seeded) {
@@ -404,6 +411,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   } else {
     if (count) EMST_TRAV(false, false, true, true); else EMST_TRAV(false, false, false, true);
   }
+#undef EMST_TRAV2
 #undef EMST_TRAV
   P.launches += 1;
 }
