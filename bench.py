@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "EMST Mpoints/s at 37M 3D clustered, plain vs learned-radius; % HBM roofline"
 WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member counts m^-1.9 on "
             "[10, 1e5], c = 5, r_vir = 0.01 (m/1e5)^(1/3)), 20% uniform, unit box, seed 2")
+TRAVERSE_DRAM_BYTES_PER_LAUNCH = None
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")
 
@@ -282,13 +283,10 @@ def main():
     avg_trav = trav_ms / max(trav_launches, 1)
     alg = traversal_algorithmic_bytes(n)
     achieved = alg / (avg_trav / 1e3) / 1e9 if avg_trav > 0 else 0.0
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("k_traverse_bytes_per_launch_at_37M")
-        except Exception:
-            traffic = None
+    # DRAM bytes per k_traverse launch from an ncu capture of this workload
+    # (profiles/k_traverse_dram_halos_37M.md); None until one is taken for the
+    # kernel as it is now.
+    traffic = TRAVERSE_DRAM_BYTES_PER_LAUNCH if n == 37_000_000 else None
     roofline = {"bound": "hbm", "kernel": "k_traverse (Algorithm 2 queries)", "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs copy)" if peak_kind == "measured" else "fallback 6.8 TB/s",
