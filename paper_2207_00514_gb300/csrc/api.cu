@@ -118,6 +118,15 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.target = c.take<uint32_t>(n);
   P.root = c.take<uint32_t>(n);
   P.edges = c.take<emst_edge>(n);
+  if (P.num_inst > 1) {
+    P.offsets = c.take<int64_t>(P.num_inst + 1);
+    P.inst_in = c.take<uint32_t>(n);
+    P.inst_of = c.take<uint32_t>(n);
+    P.inst_root = c.take<uint32_t>(P.num_inst);
+  } else {
+    P.offsets = nullptr;
+    P.inst_in = P.inst_of = P.inst_root = nullptr;
+  }
   float *pcopy = c.take<float>(copy_points ? n * P.dim : 1);
   if (copy_points) P.points = pcopy;
   emst_edge *ecopy = c.take<emst_edge>(copy_edges ? n : 1);
@@ -153,6 +162,7 @@ int bits_for(int64_t v) {  // bits needed to represent values in [0, v]
 // A1-A4: scene box, codes, sort, gather, hierarchy, refit.
 void run_build(Problem &P, bool init_labels) {
   launch_scene_box(P);
+  if (P.num_inst > 1) launch_instance_ids(P);
   launch_morton(P);
   int src = radix_sort_pairs(P, P.n, 0, 8, 0);
   if (src != 0) {  // keep the sorted codes in keys[0] and the order in vals[0]
@@ -165,6 +175,7 @@ void run_build(Problem &P, bool init_labels) {
     cudaMemsetAsync(P.arrivals, 0, sizeof(uint32_t) * (size_t)(P.nc - 1), P.stream);
     launch_hierarchy(P);
     launch_refit(P, init_labels);
+    if (P.num_inst > 1) launch_instance_roots(P);
   }
 }
 
@@ -187,12 +198,17 @@ void reset_round_state(Problem &P) {
 
 // A12: the n-1 edges in (w, i, j) order into `out` (device).
 void run_output(Problem &P, emst_edge *out) {
-  const int64_t m = P.n - 1;
+  const int64_t m = P.num_inst > 1 ? P.edges_expected : P.n - 1;
+  if (m <= 0) return;
   const int L = bits_for(P.n - 1);
   launch_edge_keys_j(P, m);
   int s = radix_sort_pairs(P, m, 0, (L + 7) / 8, 0);
   launch_edge_keys_wi(P, m, s, L);
   s = radix_sort_pairs(P, m, 0, (32 + L + 7) / 8, s);
+  if (P.num_inst > 1) {  // instance is the most significant key (stable LSD)
+    launch_edge_keys_inst(P, m, s);
+    s = radix_sort_pairs(P, m, 0, (P.inst_bits + 7) / 8, s);
+  }
   launch_edge_gather(P, m, P.vals[s], out);
 }
 
@@ -217,11 +233,32 @@ struct Timer {
 
 }  // namespace
 
-int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStream_t stream,
-                const emst_options *opt, emst_stats *stats) {
+// The method on one point set, or (offsets != nullptr) on num_inst
+// independent instances in one launch sequence.  offsets / out_offsets are
+// host arrays of num_inst + 1 entries.
+int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets, int64_t num_inst,
+                 emst_edge *out, int64_t *out_offsets, cudaStream_t stream,
+                 const emst_options *opt, emst_stats *stats) {
   int rc = check_args(points, n, dim);
   if (rc != EMST_OK) return rc;
-  if (n >= 2 && !out) return EMST_ERR_INVALID_ARG;
+  int64_t expected = n > 1 ? n - 1 : 0, largest = n;
+  if (offsets) {
+    if (num_inst < 1 || num_inst > (int64_t)1 << 30 || offsets[0] != 0 || offsets[num_inst] != n)
+      return EMST_ERR_INVALID_ARG;
+    expected = 0;
+    largest = 0;
+    for (int64_t I = 0; I < num_inst; ++I) {
+      const int64_t nk = offsets[I + 1] - offsets[I];
+      if (nk < 0) return EMST_ERR_INVALID_ARG;
+      if (out_offsets) out_offsets[I] = expected;
+      expected += nk > 1 ? nk - 1 : 0;
+      largest = nk > largest ? nk : largest;
+    }
+    if (out_offsets) out_offsets[num_inst] = expected;
+  } else {
+    num_inst = 1;
+  }
+  if (expected > 0 && !out) return EMST_ERR_INVALID_ARG;
   if (stats) {
     int32_t sz = stats->struct_size;
     std::memset(stats, 0, sizeof(emst_stats));
@@ -245,14 +282,18 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
   cudaMemPool_t pool;
   if (get_pool(dev, &pool) != cudaSuccess) return EMST_ERR_CUDA;
   const bool pts_dev = device_accessible(points);
-  const bool out_dev = n < 2 || device_accessible(out);
+  const bool out_dev = expected == 0 || device_accessible(out);
 
   Problem P;
   P.n = n;
   P.dim = dim;
   P.stream = stream;
   P.points = points;
-  P.leaf = effective_leaf(n, leaf_req);
+  P.num_inst = num_inst;
+  P.inst_bits = num_inst > 1 ? bits_for(num_inst - 1) : 0;
+  P.edges_expected = expected;
+  // (a batched problem keeps one point per leaf: chunks would mix instances)
+  P.leaf = num_inst > 1 ? 1 : effective_leaf(n, leaf_req);
   const size_t need = layout(P, nullptr, !pts_dev, !out_dev);
   char *base = nullptr;
   uint32_t host_counters[16] = {0};
@@ -270,6 +311,9 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
   if (!pts_dev)
     CU(cudaMemcpyAsync((void *)P.points, points, sizeof(float) * (size_t)n * dim,
                        cudaMemcpyHostToDevice, stream));
+  if (num_inst > 1)
+    CU(cudaMemcpyAsync(P.offsets, offsets, sizeof(int64_t) * (size_t)(num_inst + 1),
+                       cudaMemcpyHostToDevice, stream));
   run_build(P, true);
   tm.mark(1, stream);
   // Non-finite input is reported before any round runs.
@@ -277,14 +321,16 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
                      stream));
   CU(cudaStreamSynchronize(stream));
   if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
-  if (n >= 2) {
+  if (expected > 0) {
     reset_round_state(P);
     // Boruvka rounds (Fig. 3 loop): each round at least halves the number of
-    // components, so more than ceil(log2 n) rounds means something is wrong.
-    const int limit = bits_for(n - 1) + 1;
+    // components of every unfinished instance, so more than ceil(log2 n)
+    // rounds (n: the largest instance) means something is wrong.
+    const int limit = bits_for(largest - 1) + 1;
     for (rounds = 0;; ++rounds) {
       if (rounds >= limit) { rc = EMST_ERR_ROUND_LIMIT; goto done; }
-      if (stats && rounds < 40) stats->components_per_round[rounds] = n - (int64_t)host_counters[0];
+      if (stats && rounds < 40)
+        stats->components_per_round[rounds] = n - (int64_t)host_counters[0];
       if (rounds > 0) launch_node_labels(P);
       else launch_upper_bounds(P);
       if (stats && rounds < 40) {
@@ -304,13 +350,13 @@ int compute_one(const float *points, int64_t n, int dim, emst_edge *out, cudaStr
       CU(cudaStreamSynchronize(stream));
       if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
       advance_round(P, (int64_t)host_counters[12]);
-      if ((int64_t)host_counters[0] >= n - 1) { ++rounds; break; }
+      if ((int64_t)host_counters[0] >= expected) { ++rounds; break; }
     }
     tm.mark(2, stream);
-    if ((int64_t)host_counters[0] != n - 1) { rc = EMST_ERR_INTERNAL; goto done; }
+    if ((int64_t)host_counters[0] != expected) { rc = EMST_ERR_INTERNAL; goto done; }
     run_output(P, out_dev ? out : P.out_stage);
     if (!out_dev)
-      CU(cudaMemcpyAsync(out, P.out_stage, sizeof(emst_edge) * (size_t)(n - 1),
+      CU(cudaMemcpyAsync(out, P.out_stage, sizeof(emst_edge) * (size_t)expected,
                          cudaMemcpyDeviceToHost, stream));
   } else {
     tm.mark(2, stream);
@@ -436,33 +482,26 @@ const char *emst_status_string(int status) {
 }
 
 int emst_compute(const float *points, int64_t n, int dim, emst_edge *out_edges, void *stream) {
-  return compute_one(points, n, dim, out_edges, (cudaStream_t)stream, nullptr, nullptr);
+  return compute_impl(points, n, dim, nullptr, 1, out_edges, nullptr, (cudaStream_t)stream,
+                      nullptr, nullptr);
 }
 
 int emst_compute_ex(const float *points, int64_t n, int dim, emst_edge *out_edges, void *stream,
                     const emst_options *options, emst_stats *stats) {
-  return compute_one(points, n, dim, out_edges, (cudaStream_t)stream, options, stats);
+  return compute_impl(points, n, dim, nullptr, 1, out_edges, nullptr, (cudaStream_t)stream,
+                      options, stats);
 }
 
 int emst_compute_batched(const float *points, const int64_t *offsets, int num_instances, int dim,
                          emst_edge *out_edges, int64_t *out_offsets, void *stream) {
   if (num_instances < 0 || !offsets || !out_offsets || (dim != 2 && dim != 3))
     return EMST_ERR_INVALID_ARG;
-  if (offsets[0] != 0) return EMST_ERR_INVALID_ARG;
-  out_offsets[0] = 0;
-  for (int k = 0; k < num_instances; ++k) {
-    int64_t nk = offsets[k + 1] - offsets[k];
-    if (nk < 0 || nk > EMST_MAX_POINTS) return EMST_ERR_INVALID_ARG;
-    out_offsets[k + 1] = out_offsets[k] + (nk > 1 ? nk - 1 : 0);
+  if (num_instances == 0) {
+    out_offsets[0] = 0;
+    return offsets[0] == 0 ? EMST_OK : EMST_ERR_INVALID_ARG;
   }
-  for (int k = 0; k < num_instances; ++k) {
-    int64_t nk = offsets[k + 1] - offsets[k];
-    if (nk == 0) continue;
-    int rc = compute_one(points + offsets[k] * dim, nk, dim, out_edges + out_offsets[k],
-                         (cudaStream_t)stream, nullptr, nullptr);
-    if (rc != EMST_OK) return rc;
-  }
-  return EMST_OK;
+  return compute_impl(points, offsets[num_instances], dim, offsets, num_instances, out_edges,
+                      out_offsets, (cudaStream_t)stream, nullptr, nullptr);
 }
 
 int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint64_t *out_codes,

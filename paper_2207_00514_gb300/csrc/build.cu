@@ -68,32 +68,96 @@ void launch_scene_box(Problem &P) {
 
 // ---------------------------------------------------------------------------
 // A2. Morton codes.  Quantisation decided in FP32 exactly as specified (B = 21
-// bits per dimension in 3D, 32 in 2D):
+// bits per dimension in 3D, 32 in 2D; fewer in the batched form, see
+// code_bits):
 //   s = 2^B / (hi - lo) (0 for a flat dimension), t = (x - lo) * s,
 //   q = t >= 2^B ? 2^B - 1 : trunc(t)
 // and the bits interleave x (most significant), y, z.
 // ---------------------------------------------------------------------------
+// With instances, the instance id goes above the interleaved bits.
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_morton(const float *__restrict__ pts, int64_t n,
                                                    const uint32_t *__restrict__ box,
+                                                   const uint32_t *__restrict__ inst_in, int bits,
                                                    uint64_t *__restrict__ keys,
                                                    uint32_t *__restrict__ vals) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const Quantizer Q = make_quantizer(box, DIM);
+  const Quantizer Q = make_quantizer(box, DIM, bits);
   uint32_t q[3] = {0, 0, 0};
 #pragma unroll
   for (int d = 0; d < DIM; ++d) q[d] = quantize(Q, d, __ldg(pts + k * DIM + d));
-  keys[k] = interleave(q[0], q[1], q[2], DIM);
+  uint64_t code = interleave(q[0], q[1], q[2], DIM);
+  if (inst_in) code |= (uint64_t)__ldg(inst_in + k) << (DIM * bits);
+  keys[k] = code;
   vals[k] = (uint32_t)k;
 }
 
 void launch_morton(Problem &P) {
   int g = grid_for(P.n, kBlock);
+  const int bits = code_bits(P.dim, P.inst_bits);
   if (P.dim == 3)
-    k_morton<3><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0]);
+    k_morton<3><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.inst_in, bits,
+                                            P.keys[0], P.vals[0]);
   else
-    k_morton<2><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.keys[0], P.vals[0]);
+    k_morton<2><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.inst_in, bits,
+                                            P.keys[0], P.vals[0]);
+  P.launches += 1;
+}
+
+// Instance id of every input row (binary search in the offsets).
+__global__ void __launch_bounds__(kBlock) k_instance_ids(const int64_t *__restrict__ offsets,
+                                                         int64_t num_inst, int64_t n,
+                                                         uint32_t *__restrict__ inst_in) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int64_t lo = 0, hi = num_inst - 1;  // last instance whose start is <= k
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(offsets + mid) <= k) lo = mid; else hi = mid - 1;
+  }
+  inst_in[k] = (uint32_t)lo;
+}
+
+void launch_instance_ids(Problem &P) {
+  k_instance_ids<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.offsets, P.num_inst, P.n,
+                                                                 P.inst_in);
+  P.launches += 1;
+}
+
+// Root node of each instance's subtree: the node whose chunk range is exactly
+// the instance's (one of its two ends is the node's index); kInvalid for an
+// instance with fewer than two chunks... of points (nothing to search).
+__global__ void __launch_bounds__(kBlock) k_instance_roots(const int64_t *__restrict__ offsets,
+                                                           int64_t num_inst, int64_t nc, int leaf,
+                                                           const uint4 *__restrict__ range,
+                                                           uint32_t *__restrict__ inst_root,
+                                                           uint32_t *status) {
+  int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= num_inst) return;
+  const int64_t a = __ldg(offsets + I), b = __ldg(offsets + I + 1) - 1;
+  if (b <= a) { inst_root[I] = kInvalid; return; }
+  const int64_t ca = a / leaf, cb = b / leaf;
+  uint32_t root = kInvalid;
+  if (ca == cb) {
+    root = kInvalid;  // inside one leaf chunk: cannot happen with leaf 1 (a < b)
+  } else {
+    if (ca < nc - 1) {
+      const uint4 r = __ldg(range + ca);
+      if (r.x == (uint32_t)ca && r.z == (uint32_t)cb) root = (uint32_t)ca;
+    }
+    if (root == kInvalid && cb < nc - 1) {
+      const uint4 r = __ldg(range + cb);
+      if (r.x == (uint32_t)ca && r.z == (uint32_t)cb) root = (uint32_t)cb;
+    }
+  }
+  if (root == kInvalid) atomicOr(status, kErrChain);
+  inst_root[I] = root;
+}
+
+void launch_instance_roots(Problem &P) {
+  k_instance_roots<<<grid_for(P.num_inst, kBlock), kBlock, 0, P.stream>>>(
+      P.offsets, P.num_inst, P.nc, P.leaf, P.range, P.inst_root, P.counters + 1);
   P.launches += 1;
 }
 
@@ -107,10 +171,13 @@ __global__ void __launch_bounds__(kBlock) k_gather(const float *__restrict__ pts
                                                    const uint32_t *__restrict__ perm, int64_t n,
                                                    float4 *__restrict__ out,
                                                    uint32_t *__restrict__ inv,
-                                                   uint32_t *__restrict__ labels) {
+                                                   uint32_t *__restrict__ labels,
+                                                   const uint32_t *__restrict__ inst_in,
+                                                   uint32_t *__restrict__ inst_of) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   uint32_t o = __ldg(perm + k);
+  if (inst_of) inst_of[k] = __ldg(inst_in + o);
   const float *p = pts + (int64_t)o * DIM;
   float x = __ldg(p), y = __ldg(p + 1), z = DIM == 3 ? __ldg(p + 2) : 0.0f;
   out[k] = make_float4(x, y, z, __uint_as_float(o));
@@ -121,9 +188,11 @@ __global__ void __launch_bounds__(kBlock) k_gather(const float *__restrict__ pts
 void launch_gather(Problem &P, const uint32_t *perm) {
   int g = grid_for(P.n, kBlock);
   if (P.dim == 3)
-    k_gather<3><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.inv, P.labels);
+    k_gather<3><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.inv, P.labels, P.inst_in,
+                                            P.inst_of);
   else
-    k_gather<2><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.inv, P.labels);
+    k_gather<2><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.inv, P.labels, P.inst_in,
+                                            P.inst_of);
   P.launches += 1;
 }
 

@@ -95,10 +95,17 @@ struct Quantizer {
   uint32_t qmax;
 };
 
-__device__ __forceinline__ Quantizer make_quantizer(const uint32_t *box, int dim) {
+// Bits per dimension of the codes: 21 in 3D and 32 in 2D, fewer when the top
+// bits carry an instance id.
+__host__ __device__ __forceinline__ int code_bits(int dim, int inst_bits) {
+  const int b = (64 - inst_bits) / dim;
+  return dim == 3 ? (b < 21 ? b : 21) : (b < 32 ? b : 32);
+}
+
+__device__ __forceinline__ Quantizer make_quantizer(const uint32_t *box, int dim, int bits) {
   Quantizer Q;
-  Q.twoB = dim == 3 ? 2097152.0f : 4294967296.0f;
-  Q.qmax = dim == 3 ? 0x1fffffu : 0xffffffffu;
+  Q.twoB = __uint_as_float((uint32_t)(127 + bits) << 23);  // 2^bits exactly
+  Q.qmax = bits >= 32 ? 0xffffffffu : ((1u << bits) - 1u);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     Q.lo[d] = 0.f;
@@ -152,6 +159,19 @@ struct Problem {
   int dim = 3;
   int leaf = 1;      // points per leaf chunk of the hierarchy
   int64_t nc = 0;    // leaf chunks: ceil(n / leaf)
+
+  // Batched form: num_inst independent instances, instance I = input rows
+  // [offsets[I], offsets[I+1]); the instance id sits in the top `inst_bits`
+  // bits of every code, so instance I is also curve positions
+  // [offsets[I], offsets[I+1]) and one subtree of the hierarchy.  With one
+  // instance all of this is off (null arrays, inst_bits 0).
+  int64_t num_inst = 1;
+  int inst_bits = 0;
+  int64_t *offsets = nullptr;       // num_inst+1, device
+  uint32_t *inst_in = nullptr;      // n: instance of each input row
+  uint32_t *inst_of = nullptr;      // n: instance of each curve position
+  uint32_t *inst_root = nullptr;    // num_inst: root node of each instance's subtree
+  int64_t edges_expected = 0;       // sum over instances of max(n_I - 1, 0)
   cudaStream_t stream = nullptr;
 
   const float *points = nullptr;  // n x dim, device
@@ -204,6 +224,8 @@ struct Problem {
 void launch_scene_box(Problem &P);
 void launch_morton(Problem &P);
 void launch_gather(Problem &P, const uint32_t *perm);
+void launch_instance_ids(Problem &P);
+void launch_instance_roots(Problem &P);
 void launch_hierarchy(Problem &P);
 void launch_refit(Problem &P, bool init_labels);
 // sort.cu
@@ -227,6 +249,7 @@ void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
 // output
 void launch_edge_keys_j(Problem &P, int64_t m);
 void launch_edge_keys_wi(Problem &P, int64_t m, int src, int shift_i);
+void launch_edge_keys_inst(Problem &P, int64_t m, int src);
 void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge *out);
 
 // api.cu: helpers of the orchestration

@@ -147,11 +147,13 @@ void launch_node_labels(Problem &P) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_upper_bounds(const float4 *__restrict__ pts,
                                                          const uint32_t *__restrict__ labels,
+                                                         const uint32_t *__restrict__ inst_of,
                                                          int64_t n, uint32_t *bound) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k + 1 >= n) return;
   uint32_t la = labels[k], lb = labels[k + 1];
   if (la == lb) return;
+  if (inst_of && __ldg(inst_of + k) != __ldg(inst_of + k + 1)) return;  // different instances
   float4 p = pts[k], q = pts[k + 1];
   uint32_t w = __float_as_uint(sq_dist(p.x, p.y, p.z, q.x, q.y, q.z));
   atomicMin(&bound[la], w);
@@ -159,7 +161,8 @@ __global__ void __launch_bounds__(kBlock) k_upper_bounds(const float4 *__restric
 }
 
 void launch_upper_bounds(Problem &P) {
-  k_upper_bounds<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.labels, P.n, P.bound);
+  k_upper_bounds<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.labels, P.inst_of, P.n,
+                                                                 P.bound);
   P.launches += 1;
 }
 
@@ -299,10 +302,26 @@ template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS>
 __global__ void __launch_bounds__(kBlock) k_traverse(
     const float4 *__restrict__ pts, const NodeRec *__restrict__ nodes,
     const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound,
-    const float *__restrict__ radius_in, int leaf, uint2 *__restrict__ res, uint32_t *__restrict__ res_id, uint64_t *__restrict__ comp_key,
+    const float *__restrict__ radius_in, int leaf, const uint32_t *__restrict__ inst_of,
+    const uint32_t *__restrict__ inst_root, const int64_t *__restrict__ offsets,
+    uint2 *__restrict__ res, uint32_t *__restrict__ res_id, uint64_t *__restrict__ comp_key,
     int64_t n, uint32_t *status, unsigned long long *visits) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  // Batched form: search only this point's instance (its subtree, its curve range).
+  uint32_t start = 0u;
+  int64_t wlo = 0, whi = n;
+  if (inst_of) {
+    const uint32_t I = __ldg(inst_of + i);
+    start = __ldg(inst_root + I);
+    wlo = __ldg(offsets + I);
+    whi = __ldg(offsets + I + 1);
+    if (start == kInvalid) {  // a one-point instance: nothing to find
+      res[i] = make_uint2(0u, kInvalid);
+      res_id[i] = kInvalid;
+      return;
+    }
+  }
   const float4 p = pts[i];
   Query q;
   q.px = p.x;
@@ -342,7 +361,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
 #pragma unroll
     for (int o = -kWindow; o <= kWindow; ++o) {
       const int64_t j = i + o;
-      if (o == 0 || j < 0 || j >= n) continue;
+      if (o == 0 || j < wlo || j >= whi) continue;
       if (__ldg(labels + j) == q.me) continue;
       const float4 c = __ldg(pts + j);
       const float d = sq_dist(q.px, q.py, q.pz, c.x, c.y, c.z);
@@ -357,7 +376,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
   unsigned long long nvis = 0;
   bool ok = true;
 
-  ok = explore<COUNT, CHUNKS>(q, 0u, nodes, pts, labels, leaf, n, st_node, st_dist, nvis);
+  ok = explore<COUNT, CHUNKS>(q, start, nodes, pts, labels, leaf, n, st_node, st_dist, nvis);
   if (!ok) atomicOr(status, kErrStack);
   if (COUNT) {
     // one atomic per warp: sum the active lanes' counts first
@@ -395,7 +414,8 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   cudaStream_t s = P.stream;
 #define EMST_TRAV2(C, R, K, S, H)                                                              \
   k_traverse<C, R, K, S, H><<<g, block, 0, s>>>(P.pts, P.nodes, P.labels, P.bound, radius_in,   \
-                                                P.leaf, P.res, P.res_id, P.comp_key, P.n,       \
+                                                P.leaf, P.inst_of, P.inst_root, P.offsets,      \
+                                                P.res, P.res_id, P.comp_key, P.n,               \
                                                 P.counters + 1, vis)
 #define EMST_TRAV(C, R, K, S)                        \
   do {                                               \
@@ -534,7 +554,8 @@ constexpr int kRelabelTile = kScanThreads * kRelabelItems;
 
 __global__ void __launch_bounds__(kScanThreads, 6) k_relabel_runs(
     const uint32_t *__restrict__ labels_old, const uint32_t *__restrict__ root,
-    const float4 *__restrict__ pts, int64_t n, uint32_t *__restrict__ labels_new,
+    const float4 *__restrict__ pts, const uint32_t *__restrict__ inst_of, int64_t n,
+    uint32_t *__restrict__ labels_new,
     uint32_t *__restrict__ bound_next, uint32_t *__restrict__ runs, uint32_t *lookback,
     uint32_t *tile_counter, uint32_t *status) {
   __shared__ uint32_t s_tile;
@@ -558,6 +579,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_relabel_runs(
     if (k < n) labels_new[k] = lab[q];
     if (k + 1 < n && lab[q] != lab[q + 1]) {
       flags |= 1u << q;
+      if (inst_of && __ldg(inst_of + k) != __ldg(inst_of + k + 1)) continue;  // no cross-instance bound
       const float4 p = __ldg(pts + k), r = __ldg(pts + k + 1);
       const uint32_t w = __float_as_uint(sq_dist(p.x, p.y, p.z, r.x, r.y, r.z));
       atomicMin(&bound_next[lab[q]], w);
@@ -626,7 +648,7 @@ void launch_merge(Problem &P) {
   cudaMemsetAsync(ctr, 0, sizeof(uint32_t), P.stream);
   cudaMemsetAsync(P.sort_lookback, 0, sizeof(uint32_t) * (size_t)tiles, P.stream);
   k_relabel_runs<<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(
-      P.labels, P.root, P.pts, P.n, P.labels_buf[P.cur ^ 1], P.bound_buf[P.cur ^ 1], P.runs,
+      P.labels, P.root, P.pts, P.inst_of, P.n, P.labels_buf[P.cur ^ 1], P.bound_buf[P.cur ^ 1], P.runs,
       P.sort_lookback, ctr, P.counters + 1);
   P.launches += 3;
 }
@@ -675,11 +697,28 @@ __global__ void k_edge_keys_wi(const emst_edge *__restrict__ edges, int64_t m,
   keys[e] = ((uint64_t)__float_as_uint(E.w) << shift_i) | (uint64_t)E.i;
 }
 
-__global__ void k_edge_gather(const emst_edge *__restrict__ edges, int64_t m,
-                              const uint32_t *__restrict__ order, emst_edge *__restrict__ out) {
+__global__ void k_edge_keys_inst(const emst_edge *__restrict__ edges, int64_t m,
+                                 uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                                 const uint32_t *__restrict__ inst_in) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
-  out[e] = edges[order[e]];
+  keys[e] = __ldg(inst_in + edges[vals[e]].i);
+}
+
+// Final order, with ids made local to their instance in the batched form.
+__global__ void k_edge_gather(const emst_edge *__restrict__ edges, int64_t m,
+                              const uint32_t *__restrict__ order, emst_edge *__restrict__ out,
+                              const uint32_t *__restrict__ inst_in,
+                              const int64_t *__restrict__ offsets) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  emst_edge E = edges[order[e]];
+  if (inst_in) {
+    const uint32_t base = (uint32_t)__ldg(offsets + __ldg(inst_in + E.i));
+    E.i -= base;
+    E.j -= base;
+  }
+  out[e] = E;
 }
 
 void launch_edge_keys_j(Problem &P, int64_t m) {
@@ -691,8 +730,14 @@ void launch_edge_keys_wi(Problem &P, int64_t m, int src, int shift_i) {
                                                                shift_i);
   P.launches += 1;
 }
+void launch_edge_keys_inst(Problem &P, int64_t m, int src) {
+  k_edge_keys_inst<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[src],
+                                                                  P.vals[src], P.inst_in);
+  P.launches += 1;
+}
 void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge *out) {
-  k_edge_gather<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, order, out);
+  k_edge_gather<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, order, out, P.inst_in,
+                                                              P.offsets);
   P.launches += 1;
 }
 

@@ -1,0 +1,83 @@
+"""The batched form (many independent EMSTs in one call) against the oracle,
+instance by instance, and against emst_compute on each instance alone."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2207_00514_gb300 as p
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p.load_library()
+    return p
+
+
+def run_batched(pkg, pts, offsets):
+    e, eo = pkg.emst_compute_batched(torch.from_numpy(pts).cuda(), offsets)
+    torch.cuda.synchronize()
+    return pkg.edges_numpy(e), eo
+
+
+def same(a, b):
+    return np.array_equal(np.asarray(a).view(np.uint8), np.asarray(b).view(np.uint8))
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_batched_matches_oracle_per_instance(pkg, dim):
+    g = np.random.default_rng(40 + dim)
+    sizes = [0, 1, 2, 3, 5, 0, 64, 1000, 1, 2500, 3073, 17, 4000]
+    parts = [synth.blobs(s, dim, 500 + k, n_blobs=3) if s > 0 else np.zeros((0, dim), np.float32)
+             for k, s in enumerate(sizes)]
+    pts = np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    got, eo = run_batched(pkg, pts, offsets)
+    want_off = np.concatenate([[0], np.cumsum([max(s - 1, 0) for s in sizes])])
+    assert np.array_equal(eo, want_off)
+    for k, s in enumerate(sizes):
+        block = got[eo[k]:eo[k + 1]]
+        if s < 2:
+            assert len(block) == 0
+            continue
+        assert same(block, oracle.prim(parts[k])), f"instance {k} (n={s})"
+
+
+def test_batched_equals_single_calls(pkg):
+    sizes = synth.batched_sizes(64, seed=7, lo=100, hi=20_000)
+    pts, offsets = synth.batched_instances(sizes, seed=7)
+    got, eo = run_batched(pkg, pts, offsets)
+    for k in range(len(sizes)):
+        part = pts[offsets[k]:offsets[k + 1]]
+        single = pkg.edges_numpy(pkg.emst_compute(torch.from_numpy(np.ascontiguousarray(part)).cuda()))
+        assert same(got[eo[k]:eo[k + 1]], single), f"instance {k}"
+    # a few instances against the oracle too
+    for k in (0, 13, 63):
+        part = pts[offsets[k]:offsets[k + 1]]
+        assert same(got[eo[k]:eo[k + 1]], oracle.emst(part, threads=os.cpu_count() or 4))
+
+
+def test_batched_host_buffers(pkg):
+    sizes = [300, 0, 2, 700]
+    pts, offsets = synth.batched_instances(sizes, seed=9)
+    dev, eo = run_batched(pkg, pts, offsets)
+    e_host, eo2 = pkg.emst_compute_batched(torch.from_numpy(pts).pin_memory(), offsets)
+    assert np.array_equal(eo, eo2)
+    assert same(pkg.edges_numpy(e_host), dev)
+
+
+def test_batched_rejects_bad_offsets(pkg):
+    pts = torch.zeros((10, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        pkg.emst_compute_batched(pts, np.array([0, 5, 4, 10]))
+    with pytest.raises(ValueError):
+        pkg.emst_compute_batched(pts, np.array([0, 5, 9]))
