@@ -273,3 +273,56 @@ def test_full_size_config_vs_kd_oracle(pkg, cfg):
     got = gpu_emst(pkg, pts)
     want = oracle.kd_boruvka(pts, threads=os.cpu_count() or 4)
     assert_same_edges(got, want, f"config {cfg}")
+
+
+def test_full_size_halos_37M_vs_kd_oracle(pkg):
+    """Config 3 at full size (37,000,000 3D halo points, seed 2): the whole
+    tree against the k-d tree Boruvka oracle (all host threads)."""
+    pts = synth.config_points(3)
+    got = gpu_emst(pkg, pts)
+    want = oracle.kd_boruvka(pts, threads=os.cpu_count() or 4)
+    assert_same_edges(got, want, "config 3")
+
+
+def test_full_size_lattice_ties_vs_kd_oracle(pkg):
+    """Config 5's tie-stress set at full size: 7,680,000 distinct sites of
+    {0..199}^3 plus 320,000 duplicates (massive equal weights, zero weights)."""
+    pts = synth.lattice_ties()
+    got = gpu_emst(pkg, pts)
+    want = oracle.kd_boruvka(pts, threads=os.cpu_count() or 4)
+    assert_same_edges(got, want, "lattice ties")
+
+
+def test_full_size_halos_100M_invariants(pkg):
+    """Config 5 at full size (100,000,000 3D halo points, seed 3).  The oracle
+    cannot redo the whole tree in test time, so this checks what holds at any
+    size: n-1 edges, one connected acyclic tree, (w, i, j) order, weights equal
+    to the FP32 weight of their endpoints (sampled), and the cut property on
+    sampled single-vertex cuts: for a vertex v the smallest edge (w, min id,
+    max id) incident to v separates {v} from the rest, so it must be in the
+    tree -- that edge is found here by brute force over all n points."""
+    from fp32ref import weight32
+    pts = synth.config_points(5)
+    n = len(pts)
+    e = gpu_emst(pkg, pts)
+    assert len(e) == n - 1
+    assert np.all(e["i"] < e["j"])
+    w_bits = e["w"].view(np.uint32).astype(np.uint64)
+    ii, jj = e["i"].astype(np.uint64), e["j"].astype(np.uint64)
+    later = (w_bits[1:] > w_bits[:-1]) | ((w_bits[1:] == w_bits[:-1]) &
+             ((ii[1:] > ii[:-1]) | ((ii[1:] == ii[:-1]) & (jj[1:] > jj[:-1]))))
+    assert np.all(later)
+    comps, cyc = oracle.count_components(e, n)
+    assert comps == 1 and not cyc
+    g = np.random.default_rng(5)
+    idx = g.choice(n - 1, 200_000, replace=False)
+    w = weight32(pts[e["i"][idx]], pts[e["j"][idx]])
+    assert np.array_equal(w.view(np.uint32), e["w"][idx].view(np.uint32))
+    for v in g.choice(n, 12, replace=False):
+        wv = weight32(np.broadcast_to(pts[v], pts.shape), pts)
+        wv[v] = np.inf
+        m = wv.min()
+        j = int(np.nonzero(wv == m)[0].min())  # equal weights: the smaller id (the key's order)
+        a, b = min(int(v), j), max(int(v), j)
+        hit = np.nonzero((e["i"] == a) & (e["j"] == b))[0]
+        assert len(hit) == 1 and e["w"][hit[0]] == m, (v, j)
