@@ -78,7 +78,10 @@ typedef struct emst_options {
                                  while fewer than 2 chunks remain).  Chunks are runs of
                                  consecutive curve positions; on clustered data they straddle
                                  the curve's jumps and search more, so 1 is the fastest there */
-  int32_t reserved[10];
+  const float *mlp_params;    /* learned search radius: the network (EMST_MLP_PARAMS floats,
+                                 host or device memory; see emst_mlp_forward), or NULL for the
+                                 plain method.  The tree is the same either way. */
+  int32_t reserved[8];
 } emst_options;
 
 /* Per-call statistics filled by emst_compute_ex when `stats` is not NULL. */
@@ -97,7 +100,10 @@ typedef struct emst_stats {
   int32_t traverse_launches; /* traversal kernels timed in traverse_ms */
   int32_t reserved1;
   double round_traverse_ms[40]; /* traversal time of each round */
-  int64_t reserved[6];
+  int64_t queried_points;  /* learned radius: queries that used a proposed cutoff */
+  int64_t rerun_points;    /* learned radius: of those, rerun because the cutoff fell below
+                              their component's found minimum */
+  int64_t reserved[4];
 } emst_stats;
 
 /* EMST of n points (§3, Fig. 3 end to end).
@@ -145,6 +151,50 @@ int emst_compute_batched(const float *points, const int64_t *offsets, int num_in
 #define EMST_NOALLOC_MAX_POINTS ((int64_t)65536)
 int emst_compute_noalloc(const float *points, int64_t n, int dim, emst_edge *out_edges,
                          void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Learned search radius (the paper has no counterpart; a proposal that only */
+/* tightens cutoffs, with a certification rerun that keeps the tree exact).  */
+/* ---------------------------------------------------------------------- */
+/* The network: EMST_MLP_FEATURES inputs -> 64 -> 64 -> 64 -> 1 (ReLU), one
+ * flat FP32 parameter vector of EMST_MLP_PARAMS entries in this order:
+ *   in_mu[8], in_sigma[8], out_mu, out_sigma, margin, pad,
+ *   W1[64][8], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], w4[64], b4.
+ * Features are normalised (f - in_mu) / in_sigma; the output y predicts the
+ * normalised log2 nearest other-component weight, de-normalised as
+ * y * out_sigma + out_mu, plus margin (a safety offset in log2 units).
+ * The 8 features of a point (curve order) in a round: its position in the
+ * scene box (3, z = 0 in 2D), log2 of the smallest and of the mean weight to
+ * its 4 + 4 curve neighbours, log2 of its component size, log2 of its lower
+ * bound from the previous round (0 in the first), log2 of its component's
+ * cutoff. */
+#define EMST_MLP_FEATURES 8
+#define EMST_MLP_PARAMS 8981
+
+/* Inference (BF16 weights and activations on the tensor cores, FP32
+ * accumulation): out_log2w[k] = predicted log2 weight of feature row k.
+ * features: m x EMST_MLP_FEATURES FP32; params, out: device memory. */
+int emst_mlp_forward(const float *features, int64_t m, const float *params, float *out_log2w,
+                     void *stream);
+
+/* Training step pieces (FP32).  emst_mlp_grad ADDS the gradient of the mean
+ * squared error (on the normalised target log2 weights) over the m samples to
+ * grad[EMST_MLP_PARAMS] and the loss to *loss; emst_mlp_adam applies one Adam
+ * step (step >= 1) to the trainable entries (from W1 on) and clears grad.
+ * All pointers are device memory. */
+int emst_mlp_grad(const float *features, const float *targets, int64_t m, const float *params,
+                  float *grad, float *loss, void *stream);
+int emst_mlp_adam(float *params, float *grad, float *m1, float *m2, int step, float lr,
+                  float beta1, float beta2, float eps, void *stream);
+
+/* Training pairs from a plain run on `points`: in every round, about one
+ * point in `every` (a fixed hash of position and round) contributes its
+ * features and the exact log2 weight of its nearest point in another
+ * component.  out_features (capacity x EMST_MLP_FEATURES) and out_targets
+ * (capacity) are device memory; *out_count (host) = pairs produced (only the
+ * first `capacity` are stored). */
+int emst_learned_samples(const float *points, int64_t n, int dim, int every, float *out_features,
+                         float *out_targets, int64_t capacity, int64_t *out_count, void *stream);
 
 /* Static string for a status code (never NULL). */
 const char *emst_status_string(int status);

@@ -34,6 +34,12 @@ __all__ = [
     "emst_build_bvh",
     "emst_round_step",
     "edges_w",
+    "EMST_MLP_PARAMS",
+    "EMST_MLP_FEATURES",
+    "emst_mlp_forward",
+    "emst_mlp_grad",
+    "emst_mlp_adam",
+    "emst_learned_samples",
     "edges_numpy",
     "EDGE_DTYPE",
 ]
@@ -42,6 +48,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libemst.so")
 _HEADER = os.path.join(os.path.dirname(_HERE), "include", "emst.h")
 EMST_MAX_POINTS = (1 << 30) - 1
+EMST_MLP_PARAMS = 8981
+EMST_MLP_FEATURES = 8
 EDGE_DTYPE = np.dtype([("i", np.uint32), ("j", np.uint32), ("w", np.float32)])
 INVALID = 0xFFFFFFFF
 
@@ -60,7 +68,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("carried_radius", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("count_visits", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("mlp_params", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 8)]
 
 
 class _Stats(ctypes.Structure):
@@ -71,7 +79,8 @@ class _Stats(ctypes.Structure):
                 ("node_visits", ctypes.c_int64), ("components_per_round", ctypes.c_int64 * 40),
                 ("traverse_ms", ctypes.c_double), ("traverse_launches", ctypes.c_int32),
                 ("reserved1", ctypes.c_int32), ("round_traverse_ms", ctypes.c_double * 40),
-                ("reserved", ctypes.c_int64 * 6)]
+                ("queried_points", ctypes.c_int64), ("rerun_points", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
 
 
 _lock = threading.Lock()
@@ -110,6 +119,15 @@ def load_library(path: str | None = None):
         lib.emst_round_step.restype = I
         lib.emst_compute_noalloc.argtypes = [V, I64, I, V, V]
         lib.emst_compute_noalloc.restype = I
+        lib.emst_mlp_forward.argtypes = [V, I64, V, V, V]
+        lib.emst_mlp_forward.restype = I
+        lib.emst_mlp_grad.argtypes = [V, V, I64, V, V, V, V]
+        lib.emst_mlp_grad.restype = I
+        F = ctypes.c_float
+        lib.emst_mlp_adam.argtypes = [V, V, V, V, I, F, F, F, F, V]
+        lib.emst_mlp_adam.restype = I
+        lib.emst_learned_samples.argtypes = [V, I64, I, I, V, V, I64, ctypes.POINTER(I64), V]
+        lib.emst_learned_samples.restype = I
         if path is None:
             _lib = lib
         return lib
@@ -202,7 +220,7 @@ def emst_compute_noalloc(points, out_edges=None, stream=None):
 
 
 def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_radius=True,
-                    use_graph=False, count_visits=False, leaf_size=0):
+                    use_graph=False, count_visits=False, leaf_size=0, mlp_params=None):
     """emst_compute with options; returns (edges, stats dict)."""
     n, dim = _check_points(points)
     out_edges = _edges_out(n, points, out_edges)
@@ -213,6 +231,10 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
     opt.use_graph = 1 if use_graph else 0
     opt.count_visits = 1 if count_visits else 0
     opt.leaf_size = int(leaf_size)
+    if mlp_params is not None:
+        if mlp_params.dtype != _torch().float32 or mlp_params.numel() != EMST_MLP_PARAMS:
+            raise ValueError(f"mlp_params must hold {EMST_MLP_PARAMS} float32 values")
+        opt.mlp_params = mlp_params.data_ptr()
     st = _Stats()
     st.struct_size = ctypes.sizeof(_Stats)
     rc = load_library().emst_compute_ex(_ptr(points), n, dim, _ptr(out_edges),
@@ -225,7 +247,8 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
                  node_visits=st.node_visits, traverse_ms=st.traverse_ms,
                  traverse_launches=st.traverse_launches,
                  round_traverse_ms=[float(st.round_traverse_ms[k]) for k in range(min(st.rounds, 40))],
-                 components_per_round=[int(st.components_per_round[k]) for k in range(min(st.rounds, 40))])
+                 components_per_round=[int(st.components_per_round[k]) for k in range(min(st.rounds, 40))],
+                 queried_points=st.queried_points, rerun_points=st.rerun_points)
     return out_edges, stats
 
 
@@ -303,3 +326,66 @@ def edges_w(edges):
 def edges_numpy(edges) -> np.ndarray:
     a = edges.detach().cpu().contiguous().numpy()
     return np.ascontiguousarray(a).view(EDGE_DTYPE).reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# Learned search radius: network pieces (see include/emst.h)
+# ----------------------------------------------------------------------------
+def _dev_f32(t, numel=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_contiguous() or t.device.type != "cuda":
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} values")
+    return t
+
+
+def emst_mlp_forward(features, params, out=None, stream=None):
+    """Predicted log2 weights for an (m, 8) float32 feature tensor (BF16 tensor-core inference)."""
+    torch = _torch()
+    _dev_f32(features)
+    _dev_f32(params, EMST_MLP_PARAMS)
+    m = features.shape[0]
+    if out is None:
+        out = torch.empty(m, dtype=torch.float32, device=features.device)
+    rc = load_library().emst_mlp_forward(_ptr(features), m, _ptr(params), _ptr(out),
+                                         _stream_ptr(stream, features.device))
+    if rc != 0:
+        raise EmstError(rc, "emst_mlp_forward")
+    return out
+
+
+def emst_mlp_grad(features, targets, params, grad, loss, stream=None):
+    """Adds the batch's mean-squared-error gradient to grad and the loss to loss[0]."""
+    for t in (features, targets, params, grad, loss):
+        _dev_f32(t)
+    rc = load_library().emst_mlp_grad(_ptr(features), _ptr(targets), features.shape[0], _ptr(params),
+                                      _ptr(grad), _ptr(loss), _stream_ptr(stream, features.device))
+    if rc != 0:
+        raise EmstError(rc, "emst_mlp_grad")
+
+
+def emst_mlp_adam(params, grad, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    for t in (params, grad, m1, m2):
+        _dev_f32(t, EMST_MLP_PARAMS)
+    rc = load_library().emst_mlp_adam(_ptr(params), _ptr(grad), _ptr(m1), _ptr(m2), int(step),
+                                      float(lr), float(beta1), float(beta2), float(eps),
+                                      _stream_ptr(stream, params.device))
+    if rc != 0:
+        raise EmstError(rc, "emst_mlp_adam")
+
+
+def emst_learned_samples(points, every, capacity, stream=None):
+    """(features (k, 8), targets (k,)) training pairs logged from a plain run."""
+    torch = _torch()
+    n, dim = _check_points(points)
+    dev = points.device if points.device.type == "cuda" else torch.device("cuda")
+    feat = torch.empty((capacity, EMST_MLP_FEATURES), dtype=torch.float32, device=dev)
+    targ = torch.empty(capacity, dtype=torch.float32, device=dev)
+    cnt = ctypes.c_int64(0)
+    rc = load_library().emst_learned_samples(_ptr(points), n, dim, int(every), _ptr(feat), _ptr(targ),
+                                             int(capacity), ctypes.byref(cnt), _stream_ptr(stream, dev))
+    if rc != 0:
+        raise EmstError(rc, "emst_learned_samples")
+    k = min(cnt.value, capacity)
+    return feat[:k], targ[:k]

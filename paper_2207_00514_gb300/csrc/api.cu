@@ -127,6 +127,14 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
     P.offsets = nullptr;
     P.inst_in = P.inst_of = P.inst_root = nullptr;
   }
+  if (P.want_learned || P.want_logging) P.comp_size = c.take<uint32_t>(n);
+  if (P.want_learned) {
+    P.pred_r = c.take<float>(n);
+    P.r_used = c.take<float>(n);
+    P.rerun_list = c.take<uint32_t>(n);
+    P.mlp = c.take<float>(EMST_MLP_PARAMS);
+  }
+  if (P.want_logging) P.log_count = c.take<unsigned long long>(1);
   float *pcopy = c.take<float>(copy_points ? n * P.dim : 1);
   if (copy_points) P.points = pcopy;
   emst_edge *ecopy = c.take<emst_edge>(copy_edges ? n : 1);
@@ -236,9 +244,19 @@ struct Timer {
 // The method on one point set, or (offsets != nullptr) on num_inst
 // independent instances in one launch sequence.  offsets / out_offsets are
 // host arrays of num_inst + 1 entries.
+// Internal extras of a call: training-pair logging and skipping the output.
+struct Extras {
+  float *log_feat = nullptr;
+  float *log_target = nullptr;
+  int64_t log_capacity = 0;
+  int log_every = 1;
+  int64_t *log_count_out = nullptr;
+  bool skip_output = false;
+};
+
 int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets, int64_t num_inst,
                  emst_edge *out, int64_t *out_offsets, cudaStream_t stream,
-                 const emst_options *opt, emst_stats *stats) {
+                 const emst_options *opt, emst_stats *stats, const Extras *ex = nullptr) {
   int rc = check_args(points, n, dim);
   if (rc != EMST_OK) return rc;
   int64_t expected = n > 1 ? n - 1 : 0, largest = n;
@@ -258,7 +276,8 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   } else {
     num_inst = 1;
   }
-  if (expected > 0 && !out) return EMST_ERR_INVALID_ARG;
+  const bool skip_output = ex && ex->skip_output;
+  if (expected > 0 && !out && !skip_output) return EMST_ERR_INVALID_ARG;
   if (stats) {
     int32_t sz = stats->struct_size;
     std::memset(stats, 0, sizeof(emst_stats));
@@ -266,11 +285,13 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   }
   if (n == 0) return EMST_OK;
   int block = 0, carried = 1, count = 0, leaf_req = 0;
+  const float *mlp_params = nullptr;
   if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
     block = opt->block_size;
     carried = opt->carried_radius;
     count = opt->count_visits;
     leaf_req = opt->leaf_size;
+    mlp_params = opt->mlp_params;
     if (leaf_req < 0 || leaf_req > 16 || (leaf_req & (leaf_req - 1)) != 0) return EMST_ERR_INVALID_ARG;
     if (block != 0 && (block < 64 || block > 1024 || block % 32 != 0)) return EMST_ERR_INVALID_ARG;
   } else if (opt && opt->struct_size != 0) {
@@ -282,7 +303,9 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   cudaMemPool_t pool;
   if (get_pool(dev, &pool) != cudaSuccess) return EMST_ERR_CUDA;
   const bool pts_dev = device_accessible(points);
-  const bool out_dev = expected == 0 || device_accessible(out);
+  const bool out_dev = expected == 0 || skip_output || device_accessible(out);
+  const bool learned = mlp_params != nullptr;
+  const bool logging = ex && ex->log_feat;
 
   Problem P;
   P.n = n;
@@ -294,6 +317,15 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   P.edges_expected = expected;
   // (a batched problem keeps one point per leaf: chunks would mix instances)
   P.leaf = num_inst > 1 ? 1 : effective_leaf(n, leaf_req);
+  P.want_learned = learned;
+  P.want_logging = logging;
+  if (logging) {
+    P.log_feat = ex->log_feat;
+    P.log_target = ex->log_target;
+    P.log_capacity = ex->log_capacity;
+    P.log_every = ex->log_every < 1 ? 1 : ex->log_every;
+  }
+  int64_t reruns = 0;
   const size_t need = layout(P, nullptr, !pts_dev, !out_dev);
   char *base = nullptr;
   uint32_t host_counters[16] = {0};
@@ -314,6 +346,10 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   if (num_inst > 1)
     CU(cudaMemcpyAsync(P.offsets, offsets, sizeof(int64_t) * (size_t)(num_inst + 1),
                        cudaMemcpyHostToDevice, stream));
+  if (learned)
+    CU(cudaMemcpyAsync((void *)P.mlp, mlp_params, sizeof(float) * EMST_MLP_PARAMS,
+                       cudaMemcpyDefault, stream));
+  if (logging) CU(cudaMemsetAsync(P.log_count, 0, sizeof(unsigned long long), stream));
   run_build(P, true);
   tm.mark(1, stream);
   // Non-finite input is reported before any round runs.
@@ -333,12 +369,23 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
         stats->components_per_round[rounds] = n - (int64_t)host_counters[0];
       if (rounds > 0) launch_node_labels(P);
       else launch_upper_bounds(P);
+      if (learned || logging) launch_comp_sizes(P);
+      if (logging) launch_log_samples(P, rounds, rounds > 0 && carried);
       if (stats && rounds < 40) {
         cudaEventCreate(&tev[2 * rounds]);
         cudaEventCreate(&tev[2 * rounds + 1]);
         cudaEventRecord(tev[2 * rounds], stream);
       }
-      launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true);
+      if (learned) {
+        // proposed cutoffs, queries with them, then the certification rerun
+        launch_predict(P, rounds > 0 && carried);
+        launch_traverse(P, rounds > 0 && carried, nullptr, block, false, true, 1);
+        CU(cudaMemsetAsync(P.counters + 13, 0, sizeof(uint32_t), stream));
+        launch_rerun_mark(P);
+        launch_traverse(P, rounds > 0 && carried, nullptr, block, false, true, 2);
+      } else {
+        launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true);
+      }
       if (stats && rounds < 40) {
         cudaEventRecord(tev[2 * rounds + 1], stream);
         n_tev = rounds + 1;
@@ -349,13 +396,14 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
                          stream));
       CU(cudaStreamSynchronize(stream));
       if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
+      if (learned) reruns += host_counters[13];
       advance_round(P, (int64_t)host_counters[12]);
       if ((int64_t)host_counters[0] >= expected) { ++rounds; break; }
     }
     tm.mark(2, stream);
     if ((int64_t)host_counters[0] != expected) { rc = EMST_ERR_INTERNAL; goto done; }
-    run_output(P, out_dev ? out : P.out_stage);
-    if (!out_dev)
+    if (!skip_output) run_output(P, out_dev ? out : P.out_stage);
+    if (!out_dev && !skip_output)
       CU(cudaMemcpyAsync(out, P.out_stage, sizeof(emst_edge) * (size_t)expected,
                          cudaMemcpyDeviceToHost, stream));
   } else {
@@ -367,6 +415,11 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   CU(cudaStreamSynchronize(stream));
   CU(cudaGetLastError());
   rc = status_from_bits(host_counters[1]);
+  if (logging && ex->log_count_out) {
+    unsigned long long c = 0;
+    CU(cudaMemcpy(&c, P.log_count, sizeof(c), cudaMemcpyDeviceToHost));
+    *ex->log_count_out = (int64_t)c;
+  }
 done:
   cudaFreeAsync(base, stream);
   if (rc == EMST_ERR_CUDA) cudaGetLastError();
@@ -386,6 +439,8 @@ done:
       stats->traverse_ms += t;
     }
     stats->traverse_launches = n_tev;
+    stats->queried_points = learned ? (int64_t)host_counters[15] : 0;
+    stats->rerun_points = reruns;
   }
   for (int r = 0; r < n_tev; ++r) {
     cudaEventDestroy(tev[2 * r]);
@@ -502,6 +557,23 @@ int emst_compute_batched(const float *points, const int64_t *offsets, int num_in
   }
   return compute_impl(points, offsets[num_instances], dim, offsets, num_instances, out_edges,
                       out_offsets, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+int emst_learned_samples(const float *points, int64_t n, int dim, int every, float *out_features,
+                         float *out_targets, int64_t capacity, int64_t *out_count, void *stream) {
+  if (every < 1 || capacity < 0 || (capacity > 0 && (!out_features || !out_targets)) || !out_count)
+    return EMST_ERR_INVALID_ARG;
+  *out_count = 0;
+  if (capacity == 0) return EMST_OK;
+  Extras ex;
+  ex.log_feat = out_features;
+  ex.log_target = out_targets;
+  ex.log_capacity = capacity;
+  ex.log_every = every;
+  ex.log_count_out = out_count;
+  ex.skip_output = true;
+  return compute_impl(points, n, dim, nullptr, 1, nullptr, nullptr, (cudaStream_t)stream, nullptr,
+                      nullptr, &ex);
 }
 
 int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint64_t *out_codes,

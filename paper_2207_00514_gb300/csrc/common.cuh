@@ -172,6 +172,23 @@ struct Problem {
   uint32_t *inst_of = nullptr;      // n: instance of each curve position
   uint32_t *inst_root = nullptr;    // num_inst: root node of each instance's subtree
   int64_t edges_expected = 0;       // sum over instances of max(n_I - 1, 0)
+
+  // Learned radius (optional): network parameters (device, EMST_MLP_PARAMS
+  // floats), proposed cutoffs, the cutoffs used, component sizes and the
+  // list of points to rerun.
+  bool want_learned = false;         // set before layout(): carve the learned-radius arrays
+  bool want_logging = false;         // set before layout(): carve the logging counter
+  const float *mlp = nullptr;
+  float *pred_r = nullptr;
+  float *r_used = nullptr;
+  uint32_t *comp_size = nullptr;
+  uint32_t *rerun_list = nullptr;
+  // Logging of training pairs (optional).
+  float *log_feat = nullptr;
+  float *log_target = nullptr;
+  int64_t log_capacity = 0;
+  int log_every = 1;
+  unsigned long long *log_count = nullptr;
   cudaStream_t stream = nullptr;
 
   const float *points = nullptr;  // n x dim, device
@@ -209,7 +226,8 @@ struct Problem {
   emst_edge *out_stage = nullptr;    // n-1: device staging of host outputs
   uint32_t *counters = nullptr;      // [0] edges emitted, [1] status bits, [2..3] node visits (u64),
                                      // [4..9] scene box (ordered), [16..23] sort tile counters,
-                                     // [12] next round's active components,
+                                     // [12] next round's active components, [13] points
+                                     // to rerun, [14..15] reruns / queries (learned radius),
                                      // [24] scan tile counter
   uint32_t *sort_hist = nullptr;     // 8 x 256
   uint32_t *sort_lookback = nullptr; // tiles x 256
@@ -242,7 +260,7 @@ void launch_node_labels(Problem &P);
 void advance_round(Problem &P, int64_t n_active);
 void launch_upper_bounds(Problem &P);
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded);
+                     bool seeded, int learned_pass = 0);
 void launch_reduce(Problem &P);
 void launch_merge(Problem &P);
 void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
@@ -250,6 +268,11 @@ void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
 void launch_edge_keys_j(Problem &P, int64_t m);
 void launch_edge_keys_wi(Problem &P, int64_t m, int src, int shift_i);
 void launch_edge_keys_inst(Problem &P, int64_t m, int src);
+// learned.cu
+void launch_comp_sizes(Problem &P);
+void launch_predict(Problem &P, bool carried);
+void launch_rerun_mark(Problem &P);
+void launch_log_samples(Problem &P, int round, bool carried);
 void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge *out);
 
 // api.cu: helpers of the orchestration

@@ -1,0 +1,277 @@
+// traverse.cuh -- the per-point query of Algorithm 2 (nearest neighbour in
+// another component), shared by the round kernels and the learned-radius
+// sample logger.
+#pragma once
+
+#include "common.cuh"
+
+namespace emst {
+
+constexpr int kStackDepth = 100;  // > 96 = the deepest possible path (see traverse_one)
+constexpr int kWindow = 4;        // curve neighbours on each side that seed a query
+
+// Per-query state of Algorithm 2.
+struct Query {
+  float px, py, pz;
+  uint32_t me;     // the query's component label
+  float radius;    // cutoff (inclusive)
+  float best;      // best weight found
+  uint32_t bj;     // its curve index (kInvalid: none yet)
+  uint32_t bid;    // its original index
+};
+
+// A candidate j at weight d <= radius: keep the smaller (w, original id).
+__device__ __forceinline__ void take_point(Query &q, uint32_t j, float d, uint32_t idj) {
+  if (q.bj == kInvalid || d < q.best) {  // first candidate, or strictly closer
+    q.best = d;
+    q.bj = j;
+    q.bid = idj;
+    q.radius = d;
+  } else if (d == q.best && idj < q.bid) {
+    q.bj = j;
+    q.bid = idj;
+  }
+}
+
+// A leaf of the hierarchy is a chunk of `leaf` consecutive curve positions
+// (the last one may be shorter).  A one-point leaf's box IS the point, so its
+// box distance d is already the exact weight and its label was tested with
+// the box; its original id is loaded only to break an exact tie.  A longer
+// chunk is scanned point by point.
+template <bool CHUNKS>
+__device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, float d1, int leaf, int64_t n,
+                                           const float4 *__restrict__ pts,
+                                           const uint32_t *__restrict__ labels) {
+  if (!CHUNKS) {
+    if (q.bj == kInvalid || d1 < q.best) {
+      q.best = d1;
+      q.bj = c;
+      q.bid = kInvalid;  // loaded lazily
+      q.radius = d1;
+    } else if (d1 == q.best) {
+      const uint32_t idj = __float_as_uint(pts[c].w);
+      if (q.bid == kInvalid) q.bid = __float_as_uint(pts[q.bj].w);
+      if (idj < q.bid) { q.bj = c; q.bid = idj; }
+    }
+    return;
+  }
+  if (q.bid == kInvalid && q.bj != kInvalid) q.bid = __float_as_uint(pts[q.bj].w);
+  const int64_t lo = (int64_t)c * leaf;
+  const int64_t hi = lo + leaf < n ? lo + leaf : n;
+  for (int64_t k = lo; k < hi; ++k) {
+    if (__ldg(labels + k) == q.me) continue;
+    const float4 t = __ldg(pts + k);
+    const float d = sq_dist(q.px, q.py, q.pz, t.x, t.y, t.z);
+    if (d <= q.radius) take_point(q, (uint32_t)k, d, __float_as_uint(t.w));
+  }
+}
+
+// Depth-first search of the subtree of internal node `node`, whose own box
+// the caller has already accepted: test both children of every visited
+// record, scan accepted leaf chunks, descend into the nearer accepted
+// internal child and stack the farther one with its box distance (re-tested
+// when popped).
+template <bool COUNT, bool CHUNKS>
+__device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
+                                        const float4 *__restrict__ pts,
+                                        const uint32_t *__restrict__ labels, int leaf, int64_t n,
+                                        uint32_t *st_node, float *st_dist,
+                                        unsigned long long &nvis) {
+  int sp = 0;
+  while (true) {
+    if (COUNT) ++nvis;
+    const float4 *r = reinterpret_cast<const float4 *>(nodes + node);
+    const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+    const uint4 dd = __ldg(reinterpret_cast<const uint4 *>(r + 3));
+    const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
+    const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
+    bool okL = (dd.z != q.me) && (dL <= q.radius);
+    bool okR = (dd.w != q.me) && (dR <= q.radius);
+    if (okL && (dd.x & kLeafBit)) { scan_chunk<CHUNKS>(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels); okL = false; }
+    if (okR && (dd.y & kLeafBit)) {
+      if (dR <= q.radius) scan_chunk<CHUNKS>(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels);
+      okR = false;
+    }
+    okL = okL && dL <= q.radius;
+    okR = okR && dR <= q.radius;
+    if (okL && okR) {
+      if (sp >= kStackDepth) return false;
+      if (dL <= dR) { st_node[sp] = dd.y; st_dist[sp] = dR; node = dd.x; }
+      else { st_node[sp] = dd.x; st_dist[sp] = dL; node = dd.y; }
+      ++sp;
+      continue;
+    }
+    if (okL) { node = dd.x; continue; }
+    if (okR) { node = dd.y; continue; }
+    bool found = false;
+    while (sp > 0) {
+      --sp;
+      if (st_dist[sp] <= q.radius) { node = st_node[sp]; found = true; break; }
+    }
+    if (!found) return true;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A7. Nearest other-component neighbour of every point (Algorithm 2), one
+// thread per point in curve order (neighbouring threads get nearby queries).
+//  - cutoff: the component's upper bound (Optimization 2), optionally
+//    tightened by the previous round's neighbour when it still lies in
+//    another component (a real cross edge of this point, so never below the
+//    component minimum);
+//  - a child is examined only if its label differs from the query's
+//    (Optimization 1) and its box is within the cutoff (inclusive: equal
+//    weights with smaller ids must survive); a leaf updates the best
+//    (w, original id) and shrinks the cutoff to w.
+// The leaves of the hierarchy are chunks of `leaf` consecutive curve
+// positions; an accepted chunk is scanned point by point.
+// The stack never overflows: every split of the hierarchy uses a strictly
+// later bit of the 96-bit augmented key (64-bit code + 32-bit index), so a
+// root-to-leaf path has at most 96 internal nodes and at most one stacked
+// sibling per level.
+// Ends with the first half of the per-component minimum (A8): an atomicMin of
+// (w bits << 32 | min original id) per component.
+// SEEDED (the emst_compute path) also tightens each cutoff with the
+// component's best weight found so far and with the point's best curve
+// neighbour in another component (both real cross edges, so never below the
+// component minimum), reports the exact nearest neighbour within that cutoff
+// (or none), and keeps a per-point lower bound for the next round (res.x):
+// a point whose bound exceeds its component's cutoff skips its query.  The
+// endpoint of every component's minimum edge still finds it, so the minima
+// (and the tree) are unchanged; which other points report differs.
+// Unseeded, each point reports exactly its nearest other-component point
+// within its cutoff (what the inspection entry point exposes).
+// ---------------------------------------------------------------------------
+struct TravArgs {
+  const float4 *pts;
+  const NodeRec *nodes;
+  const uint32_t *labels;
+  const uint32_t *bound;
+  const float *radius_in;
+  int leaf;
+  const uint32_t *inst_of;
+  const uint32_t *inst_root;
+  const int64_t *offsets;
+  uint2 *res;
+  uint32_t *res_id;
+  uint64_t *comp_key;
+  int64_t n;
+  uint32_t *status;
+  unsigned long long *visits;
+  const float *pred_r;  // LEARNED: proposed cutoff of each point
+  float *r_used;        // LEARNED: cutoff each query was exact within (+inf: skipped)
+};
+
+// LEARNED also tightens the cutoff with the proposed radius pred_r[i] (any
+// value: exactness is restored afterwards by rerunning every point whose
+// cutoff fell below its component's found minimum) and records it in r_used.
+template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED>
+__device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
+  const float kInf = __int_as_float(0x7f800000);
+  const int64_t n = A.n;
+  // Batched form: search only this point's instance (its subtree, its curve range).
+  uint32_t start = 0u;
+  int64_t wlo = 0, whi = n;
+  if (A.inst_of) {
+    const uint32_t I = __ldg(A.inst_of + i);
+    start = __ldg(A.inst_root + I);
+    wlo = __ldg(A.offsets + I);
+    whi = __ldg(A.offsets + I + 1);
+    if (start == kInvalid) {  // a one-point instance: nothing to find
+      A.res[i] = make_uint2(0u, kInvalid);
+      A.res_id[i] = kInvalid;
+      if (LEARNED) A.r_used[i] = kInf;
+      return;
+    }
+  }
+  const float4 p = A.pts[i];
+  Query q;
+  q.px = p.x;
+  q.py = p.y;
+  q.pz = p.z;
+  q.me = A.labels[i];
+  q.best = kInf;
+  q.bj = kInvalid;
+  q.bid = kInvalid;
+  if (RADIUS_IN) q.radius = A.radius_in[i];
+  else q.radius = bound_to_radius(A.bound[q.me]);
+  uint2 prev = make_uint2(0u, kInvalid);
+  if (CARRIED) prev = A.res[i];
+  if (SEEDED) {
+    // The component's best weight found so far this round: a real cross edge
+    // of the component, so never below its minimum.
+    const uint32_t cw =
+        (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(A.comp_key + q.me)) >> 32);
+    q.radius = fminf(q.radius, bound_to_radius(cw));
+    // prev.x is a lower bound of this point's nearest other-component weight
+    // (components only grow, so that weight never decreases).  Above the
+    // component-level cutoff, this point cannot be an endpoint of the
+    // component's minimum edge: skip the query.
+    if (CARRIED && __uint_as_float(prev.x) > q.radius) {
+      A.res[i] = make_uint2(prev.x, kInvalid);
+      A.res_id[i] = kInvalid;
+      if (LEARNED) A.r_used[i] = kInf;
+      return;
+    }
+  }
+  // The previous round's neighbour, if still in another component, is a real
+  // cross edge of this point: a per-point cutoff.
+  if (CARRIED && prev.y != kInvalid && A.labels[prev.y] != q.me)
+    q.radius = fminf(q.radius, __uint_as_float(prev.x));
+  if (SEEDED) {
+    // Curve neighbours within kWindow positions in other components: real
+    // candidates, so their best weight is a valid (inclusive) cutoff.
+#pragma unroll
+    for (int o = -kWindow; o <= kWindow; ++o) {
+      const int64_t j = i + o;
+      if (o == 0 || j < wlo || j >= whi) continue;
+      if (__ldg(A.labels + j) == q.me) continue;
+      const float4 c = __ldg(A.pts + j);
+      const float d = sq_dist(q.px, q.py, q.pz, c.x, c.y, c.z);
+      const uint32_t idj = __float_as_uint(c.w);
+      if (q.bj == kInvalid || d < q.best || (d == q.best && idj < q.bid)) {
+        q.best = d;
+        q.bj = (uint32_t)j;
+        q.bid = idj;
+      }
+    }
+    q.radius = fminf(q.radius, q.best);
+  }
+  if (LEARNED) q.radius = fminf(q.radius, __ldg(A.pred_r + i));
+  const float r0 = q.radius;  // the search is exact within this cutoff
+  if (LEARNED) A.r_used[i] = r0;
+  uint32_t st_node[kStackDepth];
+  float st_dist[kStackDepth];
+  unsigned long long nvis = 0;
+  const bool ok = explore<COUNT, CHUNKS>(q, start, A.nodes, A.pts, A.labels, A.leaf, n, st_node,
+                                         st_dist, nvis);
+  if (!ok) atomicOr(A.status, kErrStack);
+  if (COUNT) {
+    // one atomic per warp: sum the active lanes' counts first
+    const unsigned mask = __activemask();
+    const unsigned v = __reduce_add_sync(mask, (unsigned)nvis);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) atomicAdd(A.visits, (unsigned long long)v);
+  }
+  if (SEEDED) {
+    // Report only the exact nearest neighbour within r0 (a seed beyond r0 is
+    // dropped); keep in res.x a lower bound for the next round: the found
+    // weight, or r0 when nothing lies within it.
+    const bool found = q.bj != kInvalid && q.best <= r0;
+    if (!found) q.bj = kInvalid;
+    const float lb = found ? q.best : (r0 < kInf ? r0 : 0.0f);
+    A.res[i] = make_uint2(__float_as_uint(lb), q.bj);
+  } else {
+    A.res[i] = make_uint2(__float_as_uint(q.best), q.bj);
+  }
+  if (q.bj != kInvalid) {
+    const uint32_t oi = __float_as_uint(p.w);
+    const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(A.pts[q.bj].w);
+    A.res_id[i] = oj;
+    const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
+    atomicMin(reinterpret_cast<unsigned long long *>(A.comp_key + q.me), (unsigned long long)key);
+  } else {
+    A.res_id[i] = kInvalid;
+  }
+}
+
+}  // namespace emst

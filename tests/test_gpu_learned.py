@@ -1,0 +1,125 @@
+"""The learned search radius: network kernels against the FP64 oracle, and
+the guarantee that any proposal leaves the spanning tree unchanged."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2207_00514_gb300 as p
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p.load_library()
+    return p
+
+
+def _params(seed, scale=1.0):
+    g = np.random.default_rng(seed)
+    p = mlp.init_params(seed, in_mu=g.standard_normal(mlp.IN), in_sigma=g.random(mlp.IN) + 0.5,
+                        out_mu=-20.0, out_sigma=3.0, margin=0.25)
+    d = mlp.unpack(p)
+    for name in ("b1", "b2", "b3"):
+        d[name] = g.standard_normal(mlp.HID) * 0.2
+    d["W1"] = d["W1"] * scale
+    return mlp.pack(d).astype(np.float32)
+
+
+def _features(seed, m):
+    g = np.random.default_rng(seed)
+    return (g.standard_normal((m, mlp.IN)) * 2).astype(np.float32)
+
+
+def test_forward_matches_oracle(pkg):
+    p = _params(1)
+    f = _features(2, 5000 + 7)  # several warp tiles and a ragged tail
+    got = pkg.emst_mlp_forward(torch.from_numpy(f).cuda(), torch.from_numpy(p).cuda()).cpu().numpy()
+    want = mlp.forward_bf16(p, f)
+    err = np.abs(got - want)
+    scale = 1.0 + np.abs(want)
+    assert np.median(err / scale) < 1e-4
+    assert np.max(err / scale) < 2e-2  # a rare BF16 rounding-boundary flip of one hidden activation
+
+
+def test_grad_matches_oracle(pkg):
+    p = _params(3)
+    f = _features(4, 3000)
+    g = np.random.default_rng(5)
+    t = (g.standard_normal(3000) * 3 - 20).astype(np.float32)
+    grad = torch.zeros(mlp.NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    pkg.emst_mlp_grad(torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(p).cuda(),
+                      grad, loss)
+    L, G = mlp.loss_and_grad(p.astype(np.float64), f.astype(np.float64), t.astype(np.float64))
+    got = grad.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - L) <= 1e-4 * max(1.0, L)
+    assert np.linalg.norm(got - G) <= 1e-4 * np.linalg.norm(G)
+    big = np.abs(G) > 1e-3 * np.abs(G).max()
+    assert np.allclose(got[big], G[big], rtol=2e-3)
+
+
+def test_adam_step(pkg):
+    p = _params(6)
+    g = np.random.default_rng(7).standard_normal(mlp.NPARAM).astype(np.float32)
+    P = torch.from_numpy(p.copy()).cuda()
+    G = torch.from_numpy(g.copy()).cuda()
+    m1 = torch.zeros_like(P)
+    m2 = torch.zeros_like(P)
+    pkg.emst_mlp_adam(P, G, m1, m2, 1, 1e-2)
+    # first Adam step: the update is lr * g / (|g| + eps) on trainable entries
+    want = p.astype(np.float64).copy()
+    tr = np.arange(mlp.TRAINABLE_FROM, mlp.NPARAM)
+    want[tr] -= 1e-2 * g[tr] / (np.abs(g[tr]) + 1e-8)
+    assert np.allclose(P.cpu().numpy(), want, rtol=1e-5, atol=1e-6)
+    assert torch.count_nonzero(G).item() == mlp.TRAINABLE_FROM  # trainable part cleared
+
+
+def test_logged_pairs(pkg):
+    pts = synth.halos(20_000, 11)
+    f, t = pkg.emst_learned_samples(torch.from_numpy(pts).cuda(), every=4, capacity=100_000)
+    f, t = f.cpu().numpy(), t.cpu().numpy()
+    assert len(t) > 1000 and np.all(np.isfinite(f)) and np.all(np.isfinite(t))
+    # position features lie in the unit box; targets are log2 of squared distances in it
+    assert f[:, :3].min() >= 0 and f[:, :3].max() <= 1
+    assert t.max() <= np.log2(3.0) + 1e-6
+    # first-round pairs (component size 1, no lower bound yet): the target is
+    # the point's nearest-neighbour weight, never below the smallest curve-window weight
+    first = (f[:, 5] == 0) & (f[:, 6] < -90)
+    assert first.sum() > 100
+    assert np.all(t[first] <= f[first, 3] + 1e-5)
+
+
+@pytest.mark.parametrize("kind", ["random", "tiny", "huge"])
+def test_any_proposal_keeps_the_tree(pkg, kind):
+    pts = synth.halos(60_000, 12)
+    x = torch.from_numpy(pts).cuda()
+    plain = pkg.edges_numpy(pkg.emst_compute(x))
+    p = _params(8)
+    if kind == "tiny":
+        p[16], p[17], p[18] = -120.0, 1e-3, 0.0  # proposes ~2^-120: every query reruns
+    elif kind == "huge":
+        p[16], p[17], p[18] = 10.0, 1e-3, 0.0    # proposes ~2^10: never binding
+    e, st = pkg.emst_compute_ex(x, mlp_params=torch.from_numpy(p).cuda())
+    assert np.array_equal(pkg.edges_numpy(e).view(np.uint8), plain.view(np.uint8))
+    assert st["queried_points"] > 0
+    if kind == "tiny":
+        assert st["rerun_points"] > 0
+    if kind == "huge":
+        assert st["rerun_points"] == 0
+
+
+def test_batched_and_2d_with_proposal(pkg):
+    p = torch.from_numpy(_params(9)).cuda()
+    pts = synth.blobs(30_000, 2, 13)
+    x = torch.from_numpy(pts).cuda()
+    e, _ = pkg.emst_compute_ex(x, mlp_params=p)
+    assert np.array_equal(pkg.edges_numpy(e).view(np.uint8), pkg.edges_numpy(pkg.emst_compute(x)).view(np.uint8))
