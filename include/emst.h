@@ -103,7 +103,9 @@ typedef struct emst_stats {
   int64_t queried_points;  /* learned radius: queries that used a proposed cutoff */
   int64_t rerun_points;    /* learned radius: of those, rerun because the cutoff fell below
                               their component's found minimum */
-  int64_t reserved[4];
+  double learned_search_ms; /* learned radius: device time of the searches with the proposed
+                               cutoffs alone (traverse_ms adds inference and the reruns) */
+  int64_t reserved[3];
 } emst_stats;
 
 /* EMST of n points (§3, Fig. 3 end to end).

@@ -80,7 +80,7 @@ class _Stats(ctypes.Structure):
                 ("traverse_ms", ctypes.c_double), ("traverse_launches", ctypes.c_int32),
                 ("reserved1", ctypes.c_int32), ("round_traverse_ms", ctypes.c_double * 40),
                 ("queried_points", ctypes.c_int64), ("rerun_points", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("learned_search_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 3)]
 
 
 _lock = threading.Lock()
@@ -248,7 +248,8 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
                  traverse_launches=st.traverse_launches,
                  round_traverse_ms=[float(st.round_traverse_ms[k]) for k in range(min(st.rounds, 40))],
                  components_per_round=[int(st.components_per_round[k]) for k in range(min(st.rounds, 40))],
-                 queried_points=st.queried_points, rerun_points=st.rerun_points)
+                 queried_points=st.queried_points, rerun_points=st.rerun_points,
+                 learned_search_ms=st.learned_search_ms)
     return out_edges, stats
 
 

@@ -332,6 +332,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   Timer tm;
   int rounds = 0;
   cudaEvent_t tev[2 * 40];
+  cudaEvent_t lev[2 * 40] = {nullptr};  // learned: around the proposed-cutoff search
   int n_tev = 0;
   if (cudaMallocFromPoolAsync((void **)&base, need, pool, stream) != cudaSuccess) {
     cudaGetLastError();
@@ -379,7 +380,15 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
       if (learned) {
         // proposed cutoffs, queries with them, then the certification rerun
         launch_predict(P, rounds > 0 && carried);
+        if (stats && rounds < 40) {
+          cudaEventCreate(&lev[2 * rounds]);
+          cudaEventRecord(lev[2 * rounds], stream);
+        }
         launch_traverse(P, rounds > 0 && carried, nullptr, block, false, true, 1);
+        if (stats && rounds < 40) {
+          cudaEventCreate(&lev[2 * rounds + 1]);
+          cudaEventRecord(lev[2 * rounds + 1], stream);
+        }
         CU(cudaMemsetAsync(P.counters + 13, 0, sizeof(uint32_t), stream));
         launch_rerun_mark(P);
         launch_traverse(P, rounds > 0 && carried, nullptr, block, false, true, 2);
@@ -441,7 +450,14 @@ done:
     stats->traverse_launches = n_tev;
     stats->queried_points = learned ? (int64_t)host_counters[15] : 0;
     stats->rerun_points = reruns;
+    for (int r = 0; r < n_tev && learned; ++r) {
+      float t = 0.f;
+      if (lev[2 * r] && lev[2 * r + 1]) cudaEventElapsedTime(&t, lev[2 * r], lev[2 * r + 1]);
+      stats->learned_search_ms += t;
+    }
   }
+  for (int r = 0; r < 2 * 40; ++r)
+    if (lev[r]) cudaEventDestroy(lev[r]);
   for (int r = 0; r < n_tev; ++r) {
     cudaEventDestroy(tev[2 * r]);
     cudaEventDestroy(tev[2 * r + 1]);

@@ -285,6 +285,18 @@ __global__ void __launch_bounds__(256) k_predict(FeatArgs A, const float *__rest
   const int64_t tiles = (A.n + 31) / 32;
   for (int64_t tile = (int64_t)blockIdx.x * 8 + warp; tile < tiles; tile += (int64_t)gridDim.x * 8) {
     const int64_t i = tile * 32 + lane;
+    // a query whose lower bound exceeds its component's cutoff is skipped by
+    // the search anyway: a warp whose 32 points are all skipped does no work
+    bool skip = i >= A.n;
+    if (!skip && A.carried) {
+      const uint32_t me = A.labels[i];
+      float U = bound_to_radius(A.bound[me]);
+      const uint32_t cw =
+          (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(A.comp_key + me)) >> 32);
+      U = fminf(U, bound_to_radius(cw));
+      skip = __uint_as_float(A.res[i].x) > U;
+    }
+    if (__all_sync(0xffffffffu, skip)) continue;
     float f[kIn];
     float U = 0.f, lb = 0.f;
     if (i < A.n) point_features(A, i, f, U, lb);
