@@ -384,14 +384,14 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
           cudaEventCreate(&lev[2 * rounds]);
           cudaEventRecord(lev[2 * rounds], stream);
         }
-        launch_traverse(P, rounds > 0 && carried, nullptr, block, false, true, 1);
+        launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, 1);
         if (stats && rounds < 40) {
           cudaEventCreate(&lev[2 * rounds + 1]);
           cudaEventRecord(lev[2 * rounds + 1], stream);
         }
         CU(cudaMemsetAsync(P.counters + 13, 0, sizeof(uint32_t), stream));
         launch_rerun_mark(P);
-        launch_traverse(P, rounds > 0 && carried, nullptr, block, false, true, 2);
+        launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, 2);
       } else {
         launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true);
       }

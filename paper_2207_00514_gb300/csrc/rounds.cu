@@ -217,7 +217,11 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   } else if (!seeded) {
     EMST_TRAV(false, false, false, false, false);
   } else if (learned_pass == 1) {
-    if (carried) EMST_TRAV(true, false, false, true, true); else EMST_TRAV(false, false, false, true, true);
+    if (carried) {
+      if (count) EMST_TRAV(true, false, true, true, true); else EMST_TRAV(true, false, false, true, true);
+    } else {
+      if (count) EMST_TRAV(false, false, true, true, true); else EMST_TRAV(false, false, false, true, true);
+    }
   } else if (carried) {
     if (count) EMST_TRAV(true, false, true, true, false); else EMST_TRAV(true, false, false, true, false);
   } else {
