@@ -329,6 +329,20 @@ def main():
     vis = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, count_visits=True)[1]
     torch.cuda.synchronize(dev)
     visits_per_query_round = vis["node_visits"] / float(n * max(vis["rounds"], 1))
+    # the learned-radius form on the same input (committed network), untimed
+    learned_form = None
+    try:
+        from paper_2207_00514_gb300 import learned
+        params = learned.load(device=dev)
+        for _ in range(2):
+            lst = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, mlp_params=params)[1]
+        torch.cuda.synchronize(dev)
+        learned_form = {"total_ms": round(lst["total_ms"], 3), "traverse_ms": round(lst["traverse_ms"], 3),
+                        "search_with_proposed_cutoffs_ms": round(lst["learned_search_ms"], 3),
+                        "rerun_fraction": lst["rerun_points"] / max(lst["queried_points"], 1),
+                        "mpoints_per_s": n / lst["total_ms"] / 1e3}
+    except FileNotFoundError:
+        learned_form = None
     # other leaf chunk sizes, untimed, for comparison
     leaf_sweep = {}
     for leaf in (2, 4, 8):
@@ -377,6 +391,7 @@ def main():
                        "components_per_round": comps,
                        "node_visits_per_query_per_round": round(visits_per_query_round, 2),
                        "leaf_size": 1,
+                       "learned_radius_form_untimed": learned_form,
                        "other_leaf_sizes_untimed": leaf_sweep,
                        "mfeatures_per_s": value * 3},
             "roofline": roofline,
