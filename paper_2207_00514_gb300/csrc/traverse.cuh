@@ -121,9 +121,9 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
 // nearer child) and the other one is stacked in shared memory with its box
 // and label, so every lane re-tests it when popped.  Each lane visits every
 // node it would visit alone (and possibly more), so its result is the same.
-// Inactive lanes (no query, or skipped) take part with no wants.  The warp
-// starts at the root of the subtree all its active lanes search (in a batch,
-// their common instance's subtree).
+// Inactive lanes (no query, or skipped) take part with no wants.  Children
+// outside [lo, hi) -- another instance of a batch -- are never wanted
+// (internal node ids and leaf ids of an instance's subtree lie in its range).
 struct WarpStack {
   uint32_t node[kStackDepth];
   uint32_t lab[kStackDepth];
@@ -131,7 +131,7 @@ struct WarpStack {
 };
 
 template <bool COUNT>
-__device__ __forceinline__ bool explore_warp(Query &q, bool active,
+__device__ __forceinline__ bool explore_warp(Query &q, bool active, int64_t lo, int64_t hi,
                                              uint32_t node, const NodeRec *__restrict__ nodes,
                                              const float4 *__restrict__ pts, WarpStack &S,
                                              unsigned long long &nvis) {
@@ -146,8 +146,8 @@ __device__ __forceinline__ bool explore_warp(Query &q, bool active,
     const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
     const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
     const uint32_t iL = dd.x & ~kLeafBit, iR = dd.y & ~kLeafBit;
-    bool okL = active && dd.z != q.me && dL <= q.radius;
-    bool okR = active && dd.w != q.me && dR <= q.radius;
+    bool okL = active && (int64_t)iL >= lo && (int64_t)iL < hi && dd.z != q.me && dL <= q.radius;
+    bool okR = active && (int64_t)iR >= lo && (int64_t)iR < hi && dd.w != q.me && dR <= q.radius;
     if (okL && (dd.x & kLeafBit)) { scan_chunk<false>(q, iL, dL, 1, 0, pts, nullptr); okL = false; }
     if (okR && (dd.y & kLeafBit)) {
       if (dR <= q.radius) scan_chunk<false>(q, iR, dR, 1, 0, pts, nullptr);
@@ -178,8 +178,9 @@ __device__ __forceinline__ bool explore_warp(Query &q, bool active,
     while (sp > 0) {
       --sp;
       const uint32_t ref = S.node[sp];
+      const uint32_t idx = ref & ~kLeafBit;
       const float *bx = S.box[sp];
-      const bool need = active && S.lab[sp] != q.me &&
+      const bool need = active && (int64_t)idx >= lo && (int64_t)idx < hi && S.lab[sp] != q.me &&
                         box_dist(q.px, q.py, q.pz, bx[0], bx[1], bx[2], bx[3], bx[4], bx[5]) <= q.radius;
       if (__any_sync(kAll, need)) { node = ref; found = true; break; }
     }
@@ -315,26 +316,9 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i, WarpS
       }
     }
     unsigned long long nvis = 0;
-    // The warp searches together when its active lanes share one subtree (one
-    // instance); a warp across an instance boundary searches lane by lane.
-    const unsigned kAll = 0xffffffffu;
-    const uint32_t inst = active ? (A.inst_of ? __ldg(A.inst_of + i) : 0u) : kInvalid;
-    const uint32_t inst0 = __reduce_min_sync(kAll, inst);
-    bool ok = true;
-    if (inst0 != kInvalid) {
-      if (__all_sync(kAll, inst == kInvalid || inst == inst0)) {
-        start = A.inst_of ? __ldg(A.inst_root + inst0) : 0u;
-        ok = explore_warp<COUNT>(q, active, start, A.nodes, A.pts, *ws, nvis);
-        if (COUNT && (threadIdx.x & 31) == 0) atomicAdd(A.visits, nvis);
-      } else if (active) {
-        uint32_t st_node[kStackDepth];
-        float st_dist[kStackDepth];
-        ok = explore<COUNT, false>(q, __ldg(A.inst_root + inst), A.nodes, A.pts, A.labels, 1, n,
-                                   st_node, st_dist, nvis);
-        if (COUNT) atomicAdd(A.visits, nvis);
-      }
-    }
-    if (!ok) atomicOr(A.status, kErrStack);
+    const bool ok = explore_warp<COUNT>(q, active, wlo, whi, start, A.nodes, A.pts, *ws, nvis);
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(A.status, kErrStack);
+    if (COUNT && (threadIdx.x & 31) == 0) atomicAdd(A.visits, nvis);
     if (!active) return;
     const bool found = q.bj != kInvalid && q.best <= r0;
     if (!found) q.bj = kInvalid;
