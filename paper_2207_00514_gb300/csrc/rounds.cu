@@ -170,12 +170,6 @@ template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bo
 __global__ void __launch_bounds__(kBlock) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (SEEDED && !CHUNKS && !list) {  // the warp-cooperative search (see explore_warp)
-    __shared__ WarpStack stacks[kBlock / 32];
-    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, true>(A, gid,
-                                                                           &stacks[threadIdx.x >> 5]);
-    return;
-  }
   if (list) {
     const int64_t count = *list_count;
     for (int64_t t = gid; t < count; t += (int64_t)gridDim.x * blockDim.x)
@@ -208,9 +202,6 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   A.r_used = P.r_used;
   // learned_pass: 0 = plain, 1 = with the proposed radii, 2 = rerun of the
   // listed points with the plain cutoff
-  // the warp-cooperative search keeps its stacks in static shared memory
-  // sized for 256-thread CTAs
-  if (seeded && !radius_in && P.leaf == 1 && learned_pass != 2) block = kBlock;
   const uint32_t *list = learned_pass == 2 ? P.rerun_list : nullptr;
   const uint32_t *list_count = learned_pass == 2 ? P.counters + 13 : nullptr;
   const int g = learned_pass == 2 ? 152 * 8 : grid_for(P.n, block);

@@ -112,83 +112,6 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
   }
 }
 
-// Warp-cooperative form of the same search: the 32 lanes (neighbouring
-// queries in curve order) walk ONE node sequence, the union of what they
-// need, so each record is one broadcast load for the warp instead of one load
-// per lane, and all lanes stay converged.  Every lane tests both children
-// against its own cutoff and takes its own leaves; an internal child is
-// entered if any lane wants it (the warp goes first where more lanes have the
-// nearer child) and the other one is stacked in shared memory with its box
-// and label, so every lane re-tests it when popped.  Each lane visits every
-// node it would visit alone (and possibly more), so its result is the same.
-// Inactive lanes (no query, or skipped) take part with no wants.  Children
-// outside [lo, hi) -- another instance of a batch -- are never wanted
-// (internal node ids and leaf ids of an instance's subtree lie in its range).
-struct WarpStack {
-  uint32_t node[kStackDepth];
-  uint32_t lab[kStackDepth];
-  float box[kStackDepth][6];
-};
-
-template <bool COUNT>
-__device__ __forceinline__ bool explore_warp(Query &q, bool active, int64_t lo, int64_t hi,
-                                             uint32_t node, const NodeRec *__restrict__ nodes,
-                                             const float4 *__restrict__ pts, WarpStack &S,
-                                             unsigned long long &nvis) {
-  const unsigned kAll = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  int sp = 0;
-  while (true) {
-    if (COUNT && lane == 0) ++nvis;
-    const float4 *r = reinterpret_cast<const float4 *>(nodes + node);
-    const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
-    const uint4 dd = __ldg(reinterpret_cast<const uint4 *>(r + 3));
-    const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
-    const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
-    const uint32_t iL = dd.x & ~kLeafBit, iR = dd.y & ~kLeafBit;
-    bool okL = active && (int64_t)iL >= lo && (int64_t)iL < hi && dd.z != q.me && dL <= q.radius;
-    bool okR = active && (int64_t)iR >= lo && (int64_t)iR < hi && dd.w != q.me && dR <= q.radius;
-    if (okL && (dd.x & kLeafBit)) { scan_chunk<false>(q, iL, dL, 1, 0, pts, nullptr); okL = false; }
-    if (okR && (dd.y & kLeafBit)) {
-      if (dR <= q.radius) scan_chunk<false>(q, iR, dR, 1, 0, pts, nullptr);
-      okR = false;
-    }
-    const bool wL = okL && dL <= q.radius, wR = okR && dR <= q.radius;
-    const unsigned bL = __ballot_sync(kAll, wL), bR = __ballot_sync(kAll, wR);
-    if (bL && bR) {
-      const int nearL = __popc(__ballot_sync(kAll, wL && (!wR || dL <= dR)));
-      const int nearR = __popc(__ballot_sync(kAll, wR && (!wL || dR < dL)));
-      const bool goL = nearL >= nearR;
-      if (sp >= kStackDepth) return false;
-      if (lane == 0) {
-        S.node[sp] = goL ? dd.y : dd.x;
-        S.lab[sp] = goL ? dd.w : dd.z;
-        const float *f = reinterpret_cast<const float *>(r) + (goL ? 6 : 0);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) S.box[sp][k] = __ldg(f + k);
-      }
-      __syncwarp();
-      ++sp;
-      node = goL ? dd.x : dd.y;
-      continue;
-    }
-    if (bL) { node = dd.x; continue; }
-    if (bR) { node = dd.y; continue; }
-    bool found = false;
-    while (sp > 0) {
-      --sp;
-      const uint32_t ref = S.node[sp];
-      const uint32_t idx = ref & ~kLeafBit;
-      const float *bx = S.box[sp];
-      const bool need = active && (int64_t)idx >= lo && (int64_t)idx < hi && S.lab[sp] != q.me &&
-                        box_dist(q.px, q.py, q.pz, bx[0], bx[1], bx[2], bx[3], bx[4], bx[5]) <= q.radius;
-      if (__any_sync(kAll, need)) { node = ref; found = true; break; }
-    }
-    __syncwarp();
-    if (!found) return true;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // A7. Nearest other-component neighbour of every point (Algorithm 2), one
 // thread per point in curve order (neighbouring threads get nearby queries).
@@ -242,99 +165,10 @@ struct TravArgs {
 // LEARNED also tightens the cutoff with the proposed radius pred_r[i] (any
 // value: exactness is restored afterwards by rerunning every point whose
 // cutoff fell below its component's found minimum) and records it in r_used.
-// PACKET: the warp-cooperative search (explore_warp); then every lane of the
-// warp must call this function together (i >= n for a lane without a point).
-template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
-          bool PACKET = false>
-__device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i, WarpStack *ws = nullptr) {
+template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED>
+__device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   const float kInf = __int_as_float(0x7f800000);
   const int64_t n = A.n;
-  if (PACKET) {
-    // all lanes reach the search; a lane without a query only helps
-    bool active = i < n;
-    uint32_t start = 0u;
-    int64_t wlo = 0, whi = n;
-    Query q;
-    q.radius = -1.0f;
-    q.best = kInf;
-    q.bj = kInvalid;
-    q.bid = kInvalid;
-    q.px = q.py = q.pz = 0.f;
-    q.me = kInvalid;
-    float r0 = -1.0f;
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (active && A.inst_of) {
-      const uint32_t I = __ldg(A.inst_of + i);
-      wlo = __ldg(A.offsets + I);
-      whi = __ldg(A.offsets + I + 1);
-      if (__ldg(A.inst_root + I) == kInvalid) {
-        A.res[i] = make_uint2(0u, kInvalid);
-        A.res_id[i] = kInvalid;
-        if (LEARNED) A.r_used[i] = kInf;
-        active = false;
-      }
-    }
-    if (active) {
-      p = A.pts[i];
-      q.px = p.x;
-      q.py = p.y;
-      q.pz = p.z;
-      q.me = A.labels[i];
-      q.radius = bound_to_radius(A.bound[q.me]);
-      uint2 prev = make_uint2(0u, kInvalid);
-      if (CARRIED) prev = A.res[i];
-      const uint32_t cw =
-          (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(A.comp_key + q.me)) >> 32);
-      q.radius = fminf(q.radius, bound_to_radius(cw));
-      if (CARRIED && __uint_as_float(prev.x) > q.radius) {  // cannot hold the minimum: skip
-        A.res[i] = make_uint2(prev.x, kInvalid);
-        A.res_id[i] = kInvalid;
-        if (LEARNED) A.r_used[i] = kInf;
-        active = false;
-        q.radius = -1.0f;
-      } else {
-        if (CARRIED && prev.y != kInvalid && A.labels[prev.y] != q.me)
-          q.radius = fminf(q.radius, __uint_as_float(prev.x));
-#pragma unroll
-        for (int o = -kWindow; o <= kWindow; ++o) {
-          const int64_t j = i + o;
-          if (o == 0 || j < wlo || j >= whi) continue;
-          if (__ldg(A.labels + j) == q.me) continue;
-          const float4 c = __ldg(A.pts + j);
-          const float d = sq_dist(q.px, q.py, q.pz, c.x, c.y, c.z);
-          const uint32_t idj = __float_as_uint(c.w);
-          if (q.bj == kInvalid || d < q.best || (d == q.best && idj < q.bid)) {
-            q.best = d;
-            q.bj = (uint32_t)j;
-            q.bid = idj;
-          }
-        }
-        q.radius = fminf(q.radius, q.best);
-        if (LEARNED) q.radius = fminf(q.radius, __ldg(A.pred_r + i));
-        r0 = q.radius;
-        if (LEARNED) A.r_used[i] = r0;
-      }
-    }
-    unsigned long long nvis = 0;
-    const bool ok = explore_warp<COUNT>(q, active, wlo, whi, start, A.nodes, A.pts, *ws, nvis);
-    if (!ok && (threadIdx.x & 31) == 0) atomicOr(A.status, kErrStack);
-    if (COUNT && (threadIdx.x & 31) == 0) atomicAdd(A.visits, nvis);
-    if (!active) return;
-    const bool found = q.bj != kInvalid && q.best <= r0;
-    if (!found) q.bj = kInvalid;
-    const float lb = found ? q.best : (r0 < kInf ? r0 : 0.0f);
-    A.res[i] = make_uint2(__float_as_uint(lb), q.bj);
-    if (q.bj != kInvalid) {
-      const uint32_t oi = __float_as_uint(p.w);
-      const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(A.pts[q.bj].w);
-      A.res_id[i] = oj;
-      const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
-      atomicMin(reinterpret_cast<unsigned long long *>(A.comp_key + q.me), (unsigned long long)key);
-    } else {
-      A.res_id[i] = kInvalid;
-    }
-    return;
-  }
   // Batched form: search only this point's instance (its subtree, its curve range).
   uint32_t start = 0u;
   int64_t wlo = 0, whi = n;
