@@ -103,18 +103,22 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     val[it] = ok ? vals_in[idx] : 0u;
   }
   // Rank within the warp, in input order: peers with the same digit in this
-  // item, plus the warp's running count of that digit.
+  // item, plus the warp's running count of that digit.  The group's leader
+  // adds the group size to the warp's counter; the old value is the group's
+  // base.  The warp issues the items' adds in order, so item it's base counts
+  // exactly the keys of items < it.
+  const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int it = 0; it < kSortItems; ++it) {
     int64_t idx = seg + it * 32 + lane;
     bool ok = idx < n;
     uint32_t dg = ok ? (uint32_t)(key[it] >> shift) & 0xffu : 0x100u + lane;
     uint32_t peers = __match_any_sync(0xffffffffu, dg);
-    uint32_t cnt = ok ? S.warp_hist[warp][dg] : 0u;
-    rank[it] = cnt + __popc(peers & lanemask_lt());
-    __syncwarp();
-    if (ok && (__ffs(peers) - 1) == lane) S.warp_hist[warp][dg] = cnt + __popc(peers);
-    __syncwarp();
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0u;
+    if (ok && leader == lane) base = atomicAdd(&S.warp_hist[warp][dg], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    rank[it] = base + __popc(peers & lt);
   }
   __syncthreads();
 
