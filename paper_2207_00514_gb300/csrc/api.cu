@@ -92,13 +92,13 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.keys[1] = c.take<uint64_t>(n);
   P.vals[0] = c.take<uint32_t>(n);
   P.vals[1] = c.take<uint32_t>(n);
-  P.inv = c.take<uint32_t>(n);
   P.nodes = c.take<NodeRec>(nc - 1);
   P.parent_leaf = c.take<uint32_t>(nc);
   P.up_delta = c.take<uint2>(nc - 1);
   P.arrivals = c.take<uint32_t>(nc - 1);
   P.range = c.take<uint4>(nc - 1);
   P.runs = c.take<uint32_t>(n);
+  P.scan_tiles = c.take<uint32_t>(2 * scan_tiles_for(n));
   P.labels_buf[0] = c.take<uint32_t>(n);
   P.labels_buf[1] = c.take<uint32_t>(n);
   P.bound_buf[0] = c.take<uint32_t>(n);
@@ -112,10 +112,12 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.next_list = P.list_buf[0];
   P.n_active = n;
   P.res = c.take<uint2>(n);
-  P.res_id = c.take<uint32_t>(n);
-  P.comp_key = c.take<uint64_t>(n);
-  P.comp_max = c.take<uint32_t>(n);
-  P.target = c.take<uint32_t>(n);
+  P.comp_key_buf[0] = c.take<uint64_t>(n);
+  P.comp_key_buf[1] = c.take<uint64_t>(n);
+  P.comp_max_buf[0] = c.take<uint64_t>(n);
+  P.comp_max_buf[1] = c.take<uint64_t>(n);
+  P.comp_key = P.comp_key_buf[0];
+  P.comp_max = P.comp_max_buf[0];
   P.root = c.take<uint32_t>(n);
   P.edges = c.take<emst_edge>(n);
   if (P.num_inst > 1) {
@@ -200,19 +202,22 @@ void run_round(Problem &P, int round, bool carried, int block, bool count) {
 
 void reset_round_state(Problem &P) {
   cudaMemsetAsync(P.bound, 0xFF, sizeof(uint32_t) * (size_t)P.n, P.stream);
+  // (the other buffer is cleared by the first round's merge)
   cudaMemsetAsync(P.comp_key, 0xFF, sizeof(uint64_t) * (size_t)P.n, P.stream);
-  cudaMemsetAsync(P.comp_max, 0xFF, sizeof(uint32_t) * (size_t)P.n, P.stream);
+  cudaMemsetAsync(P.comp_max, 0xFF, sizeof(uint64_t) * (size_t)P.n, P.stream);
 }
 
-// A12: the n-1 edges in (w, i, j) order into `out` (device).
-void run_output(Problem &P, emst_edge *out) {
+// A12: the n-1 edges in (w, i, j) order into `out` (device).  w_bits: the
+// largest emitted weight's bits (counters[11]): the sort key needs
+// L + significant bits of it.
+void run_output(Problem &P, emst_edge *out, uint32_t w_bits) {
   const int64_t m = P.num_inst > 1 ? P.edges_expected : P.n - 1;
   if (m <= 0) return;
   const int L = bits_for(P.n - 1);
-  launch_edge_keys_j(P, m);
-  int s = radix_sort_pairs(P, m, 0, (L + 7) / 8, 0);
-  launch_edge_keys_wi(P, m, s, L);
-  s = radix_sort_pairs(P, m, 0, (32 + L + 7) / 8, s);
+  const int wb = w_bits ? 32 - __builtin_clz(w_bits) : 0;
+  launch_edge_keys_wi(P, m, L);
+  int s = radix_sort_pairs(P, m, 0, (L + wb + 7) / 8, 0);
+  launch_edge_ties(P, m, s);
   if (P.num_inst > 1) {  // instance is the most significant key (stable LSD)
     launch_edge_keys_inst(P, m, s);
     s = radix_sort_pairs(P, m, 0, (P.inst_bits + 7) / 8, s);
@@ -411,7 +416,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     }
     tm.mark(2, stream);
     if ((int64_t)host_counters[0] != expected) { rc = EMST_ERR_INTERNAL; goto done; }
-    if (!skip_output) run_output(P, out_dev ? out : P.out_stage);
+    if (!skip_output) run_output(P, out_dev ? out : P.out_stage, host_counters[11]);
     if (!out_dev && !skip_output)
       CU(cudaMemcpyAsync(out, P.out_stage, sizeof(emst_edge) * (size_t)expected,
                          cudaMemcpyDeviceToHost, stream));

@@ -18,16 +18,25 @@ __global__ void __launch_bounds__(kBlock) k_scene_box(const float *__restrict__ 
   float lo[3] = {INFINITY, INFINITY, INFINITY};
   float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   bool bad = false;
-  const int64_t total = n * DIM;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    float x = __ldg(pts + e);
-    int d = (int)(e % DIM);
-    if (!isfinite(x)) { bad = true; continue; }
+  auto take = [&](int64_t k) {
 #pragma unroll
-    for (int q = 0; q < DIM; ++q)
-      if (q == d) { lo[q] = fminf(lo[q], x); hi[q] = fmaxf(hi[q], x); }
+    for (int q = 0; q < DIM; ++q) {
+      const float x = __ldg(pts + k * DIM + q);
+      if (!isfinite(x)) { bad = true; continue; }
+      lo[q] = fminf(lo[q], x);
+      hi[q] = fmaxf(hi[q], x);
+    }
+  };
+  // whole points per thread, four independent ones per step (loads in flight)
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; k + 3 * stride < n; k += 4 * stride) {
+    take(k);
+    take(k + stride);
+    take(k + 2 * stride);
+    take(k + 3 * stride);
   }
+  for (; k < n; k += stride) take(k);
 #pragma unroll
   for (int q = 0; q < DIM; ++q) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -57,7 +66,7 @@ void launch_scene_box(Problem &P) {
   uint32_t *box = P.counters + 4;
   k_box_init<<<1, 32, 0, P.stream>>>(box);
   int grid = 152 * 4;
-  int64_t need = (P.n * P.dim + kBlock - 1) / kBlock;
+  int64_t need = (P.n + kBlock - 1) / kBlock;
   if (need < grid) grid = (int)(need < 1 ? 1 : need);
   if (P.dim == 3)
     k_scene_box<3><<<grid, kBlock, 0, P.stream>>>(P.points, P.n, box, P.counters + 1);
@@ -163,14 +172,12 @@ void launch_instance_roots(Problem &P) {
 
 // ---------------------------------------------------------------------------
 // A4 (a). Gather the points into curve order as float4 (x, y, z, original
-// index bits), the inverse permutation, and the first labels (labels(i) = i,
-// Fig. 3), in curve indices.
+// index bits) and the first labels (labels(i) = i, Fig. 3), in curve indices.
 // ---------------------------------------------------------------------------
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_gather(const float *__restrict__ pts,
                                                    const uint32_t *__restrict__ perm, int64_t n,
                                                    float4 *__restrict__ out,
-                                                   uint32_t *__restrict__ inv,
                                                    uint32_t *__restrict__ labels,
                                                    const uint32_t *__restrict__ inst_in,
                                                    uint32_t *__restrict__ inst_of) {
@@ -181,17 +188,16 @@ __global__ void __launch_bounds__(kBlock) k_gather(const float *__restrict__ pts
   const float *p = pts + (int64_t)o * DIM;
   float x = __ldg(p), y = __ldg(p + 1), z = DIM == 3 ? __ldg(p + 2) : 0.0f;
   out[k] = make_float4(x, y, z, __uint_as_float(o));
-  inv[o] = (uint32_t)k;
   labels[k] = (uint32_t)k;
 }
 
 void launch_gather(Problem &P, const uint32_t *perm) {
   int g = grid_for(P.n, kBlock);
   if (P.dim == 3)
-    k_gather<3><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.inv, P.labels, P.inst_in,
+    k_gather<3><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.labels, P.inst_in,
                                             P.inst_of);
   else
-    k_gather<2><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.inv, P.labels, P.inst_in,
+    k_gather<2><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.labels, P.inst_in,
                                             P.inst_of);
   P.launches += 1;
 }

@@ -196,7 +196,6 @@ struct Problem {
   uint64_t *keys[2] = {nullptr, nullptr};
   uint32_t *vals[2] = {nullptr, nullptr};
   uint32_t *perm = nullptr;       // curve index -> original index
-  uint32_t *inv = nullptr;        // original index -> curve index
   NodeRec *nodes = nullptr;       // nc-1 internal nodes
   uint32_t *parent_leaf = nullptr;   // nc: (parent << 1) | slot of each leaf chunk
   uint2 *up_delta = nullptr;         // n-1: x = (parent << 1) | slot (root: kInvalid),
@@ -206,7 +205,10 @@ struct Problem {
   uint32_t *arrivals = nullptr;      // n-1 arrival counters (parity = who is second)
   uint4 *range = nullptr;            // nc-1: (first, split, last, 0) of each internal node: its
                                      //      leaf-chunk range and the last chunk of its left child
-  uint32_t *runs = nullptr;          // n: label boundaries before each curve position
+  uint32_t *runs = nullptr;          // n: label boundaries before each curve position within
+                                     //    its scan tile (plus the tile's entry of tile_prefix)
+  uint32_t *scan_tiles = nullptr;    // 2 x scan tiles: boundary total of each tile, then the
+                                     //    exclusive prefix of those totals
   uint32_t *labels = nullptr;        // n, current round (= labels_buf[cur])
   uint32_t *bound = nullptr;         // n, FP32 bits of the component upper bound (= bound_buf[cur])
   uint32_t *labels_buf[2] = {nullptr, nullptr};
@@ -217,18 +219,22 @@ struct Problem {
   uint32_t *next_list = nullptr;     // roots appended by the merge
   int64_t n_active = 0;
   uint2 *res = nullptr;              // n: (w bits, neighbour curve index)
-  uint32_t *res_id = nullptr;        // n: neighbour original index
-  uint64_t *comp_key = nullptr;      // n: (w bits << 32) | min original id
-  uint32_t *comp_max = nullptr;      // n: max original id of the winning edge
-  uint32_t *target = nullptr;        // n: component the edge points to
+  // Per-component minimum edge, in two stages (A8), ping-pong by round: the
+  // merge of round r clears the other buffer's entries of its active labels.
+  uint64_t *comp_key_buf[2] = {nullptr, nullptr};  // n: (w bits << 32) | min original id
+  uint64_t *comp_max_buf[2] = {nullptr, nullptr};  // n: (max original id << 32) | label of the
+                                                   //    edge's endpoint outside the component
+  uint64_t *comp_key = nullptr;      // = comp_key_buf[cur]
+  uint64_t *comp_max = nullptr;      // = comp_max_buf[cur]
   uint32_t *root = nullptr;          // n: new label of a component
   emst_edge *edges = nullptr;        // n: edges in emission order
   emst_edge *out_stage = nullptr;    // n-1: device staging of host outputs
   uint32_t *counters = nullptr;      // [0] edges emitted, [1] status bits, [2..3] node visits (u64),
-                                     // [4..9] scene box (ordered), [16..23] sort tile counters,
+                                     // [4..9] scene box (ordered), [11] largest emitted
+                                     // weight bits, [16..23] sort tile counters,
                                      // [12] next round's active components, [13] points
                                      // to rerun, [14..15] reruns / queries (learned radius),
-                                     // [24] scan tile counter
+                                     // [24] scan tiles finished
   uint32_t *sort_hist = nullptr;     // 8 x 256
   uint32_t *sort_lookback = nullptr; // tiles x 256
   int64_t sort_tiles = 0;
@@ -247,14 +253,25 @@ void launch_instance_roots(Problem &P);
 void launch_hierarchy(Problem &P);
 void launch_refit(Problem &P, bool init_labels);
 // sort.cu
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
+// Tile shape of one sort pass (compile-time knobs; the defaults are the measured best).
+#ifndef EMST_SORT_THREADS
+#define EMST_SORT_THREADS 256
+#endif
+#ifndef EMST_SORT_ITEMS
+#define EMST_SORT_ITEMS 8
+#endif
+#ifndef EMST_SORT_MIN_BLOCKS
+#define EMST_SORT_MIN_BLOCKS 4
+#endif
+constexpr int kSortThreads = EMST_SORT_THREADS;
+constexpr int kSortItems = EMST_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems;
 int64_t sort_tiles_for(int64_t n);
 // Stable LSD radix sort of (keys, vals) pairs on digits [digit_begin, digit_end)
 // (8-bit digits).  Returns the index (0/1) of the buffers holding the result.
 int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int src);
 // rounds.cu
+int64_t scan_tiles_for(int64_t n);
 void launch_label_runs(Problem &P);
 void launch_node_labels(Problem &P);
 void advance_round(Problem &P, int64_t n_active);
@@ -265,8 +282,8 @@ void launch_reduce(Problem &P);
 void launch_merge(Problem &P);
 void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
 // output
-void launch_edge_keys_j(Problem &P, int64_t m);
-void launch_edge_keys_wi(Problem &P, int64_t m, int src, int shift_i);
+void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i);
+void launch_edge_ties(Problem &P, int64_t m, int src);
 void launch_edge_keys_inst(Problem &P, int64_t m, int src);
 // learned.cu
 void launch_comp_sizes(Problem &P);
@@ -289,7 +306,7 @@ void run_round(Problem &P, int round, bool carried, int block, bool count);
 // Leaf chunk size actually used for n points and a requested size (0 =
 // default): a power of two, at most the request, leaving at least 2 chunks.
 int effective_leaf(int64_t n, int requested);
-void run_output(Problem &P, emst_edge *out);
+void run_output(Problem &P, emst_edge *out, uint32_t w_bits);
 
 inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;

@@ -622,7 +622,6 @@ void launch_log_samples(Problem &P, int round, bool carried) {
   T.inst_root = P.inst_root;
   T.offsets = P.offsets;
   T.res = P.res;
-  T.res_id = P.res_id;
   T.comp_key = P.comp_key;
   T.n = P.n;
   T.status = P.counters + 1;

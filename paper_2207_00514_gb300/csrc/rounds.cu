@@ -14,95 +14,172 @@ constexpr int kBlock = 256;
 // node's label is the label shared by all of its leaves, else kInvalid.  The
 // leaves of a node are a contiguous range [a, b] of curve positions, so the
 // node is single-component iff no label boundary lies inside the range.  With
-// runs[k] = number of positions m < k where labels[m] != labels[m+1] (one
-// prefix scan), that is runs[b] == runs[a], and the label is labels[a].  The
+// runs[k] = number of positions m < k where labels[m] != labels[m+1] (a
+// prefix count), that is runs[b] == runs[a], and the label is labels[a].  The
 // result equals the bottom-up combination of the paper (equal child labels ->
 // that label, else invalid) without its atomics and climbing threads.
+//
+// runs[k] is kept in two parts, so no tile waits on another: the count
+// within k's tile of kScanTile positions (runs_local) plus the count of all
+// earlier tiles (tile_prefix, an exclusive scan of the tile totals done by
+// the last tile to finish).
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
-constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr uint32_t kScanAggregate = 1u << 30;
-constexpr uint32_t kScanPrefix = 2u << 30;
-constexpr uint32_t kScanMask = (1u << 30) - 1u;
+constexpr int kScanItems = 16;  // rows of 32 positions per warp
+constexpr int kScanTileShift = 12;
+constexpr int kScanTile = 1 << kScanTileShift;
+static_assert(kScanTile == kScanThreads * kScanItems, "scan tile shape");
 
-// Single-pass exclusive scan of the boundary flags with decoupled look-back.
-__global__ void __launch_bounds__(kScanThreads) k_label_runs(const uint32_t *__restrict__ labels,
-                                                             int64_t n, uint32_t *__restrict__ runs,
-                                                             uint32_t *lookback,
-                                                             uint32_t *tile_counter,
-                                                             uint32_t *status) {
-  __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_warp[kScanThreads / 32];
-  __shared__ uint32_t s_prefix;
+int64_t scan_tiles_for(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+__device__ __forceinline__ uint32_t runs_at(const uint32_t *__restrict__ runs_local,
+                                            const uint32_t *__restrict__ tile_prefix, int64_t k) {
+  return __ldg(runs_local + k) + __ldg(tile_prefix + (k >> kScanTileShift));
+}
+
+// Exclusive scan of count values by one CTA of kScanThreads threads, each
+// summing a contiguous chunk (the values come from other CTAs of the same
+// launch: read through L2).
+__device__ void block_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t count) {
+  __shared__ uint32_t s_part[kScanThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const int64_t first = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
-  uint32_t flags = 0;  // bit q: boundary after position first+q
-  uint32_t lab[kScanItems + 1];
+  const int64_t chunk = (count + kScanThreads - 1) / kScanThreads;
+  const int64_t lo = (int64_t)tid * chunk, hi = lo + chunk < count ? lo + chunk : count;
+  uint32_t sum = 0;
+  for (int64_t t = lo; t < hi; ++t) sum += __ldcg(in + t);
+  uint32_t x = sum;
 #pragma unroll
-  for (int q = 0; q <= kScanItems; ++q) {
-    int64_t k = first + q;
-    lab[q] = k < n ? __ldg(labels + k) : kInvalid;
-  }
-#pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    int64_t k = first + q;
-    if (k + 1 < n && lab[q] != lab[q + 1]) flags |= 1u << q;
-  }
-  const uint32_t mine = __popc(flags);
-  uint32_t x = mine;
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) s_warp[warp] = x;
+  if (lane == 31) s_part[warp] = x;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
-    uint32_t z = w;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
-      if (lane >= o) z += y;
-    }
-    if (lane < kScanThreads / 32) s_warp[lane] = z - w;  // exclusive per warp
-    const uint32_t total = __shfl_sync(0xffffffffu, z, kScanThreads / 32 - 1);
-    if (lane == 0) {
-      volatile uint32_t *lb = lookback + tile;
-      *lb = (tile == 0 ? kScanPrefix : kScanAggregate) | total;
-      uint32_t excl = 0;
-      if (tile > 0) {
-        for (int64_t j = (int64_t)tile - 1; j >= 0; --j) {
-          const volatile uint32_t *pj = lookback + j;
-          uint32_t wv = *pj;
-          int spins = 0;
-          while ((wv & ~kScanMask) == 0u) {
-            if (++spins > (1 << 22)) { atomicOr(status, kErrSpin); wv = kScanPrefix; break; }
-            __nanosleep(32);
-            wv = *pj;
-          }
-          excl += wv & kScanMask;
-          if ((wv & ~kScanMask) == kScanPrefix) break;
-        }
-        *lb = kScanPrefix | ((excl + total) & kScanMask);
-      }
-      s_prefix = excl;
-    }
-  }
-  __syncthreads();
-  uint32_t run = s_prefix + s_warp[warp] + x - mine;
-#pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    int64_t k = first + q;
-    if (k < n) runs[k] = run;
-    run += (flags >> q) & 1u;
+  uint32_t base = 0;
+  for (int w = 0; w < warp; ++w) base += s_part[w];
+  uint32_t run = base + x - sum;
+  for (int64_t t = lo; t < hi; ++t) {
+    const uint32_t v = __ldcg(in + t);
+    out[t] = run;
+    run += v;
   }
 }
 
+// The local boundary counts (runs_local) and tile totals, one tile of
+// kScanTile positions per CTA.  Warp-striped: warp w of the tile owns
+// kScanItems rows of 32 consecutive positions, so every load and store is one
+// coalesced 128-byte row, and the row's flags rank by one ballot.  RELABEL:
+// the labels are first mapped through root (the merge's new labels, written
+// to labels_new), and every boundary between two curve neighbours of one
+// instance lowers both components' bounds for the next round (A6) -- one
+// pass for A9's relabel, A6 and A5's counts.
+template <bool RELABEL>
+__global__ void __launch_bounds__(kScanThreads, 6) k_runs(
+    const uint32_t *__restrict__ labels_old, const uint32_t *__restrict__ root,
+    const float4 *__restrict__ pts, const uint32_t *__restrict__ inst_of, int64_t n,
+    uint32_t *__restrict__ labels_new, uint32_t *__restrict__ bound_next,
+    uint32_t *__restrict__ runs_local, uint32_t *tile_total, uint32_t *tile_prefix,
+    uint32_t *done) {
+  __shared__ uint32_t s_warp[kScanThreads / 32];
+  __shared__ uint32_t s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t tile = blockIdx.x;
+  const int64_t seg = (int64_t)tile * kScanTile + (int64_t)warp * 32 * kScanItems;
+  // positions of this warp that exist (32-bit indexing within the segment)
+  const int64_t rem64 = n - seg;
+  const int rem = rem64 > 32 * kScanItems ? 32 * kScanItems + 1 : (int)(rem64 > 0 ? rem64 : 0);
+  const uint32_t *lo = labels_old + seg;
+  uint32_t lab[kScanItems];
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    const int k = q * 32 + lane;
+    lab[q] = k < rem ? __ldg(lo + k) : kInvalid;
+  }
+  // the position after the warp's last row
+  uint32_t tail = kInvalid;
+  if (lane == 0 && 32 * kScanItems < rem) tail = __ldg(lo + 32 * kScanItems);
+  if (RELABEL) {
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q)
+      if (lab[q] != kInvalid) lab[q] = __ldg(root + lab[q]);
+    if (tail != kInvalid) tail = __ldg(root + tail);
+  }
+  tail = __shfl_sync(0xffffffffu, tail, 0);
+  uint32_t flags = 0;  // bit q: boundary between row q's position and the next one
+  uint32_t wtotal = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    const int k = q * 32 + lane;
+    uint32_t nxt = __shfl_down_sync(0xffffffffu, lab[q], 1);
+    const uint32_t row_next =
+        q + 1 < kScanItems ? __shfl_sync(0xffffffffu, lab[q + 1 < kScanItems ? q + 1 : q], 0) : tail;
+    if (lane == 31) nxt = row_next;
+    const bool f = k + 1 < rem && lab[q] != nxt;
+    if (f) {
+      flags |= 1u << q;
+      if (RELABEL && !(inst_of && __ldg(inst_of + seg + k) != __ldg(inst_of + seg + k + 1))) {
+        // (no bound across instances)
+        const float4 p = __ldg(pts + seg + k), r = __ldg(pts + seg + k + 1);
+        const uint32_t w = __float_as_uint(sq_dist(p.x, p.y, p.z, r.x, r.y, r.z));
+        atomicMin(&bound_next[lab[q]], w);
+        atomicMin(&bound_next[nxt], w);
+      }
+    }
+    if (RELABEL && k < rem) labels_new[seg + k] = lab[q];
+    wtotal += __popc(__ballot_sync(0xffffffffu, f));
+  }
+  if (lane == 0) s_warp[warp] = wtotal;
+  __syncthreads();
+  uint32_t run = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kScanThreads / 32; ++w) {
+    const uint32_t v = s_warp[w];
+    run += w < warp ? v : 0u;
+    total += v;
+  }
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t *out = runs_local + seg;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    const int k = q * 32 + lane;
+    const uint32_t b = __ballot_sync(0xffffffffu, (flags >> q) & 1u);
+    if (k < rem) out[k] = run + __popc(b & lt);
+    run += __popc(b);
+  }
+  // the last tile to finish scans the tile totals
+  if (tid == 0) {
+    tile_total[tile] = total;
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    block_exclusive_scan(tile_total, tile_prefix, gridDim.x);
+  }
+}
+
+static void launch_runs(Problem &P, bool relabel) {
+  const int64_t tiles = scan_tiles_for(P.n);
+  uint32_t *done = P.counters + 24;
+  uint32_t *tile_total = P.scan_tiles, *tile_prefix = P.scan_tiles + tiles;
+  cudaMemsetAsync(done, 0, sizeof(uint32_t), P.stream);
+  if (relabel)
+    k_runs<true><<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(
+        P.labels, P.root, P.pts, P.inst_of, P.n, P.labels_buf[P.cur ^ 1], P.bound_buf[P.cur ^ 1],
+        P.runs, tile_total, tile_prefix, done);
+  else
+    k_runs<false><<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(
+        P.labels, nullptr, P.pts, P.inst_of, P.n, nullptr, nullptr, P.runs, tile_total,
+        tile_prefix, done);
+  P.launches += 1;
+}
+
+void launch_label_runs(Problem &P) { launch_runs(P, false); }
+
 __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restrict__ labels,
-                                                        const uint32_t *__restrict__ runs,
+                                                        const uint32_t *__restrict__ runs_local,
+                                                        const uint32_t *__restrict__ tile_prefix,
                                                         const uint4 *__restrict__ range,
                                                         int64_t n, int64_t nc, int leaf,
                                                         NodeRec *__restrict__ nodes) {
@@ -115,25 +192,16 @@ __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restri
   const int64_t a1 = b0 + 1;
   const int64_t b1 = ((int64_t)r.z + 1) * leaf < n ? ((int64_t)r.z + 1) * leaf - 1 : n - 1;
   const uint32_t l0 = __ldg(labels + a0), l1 = __ldg(labels + a1);
-  const uint32_t lab0 = (__ldg(runs + b0) == __ldg(runs + a0)) ? l0 : kInvalid;
-  const uint32_t lab1 = (__ldg(runs + b1) == __ldg(runs + a1)) ? l1 : kInvalid;
+  const uint32_t lab0 =
+      runs_at(runs_local, tile_prefix, b0) == runs_at(runs_local, tile_prefix, a0) ? l0 : kInvalid;
+  const uint32_t lab1 =
+      runs_at(runs_local, tile_prefix, b1) == runs_at(runs_local, tile_prefix, a1) ? l1 : kInvalid;
   reinterpret_cast<uint2 *>(&nodes[i].d)[1] = make_uint2(lab0, lab1);
-}
-
-void launch_label_runs(Problem &P) {
-  const int64_t tiles = (P.n + kScanTile - 1) / kScanTile;
-  uint32_t *ctr = P.counters + 24;
-  cudaMemsetAsync(ctr, 0, sizeof(uint32_t), P.stream);
-  cudaMemsetAsync(P.sort_lookback, 0, sizeof(uint32_t) * (size_t)tiles, P.stream);
-  k_label_runs<<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(P.labels, P.n, P.runs,
-                                                               P.sort_lookback, ctr,
-                                                               P.counters + 1);
-  P.launches += 1;
 }
 
 void launch_node_labels(Problem &P) {
   k_node_labels<<<grid_for(P.nc - 1, kBlock), kBlock, 0, P.stream>>>(
-      P.labels, P.runs, P.range, P.n, P.nc, P.leaf, P.nodes);
+      P.labels, P.runs, P.scan_tiles + scan_tiles_for(P.n), P.range, P.n, P.nc, P.leaf, P.nodes);
   P.launches += 1;
 }
 
@@ -193,7 +261,6 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   A.inst_root = P.inst_root;
   A.offsets = P.offsets;
   A.res = P.res;
-  A.res_id = P.res_id;
   A.comp_key = P.comp_key;
   A.n = P.n;
   A.status = P.counters + 1;
@@ -235,31 +302,32 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
 // ---------------------------------------------------------------------------
 // A8 (second half). Among the points whose (w, min id) equals the component's
 // winner, the smallest max id: together the exact minimum of the key
-// (w, min id, max id) of §2 over the component.  Also clears the other
-// round's bound buffer (bound_next) for the relabel pass that fills it.
+// (w, min id, max id) of §2 over the component.  The stage-B value carries
+// the label of the edge's endpoint outside the component (the neighbour's
+// label: one pair, one label), which is the merge's target.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_reduce_max(const float4 *__restrict__ pts,
                                                        const uint32_t *__restrict__ labels,
                                                        const uint2 *__restrict__ res,
-                                                       const uint32_t *__restrict__ res_id,
                                                        const uint64_t *__restrict__ comp_key,
-                                                       uint32_t *comp_max,
-                                                       uint32_t *__restrict__ bound_next,
+                                                       unsigned long long *comp_max,
                                                        int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (bound_next) bound_next[i] = kNoBound;
-  uint2 r = res[i];
+  const uint2 r = res[i];
   if (r.y == kInvalid) return;
-  uint32_t me = labels[i];
-  uint32_t oi = __float_as_uint(pts[i].w), oj = res_id[i];
-  uint64_t key = ((uint64_t)r.x << 32) | (uint64_t)(oi < oj ? oi : oj);
-  if (key == comp_key[me]) atomicMin(&comp_max[me], oi < oj ? oj : oi);
+  const uint32_t me = labels[i];
+  const uint64_t ck = __ldg(reinterpret_cast<const unsigned long long *>(comp_key + me));
+  if (r.x != (uint32_t)(ck >> 32)) return;  // not the component's minimum weight
+  const uint32_t oi = __float_as_uint(pts[i].w), oj = __float_as_uint(__ldg(&pts[r.y].w));
+  if ((oi < oj ? oi : oj) != (uint32_t)ck) return;
+  const uint64_t v = ((uint64_t)(oi < oj ? oj : oi) << 32) | (uint64_t)__ldg(labels + r.y);
+  atomicMin(comp_max + me, (unsigned long long)v);
 }
 
 void launch_reduce(Problem &P) {
   k_reduce_max<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(
-      P.pts, P.labels, P.res, P.res_id, P.comp_key, P.comp_max, P.bound_buf[P.cur ^ 1], P.n);
+      P.pts, P.labels, P.res, P.comp_key, reinterpret_cast<unsigned long long *>(P.comp_max), P.n);
   P.launches += 1;
 }
 
@@ -277,176 +345,106 @@ void launch_reduce(Problem &P) {
 // in the same pass, prepare the next round: its curve-pair upper bounds (A6)
 // and the label-boundary prefix scan the node labels (A5) need.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_merge_targets(const uint32_t *__restrict__ list,
-                                                          int64_t count,
-                                                          const uint64_t *__restrict__ comp_key,
-                                                          const uint32_t *__restrict__ comp_max,
-                                                          const uint32_t *__restrict__ inv,
-                                                          const uint32_t *__restrict__ labels,
-                                                          uint32_t *__restrict__ target,
-                                                          uint32_t *status) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
-  const uint32_t c = list ? list[t] : (uint32_t)t;
-  uint64_t key = comp_key[c];
-  const uint32_t mx = comp_max[c];
-  if (key == kEmptyKey || mx == kInvalid) {
-    // (the second case cannot happen: the winner of the first half always
-    // matches its own key in the second; guarded so no index is ever wild)
-    if (key != kEmptyKey) atomicOr(status, kErrChain);
-    target[c] = kInvalid;
-    return;
-  }
-  uint32_t lmn = labels[inv[(uint32_t)key]];
-  uint32_t lmx = labels[inv[mx]];
-  target[c] = (lmn == c) ? lmx : lmn;
+__device__ __forceinline__ uint32_t merge_target(const uint64_t *comp_key,
+                                                 const uint64_t *comp_max, uint32_t x) {
+  if (comp_key[x] == kEmptyKey) return kInvalid;
+  const uint64_t mx = comp_max[x];
+  return mx == kEmptyKey ? kInvalid : (uint32_t)mx;
 }
 
+// One thread per listed component.  The edges and the next round's list are
+// appended through one atomic per CTA (their order carries no meaning: the
+// output is sorted, the list is a set).  key_clear / max_clear: the other
+// round's buffers, cleared for the listed labels; bound_next: the next
+// round's bounds, cleared for the new roots (the only labels it reads) before
+// the relabel pass lowers them.
 __global__ void __launch_bounds__(kBlock) k_merge_roots(const uint32_t *__restrict__ list,
                                                         int64_t count,
-                                                        uint64_t *__restrict__ comp_key,
-                                                        uint32_t *__restrict__ comp_max,
-                                                        const uint32_t *__restrict__ target,
+                                                        const uint64_t *__restrict__ comp_key,
+                                                        const uint64_t *__restrict__ comp_max,
+                                                        uint64_t *__restrict__ key_clear,
+                                                        uint64_t *__restrict__ max_clear,
+                                                        uint32_t *__restrict__ bound_next,
                                                         uint32_t *__restrict__ root,
                                                         emst_edge *__restrict__ edges,
                                                         uint32_t *__restrict__ next_list,
                                                         uint32_t *counters, int64_t n) {
-  int64_t t64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t64 >= count) return;
-  const uint32_t c = list ? list[t64] : (uint32_t)t64;
-  const uint64_t key = comp_key[c];
-  const uint32_t t = key == kEmptyKey ? kInvalid : target[c];
-  uint32_t r = c;
-  if (t != kInvalid) {
-    const bool mutual = target[t] == c;
-    if (!mutual || c < t) {
-      uint32_t e = atomicAdd(&counters[0], 1u);
-      emst_edge E;
+  __shared__ uint32_t s_warp[2][kBlock / 32];
+  __shared__ uint32_t s_wmax[kBlock / 32];
+  __shared__ uint32_t s_base[2];
+  const int64_t t64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool emit = false, is_root = false;
+  uint32_t c = 0;
+  emst_edge E = {0u, 0u, 0.0f};
+  if (t64 < count) {
+    c = list ? list[t64] : (uint32_t)t64;
+    const uint64_t key = comp_key[c];
+    const uint64_t mx = comp_max[c];
+    // (a key without a stage-B winner cannot happen: the winner of the first
+    // half always matches its own key in the second; guarded so no index is
+    // ever wild)
+    if (key != kEmptyKey && mx == kEmptyKey) atomicOr(&counters[1], kErrChain);
+    const uint32_t t = (key == kEmptyKey || mx == kEmptyKey) ? kInvalid : (uint32_t)mx;
+    uint32_t r = c;
+    if (t != kInvalid) {
+      emit = !(merge_target(comp_key, comp_max, t) == c) || c < t;
       E.i = (uint32_t)key;
-      E.j = comp_max[c];
+      E.j = (uint32_t)(mx >> 32);
       E.w = __uint_as_float((uint32_t)(key >> 32));
-      edges[e] = E;
-    }
-    uint32_t x = c;
-    for (int64_t steps = 0;; ++steps) {
-      uint32_t y = target[x];
-      if (y == kInvalid) { r = x; break; }  // chain ends at a component without an edge
-      if (target[y] == x) { r = x < y ? x : y; break; }
-      x = y;
-      if (steps > n) { atomicOr(&counters[1], kErrChain); r = x; break; }
-    }
-    comp_key[c] = kEmptyKey;
-    comp_max[c] = kInvalid;
-  }
-  root[c] = r;
-  if (r == c) next_list[atomicAdd(&counters[12], 1u)] = c;
-}
-
-// Relabel + next round's bounds + label-boundary scan, one tile of positions
-// per CTA, decoupled look-back for the scan.  New labels go to a second
-// buffer (neighbouring tiles still read the old ones).
-constexpr int kRelabelItems = 8;
-constexpr int kRelabelTile = kScanThreads * kRelabelItems;
-
-__global__ void __launch_bounds__(kScanThreads, 6) k_relabel_runs(
-    const uint32_t *__restrict__ labels_old, const uint32_t *__restrict__ root,
-    const float4 *__restrict__ pts, const uint32_t *__restrict__ inst_of, int64_t n,
-    uint32_t *__restrict__ labels_new,
-    uint32_t *__restrict__ bound_next, uint32_t *__restrict__ runs, uint32_t *lookback,
-    uint32_t *tile_counter, uint32_t *status) {
-  __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_warp[kScanThreads / 32];
-  __shared__ uint32_t s_prefix;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const int64_t first = (int64_t)tile * kRelabelTile + (int64_t)tid * kRelabelItems;
-  uint32_t lab[kRelabelItems + 1];
-#pragma unroll
-  for (int q = 0; q <= kRelabelItems; ++q) {
-    int64_t k = first + q;
-    lab[q] = k < n ? __ldg(root + __ldg(labels_old + k)) : kInvalid;
-  }
-  uint32_t flags = 0;
-#pragma unroll
-  for (int q = 0; q < kRelabelItems; ++q) {
-    int64_t k = first + q;
-    if (k < n) labels_new[k] = lab[q];
-    if (k + 1 < n && lab[q] != lab[q + 1]) {
-      flags |= 1u << q;
-      if (inst_of && __ldg(inst_of + k) != __ldg(inst_of + k + 1)) continue;  // no cross-instance bound
-      const float4 p = __ldg(pts + k), r = __ldg(pts + k + 1);
-      const uint32_t w = __float_as_uint(sq_dist(p.x, p.y, p.z, r.x, r.y, r.z));
-      atomicMin(&bound_next[lab[q]], w);
-      atomicMin(&bound_next[lab[q + 1]], w);
-    }
-  }
-  const uint32_t mine = __popc(flags);
-  uint32_t x = mine;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
-    uint32_t z = w;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
-      if (lane >= o) z += y;
-    }
-    if (lane < kScanThreads / 32) s_warp[lane] = z - w;
-    const uint32_t total = __shfl_sync(0xffffffffu, z, kScanThreads / 32 - 1);
-    if (lane == 0) {
-      volatile uint32_t *lb = lookback + tile;
-      *lb = (tile == 0 ? kScanPrefix : kScanAggregate) | total;
-      uint32_t excl = 0;
-      if (tile > 0) {
-        for (int64_t j = (int64_t)tile - 1; j >= 0; --j) {
-          const volatile uint32_t *pj = lookback + j;
-          uint32_t wv = *pj;
-          int spins = 0;
-          while ((wv & ~kScanMask) == 0u) {
-            if (++spins > (1 << 22)) { atomicOr(status, kErrSpin); wv = kScanPrefix; break; }
-            __nanosleep(32);
-            wv = *pj;
-          }
-          excl += wv & kScanMask;
-          if ((wv & ~kScanMask) == kScanPrefix) break;
-        }
-        *lb = kScanPrefix | ((excl + total) & kScanMask);
+      uint32_t x = c, y = t;
+      for (int64_t steps = 0;; ++steps) {
+        if (y == kInvalid) { r = x; break; }  // chain ends at a component without an edge
+        const uint32_t z = merge_target(comp_key, comp_max, y);
+        if (z == x) { r = x < y ? x : y; break; }
+        x = y;
+        y = z;
+        if (steps > n) { atomicOr(&counters[1], kErrChain); r = x; break; }
       }
-      s_prefix = excl;
     }
+    key_clear[c] = kEmptyKey;
+    max_clear[c] = kEmptyKey;
+    root[c] = r;
+    is_root = r == c;
+    if (is_root) bound_next[c] = kNoBound;
+  }
+  const uint32_t be = __ballot_sync(0xffffffffu, emit), br = __ballot_sync(0xffffffffu, is_root);
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, emit ? __float_as_uint(E.w) : 0u);
+  if (lane == 0) {
+    s_warp[0][warp] = __popc(be);
+    s_warp[1][warp] = __popc(br);
+    s_wmax[warp] = wmax;
   }
   __syncthreads();
-  uint32_t run = s_prefix + s_warp[warp] + x - mine;
-#pragma unroll
-  for (int q = 0; q < kRelabelItems; ++q) {
-    int64_t k = first + q;
-    if (k < n) runs[k] = run;
-    run += (flags >> q) & 1u;
+  if (threadIdx.x == 32) {  // the largest weight emitted (for the output's key width)
+    uint32_t m = 0;
+    for (int w = 0; w < kBlock / 32; ++w) m = m > s_wmax[w] ? m : s_wmax[w];
+    if (m) atomicMax(&counters[11], m);
   }
+  if (threadIdx.x < 2) {
+    uint32_t tot = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+      const uint32_t v = s_warp[threadIdx.x][w];
+      s_warp[threadIdx.x][w] = tot;
+      tot += v;
+    }
+    s_base[threadIdx.x] = tot ? atomicAdd(&counters[threadIdx.x == 0 ? 0 : 12], tot) : 0u;
+  }
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  if (emit) edges[s_base[0] + s_warp[0][warp] + __popc(be & lt)] = E;
+  if (is_root) next_list[s_base[1] + s_warp[1][warp] + __popc(br & lt)] = c;
 }
 
 void launch_merge(Problem &P) {
   const int64_t count = P.active_list ? P.n_active : P.n;
   const int g = grid_for(count, kBlock);
   cudaMemsetAsync(P.counters + 12, 0, sizeof(uint32_t), P.stream);
-  k_merge_targets<<<g, kBlock, 0, P.stream>>>(P.active_list, count, P.comp_key, P.comp_max, P.inv,
-                                              P.labels, P.target, P.counters + 1);
-  k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.active_list, count, P.comp_key, P.comp_max, P.target,
-                                            P.root, P.edges, P.next_list, P.counters, P.n);
-  const int64_t tiles = (P.n + kRelabelTile - 1) / kRelabelTile;
-  uint32_t *ctr = P.counters + 24;
-  cudaMemsetAsync(ctr, 0, sizeof(uint32_t), P.stream);
-  cudaMemsetAsync(P.sort_lookback, 0, sizeof(uint32_t) * (size_t)tiles, P.stream);
-  k_relabel_runs<<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(
-      P.labels, P.root, P.pts, P.inst_of, P.n, P.labels_buf[P.cur ^ 1], P.bound_buf[P.cur ^ 1], P.runs,
-      P.sort_lookback, ctr, P.counters + 1);
-  P.launches += 3;
+  k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.active_list, count, P.comp_key, P.comp_max,
+                                            P.comp_key_buf[P.cur ^ 1], P.comp_max_buf[P.cur ^ 1],
+                                            P.bound_buf[P.cur ^ 1], P.root, P.edges, P.next_list, P.counters, P.n);
+  P.launches += 1;
+  launch_runs(P, true);
 }
 
 // After the host has seen a round finish: the next round's labels, bounds and
@@ -455,6 +453,8 @@ void advance_round(Problem &P, int64_t n_active) {
   P.cur ^= 1;
   P.labels = P.labels_buf[P.cur];
   P.bound = P.bound_buf[P.cur];
+  P.comp_key = P.comp_key_buf[P.cur];
+  P.comp_max = P.comp_max_buf[P.cur];
   uint32_t *t = P.list_buf[0] == P.next_list ? P.list_buf[1] : P.list_buf[0];
   P.active_list = P.next_list;
   P.next_list = t;
@@ -473,24 +473,42 @@ void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count) {
 }
 
 // ---------------------------------------------------------------------------
-// A12. Output order: (w, i, j) ascending, by two stable radix sorts (first by
-// j, then by (w bits << L) | i), then a gather.
+// A12. Output order: (w, i, j) ascending.  One radix sort by (w bits << L) | i
+// (only as many digits as the largest weight needs), then the runs of equal
+// (w, i) -- edges of one point with equal weights, at most the kissing
+// number of them in a minimum spanning tree -- are put in j order, then a
+// gather.
 // ---------------------------------------------------------------------------
-__global__ void k_edge_keys_j(const emst_edge *__restrict__ edges, int64_t m,
-                              uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m) return;
-  keys[e] = edges[e].j;
-  vals[e] = (uint32_t)e;
-}
-
 __global__ void k_edge_keys_wi(const emst_edge *__restrict__ edges, int64_t m,
-                               uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                               uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
                                int shift_i) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
-  emst_edge E = edges[vals[e]];
+  const emst_edge E = edges[e];
   keys[e] = ((uint64_t)__float_as_uint(E.w) << shift_i) | (uint64_t)E.i;
+  vals[e] = (uint32_t)e;
+}
+
+// The first thread of each run of equal keys orders the run by j (insertion
+// sort: the runs are a handful of edges long).
+__global__ void k_edge_ties(const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                            const emst_edge *__restrict__ edges, int64_t m) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e + 1 >= m) return;
+  const uint64_t key = keys[e];
+  if (keys[e + 1] != key || (e > 0 && keys[e - 1] == key)) return;
+  int64_t end = e + 2;
+  while (end < m && keys[end] == key) ++end;
+  for (int64_t a = e + 1; a < end; ++a) {
+    const uint32_t v = vals[a];
+    const uint32_t j = edges[v].j;
+    int64_t b = a;
+    while (b > e && edges[vals[b - 1]].j > j) {
+      vals[b] = vals[b - 1];
+      --b;
+    }
+    vals[b] = v;
+  }
 }
 
 __global__ void k_edge_keys_inst(const emst_edge *__restrict__ edges, int64_t m,
@@ -517,13 +535,13 @@ __global__ void k_edge_gather(const emst_edge *__restrict__ edges, int64_t m,
   out[e] = E;
 }
 
-void launch_edge_keys_j(Problem &P, int64_t m) {
-  k_edge_keys_j<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[0], P.vals[0]);
+void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i) {
+  k_edge_keys_wi<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[0], P.vals[0],
+                                                               shift_i);
   P.launches += 1;
 }
-void launch_edge_keys_wi(Problem &P, int64_t m, int src, int shift_i) {
-  k_edge_keys_wi<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[src], P.vals[src],
-                                                               shift_i);
+void launch_edge_ties(Problem &P, int64_t m, int src) {
+  k_edge_ties<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], P.edges, m);
   P.launches += 1;
 }
 void launch_edge_keys_inst(Problem &P, int64_t m, int src) {

@@ -13,6 +13,7 @@ namespace emst {
 
 constexpr int kRadix = 256;
 constexpr int kWarps = kSortThreads / 32;
+static_assert(kSortThreads == kRadix, "a sort pass gives each thread one digit");
 constexpr uint32_t kFlagAggregate = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1u;
@@ -74,7 +75,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-__global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
+__global__ void __launch_bounds__(kSortThreads, EMST_SORT_MIN_BLOCKS) k_sort_pass(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n, int shift,
     const uint32_t *__restrict__ digit_offset, uint32_t *lookback, uint32_t *tile_counter,

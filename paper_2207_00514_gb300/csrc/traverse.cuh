@@ -153,7 +153,6 @@ struct TravArgs {
   const uint32_t *inst_root;
   const int64_t *offsets;
   uint2 *res;
-  uint32_t *res_id;
   uint64_t *comp_key;
   int64_t n;
   uint32_t *status;
@@ -179,7 +178,6 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
     whi = __ldg(A.offsets + I + 1);
     if (start == kInvalid) {  // a one-point instance: nothing to find
       A.res[i] = make_uint2(0u, kInvalid);
-      A.res_id[i] = kInvalid;
       if (LEARNED) A.r_used[i] = kInf;
       return;
     }
@@ -209,7 +207,6 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
     // component's minimum edge: skip the query.
     if (CARRIED && __uint_as_float(prev.x) > q.radius) {
       A.res[i] = make_uint2(prev.x, kInvalid);
-      A.res_id[i] = kInvalid;
       if (LEARNED) A.r_used[i] = kInf;
       return;
     }
@@ -266,11 +263,11 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   if (q.bj != kInvalid) {
     const uint32_t oi = __float_as_uint(p.w);
     const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(A.pts[q.bj].w);
-    A.res_id[i] = oj;
     const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
-    atomicMin(reinterpret_cast<unsigned long long *>(A.comp_key + q.me), (unsigned long long)key);
-  } else {
-    A.res_id[i] = kInvalid;
+    // (many points of a large component find edges: only one that improves
+    // on the value seen now needs the atomic)
+    unsigned long long *ck = reinterpret_cast<unsigned long long *>(A.comp_key + q.me);
+    if ((unsigned long long)key < __ldcg(ck)) atomicMin(ck, (unsigned long long)key);
   }
 }
 
