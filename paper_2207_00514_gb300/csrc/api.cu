@@ -170,7 +170,7 @@ int bits_for(int64_t v) {  // bits needed to represent values in [0, v]
 }
 
 // A1-A4: scene box, codes, sort, gather, hierarchy, refit.
-void run_build(Problem &P, bool init_labels) {
+void run_build(Problem &P) {
   launch_scene_box(P);
   if (P.num_inst > 1) launch_instance_ids(P);
   launch_morton(P);
@@ -184,7 +184,7 @@ void run_build(Problem &P, bool init_labels) {
   if (P.n >= 2) {
     cudaMemsetAsync(P.arrivals, 0, sizeof(uint32_t) * (size_t)(P.nc - 1), P.stream);
     launch_hierarchy(P);
-    launch_refit(P, init_labels);
+    launch_refit(P);
     if (P.num_inst > 1) launch_instance_roots(P);
   }
 }
@@ -218,10 +218,13 @@ void run_output(Problem &P, emst_edge *out, uint32_t w_bits) {
   launch_edge_keys_wi(P, m, L);
   int s = radix_sort_pairs(P, m, 0, (L + wb + 7) / 8, 0);
   launch_edge_ties(P, m, s);
-  if (P.num_inst > 1) {  // instance is the most significant key (stable LSD)
-    launch_edge_keys_inst(P, m, s);
-    s = radix_sort_pairs(P, m, 0, (P.inst_bits + 7) / 8, s);
+  if (P.num_inst == 1) {
+    launch_edge_from_keys(P, m, s, L, out);
+    return;
   }
+  // instance is the most significant key (stable LSD)
+  launch_edge_keys_inst(P, m, s);
+  s = radix_sort_pairs(P, m, 0, (P.inst_bits + 7) / 8, s);
   launch_edge_gather(P, m, P.vals[s], out);
 }
 
@@ -356,7 +359,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     CU(cudaMemcpyAsync((void *)P.mlp, mlp_params, sizeof(float) * EMST_MLP_PARAMS,
                        cudaMemcpyDefault, stream));
   if (logging) CU(cudaMemsetAsync(P.log_count, 0, sizeof(unsigned long long), stream));
-  run_build(P, true);
+  run_build(P);
   tm.mark(1, stream);
   // Non-finite input is reported before any round runs.
   CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(host_counters), cudaMemcpyDeviceToHost,
@@ -604,7 +607,7 @@ int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint6
   int rc = open_session(S, points, n, dim, leaf_size, s);
   if (rc != EMST_OK) return rc;
   Problem &P = S.P;
-  run_build(P, true);
+  run_build(P);
   const int64_t m = P.nc - 1;
   if (out_codes) cudaMemcpyAsync(out_codes, P.keys[0], 8 * (size_t)n, cudaMemcpyDeviceToDevice, s);
   if (out_perm) cudaMemcpyAsync(out_perm, P.perm, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
@@ -627,7 +630,7 @@ int emst_round_step(const float *points, int64_t n, int dim, int leaf_size,
   int rc = open_session(S, points, n, dim, leaf_size, s);
   if (rc != EMST_OK) return rc;
   Problem &P = S.P;
-  run_build(P, false);
+  run_build(P);
   cudaMemcpyAsync(P.labels, labels_in, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
   reset_round_state(P);
   launch_label_runs(P);

@@ -219,7 +219,7 @@ __device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k, int6
 }
 
 __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict__ keys, int64_t nc,
-                                                      int leaf, NodeRec *__restrict__ nodes,
+                                                      int leaf,
                                                       uint32_t *__restrict__ parent_leaf,
                                                       uint2 *__restrict__ up_delta,
                                                       uint4 *__restrict__ range) {
@@ -243,7 +243,6 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
   int64_t lo = i < j ? i : j, hi = i < j ? j : i;
   uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
   uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
-  reinterpret_cast<uint2 *>(&nodes[i].d)[0] = make_uint2(left, right);
   range[i] = make_uint4((uint32_t)lo, (uint32_t)gamma, (uint32_t)hi, 0u);
   reinterpret_cast<uint32_t *>(up_delta + i)[1] = (uint32_t)dnode;
   uint32_t up = (uint32_t)i << 1;
@@ -256,30 +255,34 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
 
 void launch_hierarchy(Problem &P) {
   k_hierarchy<<<grid_for(P.nc - 1, kBlock), kBlock, 0, P.stream>>>(
-      P.keys[0] /*sorted*/, P.nc, P.leaf, P.nodes, P.parent_leaf, P.up_delta, P.range);
+      P.keys[0] /*sorted*/, P.nc, P.leaf, P.parent_leaf, P.up_delta, P.range);
   P.launches += 1;
 }
 
 // ---------------------------------------------------------------------------
-// A4 (c). Refit: bottom-up boxes.  One thread per leaf chunk writes the box of
-// its points into its slot of the parent record, then climbs: at every node the first
-// arriver stops and the second merges the two child boxes and carries the
-// union one level up.  Wait-free.
+// A4 (c). Refit: bottom-up boxes.  One thread per leaf chunk computes the box
+// of its points and climbs: at every node the first arriver leaves its box
+// for its sibling and stops; the second merges the two child boxes, writes
+// the node's whole record once (both boxes, the child references from the
+// node's range, and the child labels) and carries the union one level up.
+// Wait-free.
 // A node whose leaf range lies inside this CTA's 256 chunks has both arrivals
-// from this CTA, so it is counted in shared memory with block-scope fences;
-// only nodes spanning CTAs use the global counters (about 2 per 256 leaves
-// per level above the CTA).  The global counters are never reset: each pass
-// adds exactly two arrivals per node, so the parity of the count before the
-// add tells first from second.
-// With init_labels, the round-0 child labels are written on the way
-// (a one-point chunk k: label k; otherwise several components, kInvalid).
+// from this CTA (and its index inside the CTA's range, one end of its range),
+// so both child boxes meet in shared memory and the arrivals are counted
+// there with block-scope fences; only nodes spanning CTAs (about 2 per 256
+// leaves per level above the CTA) pass the box through their global record
+// and use the global counters.  The global counters are never reset: each
+// pass adds exactly two arrivals per node, so the parity of the count before
+// the add tells first from second.
+// The child labels are the round-0 ones (a one-point chunk k: label k;
+// otherwise several components, kInvalid); a caller with other labels
+// rewrites them (A5).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, float lx, float ly, float lz,
-                                               float hx, float hy, float hz) {
+__device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, const float *bx) {
   float2 *f = reinterpret_cast<float2 *>(rec) + 3 * slot;
-  f[0] = make_float2(lx, ly);
-  f[1] = make_float2(lz, hx);
-  f[2] = make_float2(hy, hz);
+  f[0] = make_float2(bx[0], bx[1]);
+  f[1] = make_float2(bx[2], bx[3]);
+  f[2] = make_float2(bx[4], bx[5]);
 }
 
 __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
@@ -287,7 +290,8 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
                                                   const uint32_t *__restrict__ parent_leaf,
                                                   const uint2 *__restrict__ up_delta,
                                                   const uint4 *__restrict__ range,
-                                                  uint32_t *arrivals, int init_labels) {
+                                                  uint32_t *arrivals) {
+  __shared__ float s_box[kBlock][2][6];  // both child boxes of each local node
   __shared__ uint32_t s_arrive[kBlock];
   const int64_t first = (int64_t)blockIdx.x * kBlock;
   const int64_t last = first + kBlock - 1;
@@ -297,57 +301,71 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
   if (k >= nc) return;
   const int64_t p0 = k * leaf, p1 = p0 + leaf < n ? p0 + leaf : n;
   float4 p = pts[p0];
-  float bx0 = p.x, by0 = p.y, bz0 = p.z, bx1 = p.x, by1 = p.y, bz1 = p.z;
+  float box[6] = {p.x, p.y, p.z, p.x, p.y, p.z};
   for (int64_t m = p0 + 1; m < p1; ++m) {
     p = pts[m];
-    bx0 = fminf(bx0, p.x); by0 = fminf(by0, p.y); bz0 = fminf(bz0, p.z);
-    bx1 = fmaxf(bx1, p.x); by1 = fmaxf(by1, p.y); bz1 = fmaxf(bz1, p.z);
+    box[0] = fminf(box[0], p.x); box[1] = fminf(box[1], p.y); box[2] = fminf(box[2], p.z);
+    box[3] = fmaxf(box[3], p.x); box[4] = fmaxf(box[4], p.y); box[5] = fmaxf(box[5], p.z);
   }
   uint32_t up = parent_leaf[k];
-  uint32_t node = up >> 1;
-  int slot = (int)(up & 1u);
-  store_slot_box(&nodes[node], slot, bx0, by0, bz0, bx1, by1, bz1);
-  if (init_labels)  // round 0: every point is its own component (label = its position)
-    reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = p1 - p0 == 1 ? (uint32_t)p0 : kInvalid;
   while (true) {
+    const uint32_t node = up >> 1;
+    const int slot = (int)(up & 1u);
     const uint4 r = __ldg(range + node);
     const bool local = (int64_t)r.x >= first && (int64_t)r.z <= last;
-    float4 a, b, c;
+    float sib[6];
     if (local) {
+#pragma unroll
+      for (int t = 0; t < 6; ++t) s_box[node - first][slot][t] = box[t];
       __threadfence_block();
-      const uint32_t before = atomicAdd(&s_arrive[node - first], 1u);
-      if (before == 0u) return;  // first arriver: the sibling will carry on
+      if (atomicAdd(&s_arrive[node - first], 1u) == 0u) return;  // first: the sibling carries on
       __threadfence_block();
-      const float4 *rec = reinterpret_cast<const float4 *>(&nodes[node]);
-      a = rec[0];
-      b = rec[1];
-      c = rec[2];
+#pragma unroll
+      for (int t = 0; t < 6; ++t) sib[t] = s_box[node - first][slot ^ 1][t];
     } else {
+      store_slot_box(&nodes[node], slot, box);
       __threadfence();
       const uint32_t before = atomicAdd(&arrivals[node], 1u);
       if ((before & 1u) == 0u) return;
       __threadfence();
-      const float4 *rec = reinterpret_cast<const float4 *>(&nodes[node]);
-      a = __ldcg(rec);
-      b = __ldcg(rec + 1);
-      c = __ldcg(rec + 2);
+      const float2 *f = reinterpret_cast<const float2 *>(&nodes[node]) + 3 * (slot ^ 1);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const float2 v = __ldcg(f + t);
+        sib[2 * t] = v.x;
+        sib[2 * t + 1] = v.y;
+      }
     }
-    // left box: a.x a.y a.z | a.w b.x b.y ; right box: b.z b.w c.x | c.y c.z c.w
-    const float lx = fminf(a.x, b.z), ly = fminf(a.y, b.w), lz = fminf(a.z, c.x);
-    const float hx = fmaxf(a.w, c.y), hy = fmaxf(b.x, c.z), hz = fmaxf(b.y, c.w);
+    const float *L = slot == 0 ? box : sib;
+    const float *R = slot == 0 ? sib : box;
+    // the whole record: boxes, references (leaves where the range ends at the
+    // split), round-0 child labels
+    const uint32_t g = r.y;
+    const bool lleaf = r.x == g, rleaf = r.z == g + 1u;
+    // a chunk of exactly one point is its own component in round 0
+    auto one_point = [&](int64_t c) { return n - c * leaf == 1 || leaf == 1; };
+    NodeRec rec;
+    rec.a = make_float4(L[0], L[1], L[2], L[3]);
+    rec.b = make_float4(L[4], L[5], R[0], R[1]);
+    rec.c = make_float4(R[2], R[3], R[4], R[5]);
+    rec.d = make_uint4(lleaf ? (kLeafBit | g) : g, rleaf ? (kLeafBit | (g + 1u)) : g + 1u,
+                       lleaf && one_point(g) ? (uint32_t)((int64_t)g * leaf) : kInvalid,
+                       rleaf && one_point(g + 1) ? (uint32_t)((int64_t)(g + 1) * leaf) : kInvalid);
+    nodes[node] = rec;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      box[t] = fminf(L[t], R[t]);
+      box[3 + t] = fmaxf(L[3 + t], R[3 + t]);
+    }
     if (node == 0) return;
     up = up_delta[node].x;
-    node = up >> 1;
-    slot = (int)(up & 1u);
-    store_slot_box(&nodes[node], slot, lx, ly, lz, hx, hy, hz);
-    if (init_labels) reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = kInvalid;
   }
 }
 
-void launch_refit(Problem &P, bool init_labels) {
-  k_refit<<<grid_for(P.nc, kBlock), kBlock, 0, P.stream>>>(P.pts, P.n, P.nc, P.leaf, P.nodes, P.parent_leaf,
-                                                          P.up_delta, P.range, P.arrivals,
-                                                          init_labels ? 1 : 0);
+void launch_refit(Problem &P) {
+  k_refit<<<grid_for(P.nc, kBlock), kBlock, 0, P.stream>>>(P.pts, P.n, P.nc, P.leaf, P.nodes,
+                                                          P.parent_leaf, P.up_delta, P.range,
+                                                          P.arrivals);
   P.launches += 1;
 }
 

@@ -251,17 +251,17 @@ void launch_gather(Problem &P, const uint32_t *perm);
 void launch_instance_ids(Problem &P);
 void launch_instance_roots(Problem &P);
 void launch_hierarchy(Problem &P);
-void launch_refit(Problem &P, bool init_labels);
+void launch_refit(Problem &P);
 // sort.cu
 // Tile shape of one sort pass (compile-time knobs; the defaults are the measured best).
 #ifndef EMST_SORT_THREADS
 #define EMST_SORT_THREADS 256
 #endif
 #ifndef EMST_SORT_ITEMS
-#define EMST_SORT_ITEMS 8
+#define EMST_SORT_ITEMS 12
 #endif
 #ifndef EMST_SORT_MIN_BLOCKS
-#define EMST_SORT_MIN_BLOCKS 4
+#define EMST_SORT_MIN_BLOCKS 3
 #endif
 constexpr int kSortThreads = EMST_SORT_THREADS;
 constexpr int kSortItems = EMST_SORT_ITEMS;
@@ -284,6 +284,7 @@ void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
 // output
 void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i);
 void launch_edge_ties(Problem &P, int64_t m, int src);
+void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, emst_edge *out);
 void launch_edge_keys_inst(Problem &P, int64_t m, int src);
 // learned.cu
 void launch_comp_sizes(Problem &P);
@@ -300,7 +301,7 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges);
 int status_from_bits(uint32_t bits);
 int check_args(const float *points, int64_t n, int dim);
 int bits_for(int64_t v);
-void run_build(Problem &P, bool init_labels);
+void run_build(Problem &P);
 void reset_round_state(Problem &P);
 void run_round(Problem &P, int round, bool carried, int block, bool count);
 // Leaf chunk size actually used for n points and a requested size (0 =

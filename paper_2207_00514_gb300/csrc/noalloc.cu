@@ -89,7 +89,7 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
   if (!pts_dev && cudaMemcpyAsync((void *)P.points, points, sizeof(float) * (size_t)n * dim,
                                   cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return EMST_ERR_CUDA;
-  run_build(P, true);  // clears its own histograms, tile counters, look-back and arrivals
+  run_build(P);  // clears its own histograms, tile counters, look-back and arrivals
   if (!sync_counters()) return EMST_ERR_CUDA;
   if (host_counters[1] != 0) return status_from_bits(host_counters[1]);
   if (n >= 2) {

@@ -476,39 +476,56 @@ void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count) {
 // A12. Output order: (w, i, j) ascending.  One radix sort by (w bits << L) | i
 // (only as many digits as the largest weight needs), then the runs of equal
 // (w, i) -- edges of one point with equal weights, at most the kissing
-// number of them in a minimum spanning tree -- are put in j order, then a
-// gather.
+// number of them in a minimum spanning tree -- are put in j order.  With one
+// instance the sorted value is j itself and the edges are rebuilt from
+// (key, value); with several the value is the edge's index (a stable sort by
+// instance follows) and a gather builds them.
 // ---------------------------------------------------------------------------
 __global__ void k_edge_keys_wi(const emst_edge *__restrict__ edges, int64_t m,
                                uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                               int shift_i) {
+                               int shift_i, int direct) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   const emst_edge E = edges[e];
   keys[e] = ((uint64_t)__float_as_uint(E.w) << shift_i) | (uint64_t)E.i;
-  vals[e] = (uint32_t)e;
+  vals[e] = direct ? E.j : (uint32_t)e;
 }
 
 // The first thread of each run of equal keys orders the run by j (insertion
 // sort: the runs are a handful of edges long).
 __global__ void k_edge_ties(const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                            const emst_edge *__restrict__ edges, int64_t m) {
+                            const emst_edge *__restrict__ edges, int64_t m, int direct) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e + 1 >= m) return;
   const uint64_t key = keys[e];
   if (keys[e + 1] != key || (e > 0 && keys[e - 1] == key)) return;
   int64_t end = e + 2;
   while (end < m && keys[end] == key) ++end;
+  auto j_of = [&](uint32_t v) { return direct ? v : edges[v].j; };
   for (int64_t a = e + 1; a < end; ++a) {
     const uint32_t v = vals[a];
-    const uint32_t j = edges[v].j;
+    const uint32_t j = j_of(v);
     int64_t b = a;
-    while (b > e && edges[vals[b - 1]].j > j) {
+    while (b > e && j_of(vals[b - 1]) > j) {
       vals[b] = vals[b - 1];
       --b;
     }
     vals[b] = v;
   }
+}
+
+// One instance: edge e of the output from its sorted key ((w << L) | i) and j.
+__global__ void k_edge_from_keys(const uint64_t *__restrict__ keys,
+                                 const uint32_t *__restrict__ vals, int64_t m, int shift_i,
+                                 emst_edge *__restrict__ out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const uint64_t k = keys[e];
+  emst_edge E;
+  E.i = (uint32_t)(k & ((1ull << shift_i) - 1ull));
+  E.j = vals[e];
+  E.w = __uint_as_float((uint32_t)(k >> shift_i));
+  out[e] = E;
 }
 
 __global__ void k_edge_keys_inst(const emst_edge *__restrict__ edges, int64_t m,
@@ -537,11 +554,17 @@ __global__ void k_edge_gather(const emst_edge *__restrict__ edges, int64_t m,
 
 void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i) {
   k_edge_keys_wi<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[0], P.vals[0],
-                                                               shift_i);
+                                                               shift_i, P.num_inst == 1);
   P.launches += 1;
 }
 void launch_edge_ties(Problem &P, int64_t m, int src) {
-  k_edge_ties<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], P.edges, m);
+  k_edge_ties<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], P.edges, m,
+                                                            P.num_inst == 1);
+  P.launches += 1;
+}
+void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, emst_edge *out) {
+  k_edge_from_keys<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], m,
+                                                                 shift_i, out);
   P.launches += 1;
 }
 void launch_edge_keys_inst(Problem &P, int64_t m, int src) {

@@ -18,6 +18,7 @@ constexpr uint32_t kFlagAggregate = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1u;
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kLookWindow = 8;  // preceding tiles read per look-back round trip
 
 int64_t sort_tiles_for(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 
@@ -144,26 +145,39 @@ __global__ void __launch_bounds__(kSortThreads, EMST_SORT_MIN_BLOCKS) k_sort_pas
     if (lane >= o) x += y;
   }
   if (lane == 31) S.warp_tot[warp] = x;
-  // Look back over preceding tiles for digit t.
+  // Look back over preceding tiles for digit t, kLookWindow tiles per round
+  // trip: sum their counts in order up to the nearest finished prefix; a
+  // tile that has not published yet is waited for.
   uint32_t excl = 0;
   if (tile > 0) {
     int64_t j = (int64_t)tile - 1;
-    while (j >= 0) {
-      const volatile uint32_t *lb = lookback + j * kRadix + t;
-      uint32_t wv = *lb;
-      int spins = 0;
-      while ((wv & ~kValueMask) == 0u) {
-        if (++spins > kSpinLimit) {
+    int spins = 0;
+    for (;;) {
+      uint32_t wv[kLookWindow];
+#pragma unroll
+      for (int w = 0; w < kLookWindow; ++w)
+        wv[w] = j - w >= 0 ? *reinterpret_cast<const volatile uint32_t *>(lookback + (j - w) * kRadix + t)
+                           : kFlagPrefix;  // before tile 0: a finished prefix of 0
+      int used = 0;
+      bool done = false, stall = false;
+#pragma unroll
+      for (int w = 0; w < kLookWindow; ++w) {
+        if (done || stall) continue;
+        const uint32_t f = wv[w] & ~kValueMask;
+        if (f == 0u) { stall = true; continue; }
+        excl += wv[w] & kValueMask;
+        ++used;
+        done = f == kFlagPrefix;
+      }
+      if (done) break;
+      j -= used;
+      if (stall) {
+        if (++spins > kSpinLimit) {  // give up: results are invalid, the status says so
           atomicOr(status, kErrSpin);
-          wv = kFlagPrefix;  // give up: results are invalid, the status says so
           break;
         }
         __nanosleep(32);
-        wv = *lb;
       }
-      excl += wv & kValueMask;
-      if ((wv & ~kValueMask) == kFlagPrefix) break;
-      --j;
     }
     volatile uint32_t *mine = lookback + (int64_t)tile * kRadix + t;
     *mine = kFlagPrefix | ((excl + total) & kValueMask);

@@ -71,6 +71,17 @@ __device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, float d1, int l
 // record, scan accepted leaf chunks, descend into the nearer accepted
 // internal child and stack the farther one with its box distance (re-tested
 // when popped).
+// One node record in two 32-byte loads (the record is 64-byte aligned).
+__device__ __forceinline__ void load_record(const NodeRec *rec, float4 &a, float4 &b, float4 &c,
+                                            uint4 &dd) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(rec));
+  asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(c.x), "=f"(c.y), "=f"(c.z), "=f"(c.w), "=r"(dd.x), "=r"(dd.y), "=r"(dd.z), "=r"(dd.w)
+      : "l"(reinterpret_cast<const char *>(rec) + 32));
+}
+
 template <bool COUNT, bool CHUNKS>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
                                         const float4 *__restrict__ pts,
@@ -80,9 +91,9 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
   int sp = 0;
   while (true) {
     if (COUNT) ++nvis;
-    const float4 *r = reinterpret_cast<const float4 *>(nodes + node);
-    const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
-    const uint4 dd = __ldg(reinterpret_cast<const uint4 *>(r + 3));
+    float4 a, b, c;
+    uint4 dd;
+    load_record(nodes + node, a, b, c, dd);
     const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
     const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
     bool okL = (dd.z != q.me) && (dL <= q.radius);
