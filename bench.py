@@ -125,10 +125,10 @@ def measured_peaks():
 
 def traversal_algorithmic_bytes(n: int) -> float:
     """Bytes one traversal launch must move at least: per query point its
-    record (16 B), label (4), bound (4), result (8 + 4) and the component
-    minimum atomic (8); plus every internal node record once (64 B): the
-    early rounds touch essentially the whole tree."""
-    return n * (16 + 4 + 4 + 8 + 4 + 8) + (n - 1) * 64.0
+    record (16 B), label (4), bound (4), the component's best so far (8), its
+    result (8) and the component minimum atomic (8); plus every internal node
+    record once (64 B): the early rounds touch essentially the whole tree."""
+    return n * (16 + 4 + 4 + 8 + 8 + 8) + (n - 1) * 64.0
 
 
 def cpu_oracle_run(pts_sample, threads):

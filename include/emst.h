@@ -67,7 +67,7 @@ typedef enum emst_status {
 /* Options for emst_compute_ex.  Zero-initialise, then set struct_size. */
 typedef struct emst_options {
   int32_t struct_size;        /* sizeof(emst_options) */
-  int32_t block_size;         /* traversal CTA size: 0 = default, else 64..1024, multiple of 32 */
+  int32_t block_size;         /* traversal CTA size: 0 = default (128), else 64..256, multiple of 32 */
   int32_t carried_radius;     /* 1 (default if struct_size==0) = seed each query with the previous
                                  round's neighbour when it is still in another component */
   int32_t use_graph;          /* 1 = run the round loop as a CUDA graph with a device-side

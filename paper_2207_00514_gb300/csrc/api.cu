@@ -301,7 +301,8 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     leaf_req = opt->leaf_size;
     mlp_params = opt->mlp_params;
     if (leaf_req < 0 || leaf_req > 16 || (leaf_req & (leaf_req - 1)) != 0) return EMST_ERR_INVALID_ARG;
-    if (block != 0 && (block < 64 || block > 1024 || block % 32 != 0)) return EMST_ERR_INVALID_ARG;
+    if (block != 0 && (block < 64 || block > kTraverseMaxBlock || block % 32 != 0))
+      return EMST_ERR_INVALID_ARG;
   } else if (opt && opt->struct_size != 0) {
     return EMST_ERR_INVALID_ARG;
   }
@@ -409,6 +410,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
       }
       launch_reduce(P);
       launch_merge(P);
+      CU(cudaPeekAtLastError());  // a launch that failed must not read as a round without edges
       CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(host_counters), cudaMemcpyDeviceToHost,
                          stream));
       CU(cudaStreamSynchronize(stream));

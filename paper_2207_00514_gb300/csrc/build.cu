@@ -311,7 +311,9 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
   while (true) {
     const uint32_t node = up >> 1;
     const int slot = (int)(up & 1u);
+    // both depend on the node only: one round trip per level
     const uint4 r = __ldg(range + node);
+    const uint32_t up_next = __ldg(&up_delta[node].x);
     const bool local = (int64_t)r.x >= first && (int64_t)r.z <= last;
     float sib[6];
     if (local) {
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
       box[3 + t] = fmaxf(L[3 + t], R[3 + t]);
     }
     if (node == 0) return;
-    up = up_delta[node].x;
+    up = up_next;
   }
 }
 

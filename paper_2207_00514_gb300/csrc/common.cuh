@@ -271,6 +271,8 @@ int64_t sort_tiles_for(int64_t n);
 // (8-bit digits).  Returns the index (0/1) of the buffers holding the result.
 int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int src);
 // rounds.cu
+constexpr int kTraverseBlock = 128;     // default traversal CTA size (measured best)
+constexpr int kTraverseMaxBlock = 256;  // largest the traversal kernels are compiled for
 int64_t scan_tiles_for(int64_t n);
 void launch_label_runs(Problem &P);
 void launch_node_labels(Problem &P);

@@ -22,6 +22,7 @@ namespace emst {
 
 constexpr int kIn = EMST_MLP_FEATURES;
 constexpr int kHid = 64;
+constexpr int kFeatureWindow = 4;  // curve neighbours on each side in features 3 and 4
 constexpr int kOffMu = 0, kOffSigma = 8, kOffOutMu = 16, kOffOutSigma = 17, kOffMargin = 18;
 constexpr int kOffW1 = 20;
 constexpr int kOffB1 = kOffW1 + kHid * kIn;
@@ -92,7 +93,7 @@ __device__ __forceinline__ void point_features(const FeatArgs &A, int64_t i, flo
   float wmin = 1e30f, wsum = 0.f;
   int cnt = 0;
 #pragma unroll
-  for (int o = -kWindow; o <= kWindow; ++o) {
+  for (int o = -kFeatureWindow; o <= kFeatureWindow; ++o) {
     const int64_t j = i + o;
     if (o == 0 || j < wlo || j >= whi) continue;
     const float4 c = __ldg(A.pts + j);

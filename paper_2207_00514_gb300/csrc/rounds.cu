@@ -235,7 +235,7 @@ void launch_upper_bounds(Problem &P) {
 // One thread per point, or (list != nullptr) a grid-stride pass over the
 // listed points (the certification reruns of the learned radius).
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED>
-__global__ void __launch_bounds__(kBlock) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
+__global__ void __launch_bounds__(kTraverseMaxBlock) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (list) {
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(TravArgs A, const uint32_t 
 
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
                      bool seeded, int learned_pass) {
-  if (block <= 0) block = kBlock;
+  if (block <= 0) block = kTraverseBlock;
   TravArgs A;
   A.pts = P.pts;
   A.nodes = P.nodes;

@@ -8,7 +8,6 @@
 namespace emst {
 
 constexpr int kStackDepth = 100;  // > 96 = the deepest possible path (see traverse_one)
-constexpr int kWindow = 4;        // curve neighbours on each side that seed a query
 
 // Per-query state of Algorithm 2.
 struct Query {
@@ -143,9 +142,8 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
 // Ends with the first half of the per-component minimum (A8): an atomicMin of
 // (w bits << 32 | min original id) per component.
 // SEEDED (the emst_compute path) also tightens each cutoff with the
-// component's best weight found so far and with the point's best curve
-// neighbour in another component (both real cross edges, so never below the
-// component minimum), reports the exact nearest neighbour within that cutoff
+// component's best weight found so far (a real cross edge, so never below
+// the component minimum), reports the exact nearest neighbour within that cutoff
 // (or none), and keeps a per-point lower bound for the next round (res.x):
 // a point whose bound exceeds its component's cutoff skips its query.  The
 // endpoint of every component's minimum edge still finds it, so the minima
@@ -179,14 +177,11 @@ template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bo
 __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   const float kInf = __int_as_float(0x7f800000);
   const int64_t n = A.n;
-  // Batched form: search only this point's instance (its subtree, its curve range).
+  // Batched form: search only this point's instance (its subtree).
   uint32_t start = 0u;
-  int64_t wlo = 0, whi = n;
   if (A.inst_of) {
     const uint32_t I = __ldg(A.inst_of + i);
     start = __ldg(A.inst_root + I);
-    wlo = __ldg(A.offsets + I);
-    whi = __ldg(A.offsets + I + 1);
     if (start == kInvalid) {  // a one-point instance: nothing to find
       A.res[i] = make_uint2(0u, kInvalid);
       if (LEARNED) A.r_used[i] = kInf;
@@ -226,25 +221,6 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   // cross edge of this point: a per-point cutoff.
   if (CARRIED && prev.y != kInvalid && A.labels[prev.y] != q.me)
     q.radius = fminf(q.radius, __uint_as_float(prev.x));
-  if (SEEDED) {
-    // Curve neighbours within kWindow positions in other components: real
-    // candidates, so their best weight is a valid (inclusive) cutoff.
-#pragma unroll
-    for (int o = -kWindow; o <= kWindow; ++o) {
-      const int64_t j = i + o;
-      if (o == 0 || j < wlo || j >= whi) continue;
-      if (__ldg(A.labels + j) == q.me) continue;
-      const float4 c = __ldg(A.pts + j);
-      const float d = sq_dist(q.px, q.py, q.pz, c.x, c.y, c.z);
-      const uint32_t idj = __float_as_uint(c.w);
-      if (q.bj == kInvalid || d < q.best || (d == q.best && idj < q.bid)) {
-        q.best = d;
-        q.bj = (uint32_t)j;
-        q.bid = idj;
-      }
-    }
-    q.radius = fminf(q.radius, q.best);
-  }
   if (LEARNED) q.radius = fminf(q.radius, __ldg(A.pred_r + i));
   const float r0 = q.radius;  // the search is exact within this cutoff
   if (LEARNED) A.r_used[i] = r0;

@@ -244,6 +244,13 @@ def test_repeatable_and_stats(pkg):
     assert st["node_visits"] > 0 and st["kernel_launches"] > 0
     c, _ = pkg.emst_compute_ex(t, carried_radius=False, block_size=128)
     assert_same_edges(pkg.edges_numpy(c), pkg.edges_numpy(b), "options")
+    for block in (64, 192, 256):
+        d, _ = pkg.emst_compute_ex(t, block_size=block)
+        assert_same_edges(pkg.edges_numpy(d), pkg.edges_numpy(b), f"block {block}")
+    # larger CTAs than the traversal is compiled for are refused, not run
+    with pytest.raises(pkg.EmstError) as ei:
+        pkg.emst_compute_ex(t, block_size=512)
+    assert ei.value.status == -1
     for leaf in (1, 2, 8, 16):
         d, _ = pkg.emst_compute_ex(t, leaf_size=leaf)
         assert_same_edges(pkg.edges_numpy(d), pkg.edges_numpy(b), f"leaf size {leaf}")
