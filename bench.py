@@ -32,6 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = "EMST Mpoints/s at 37M 3D clustered, plain vs learned-radius; % HBM roofline"
 WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member counts m^-1.9 on "
             "[10, 1e5], c = 5, r_vir = 0.01 (m/1e5)^(1/3)), 20% uniform, unit box, seed 2")
+# DRAM bytes (read + write) per k_traverse launch on this workload: the average
+# over one call's 11 launches of an ncu capture of this command
+# (--metrics dram__bytes_read.sum,dram__bytes_write.sum; profiles/k_traverse_dram_halos_37M.md).
+# Set back to None whenever the traversal kernel changes.
 TRAVERSE_DRAM_BYTES_PER_LAUNCH = None
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")

@@ -271,6 +271,9 @@ int64_t sort_tiles_for(int64_t n);
 // (8-bit digits).  Returns the index (0/1) of the buffers holding the result.
 int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int src);
 // rounds.cu
+#ifndef EMST_TRAVERSE_MIN_BLOCKS
+#define EMST_TRAVERSE_MIN_BLOCKS 8      // resident 256-thread CTAs the traversal's registers must allow (32 registers: measured best)
+#endif
 constexpr int kTraverseBlock = 128;     // default traversal CTA size (measured best)
 constexpr int kTraverseMaxBlock = 256;  // largest the traversal kernels are compiled for
 int64_t scan_tiles_for(int64_t n);

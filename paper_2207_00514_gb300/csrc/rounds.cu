@@ -235,7 +235,7 @@ void launch_upper_bounds(Problem &P) {
 // One thread per point, or (list != nullptr) a grid-stride pass over the
 // listed points (the certification reruns of the learned radius).
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED>
-__global__ void __launch_bounds__(kTraverseMaxBlock) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
+__global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (list) {
