@@ -93,6 +93,7 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.vals[0] = c.take<uint32_t>(n);
   P.vals[1] = c.take<uint32_t>(n);
   P.nodes = c.take<NodeRec>(nc - 1);
+  P.nlabels = c.take<uint2>(nc - 1);
   P.parent_leaf = c.take<uint32_t>(nc);
   P.up_delta = c.take<uint2>(nc - 1);
   P.arrivals = c.take<uint32_t>(nc - 1);
@@ -638,8 +639,8 @@ int emst_round_step(const float *points, int64_t n, int dim, int leaf_size,
   launch_label_runs(P);
   launch_node_labels(P);
   if (out_node_labels)
-    cudaMemcpy2DAsync(out_node_labels, 8, reinterpret_cast<char *>(P.nodes) + 56, 64, 8,
-                      (size_t)(P.nc - 1), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(out_node_labels, P.nlabels, sizeof(uint2) * (size_t)(P.nc - 1),
+                    cudaMemcpyDeviceToDevice, s);
   launch_upper_bounds(P);
   if (out_upper_bound)
     k_bound_to_float<<<grid_for(n, 256), 256, 0, s>>>(P.bound, out_upper_bound, n);

@@ -263,8 +263,8 @@ void launch_hierarchy(Problem &P) {
 // A4 (c). Refit: bottom-up boxes.  One thread per leaf chunk computes the box
 // of its points and climbs: at every node the first arriver leaves its box
 // for its sibling and stops; the second merges the two child boxes, writes
-// the node's whole record once (both boxes, the child references from the
-// node's range, and the child labels) and carries the union one level up.
+// the node's whole record once (both boxes and the child references from the
+// node's range) and its child labels, and carries the union one level up.
 // Wait-free.
 // A node whose leaf range lies inside this CTA's 256 chunks has both arrivals
 // from this CTA (and its index inside the CTA's range, one end of its range),
@@ -287,6 +287,7 @@ __device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, const flo
 
 __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
                                                   int64_t nc, int leaf, NodeRec *nodes,
+                                                  uint2 *__restrict__ nlabels,
                                                   const uint32_t *__restrict__ parent_leaf,
                                                   const uint2 *__restrict__ up_delta,
                                                   const uint4 *__restrict__ range,
@@ -350,10 +351,10 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
     rec.a = make_float4(L[0], L[1], L[2], L[3]);
     rec.b = make_float4(L[4], L[5], R[0], R[1]);
     rec.c = make_float4(R[2], R[3], R[4], R[5]);
-    rec.d = make_uint4(lleaf ? (kLeafBit | g) : g, rleaf ? (kLeafBit | (g + 1u)) : g + 1u,
-                       lleaf && one_point(g) ? (uint32_t)((int64_t)g * leaf) : kInvalid,
-                       rleaf && one_point(g + 1) ? (uint32_t)((int64_t)(g + 1) * leaf) : kInvalid);
+    rec.d = make_uint4(lleaf ? (kLeafBit | g) : g, rleaf ? (kLeafBit | (g + 1u)) : g + 1u, 0u, 0u);
     nodes[node] = rec;
+    nlabels[node] = make_uint2(lleaf && one_point(g) ? (uint32_t)((int64_t)g * leaf) : kInvalid,
+                               rleaf && one_point(g + 1) ? (uint32_t)((int64_t)(g + 1) * leaf) : kInvalid);
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
       box[t] = fminf(L[t], R[t]);
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
 
 void launch_refit(Problem &P) {
   k_refit<<<grid_for(P.nc, kBlock), kBlock, 0, P.stream>>>(P.pts, P.n, P.nc, P.leaf, P.nodes,
-                                                          P.parent_leaf, P.up_delta, P.range,
+                                                          P.nlabels, P.parent_leaf, P.up_delta, P.range,
                                                           P.arrivals);
   P.launches += 1;
 }

@@ -25,11 +25,12 @@ enum : uint32_t {
 // One internal node of the hierarchy, 64 bytes.  The boxes of both children
 // travel with the parent, so a query visiting the node tests both children
 // with one record load (Algorithm 2, the loop over children).  Child labels
-// (Optimization 1) live in the same record and are rewritten every round.
+// (Optimization 1) are rewritten every round, so they live beside the record
+// (nlabels, 8 bytes per node): the round's pass writes whole sectors.
 //   f[0..5]   left child box  (lo x,y,z, hi x,y,z)
 //   f[6..11]  right child box
 //   u[12..13] child references (leaf k: kLeafBit|k; internal node: its index)
-//   u[14..15] child labels (kInvalid: leaves of several components)
+//   u[14..15] unused
 struct __align__(16) NodeRec {
   float4 a, b, c;
   uint4 d;
@@ -197,6 +198,7 @@ struct Problem {
   uint32_t *vals[2] = {nullptr, nullptr};
   uint32_t *perm = nullptr;       // curve index -> original index
   NodeRec *nodes = nullptr;       // nc-1 internal nodes
+  uint2 *nlabels = nullptr;       // nc-1: child labels of each internal node (A5)
   uint32_t *parent_leaf = nullptr;   // nc: (parent << 1) | slot of each leaf chunk
   uint2 *up_delta = nullptr;         // n-1: x = (parent << 1) | slot (root: kInvalid),
                                      //      y = leading bits shared by the node's (code,

@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(128) k_log_samples(FeatArgs F, TravArgs T, int
   uint32_t st_node[kStackDepth];
   float st_dist[kStackDepth];
   unsigned long long nv = 0;
-  if (!explore<false, false>(q, start, T.nodes, T.pts, T.labels, 1, F.n, st_node, st_dist, nv)) {
+  if (!explore<false, false>(q, start, T.nodes, T.nlabels, T.pts, T.labels, 1, F.n, st_node, st_dist, nv)) {
     atomicOr(T.status, kErrStack);
     return;
   }
@@ -615,6 +615,7 @@ void launch_log_samples(Problem &P, int round, bool carried) {
   TravArgs T;
   T.pts = P.pts;
   T.nodes = P.nodes;
+  T.nlabels = P.nlabels;
   T.labels = P.labels;
   T.bound = P.bound;
   T.radius_in = nullptr;

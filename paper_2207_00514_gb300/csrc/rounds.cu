@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restri
                                                         const uint32_t *__restrict__ tile_prefix,
                                                         const uint4 *__restrict__ range,
                                                         int64_t n, int64_t nc, int leaf,
-                                                        NodeRec *__restrict__ nodes) {
+                                                        uint2 *__restrict__ nlabels) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc - 1) return;
   // the children split the node's chunk range [first, last] after `split`
@@ -196,12 +196,12 @@ __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restri
       runs_at(runs_local, tile_prefix, b0) == runs_at(runs_local, tile_prefix, a0) ? l0 : kInvalid;
   const uint32_t lab1 =
       runs_at(runs_local, tile_prefix, b1) == runs_at(runs_local, tile_prefix, a1) ? l1 : kInvalid;
-  reinterpret_cast<uint2 *>(&nodes[i].d)[1] = make_uint2(lab0, lab1);
+  nlabels[i] = make_uint2(lab0, lab1);
 }
 
 void launch_node_labels(Problem &P) {
   k_node_labels<<<grid_for(P.nc - 1, kBlock), kBlock, 0, P.stream>>>(
-      P.labels, P.runs, P.scan_tiles + scan_tiles_for(P.n), P.range, P.n, P.nc, P.leaf, P.nodes);
+      P.labels, P.runs, P.scan_tiles + scan_tiles_for(P.n), P.range, P.n, P.nc, P.leaf, P.nlabels);
   P.launches += 1;
 }
 
@@ -253,6 +253,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   TravArgs A;
   A.pts = P.pts;
   A.nodes = P.nodes;
+  A.nlabels = P.nlabels;
   A.labels = P.labels;
   A.bound = P.bound;
   A.radius_in = radius_in;

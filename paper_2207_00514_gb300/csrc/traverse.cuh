@@ -83,6 +83,7 @@ __device__ __forceinline__ void load_record(const NodeRec *rec, float4 &a, float
 
 template <bool COUNT, bool CHUNKS>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
+                                        const uint2 *__restrict__ nlabels,
                                         const float4 *__restrict__ pts,
                                         const uint32_t *__restrict__ labels, int leaf, int64_t n,
                                         uint32_t *st_node, float *st_dist,
@@ -93,10 +94,11 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
     float4 a, b, c;
     uint4 dd;
     load_record(nodes + node, a, b, c, dd);
+    const uint2 lab = __ldg(nlabels + node);
     const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
     const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
-    bool okL = (dd.z != q.me) && (dL <= q.radius);
-    bool okR = (dd.w != q.me) && (dR <= q.radius);
+    bool okL = (lab.x != q.me) && (dL <= q.radius);
+    bool okR = (lab.y != q.me) && (dR <= q.radius);
     if (okL && (dd.x & kLeafBit)) { scan_chunk<CHUNKS>(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels); okL = false; }
     if (okR && (dd.y & kLeafBit)) {
       if (dR <= q.radius) scan_chunk<CHUNKS>(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels);
@@ -154,6 +156,7 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
 struct TravArgs {
   const float4 *pts;
   const NodeRec *nodes;
+  const uint2 *nlabels;
   const uint32_t *labels;
   const uint32_t *bound;
   const float *radius_in;
@@ -227,7 +230,7 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   uint32_t st_node[kStackDepth];
   float st_dist[kStackDepth];
   unsigned long long nvis = 0;
-  const bool ok = explore<COUNT, CHUNKS>(q, start, A.nodes, A.pts, A.labels, A.leaf, n, st_node,
+  const bool ok = explore<COUNT, CHUNKS>(q, start, A.nodes, A.nlabels, A.pts, A.labels, A.leaf, n, st_node,
                                          st_dist, nvis);
   if (!ok) atomicOr(A.status, kErrStack);
   if (COUNT) {
