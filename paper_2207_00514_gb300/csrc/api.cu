@@ -196,7 +196,7 @@ void run_build(Problem &P) {
 void run_round(Problem &P, int round, bool carried, int block, bool count) {
   if (round > 0) launch_node_labels(P);
   else launch_upper_bounds(P);
-  launch_traverse(P, round > 0 && carried, nullptr, block, count, true);
+  launch_traverse(P, round > 0 && carried, nullptr, block, count, true, 0, round == 0);
   launch_reduce(P);
   launch_merge(P);
 }
@@ -403,7 +403,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
         launch_rerun_mark(P);
         launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, 2);
       } else {
-        launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true);
+        launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, 0, rounds == 0);
       }
       if (stats && rounds < 40) {
         cudaEventRecord(tev[2 * rounds + 1], stream);

@@ -283,8 +283,9 @@ void launch_label_runs(Problem &P);
 void launch_node_labels(Problem &P);
 void advance_round(Problem &P, int64_t n_active);
 void launch_upper_bounds(Problem &P);
+// first: the first round of the plain form (labels = curve indices)
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded, int learned_pass = 0);
+                     bool seeded, int learned_pass = 0, bool first = false);
 void launch_reduce(Problem &P);
 void launch_merge(Problem &P);
 void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);

@@ -234,21 +234,22 @@ void launch_upper_bounds(Problem &P) {
 
 // One thread per point, or (list != nullptr) a grid-stride pass over the
 // listed points (the certification reruns of the learned radius).
-template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED>
+template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
+          bool FIRST>
 __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (list) {
     const int64_t count = *list_count;
     for (int64_t t = gid; t < count; t += (int64_t)gridDim.x * blockDim.x)
-      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED>(A, __ldg(list + t));
+      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST>(A, __ldg(list + t));
   } else if (gid < A.n) {
-    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED>(A, gid);
+    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST>(A, gid);
   }
 }
 
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded, int learned_pass) {
+                     bool seeded, int learned_pass, bool first) {
   if (block <= 0) block = kTraverseBlock;
   TravArgs A;
   A.pts = P.pts;
@@ -274,7 +275,8 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   const uint32_t *list_count = learned_pass == 2 ? P.counters + 13 : nullptr;
   const int g = learned_pass == 2 ? 152 * 8 : grid_for(P.n, block);
   cudaStream_t s = P.stream;
-#define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L><<<g, block, 0, s>>>(A, list, list_count)
+#define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L, false><<<g, block, 0, s>>>(A, list, list_count)
+#define EMST_TRAV_FIRST(K, H) k_traverse<false, false, K, true, H, false, true><<<g, block, 0, s>>>(A, list, list_count)
 #define EMST_TRAV(C, R, K, S, L)                       \
   do {                                                 \
     if (P.leaf > 1) EMST_TRAV2(C, R, K, S, true, L);   \
@@ -292,11 +294,18 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
     }
   } else if (carried) {
     if (count) EMST_TRAV(true, false, true, true, false); else EMST_TRAV(true, false, false, true, false);
+  } else if (first) {  // the first round of the plain form: labels are the curve indices
+    if (P.leaf > 1) {
+      if (count) EMST_TRAV_FIRST(true, true); else EMST_TRAV_FIRST(false, true);
+    } else {
+      if (count) EMST_TRAV_FIRST(true, false); else EMST_TRAV_FIRST(false, false);
+    }
   } else {
     if (count) EMST_TRAV(false, false, true, true, false); else EMST_TRAV(false, false, false, true, false);
   }
 #undef EMST_TRAV
 #undef EMST_TRAV2
+#undef EMST_TRAV_FIRST
   P.launches += 1;
 }
 

@@ -81,7 +81,10 @@ __device__ __forceinline__ void load_record(const NodeRec *rec, float4 &a, float
       : "l"(reinterpret_cast<const char *>(rec) + 32));
 }
 
-template <bool COUNT, bool CHUNKS>
+// FIRST: the first round, where every label is the point's own curve index,
+// so no internal child is single-component and the only one-point leaf to
+// skip is the query itself: no label load.
+template <bool COUNT, bool CHUNKS, bool FIRST>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
                                         const uint2 *__restrict__ nlabels,
                                         const float4 *__restrict__ pts,
@@ -94,7 +97,13 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
     float4 a, b, c;
     uint4 dd;
     load_record(nodes + node, a, b, c, dd);
-    const uint2 lab = __ldg(nlabels + node);
+    uint2 lab;
+    if (FIRST) {
+      lab.x = (!CHUNKS && (dd.x & kLeafBit)) ? (dd.x & ~kLeafBit) : kInvalid;
+      lab.y = (!CHUNKS && (dd.y & kLeafBit)) ? (dd.y & ~kLeafBit) : kInvalid;
+    } else {
+      lab = __ldg(nlabels + node);
+    }
     const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
     const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
     bool okL = (lab.x != q.me) && (dL <= q.radius);
@@ -176,7 +185,8 @@ struct TravArgs {
 // LEARNED also tightens the cutoff with the proposed radius pred_r[i] (any
 // value: exactness is restored afterwards by rerunning every point whose
 // cutoff fell below its component's found minimum) and records it in r_used.
-template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED>
+template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
+          bool FIRST = false>
 __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   const float kInf = __int_as_float(0x7f800000);
   const int64_t n = A.n;
@@ -230,7 +240,7 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   uint32_t st_node[kStackDepth];
   float st_dist[kStackDepth];
   unsigned long long nvis = 0;
-  const bool ok = explore<COUNT, CHUNKS>(q, start, A.nodes, A.nlabels, A.pts, A.labels, A.leaf, n, st_node,
+  const bool ok = explore<COUNT, CHUNKS, FIRST>(q, start, A.nodes, A.nlabels, A.pts, A.labels, A.leaf, n, st_node,
                                          st_dist, nvis);
   if (!ok) atomicOr(A.status, kErrStack);
   if (COUNT) {
