@@ -266,18 +266,23 @@ void launch_hierarchy(Problem &P) {
 // the node's whole record once (both boxes and the child references from the
 // node's range) and its child labels, and carries the union one level up.
 // Wait-free.
-// A node whose leaf range lies inside this CTA's 256 chunks has both arrivals
+// A node whose leaf range lies inside this CTA's chunks has both arrivals
 // from this CTA (and its index inside the CTA's range, one end of its range),
 // so both child boxes meet in shared memory and the arrivals are counted
-// there with block-scope fences; only nodes spanning CTAs (about 2 per 256
-// leaves per level above the CTA) pass the box through their global record
-// and use the global counters.  The global counters are never reset: each
+// there with block-scope fences; only nodes spanning CTAs (about 2 per CTA
+// per level above it) pass the box through their global record and use the
+// global counters.  The global counters are never reset: each
 // pass adds exactly two arrivals per node, so the parity of the count before
 // the add tells first from second.
 // The child labels are the round-0 ones (a one-point chunk k: label k;
 // otherwise several components, kInvalid); a caller with other labels
 // rewrites them (A5).
 // ---------------------------------------------------------------------------
+#ifndef EMST_REFIT_BLOCK
+#define EMST_REFIT_BLOCK 128
+#endif
+constexpr int kRefitBlock = EMST_REFIT_BLOCK;  // leaf chunks per refit CTA
+
 __device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, const float *bx) {
   float2 *f = reinterpret_cast<float2 *>(rec) + 3 * slot;
   f[0] = make_float2(bx[0], bx[1]);
@@ -285,17 +290,17 @@ __device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, const flo
   f[2] = make_float2(bx[4], bx[5]);
 }
 
-__global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
+__global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
                                                   int64_t nc, int leaf, NodeRec *nodes,
                                                   uint2 *__restrict__ nlabels,
                                                   const uint32_t *__restrict__ parent_leaf,
                                                   const uint2 *__restrict__ up_delta,
                                                   const uint4 *__restrict__ range,
                                                   uint32_t *arrivals) {
-  __shared__ float s_box[kBlock][2][6];  // both child boxes of each local node
-  __shared__ uint32_t s_arrive[kBlock];
-  const int64_t first = (int64_t)blockIdx.x * kBlock;
-  const int64_t last = first + kBlock - 1;
+  __shared__ float s_box[kRefitBlock][2][6];  // both child boxes of each local node
+  __shared__ uint32_t s_arrive[kRefitBlock];
+  const int64_t first = (int64_t)blockIdx.x * kRefitBlock;
+  const int64_t last = first + kRefitBlock - 1;
   s_arrive[threadIdx.x] = 0u;
   __syncthreads();
   const int64_t k = first + threadIdx.x;  // this thread's chunk
@@ -366,7 +371,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(const float4 *__restrict__ pts
 }
 
 void launch_refit(Problem &P) {
-  k_refit<<<grid_for(P.nc, kBlock), kBlock, 0, P.stream>>>(P.pts, P.n, P.nc, P.leaf, P.nodes,
+  k_refit<<<grid_for(P.nc, kRefitBlock), kRefitBlock, 0, P.stream>>>(P.pts, P.n, P.nc, P.leaf, P.nodes,
                                                           P.nlabels, P.parent_leaf, P.up_delta, P.range,
                                                           P.arrivals);
   P.launches += 1;
