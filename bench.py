@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="halos37M", choices=["halos37M", "batched"],
+    ap.add_argument("--workload", default="halos37M", choices=["halos37M", "batched", "sweep"],
                     help="batched: 4,096 independent 3D instances (sizes log-uniform in [100, 1e6]) "
                          "in one emst_compute_batched call, against one emst_compute per instance")
     ap.add_argument("--instances", type=int, default=4096)
@@ -230,6 +230,49 @@ def run_batched(args, rank, world, local):
             "identical_output": bool(same)}), flush=True)
 
 
+def run_sweep(args, rank, world, local):
+    """Throughput against n (1e4 .. 1e8) on the 2D blob and 3D halo
+    generators: one JSON line per (generator, n), whole-call CUDA-event time
+    with the input resident, best of the timed calls."""
+    if rank != 0:
+        return
+    import torch
+    import synth
+    import paper_2207_00514_gb300 as pkg
+
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sizes = [10_000, 30_000, 100_000, 300_000, 1_000_000, 3_000_000, 10_000_000, 30_000_000,
+             100_000_000]
+    gens = {"2D blobs (config 2 generator, seed 1)": lambda n: synth.blobs(n, 2, 1),
+            "3D halos (config 3 generator, seed 2)": lambda n: synth.halos(n, 2)}
+    for name, gen in gens.items():
+        for n in sizes:
+            pts = torch.from_numpy(gen(n)).to(dev)
+            out = torch.empty((n - 1, 3), dtype=torch.int32, device=dev)
+            for _ in range(max(args.warmup, 2)):
+                pkg.emst_compute(pts, out_edges=out, stream=stream)
+            torch.cuda.synchronize(dev)
+            best, rounds = None, 0
+            for _ in range(max(args.steps, 3)):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = pkg.emst_compute_ex(pts, out_edges=out, stream=stream)[1]
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1)
+                rounds = st["rounds"]
+                best = ms if best is None else min(best, ms)
+            print(json.dumps({"workload": name, "n": n, "ms": round(best, 4),
+                              "mpoints_per_s": round(n / best / 1e3, 2), "rounds": rounds}),
+                  flush=True)
+            del pts, out
+            torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -238,6 +281,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, rank, world, local)
+        return
+    if args.workload == "sweep":
+        run_sweep(args, rank, world, local)
         return
 
     import torch
