@@ -65,6 +65,11 @@ def _load():
                 "oracle_merge": (I64, [P, P, P, P, P, I64, P, P]),
                 "oracle_boruvka_steps": (I, [P, P, I64, I, P, P]),
                 "oracle_kd_boruvka": (I, [P, I64, I, P, I, P]),
+                "oracle_prim_mrd": (I, [P, P, I64, I, P]),
+                "oracle_kruskal_mrd": (I, [P, P, I64, I, P]),
+                "oracle_kd_boruvka_mrd": (I, [P, P, I64, I, P, I, P]),
+                "oracle_core_dist2_brute": (I, [P, I64, I, I, P]),
+                "oracle_kd_core_dist2": (I, [P, I64, I, I, P, I]),
                 "oracle_count_components": (I64, [P, I64, I64, P]),
             }
             for name, (res, args) in sig.items():
@@ -129,6 +134,57 @@ def kd_boruvka(points, threads: int = 1, return_rounds: bool = False):
     assert rc == 0, rc
     e = canonical(e)
     return (e, int(rounds[0])) if return_rounds else e
+
+
+def core_dist2(points, k: int, brute: bool = False, threads: int = 1) -> np.ndarray:
+    """Squared core distances (§4.5): the (k-1)-th smallest FP32 weight from
+    each point to the others (the point itself is the first neighbour), by a
+    full selection (brute) or the k-d tree."""
+    p = _pts(points)
+    n = len(p)
+    out = np.zeros(n, dtype=np.float32)
+    if brute:
+        rc = _load().oracle_core_dist2_brute(_p(p), n, p.shape[1], int(k), _p(out))
+    else:
+        rc = _load().oracle_kd_core_dist2(_p(p), n, p.shape[1], int(k), _p(out), int(threads))
+    assert rc == 0, rc
+    return out
+
+
+def _core(core2, n):
+    c = np.ascontiguousarray(core2, dtype=np.float32)
+    assert c.shape == (n,)
+    return c
+
+
+def prim_mrd(points, core2) -> np.ndarray:
+    """Mutual-reachability MST (§4.5) by O(n^2) Prim, canonical order."""
+    p = _pts(points)
+    n = len(p)
+    e = _edges(n - 1)
+    rc = _load().oracle_prim_mrd(_p(p), _p(_core(core2, n)), n, p.shape[1], _p(e))
+    assert rc == 0
+    return canonical(e)
+
+
+def kruskal_mrd(points, core2) -> np.ndarray:
+    p = _pts(points)
+    n = len(p)
+    e = _edges(n - 1)
+    rc = _load().oracle_kruskal_mrd(_p(p), _p(_core(core2, n)), n, p.shape[1], _p(e))
+    assert rc == 0
+    return canonical(e)
+
+
+def kd_boruvka_mrd(points, core2, threads: int = 1) -> np.ndarray:
+    p = _pts(points)
+    n = len(p)
+    e = _edges(n - 1)
+    rounds = np.zeros(1, dtype=np.int64)
+    rc = _load().oracle_kd_boruvka_mrd(_p(p), _p(_core(core2, n)), n, p.shape[1], _p(e),
+                                       int(threads), _p(rounds))
+    assert rc == 0, rc
+    return canonical(e)
 
 
 def boruvka_steps(points, orig_ids=None, return_rounds: bool = False):

@@ -23,6 +23,13 @@
  *    ("Boruvka's algorithm", last paragraph).  Under this strict total order
  *    the MST is unique (§2, "MST computation").
  *  - ids are the caller's original point indices.
+ *  - mutual reachability (§4.5): d_core(u) is the distance to u's k_pts-th
+ *    nearest neighbour counting u itself, and the weight of (u, v) is
+ *    max(d_core(u), d_core(v), ||u - v||).  Kept squared like the EMST
+ *    weight: core2(u) = the (k_pts - 1)-th smallest w(u, v) over v != u
+ *    (0 for k_pts = 1), and w_m(u, v) = max(core2(u), core2(v), w(u, v)); the
+ *    order (w_m, min id, max id) is the same tie-break.  k_pts = 1 gives the
+ *    EMST itself.
  */
 #include <math.h>
 #include <pthread.h>
@@ -92,7 +99,18 @@ void oracle_canonical_sort(oracle_edge *e, int64_t m) {
  * outside vertex v keeps its best edge to the tree as (w, u); the next vertex
  * is the one whose best edge is smallest under the full key.  Output: n-1
  * edges in the order they were added. */
-int oracle_prim(const float *pts, int64_t n, int dim, oracle_edge *out) {
+/* The edge weight: the squared distance, or with core2 != NULL the squared
+ * mutual reachability distance (§4.5). */
+static float edge_weight(const float *pts, const float *core2, int64_t u, int64_t v, int dim) {
+  float w = oracle_weight(pts + u * dim, pts + v * dim, dim);
+  if (core2) {
+    if (core2[u] > w) w = core2[u];
+    if (core2[v] > w) w = core2[v];
+  }
+  return w;
+}
+
+static int prim_impl(const float *pts, const float *core2, int64_t n, int dim, oracle_edge *out) {
   if (n <= 1) return 0;
   float *bw = (float *)malloc(sizeof(float) * (size_t)n);
   uint32_t *bu = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
@@ -100,7 +118,7 @@ int oracle_prim(const float *pts, int64_t n, int dim, oracle_edge *out) {
   if (!bw || !bu || !in) { free(bw); free(bu); free(in); return -1; }
   in[0] = 1;
   for (int64_t v = 1; v < n; ++v) {
-    bw[v] = oracle_weight(pts + 0, pts + v * dim, dim);
+    bw[v] = edge_weight(pts, core2, 0, v, dim);
     bu[v] = 0;
   }
   for (int64_t step = 0; step < n - 1; ++step) {
@@ -114,10 +132,9 @@ int oracle_prim(const float *pts, int64_t n, int dim, oracle_edge *out) {
     out[step].i = bu[pick];
     out[step].j = (uint32_t)pick;
     out[step].w = bw[pick];
-    const float *pp = pts + pick * dim;
     for (int64_t v = 0; v < n; ++v) {
       if (in[v]) continue;
-      float w = oracle_weight(pp, pts + v * dim, dim);
+      float w = edge_weight(pts, core2, pick, v, dim);
       if (key_cmp(w, (uint32_t)v, (uint32_t)pick, bw[v], (uint32_t)v, bu[v]) < 0) {
         bw[v] = w;
         bu[v] = (uint32_t)pick;
@@ -128,6 +145,15 @@ int oracle_prim(const float *pts, int64_t n, int dim, oracle_edge *out) {
   free(bu);
   free(in);
   return 0;
+}
+
+int oracle_prim(const float *pts, int64_t n, int dim, oracle_edge *out) {
+  return prim_impl(pts, NULL, n, dim, out);
+}
+
+/* Prim on the mutual reachability weights (§4.5), core2 as above. */
+int oracle_prim_mrd(const float *pts, const float *core2, int64_t n, int dim, oracle_edge *out) {
+  return prim_impl(pts, core2, n, dim, out);
 }
 
 /* Union-find with path halving and union by index (smaller root wins). */
@@ -141,7 +167,8 @@ static uint32_t uf_find(uint32_t *par, uint32_t x) {
 
 /* Kruskal's algorithm over all n(n-1)/2 pairs (§2, "MST computation"): sort
  * every edge by the total order, keep those joining two different trees. */
-int oracle_kruskal(const float *pts, int64_t n, int dim, oracle_edge *out) {
+static int kruskal_impl(const float *pts, const float *core2, int64_t n, int dim,
+                        oracle_edge *out) {
   if (n <= 1) return 0;
   int64_t m = n * (n - 1) / 2;
   oracle_edge *all = (oracle_edge *)malloc(sizeof(oracle_edge) * (size_t)m);
@@ -152,7 +179,7 @@ int oracle_kruskal(const float *pts, int64_t n, int dim, oracle_edge *out) {
     for (int64_t b = a + 1; b < n; ++b) {
       all[k].i = (uint32_t)a;
       all[k].j = (uint32_t)b;
-      all[k].w = oracle_weight(pts + a * dim, pts + b * dim, dim);
+      all[k].w = edge_weight(pts, core2, a, b, dim);
       ++k;
     }
   qsort(all, (size_t)m, sizeof(oracle_edge), edge_qsort_cmp);
@@ -167,6 +194,40 @@ int oracle_kruskal(const float *pts, int64_t n, int dim, oracle_edge *out) {
   free(all);
   free(par);
   return got == n - 1 ? 0 : -2;
+}
+
+int oracle_kruskal(const float *pts, int64_t n, int dim, oracle_edge *out) {
+  return kruskal_impl(pts, NULL, n, dim, out);
+}
+
+int oracle_kruskal_mrd(const float *pts, const float *core2, int64_t n, int dim,
+                       oracle_edge *out) {
+  return kruskal_impl(pts, core2, n, dim, out);
+}
+
+/* Core distances (§4.5), by definition: for each u, the (k - 1)-th smallest
+ * weight w(u, v) over all v != u (u itself is the first neighbour, at 0), by
+ * a full selection over all n - 1 others.  k = 1: 0.  Returns -1 for k < 1 or
+ * k > n. */
+static int cmp_float(const void *x, const void *y) {
+  float a = *(const float *)x, b = *(const float *)y;
+  return (a > b) - (a < b);
+}
+
+int oracle_core_dist2_brute(const float *pts, int64_t n, int dim, int k, float *core2) {
+  if (k < 1 || k > n) return -1;
+  float *w = (float *)malloc(sizeof(float) * (size_t)(n > 1 ? n - 1 : 1));
+  if (!w) return -1;
+  for (int64_t u = 0; u < n; ++u) {
+    if (k == 1) { core2[u] = 0.0f; continue; }
+    int64_t m = 0;
+    for (int64_t v = 0; v < n; ++v)
+      if (v != u) w[m++] = oracle_weight(pts + u * dim, pts + v * dim, dim);
+    qsort(w, (size_t)m, sizeof(float), cmp_float);
+    core2[u] = w[k - 2];
+  }
+  free(w);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -552,6 +613,7 @@ static float box_weight(const float *p, const kd_node *nd, int dim) {
 
 typedef struct {
   kd_tree *t;
+  const float *core2;        /* squared core distances (mutual reachability), or NULL */
   const uint32_t *comp;      /* component root per point (original index) */
   const uint32_t *node_comp; /* component of a single-component node, else INVALID */
   uint32_t *comp_radius;     /* float bits of the best weight found so far per component */
@@ -578,6 +640,8 @@ static void *kd_query_range(void *arg) {
     uint32_t i = t->idx[pos];
     uint32_t c = job->comp[i];
     const float *p = t->pts + (int64_t)i * dim;
+    /* with core distances every weight from i is at least core2[i] */
+    const float wi = job->core2 ? job->core2[i] : 0.0f;
     float best_w = INFINITY;
     uint32_t best_j = ORACLE_INVALID;
     int64_t sp = 0;
@@ -588,12 +652,14 @@ static void *kd_query_range(void *arg) {
       if (job->node_comp[v] == c) continue; /* every point here is in i's component */
       float radius = u2f(__atomic_load_n(&job->comp_radius[c], __ATOMIC_RELAXED));
       if (best_w < radius) radius = best_w;
-      if (box_weight(p, nd, dim) > radius) continue;
+      float lb = box_weight(p, nd, dim);
+      if (wi > lb) lb = wi;
+      if (lb > radius) continue;
       if (nd->left < 0) {
         for (int64_t k = nd->begin; k < nd->end; ++k) {
           uint32_t j = t->idx[k];
           if (job->comp[j] == c) continue;
-          float w = oracle_weight(p, t->pts + (int64_t)j * dim, dim);
+          float w = edge_weight(t->pts, job->core2, i, j, dim);
           if (w > radius) continue;
           if (w < best_w || (w == best_w && j < best_j)) {
             best_w = w;
@@ -633,8 +699,8 @@ static void kd_node_comp(const kd_tree *t, const uint32_t *comp, uint32_t *node_
   }
 }
 
-int oracle_kd_boruvka(const float *pts, int64_t n, int dim, oracle_edge *out, int nthreads,
-                      int64_t *rounds_out) {
+static int kd_boruvka_impl(const float *pts, const float *core2, int64_t n, int dim,
+                           oracle_edge *out, int nthreads, int64_t *rounds_out) {
   if (rounds_out) *rounds_out = 0;
   if (n <= 1) return 0;
   if (nthreads < 1) nthreads = 1;
@@ -673,13 +739,14 @@ int oracle_kd_boruvka(const float *pts, int64_t n, int dim, oracle_edge *out, in
     for (int64_t k = 0; k + 1 < n; ++k) {
       uint32_t a = t.idx[k], b = t.idx[k + 1];
       if (comp[a] == comp[b]) continue;
-      uint32_t wb = f2u(oracle_weight(pts + (int64_t)a * dim, pts + (int64_t)b * dim, dim));
+      uint32_t wb = f2u(edge_weight(pts, core2, a, b, dim));
       if (wb < rad[comp[a]]) rad[comp[a]] = wb;
       if (wb < rad[comp[b]]) rad[comp[b]] = wb;
     }
     int64_t chunk = (n + nthreads - 1) / nthreads;
     for (int q = 0; q < nthreads; ++q) {
-      jobs[q].t = &t; jobs[q].comp = comp; jobs[q].node_comp = node_comp; jobs[q].comp_radius = rad;
+      jobs[q].t = &t; jobs[q].core2 = core2; jobs[q].comp = comp; jobs[q].node_comp = node_comp;
+      jobs[q].comp_radius = rad;
       jobs[q].res_w = res_w; jobs[q].res_j = res_j;
       jobs[q].begin = q * chunk < n ? q * chunk : n;
       jobs[q].end = (q + 1) * chunk < n ? (q + 1) * chunk : n;
@@ -721,6 +788,106 @@ int oracle_kd_boruvka(const float *pts, int64_t n, int dim, oracle_edge *out, in
   free(t.idx); free(t.nodes); free(par); free(comp); free(node_comp); free(rad);
   free(res_w); free(res_j); free(cw); free(ca); free(cb);
   return status;
+}
+
+int oracle_kd_boruvka(const float *pts, int64_t n, int dim, oracle_edge *out, int nthreads,
+                      int64_t *rounds_out) {
+  return kd_boruvka_impl(pts, NULL, n, dim, out, nthreads, rounds_out);
+}
+
+/* The same Boruvka loop on the mutual reachability weights (§4.5): the
+ * queries prune with max(core2[i], box weight), a lower bound of every weight
+ * from i into the box. */
+int oracle_kd_boruvka_mrd(const float *pts, const float *core2, int64_t n, int dim,
+                          oracle_edge *out, int nthreads, int64_t *rounds_out) {
+  return kd_boruvka_impl(pts, core2, n, dim, out, nthreads, rounds_out);
+}
+
+/* Core distances with the k-d tree: each point keeps its k - 1 smallest
+ * weights to other points (sorted), searching with the largest of them as
+ * the cutoff once it has k - 1 (§4.5's definition, faster than the full
+ * selection above for large n). */
+typedef struct {
+  kd_tree *t;
+  int k;
+  float *core2;
+  int64_t begin, end;
+} kd_knn_job;
+
+static void *kd_knn_range(void *arg) {
+  kd_knn_job *job = (kd_knn_job *)arg;
+  kd_tree *t = job->t;
+  const int dim = t->dim, m = job->k - 1;
+  int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * t->max_depth + 8));
+  float *best = (float *)malloc(sizeof(float) * (size_t)(m > 0 ? m : 1));
+  for (int64_t pos = job->begin; pos < job->end; ++pos) {
+    uint32_t i = t->idx[pos];
+    if (m == 0) { job->core2[i] = 0.0f; continue; }
+    const float *p = t->pts + (int64_t)i * dim;
+    int have = 0;
+    int64_t sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+      const kd_node *nd = &t->nodes[stack[--sp]];
+      const float radius = have == m ? best[m - 1] : INFINITY;
+      if (box_weight(p, nd, dim) > radius) continue;
+      if (nd->left < 0) {
+        for (int64_t q = nd->begin; q < nd->end; ++q) {
+          uint32_t j = t->idx[q];
+          if (j == i) continue;
+          float w = oracle_weight(p, t->pts + (int64_t)j * dim, dim);
+          if (have == m && w >= best[m - 1]) continue;
+          int at = have < m ? have++ : m - 1; /* drop the largest when full */
+          while (at > 0 && best[at - 1] > w) { best[at] = best[at - 1]; --at; }
+          best[at] = w;
+        }
+        continue;
+      }
+      const kd_node *L = &t->nodes[nd->left], *R = &t->nodes[nd->right];
+      float dl = box_weight(p, L, dim), dr = box_weight(p, R, dim);
+      if (dl <= dr) { stack[sp++] = nd->right; stack[sp++] = nd->left; }
+      else { stack[sp++] = nd->left; stack[sp++] = nd->right; }
+    }
+    job->core2[i] = best[m - 1];
+  }
+  free(stack);
+  free(best);
+  return NULL;
+}
+
+int oracle_kd_core_dist2(const float *pts, int64_t n, int dim, int k, float *core2, int nthreads) {
+  if (k < 1 || k > n) return -1;
+  if (nthreads < 1) nthreads = 1;
+  kd_tree t;
+  t.pts = pts;
+  t.dim = dim;
+  t.n = n;
+  t.idx = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+  t.nodes = (kd_node *)malloc(sizeof(kd_node) * (size_t)(2 * (n / (KD_LEAF / 2) + 2)));
+  t.n_nodes = 0;
+  t.max_depth = 0;
+  for (int64_t q = 0; q < n; ++q) t.idx[q] = (uint32_t)q;
+  kd_build_rec(&t, 0, n, 0);
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+  kd_knn_job *jobs = (kd_knn_job *)malloc(sizeof(kd_knn_job) * (size_t)nthreads);
+  int64_t chunk = (n + nthreads - 1) / nthreads;
+  for (int q = 0; q < nthreads; ++q) {
+    jobs[q].t = &t;
+    jobs[q].k = k;
+    jobs[q].core2 = core2;
+    jobs[q].begin = q * chunk < n ? q * chunk : n;
+    jobs[q].end = (q + 1) * chunk < n ? (q + 1) * chunk : n;
+  }
+  if (nthreads == 1) kd_knn_range(&jobs[0]);
+  else {
+    for (int q = 0; q < nthreads; ++q) pthread_create(&th[q], NULL, kd_knn_range, &jobs[q]);
+    for (int q = 0; q < nthreads; ++q) pthread_join(th[q], NULL);
+  }
+  free(th);
+  free(jobs);
+  free(t.idx);
+  free(t.nodes);
+  return 0;
 }
 
 /* Checks used by the tests: number of distinct components of an edge list
