@@ -70,8 +70,9 @@ typedef struct emst_options {
   int32_t block_size;         /* traversal CTA size: 0 = default (128), else 64..256, multiple of 32 */
   int32_t carried_radius;     /* 1 (default if struct_size==0) = seed each query with the previous
                                  round's neighbour when it is still in another component */
-  int32_t use_graph;          /* 1 = run the round loop as a CUDA graph with a device-side
-                                 loop condition; 0 = host loop (one sync per round) */
+  int32_t use_graph;          /* accepted and ignored: the rounds run from a host loop with one
+                                 synchronisation per round (the host gaps of a whole call are
+                                 about 1 % of its device time at 37M points) */
   int32_t count_visits;       /* 1 = count node visits per round into emst_stats */
   int32_t leaf_size;          /* points per leaf chunk of the hierarchy: 0 = default (1, one
                                  point per leaf as in the paper), else 1, 2, 4, 8 or 16 (halved
@@ -81,8 +82,17 @@ typedef struct emst_options {
   const float *mlp_params;    /* learned search radius: the network (EMST_MLP_PARAMS floats,
                                  host or device memory; see emst_mlp_forward), or NULL for the
                                  plain method.  The tree is the same either way. */
-  int32_t reserved[8];
+  int32_t mrd_k;              /* mutual reachability (§4.5, the metric of HDBSCAN*): 0 or 1 =
+                                 the Euclidean MST; 2 <= k <= EMST_MRD_MAX_K (and k <= n) = the
+                                 MST under max(core(u), core(v), |u - v|), core(u) the distance
+                                 from u to its k-th nearest neighbour counting u itself; edge
+                                 weights are then FP32 squared mutual reachability distances,
+                                 ordered and tie-broken like the Euclidean ones.  Not together
+                                 with mlp_params. */
+  int32_t reserved[7];
 } emst_options;
+
+#define EMST_MRD_MAX_K 32
 
 /* Per-call statistics filled by emst_compute_ex when `stats` is not NULL. */
 typedef struct emst_stats {
@@ -105,7 +115,8 @@ typedef struct emst_stats {
                               their component's found minimum */
   double learned_search_ms; /* learned radius: device time of the searches with the proposed
                                cutoffs alone (traverse_ms adds inference and the reruns) */
-  int64_t reserved[3];
+  double core_ms;          /* mutual reachability: device time of the core distances */
+  int64_t reserved[2];
 } emst_stats;
 
 /* EMST of n points (§3, Fig. 3 end to end).
@@ -131,6 +142,18 @@ int emst_compute_ex(const float *points, int64_t n, int dim, emst_edge *out_edge
  * Returns EMST_OK or an emst_status error. */
 int emst_compute_batched(const float *points, const int64_t *offsets, int num_instances, int dim,
                          emst_edge *out_edges, int64_t *out_offsets, void *stream);
+
+/* Squared core distances of the mutual reachability distance (§4.5): for
+ * every point, the FP32 squared distance to its k-th nearest neighbour, the
+ * point itself counting as the first (k = 1: 0).  A k-nearest-neighbour
+ * search of the same hierarchy the EMST builds.
+ *   points    n x dim FP32, device or host memory, read only.
+ *   n, dim    1 <= n <= EMST_MAX_POINTS, dim in {2, 3}.
+ *   k         1 <= k <= min(n, EMST_MRD_MAX_K).
+ *   out_core2 n FP32, device or host memory, in the caller's point order.
+ * Returns EMST_OK or an emst_status error. */
+int emst_core_distances(const float *points, int64_t n, int dim, int k, float *out_core2,
+                        void *stream);
 
 /* EMST with no device allocation (the paper has no counterpart: this is a
  * deployment variant of emst_compute).  For callers that cannot allocate

@@ -28,6 +28,8 @@ __all__ = [
     "emst_compute",
     "emst_compute_ex",
     "emst_compute_batched",
+    "emst_core_distances",
+    "EMST_MRD_MAX_K",
     "emst_compute_noalloc",
     "EMST_NOALLOC_MAX_POINTS",
     "emst_status_string",
@@ -50,6 +52,7 @@ _HEADER = os.path.join(os.path.dirname(_HERE), "include", "emst.h")
 EMST_MAX_POINTS = (1 << 30) - 1
 EMST_MLP_PARAMS = 8981
 EMST_MLP_FEATURES = 8
+EMST_MRD_MAX_K = 32
 EDGE_DTYPE = np.dtype([("i", np.uint32), ("j", np.uint32), ("w", np.float32)])
 INVALID = 0xFFFFFFFF
 
@@ -68,7 +71,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("carried_radius", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("count_visits", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
-                ("mlp_params", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 8)]
+                ("mlp_params", ctypes.c_void_p), ("mrd_k", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class _Stats(ctypes.Structure):
@@ -80,7 +84,8 @@ class _Stats(ctypes.Structure):
                 ("traverse_ms", ctypes.c_double), ("traverse_launches", ctypes.c_int32),
                 ("reserved1", ctypes.c_int32), ("round_traverse_ms", ctypes.c_double * 40),
                 ("queried_points", ctypes.c_int64), ("rerun_points", ctypes.c_int64),
-                ("learned_search_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 3)]
+                ("learned_search_ms", ctypes.c_double), ("core_ms", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 2)]
 
 
 _lock = threading.Lock()
@@ -111,6 +116,8 @@ def load_library(path: str | None = None):
         lib.emst_compute_ex.restype = I
         lib.emst_compute_batched.argtypes = [V, V, I, I, V, V, V]
         lib.emst_compute_batched.restype = I
+        lib.emst_core_distances.argtypes = [V, I64, I, I, V, V]
+        lib.emst_core_distances.restype = I
         lib.emst_status_string.argtypes = [I]
         lib.emst_status_string.restype = ctypes.c_char_p
         lib.emst_build_bvh.argtypes = [V, I64, I, I, V, V, V, V, V]
@@ -220,8 +227,9 @@ def emst_compute_noalloc(points, out_edges=None, stream=None):
 
 
 def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_radius=True,
-                    use_graph=False, count_visits=False, leaf_size=0, mlp_params=None):
-    """emst_compute with options; returns (edges, stats dict)."""
+                    use_graph=False, count_visits=False, leaf_size=0, mlp_params=None, mrd_k=0):
+    """emst_compute with options; returns (edges, stats dict).  mrd_k >= 2:
+    the mutual-reachability MST (squared MRD weights)."""
     n, dim = _check_points(points)
     out_edges = _edges_out(n, points, out_edges)
     opt = _Options()
@@ -231,6 +239,7 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
     opt.use_graph = 1 if use_graph else 0
     opt.count_visits = 1 if count_visits else 0
     opt.leaf_size = int(leaf_size)
+    opt.mrd_k = int(mrd_k)
     if mlp_params is not None:
         if mlp_params.dtype != _torch().float32 or mlp_params.numel() != EMST_MLP_PARAMS:
             raise ValueError(f"mlp_params must hold {EMST_MLP_PARAMS} float32 values")
@@ -249,8 +258,23 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
                  round_traverse_ms=[float(st.round_traverse_ms[k]) for k in range(min(st.rounds, 40))],
                  components_per_round=[int(st.components_per_round[k]) for k in range(min(st.rounds, 40))],
                  queried_points=st.queried_points, rerun_points=st.rerun_points,
-                 learned_search_ms=st.learned_search_ms)
+                 learned_search_ms=st.learned_search_ms, core_ms=st.core_ms)
     return out_edges, stats
+
+
+def emst_core_distances(points, k, out=None, stream=None):
+    """Squared core distances (k-th nearest neighbour, the point itself
+    first) of the mutual reachability distance, in the points' order."""
+    torch = _torch()
+    n, dim = _check_points(points)
+    if out is None:
+        pin = points.device.type == "cpu" and torch.cuda.is_available()
+        out = torch.empty(n, dtype=torch.float32, device=points.device, pin_memory=pin)
+    rc = load_library().emst_core_distances(_ptr(points), n, dim, int(k), _ptr(out),
+                                            _stream_ptr(stream, points.device))
+    if rc != 0:
+        raise EmstError(rc, "emst_core_distances")
+    return out
 
 
 def emst_compute_batched(points, offsets, out_edges=None, stream=None):

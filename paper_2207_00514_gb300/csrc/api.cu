@@ -138,6 +138,7 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
     P.mlp = c.take<float>(EMST_MLP_PARAMS);
   }
   if (P.want_logging) P.log_count = c.take<unsigned long long>(1);
+  P.core2 = P.want_mrd ? c.take<float>(n) : nullptr;
   float *pcopy = c.take<float>(copy_points ? n * P.dim : 1);
   if (copy_points) P.points = pcopy;
   emst_edge *ecopy = c.take<emst_edge>(copy_edges ? n : 1);
@@ -293,7 +294,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     stats->struct_size = sz;
   }
   if (n == 0) return EMST_OK;
-  int block = 0, carried = 1, count = 0, leaf_req = 0;
+  int block = 0, carried = 1, count = 0, leaf_req = 0, mrd_k = 0;
   const float *mlp_params = nullptr;
   if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
     block = opt->block_size;
@@ -301,6 +302,9 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     count = opt->count_visits;
     leaf_req = opt->leaf_size;
     mlp_params = opt->mlp_params;
+    mrd_k = opt->mrd_k;
+    if (mrd_k < 0 || mrd_k > EMST_MRD_MAX_K || (mrd_k >= 2 && (mlp_params || n < mrd_k)))
+      return EMST_ERR_INVALID_ARG;
     if (leaf_req < 0 || leaf_req > 16 || (leaf_req & (leaf_req - 1)) != 0) return EMST_ERR_INVALID_ARG;
     if (block != 0 && (block < 64 || block > kTraverseMaxBlock || block % 32 != 0))
       return EMST_ERR_INVALID_ARG;
@@ -329,6 +333,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   P.leaf = num_inst > 1 ? 1 : effective_leaf(n, leaf_req);
   P.want_learned = learned;
   P.want_logging = logging;
+  P.want_mrd = mrd_k >= 2 && !offsets && n >= 2;
   if (logging) {
     P.log_feat = ex->log_feat;
     P.log_target = ex->log_target;
@@ -343,6 +348,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   int rounds = 0;
   cudaEvent_t tev[2 * 40];
   cudaEvent_t lev[2 * 40] = {nullptr};  // learned: around the proposed-cutoff search
+  cudaEvent_t cev[2] = {nullptr, nullptr};  // mutual reachability: around the core distances
   int n_tev = 0;
   if (cudaMallocFromPoolAsync((void **)&base, need, pool, stream) != cudaSuccess) {
     cudaGetLastError();
@@ -369,6 +375,15 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   CU(cudaStreamSynchronize(stream));
   if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
   if (expected > 0) {
+    if (P.core2) {  // mutual reachability: core distances on the finished hierarchy
+      if (stats) {
+        cudaEventCreate(&cev[0]);
+        cudaEventCreate(&cev[1]);
+        cudaEventRecord(cev[0], stream);
+      }
+      launch_core_knn(P, mrd_k);
+      if (stats) cudaEventRecord(cev[1], stream);
+    }
     reset_round_state(P);
     // Boruvka rounds (Fig. 3 loop): each round at least halves the number of
     // components of every unfinished instance, so more than ceil(log2 n)
@@ -469,6 +484,13 @@ done:
   }
   for (int r = 0; r < 2 * 40; ++r)
     if (lev[r]) cudaEventDestroy(lev[r]);
+  if (cev[0] && cev[1] && stats) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, cev[0], cev[1]);
+    stats->core_ms = t;
+  }
+  for (auto &e : cev)
+    if (e) cudaEventDestroy(e);
   for (int r = 0; r < n_tev; ++r) {
     cudaEventDestroy(tev[2 * r]);
     cudaEventDestroy(tev[2 * r + 1]);
@@ -601,6 +623,34 @@ int emst_learned_samples(const float *points, int64_t n, int dim, int every, flo
   ex.skip_output = true;
   return compute_impl(points, n, dim, nullptr, 1, nullptr, nullptr, (cudaStream_t)stream, nullptr,
                       nullptr, &ex);
+}
+
+int emst_core_distances(const float *points, int64_t n, int dim, int k, float *out_core2,
+                        void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!out_core2 || n < 1 || k < 1 || k > n || k > EMST_MRD_MAX_K) return EMST_ERR_INVALID_ARG;
+  int rc = check_args(points, n, dim);
+  if (rc != EMST_OK) return rc;
+  if (n == 1) {  // k = 1: the point itself
+    const float zero = 0.0f;
+    if (cudaMemcpyAsync(out_core2, &zero, sizeof(float), cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return EMST_ERR_CUDA;
+    return EMST_OK;
+  }
+  Session S;
+  S.P.want_mrd = true;
+  rc = open_session(S, points, n, dim, 1, s);
+  if (rc != EMST_OK) return rc;
+  Problem &P = S.P;
+  run_build(P);
+  launch_core_knn(P, k);
+  const bool out_dev = device_accessible(out_core2);
+  float *dst = out_dev ? out_core2 : reinterpret_cast<float *>(P.keys[1]);  // n floats of scratch
+  launch_core_to_input(P, dst);
+  if (!out_dev)
+    cudaMemcpyAsync(out_core2, dst, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s);
+  return finish_session(S);
 }
 
 int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint64_t *out_codes,

@@ -179,6 +179,7 @@ struct Problem {
   // list of points to rerun.
   bool want_learned = false;         // set before layout(): carve the learned-radius arrays
   bool want_logging = false;         // set before layout(): carve the logging counter
+  bool want_mrd = false;             // set before layout(): carve the core distances
   const float *mlp = nullptr;
   float *pred_r = nullptr;
   float *r_used = nullptr;
@@ -221,6 +222,8 @@ struct Problem {
   uint32_t *next_list = nullptr;     // roots appended by the merge
   int64_t n_active = 0;
   uint2 *res = nullptr;              // n: (w bits, neighbour curve index)
+  float *core2 = nullptr;            // n: mutual reachability -- squared core distances in
+                                     //    curve order (nullptr: the Euclidean weight)
   // Per-component minimum edge, in two stages (A8), ping-pong by round: the
   // merge of round r clears the other buffer's entries of its active labels.
   uint64_t *comp_key_buf[2] = {nullptr, nullptr};  // n: (w bits << 32) | min original id
@@ -283,6 +286,9 @@ void launch_label_runs(Problem &P);
 void launch_node_labels(Problem &P);
 void advance_round(Problem &P, int64_t n_active);
 void launch_upper_bounds(Problem &P);
+// mrd.cu: squared core distances (k-th nearest neighbour, §4.5) into P.core2
+void launch_core_knn(Problem &P, int k);
+void launch_core_to_input(Problem &P, float *out);
 // first: the first round of the plain form (labels = curve indices)
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
                      bool seeded, int learned_pass = 0, bool first = false);

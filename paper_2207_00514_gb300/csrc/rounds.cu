@@ -9,6 +9,15 @@ namespace emst {
 
 constexpr int kBlock = 256;
 
+// The weight of curve neighbours k and k + 1 (core2: the mutual reachability
+// weight, §4.5).
+__device__ __forceinline__ float pair_weight(const float4 &p, const float4 &q,
+                                             const float *__restrict__ core2, int64_t k) {
+  float w = sq_dist(p.x, p.y, p.z, q.x, q.y, q.z);
+  if (core2) w = fmaxf(w, fmaxf(__ldg(core2 + k), __ldg(core2 + k + 1)));
+  return w;
+}
+
 // ---------------------------------------------------------------------------
 // A5. Node labels (the reduceLabels step of §3, Optimization 1; Fig. 4): a
 // node's label is the label shared by all of its leaves, else kInvalid.  The
@@ -76,7 +85,8 @@ __device__ void block_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t 
 template <bool RELABEL>
 __global__ void __launch_bounds__(kScanThreads, 6) k_runs(
     const uint32_t *__restrict__ labels_old, const uint32_t *__restrict__ root,
-    const float4 *__restrict__ pts, const uint32_t *__restrict__ inst_of, int64_t n,
+    const float4 *__restrict__ pts, const uint32_t *__restrict__ inst_of,
+    const float *__restrict__ core2, int64_t n,
     uint32_t *__restrict__ labels_new, uint32_t *__restrict__ bound_next,
     uint32_t *__restrict__ runs_local, uint32_t *tile_total, uint32_t *tile_prefix,
     uint32_t *done) {
@@ -120,7 +130,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_runs(
       if (RELABEL && !(inst_of && __ldg(inst_of + seg + k) != __ldg(inst_of + seg + k + 1))) {
         // (no bound across instances)
         const float4 p = __ldg(pts + seg + k), r = __ldg(pts + seg + k + 1);
-        const uint32_t w = __float_as_uint(sq_dist(p.x, p.y, p.z, r.x, r.y, r.z));
+        const uint32_t w = __float_as_uint(pair_weight(p, r, core2, seg + k));
         atomicMin(&bound_next[lab[q]], w);
         atomicMin(&bound_next[nxt], w);
       }
@@ -166,11 +176,11 @@ static void launch_runs(Problem &P, bool relabel) {
   cudaMemsetAsync(done, 0, sizeof(uint32_t), P.stream);
   if (relabel)
     k_runs<true><<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(
-        P.labels, P.root, P.pts, P.inst_of, P.n, P.labels_buf[P.cur ^ 1], P.bound_buf[P.cur ^ 1],
-        P.runs, tile_total, tile_prefix, done);
+        P.labels, P.root, P.pts, P.inst_of, P.core2, P.n, P.labels_buf[P.cur ^ 1],
+        P.bound_buf[P.cur ^ 1], P.runs, tile_total, tile_prefix, done);
   else
     k_runs<false><<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(
-        P.labels, nullptr, P.pts, P.inst_of, P.n, nullptr, nullptr, P.runs, tile_total,
+        P.labels, nullptr, P.pts, P.inst_of, nullptr, P.n, nullptr, nullptr, P.runs, tile_total,
         tile_prefix, done);
   P.launches += 1;
 }
@@ -214,6 +224,7 @@ void launch_node_labels(Problem &P) {
 __global__ void __launch_bounds__(kBlock) k_upper_bounds(const float4 *__restrict__ pts,
                                                          const uint32_t *__restrict__ labels,
                                                          const uint32_t *__restrict__ inst_of,
+                                                         const float *__restrict__ core2,
                                                          int64_t n, uint32_t *bound) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k + 1 >= n) return;
@@ -221,30 +232,30 @@ __global__ void __launch_bounds__(kBlock) k_upper_bounds(const float4 *__restric
   if (la == lb) return;
   if (inst_of && __ldg(inst_of + k) != __ldg(inst_of + k + 1)) return;  // different instances
   float4 p = pts[k], q = pts[k + 1];
-  uint32_t w = __float_as_uint(sq_dist(p.x, p.y, p.z, q.x, q.y, q.z));
+  uint32_t w = __float_as_uint(pair_weight(p, q, core2, k));
   atomicMin(&bound[la], w);
   atomicMin(&bound[lb], w);
 }
 
 void launch_upper_bounds(Problem &P) {
-  k_upper_bounds<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.labels, P.inst_of, P.n,
-                                                                 P.bound);
+  k_upper_bounds<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(P.pts, P.labels, P.inst_of,
+                                                                 P.core2, P.n, P.bound);
   P.launches += 1;
 }
 
 // One thread per point, or (list != nullptr) a grid-stride pass over the
 // listed points (the certification reruns of the learned radius).
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
-          bool FIRST>
+          bool FIRST, bool MRD>
 __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (list) {
     const int64_t count = *list_count;
     for (int64_t t = gid; t < count; t += (int64_t)gridDim.x * blockDim.x)
-      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST>(A, __ldg(list + t));
+      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD>(A, __ldg(list + t));
   } else if (gid < A.n) {
-    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST>(A, gid);
+    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD>(A, gid);
   }
 }
 
@@ -255,6 +266,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   A.pts = P.pts;
   A.nodes = P.nodes;
   A.nlabels = P.nlabels;
+  A.core2 = P.core2;
   A.labels = P.labels;
   A.bound = P.bound;
   A.radius_in = radius_in;
@@ -275,8 +287,9 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   const uint32_t *list_count = learned_pass == 2 ? P.counters + 13 : nullptr;
   const int g = learned_pass == 2 ? 152 * 8 : grid_for(P.n, block);
   cudaStream_t s = P.stream;
-#define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L, false><<<g, block, 0, s>>>(A, list, list_count)
-#define EMST_TRAV_FIRST(K, H) k_traverse<false, false, K, true, H, false, true><<<g, block, 0, s>>>(A, list, list_count)
+#define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L, false, false><<<g, block, 0, s>>>(A, list, list_count)
+#define EMST_TRAV_FIRST(K, H) k_traverse<false, false, K, true, H, false, true, false><<<g, block, 0, s>>>(A, list, list_count)
+#define EMST_TRAV_MRD(C, K, H) k_traverse<C, false, K, true, H, false, false, true><<<g, block, 0, s>>>(A, list, list_count)
 #define EMST_TRAV(C, R, K, S, L)                       \
   do {                                                 \
     if (P.leaf > 1) EMST_TRAV2(C, R, K, S, true, L);   \
@@ -292,6 +305,15 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
     } else {
       if (count) EMST_TRAV(false, false, true, true, true); else EMST_TRAV(false, false, false, true, true);
     }
+  } else if (P.core2) {  // mutual reachability weights (the plain form's rounds)
+    const bool h = P.leaf > 1;
+    if (carried) {
+      if (count) { if (h) EMST_TRAV_MRD(true, true, true); else EMST_TRAV_MRD(true, true, false); }
+      else { if (h) EMST_TRAV_MRD(true, false, true); else EMST_TRAV_MRD(true, false, false); }
+    } else {
+      if (count) { if (h) EMST_TRAV_MRD(false, true, true); else EMST_TRAV_MRD(false, true, false); }
+      else { if (h) EMST_TRAV_MRD(false, false, true); else EMST_TRAV_MRD(false, false, false); }
+    }
   } else if (carried) {
     if (count) EMST_TRAV(true, false, true, true, false); else EMST_TRAV(true, false, false, true, false);
   } else if (first) {  // the first round of the plain form: labels are the curve indices
@@ -306,6 +328,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
 #undef EMST_TRAV
 #undef EMST_TRAV2
 #undef EMST_TRAV_FIRST
+#undef EMST_TRAV_MRD
   P.launches += 1;
 }
 

@@ -12,6 +12,7 @@ constexpr int kStackDepth = 100;  // > 96 = the deepest possible path (see trave
 // Per-query state of Algorithm 2.
 struct Query {
   float px, py, pz;
+  float core;      // mutual reachability: the query's squared core distance (else 0)
   uint32_t me;     // the query's component label
   float radius;    // cutoff (inclusive)
   float best;      // best weight found
@@ -37,11 +38,18 @@ __device__ __forceinline__ void take_point(Query &q, uint32_t j, float d, uint32
 // box distance d is already the exact weight and its label was tested with
 // the box; its original id is loaded only to break an exact tie.  A longer
 // chunk is scanned point by point.
-template <bool CHUNKS>
+// MRD: the weight is the mutual reachability one, max(core(query), core(j), d)
+// (§4.5), so a candidate within the cutoff by distance may fall outside it.
+template <bool CHUNKS, bool MRD>
 __device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, float d1, int leaf, int64_t n,
                                            const float4 *__restrict__ pts,
-                                           const uint32_t *__restrict__ labels) {
+                                           const uint32_t *__restrict__ labels,
+                                           const float *__restrict__ core2) {
   if (!CHUNKS) {
+    if (MRD) {
+      d1 = fmaxf(d1, fmaxf(q.core, __ldg(core2 + c)));
+      if (d1 > q.radius) return;
+    }
     if (q.bj == kInvalid || d1 < q.best) {
       q.best = d1;
       q.bj = c;
@@ -60,7 +68,8 @@ __device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, float d1, int l
   for (int64_t k = lo; k < hi; ++k) {
     if (__ldg(labels + k) == q.me) continue;
     const float4 t = __ldg(pts + k);
-    const float d = sq_dist(q.px, q.py, q.pz, t.x, t.y, t.z);
+    float d = sq_dist(q.px, q.py, q.pz, t.x, t.y, t.z);
+    if (MRD) d = fmaxf(d, fmaxf(q.core, __ldg(core2 + k)));
     if (d <= q.radius) take_point(q, (uint32_t)k, d, __float_as_uint(t.w));
   }
 }
@@ -84,13 +93,18 @@ __device__ __forceinline__ void load_record(const NodeRec *rec, float4 &a, float
 // FIRST: the first round, where every label is the point's own curve index,
 // so no internal child is single-component and the only one-point leaf to
 // skip is the query itself: no label load.
-template <bool COUNT, bool CHUNKS, bool FIRST>
+// MRD: mutual reachability weights (§4.5).  The boxes prune exactly as for
+// the plain weight: the caller only searches with a cutoff at or above the
+// query's core distance, and every weight from the query is at least that,
+// so max(core, box distance) <= cutoff  <=>  box distance <= cutoff.
+template <bool COUNT, bool CHUNKS, bool FIRST, bool MRD = false>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
                                         const uint2 *__restrict__ nlabels,
                                         const float4 *__restrict__ pts,
                                         const uint32_t *__restrict__ labels, int leaf, int64_t n,
                                         uint32_t *st_node, float *st_dist,
-                                        unsigned long long &nvis) {
+                                        unsigned long long &nvis,
+                                        const float *__restrict__ core2 = nullptr) {
   int sp = 0;
   while (true) {
     if (COUNT) ++nvis;
@@ -108,9 +122,12 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
     const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
     bool okL = (lab.x != q.me) && (dL <= q.radius);
     bool okR = (lab.y != q.me) && (dR <= q.radius);
-    if (okL && (dd.x & kLeafBit)) { scan_chunk<CHUNKS>(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels); okL = false; }
+    if (okL && (dd.x & kLeafBit)) {
+      scan_chunk<CHUNKS, MRD>(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels, core2);
+      okL = false;
+    }
     if (okR && (dd.y & kLeafBit)) {
-      if (dR <= q.radius) scan_chunk<CHUNKS>(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels);
+      if (dR <= q.radius) scan_chunk<CHUNKS, MRD>(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels, core2);
       okR = false;
     }
     okL = okL && dL <= q.radius;
@@ -166,6 +183,7 @@ struct TravArgs {
   const float4 *pts;
   const NodeRec *nodes;
   const uint2 *nlabels;
+  const float *core2;  // MRD: squared core distances in curve order
   const uint32_t *labels;
   const uint32_t *bound;
   const float *radius_in;
@@ -185,8 +203,10 @@ struct TravArgs {
 // LEARNED also tightens the cutoff with the proposed radius pred_r[i] (any
 // value: exactness is restored afterwards by rerunning every point whose
 // cutoff fell below its component's found minimum) and records it in r_used.
+// MRD: the mutual reachability weights (§4.5); a query whose own core
+// distance lies above its cutoff finds nothing and is skipped.
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
-          bool FIRST = false>
+          bool FIRST = false, bool MRD = false>
 __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   const float kInf = __int_as_float(0x7f800000);
   const int64_t n = A.n;
@@ -206,6 +226,7 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   q.px = p.x;
   q.py = p.y;
   q.pz = p.z;
+  q.core = MRD ? __ldg(A.core2 + i) : 0.0f;
   q.me = A.labels[i];
   q.best = kInf;
   q.bj = kInvalid;
@@ -237,11 +258,15 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   if (LEARNED) q.radius = fminf(q.radius, __ldg(A.pred_r + i));
   const float r0 = q.radius;  // the search is exact within this cutoff
   if (LEARNED) A.r_used[i] = r0;
+  if (MRD && q.core > r0) {  // every weight from this point is at least its core distance
+    A.res[i] = make_uint2(__float_as_uint(q.core), kInvalid);
+    return;
+  }
   uint32_t st_node[kStackDepth];
   float st_dist[kStackDepth];
   unsigned long long nvis = 0;
-  const bool ok = explore<COUNT, CHUNKS, FIRST>(q, start, A.nodes, A.nlabels, A.pts, A.labels, A.leaf, n, st_node,
-                                         st_dist, nvis);
+  const bool ok = explore<COUNT, CHUNKS, FIRST, MRD>(q, start, A.nodes, A.nlabels, A.pts, A.labels,
+                                                     A.leaf, n, st_node, st_dist, nvis, A.core2);
   if (!ok) atomicOr(A.status, kErrStack);
   if (COUNT) {
     // one atomic per warp: sum the active lanes' counts first
