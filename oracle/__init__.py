@@ -70,6 +70,9 @@ def _load():
                 "oracle_kd_boruvka_mrd": (I, [P, P, I64, I, P, I, P]),
                 "oracle_core_dist2_brute": (I, [P, I64, I, I, P]),
                 "oracle_kd_core_dist2": (I, [P, I64, I, I, P, I]),
+                "oracle_morton128": (None, [P, I64, I, P, P, P, P]),
+                "oracle_sort_perm128": (None, [P, P, I64, P]),
+                "oracle_radix_tree128": (None, [P, P, I64, P, P, P, P]),
                 "oracle_count_components": (I64, [P, I64, I64, P]),
             }
             for name, (res, args) in sig.items():
@@ -226,6 +229,36 @@ def morton(points, lo, hi) -> np.ndarray:
     return codes
 
 
+def morton128(points, lo, hi):
+    """128-bit codes (42 bits per dimension in 3D, 64 in 2D, FP64 quantiser):
+    (high words, low words)."""
+    p = _pts(points)
+    lo = np.ascontiguousarray(lo, np.float32)
+    hi = np.ascontiguousarray(hi, np.float32)
+    ch = np.zeros(len(p), np.uint64)
+    cl = np.zeros(len(p), np.uint64)
+    _load().oracle_morton128(_p(p), len(p), p.shape[1], _p(lo), _p(hi), _p(ch), _p(cl))
+    return ch, cl
+
+
+def sort_perm128(code_hi, code_lo) -> np.ndarray:
+    h = np.ascontiguousarray(code_hi, np.uint64)
+    l = np.ascontiguousarray(code_lo, np.uint64)
+    perm = np.zeros(len(h), np.uint32)
+    _load().oracle_sort_perm128(_p(h), _p(l), len(h), _p(perm))
+    return perm
+
+
+def radix_tree128(sorted_hi, sorted_lo):
+    h = np.ascontiguousarray(sorted_hi, np.uint64)
+    l = np.ascontiguousarray(sorted_lo, np.uint64)
+    n = len(h)
+    m = max(n - 1, 0)
+    left, right, first, last = (np.zeros(m, np.int64) for _ in range(4))
+    _load().oracle_radix_tree128(_p(h), _p(l), n, _p(left), _p(right), _p(first), _p(last))
+    return left, right, first, last
+
+
 def sort_perm(codes) -> np.ndarray:
     c = np.ascontiguousarray(codes, np.uint64)
     perm = np.zeros(len(c), np.uint32)
@@ -322,11 +355,23 @@ def count_components(edges, n):
     return int(comps), bool(cyc.value)
 
 
-def bvh_reference(points):
+def bvh_reference(points, morton_bits: int = 64):
     """Steps A1-A4 end to end: scene box, codes, stable order, radix tree and
-    node boxes.  Returns a dict of numpy arrays (sorted order throughout)."""
+    node boxes.  Returns a dict of numpy arrays (sorted order throughout);
+    with 128-bit codes `codes` / `sorted_codes` hold (high, low) word pairs."""
     p = _pts(points)
     lo, hi, finite = scene_box(p)
+    if morton_bits == 128:
+        ch, cl = morton128(p, lo, hi)
+        perm = sort_perm128(ch, cl)
+        codes = np.stack([ch, cl], 1)
+        sc = codes[perm]
+        left, right, first, last = radix_tree128(sc[:, 0], sc[:, 1])
+        sp = p[perm]
+        blo, bhi = node_boxes(sp, first, last)
+        return dict(lo=lo, hi=hi, codes=codes, perm=perm, sorted_codes=sc, left=left,
+                    right=right, first=first, last=last, box_lo=blo, box_hi=bhi,
+                    sorted_points=sp)
     codes = morton(p, lo, hi)
     perm = sort_perm(codes)
     sc = codes[perm]

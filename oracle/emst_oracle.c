@@ -287,6 +287,42 @@ void oracle_morton(const float *pts, int64_t n, int dim, const float *lo, const 
   }
 }
 
+/* A2 at the finer grid §4.2 suggests for very dense data ("128-bit Morton
+ * codes instead of 64-bit ones"): B = 42 bits per dimension in 3D, 64 in 2D.
+ * The quantiser runs in FP64 so the finer grid resolves FP32 coordinates
+ * (x - lo of two FP32 values is exact in FP64 unless their exponents are far
+ * apart): s = 2^B / (hi - lo) (0 for a flat dimension), t = (x - lo) * s,
+ * q = t >= 2^B ? 2^B - 1 : floor(t); bits interleaved x most significant, the
+ * 128-bit code split into a high and a low 64-bit word. */
+void oracle_morton128(const float *pts, int64_t n, int dim, const float *lo, const float *hi,
+                      uint64_t *code_hi, uint64_t *code_lo) {
+  const int B = dim == 3 ? 42 : 64;
+  const double twoB = ldexp(1.0, B);
+  const uint64_t qmax = B == 64 ? ~0ull : ((1ull << B) - 1);
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < dim; ++d) {
+    double ext = (double)hi[d] - (double)lo[d];
+    s[d] = ext > 0.0 ? twoB / ext : 0.0;
+  }
+  for (int64_t k = 0; k < n; ++k) {
+    uint64_t q[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) {
+      double t = ((double)pts[k * dim + d] - (double)lo[d]) * s[d];
+      q[d] = (t >= twoB) ? qmax : (uint64_t)t;
+    }
+    uint64_t ch = 0, cl = 0;
+    for (int b = 0; b < B; ++b)
+      for (int d = 0; d < dim; ++d) {
+        int pos = dim * b + (dim - 1 - d);
+        uint64_t bit = (q[d] >> b) & 1ull;
+        if (pos < 64) cl |= bit << pos;
+        else ch |= bit << (pos - 64);
+      }
+    code_hi[k] = ch;
+    code_lo[k] = cl;
+  }
+}
+
 /* A3. Sort along the Z-curve: the stable order of the codes (equal codes keep
  * their input order).  perm[k] = input index of the k-th point in order. */
 static const uint64_t *g_sort_codes;
@@ -302,6 +338,22 @@ void oracle_sort_perm(const uint64_t *codes, int64_t n, uint32_t *perm) {
   qsort(perm, (size_t)n, sizeof(uint32_t), perm_cmp);
 }
 
+/* A3 for 128-bit codes: stable order of (hi, lo). */
+static const uint64_t *g_sort_hi, *g_sort_lo;
+static int perm_cmp128(const void *x, const void *y) {
+  uint32_t a = *(const uint32_t *)x, b = *(const uint32_t *)y;
+  if (g_sort_hi[a] != g_sort_hi[b]) return g_sort_hi[a] < g_sort_hi[b] ? -1 : 1;
+  if (g_sort_lo[a] != g_sort_lo[b]) return g_sort_lo[a] < g_sort_lo[b] ? -1 : 1;
+  return a < b ? -1 : (a > b ? 1 : 0);
+}
+void oracle_sort_perm128(const uint64_t *code_hi, const uint64_t *code_lo, int64_t n,
+                         uint32_t *perm) {
+  for (int64_t k = 0; k < n; ++k) perm[k] = (uint32_t)k;
+  g_sort_hi = code_hi;
+  g_sort_lo = code_lo;
+  qsort(perm, (size_t)n, sizeof(uint32_t), perm_cmp128);
+}
+
 /* A4. Binary radix tree over the sorted codes (the linear BVH hierarchy of
  * §2 "ArborX": n leaves, n-1 internal nodes), by its definition, top-down:
  * the node covering sorted positions [a, b] splits after the last position s
@@ -311,14 +363,34 @@ void oracle_sort_perm(const uint64_t *codes, int64_t n, uint32_t *perm) {
  * covering [a, s] is numbered s, one covering [s+1, b] is numbered s+1.
  * Output per internal node: children as refs (internal id in [0, n-1), leaf
  * k as n-1+k) and the covered range [first, last]. */
-static int prefix_len(const uint64_t *c, int64_t a, int64_t b) {
-  /* a != b: leading bits shared by the augmented keys (code, position) */
-  if (c[a] != c[b]) return __builtin_clzll(c[a] ^ c[b]);
-  return 64 + __builtin_clz((uint32_t)a ^ (uint32_t)b);
+
+/* a != b: leading bits shared by the augmented keys (code, position); with
+ * h != NULL the code is 128 bits, h its high word */
+static int prefix_len2(const uint64_t *h, const uint64_t *c, int64_t a, int64_t b) {
+  int base = 0;
+  if (h) {
+    if (h[a] != h[b]) return __builtin_clzll(h[a] ^ h[b]);
+    base = 64;
+  }
+  if (c[a] != c[b]) return base + __builtin_clzll(c[a] ^ c[b]);
+  return base + 64 + __builtin_clz((uint32_t)a ^ (uint32_t)b);
 }
+
+static void radix_tree_impl(const uint64_t *sorted_hi, const uint64_t *sorted_codes, int64_t n,
+                            int64_t *left, int64_t *right, int64_t *first, int64_t *last);
 
 void oracle_radix_tree(const uint64_t *sorted_codes, int64_t n, int64_t *left, int64_t *right,
                        int64_t *first, int64_t *last) {
+  radix_tree_impl(NULL, sorted_codes, n, left, right, first, last);
+}
+
+void oracle_radix_tree128(const uint64_t *sorted_hi, const uint64_t *sorted_lo, int64_t n,
+                          int64_t *left, int64_t *right, int64_t *first, int64_t *last) {
+  radix_tree_impl(sorted_hi, sorted_lo, n, left, right, first, last);
+}
+
+static void radix_tree_impl(const uint64_t *sorted_hi, const uint64_t *sorted_codes, int64_t n,
+                            int64_t *left, int64_t *right, int64_t *first, int64_t *last) {
   if (n < 2) return;
   /* explicit stack of (node id, a, b) */
   int64_t cap = 2 * n + 8;
@@ -330,10 +402,10 @@ void oracle_radix_tree(const uint64_t *sorted_codes, int64_t n, int64_t *left, i
     int64_t id = st[3 * sp], a = st[3 * sp + 1], b = st[3 * sp + 2];
     first[id] = a;
     last[id] = b;
-    int common = prefix_len(sorted_codes, a, b);
+    int common = prefix_len2(sorted_hi, sorted_codes, a, b);
     int64_t s = a;
     for (int64_t k = a + 1; k < b; ++k)
-      if (prefix_len(sorted_codes, a, k) > common) s = k;
+      if (prefix_len2(sorted_hi, sorted_codes, a, k) > common) s = k;
     /* left child [a, s], right child [s+1, b] */
     if (s == a) left[id] = (n - 1) + a;
     else { left[id] = s; st[3 * sp] = s; st[3 * sp + 1] = a; st[3 * sp + 2] = s; ++sp; }

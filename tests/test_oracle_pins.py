@@ -420,3 +420,99 @@ def test_component_min_uses_full_key(oracle_lib):
     j = np.array([1, 0, 0, 1], np.int64)
     cw, ca, cb = oracle_lib.component_min(labels, ids, w, j)
     assert (ca[1], cb[1]) == (1, 0)
+
+
+# ---------------------------------------------------------------------------
+# 128-bit Morton codes (§4.2's finer grid): codes, order, radix tree
+# ---------------------------------------------------------------------------
+def test_morton128_hand_values(oracle_lib):
+    # lo = 0, hi = 1 on every axis: (0.5, 0.25, 0.75) quantises to x = 2^41,
+    # y = 2^40, z = 2^41 + 2^40 on the 42-bit grid; interleaved (x first) those
+    # are bits 125, 121, 123 and 120 of the 128-bit code
+    p = np.array([[0, 0, 0], [1, 1, 1], [0.5, 0.25, 0.75]], np.float32)
+    lo, hi, _ = oracle_lib.scene_box(p)
+    ch, cl = oracle_lib.morton128(p, lo, hi)
+    assert [int(x) for x in ch] == [0, 2 ** 62 - 1, (1 << 61) | (1 << 59) | (1 << 57) | (1 << 56)]
+    assert [int(x) for x in cl] == [0, 2 ** 64 - 1, 0]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_morton128_extends_the_64bit_code_on_a_dyadic_grid(oracle_lib, dim):
+    # coordinates k / 2^10 in [0, 1] with both corners present: both quantisers
+    # are exact, the 64-bit cell is the top half of the 128-bit cell's bits,
+    # so the 128-bit code starts with the 64-bit one
+    g = np.random.default_rng(5)
+    p = (g.integers(0, 1024, size=(2000, dim)) / 1024.0).astype(np.float32)
+    p[0] = 0.0
+    p[1] = 1.0
+    lo, hi, _ = oracle_lib.scene_box(p)
+    c64 = oracle_lib.morton(p, lo, hi)
+    ch, cl = oracle_lib.morton128(p, lo, hi)
+    wide = [(int(h) << 64) | int(l) for h, l in zip(ch, cl)]
+    shift = 128 - 64 if dim == 2 else 126 - 63
+    assert [w >> shift for w in wide] == [int(c) for c in c64]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_morton128_deinterleave_monotone_and_finer(oracle_lib, dim):
+    # clusters denser than the 3D 64-bit grid (cells of 2^-21) but resolved by
+    # FP32: the de-interleaved cells are monotone in each coordinate, and in
+    # 3D the 128-bit codes separate many points the 64-bit codes do not (2D
+    # 64-bit codes already have 32 bits per axis)
+    g = np.random.default_rng(6)
+    centres = g.random((20, dim))
+    p = (centres[g.integers(0, 20, 4000)] + g.normal(0, 2e-7, (4000, dim))).astype(np.float32)
+    lo, hi, _ = oracle_lib.scene_box(p)
+    ch, cl = oracle_lib.morton128(p, lo, hi)
+    B = 42 if dim == 3 else 64
+    wide = [(int(h) << 64) | int(l) for h, l in zip(ch, cl)]
+    q = np.zeros((len(p), dim), dtype=object)
+    for i, w in enumerate(wide):
+        for d in range(dim):
+            v = 0
+            for b in range(B):
+                v |= ((w >> (dim * b + dim - 1 - d)) & 1) << b
+            q[i, d] = v
+    for d in range(dim):
+        o = np.argsort(p[:, d], kind="stable")
+        assert all(q[o[k], d] <= q[o[k + 1], d] for k in range(len(p) - 1))
+    c64 = oracle_lib.morton(p, lo, hi)
+    n128, n64 = len(set(wide)), len(set(int(c) for c in c64))
+    assert n128 >= n64
+    if dim == 3:
+        assert n128 > 2 * n64
+
+
+def test_sort_perm128_is_lexsort(oracle_lib):
+    g = np.random.default_rng(7)
+    ch = g.integers(0, 8, 4000).astype(np.uint64)
+    cl = g.integers(0, 8, 4000).astype(np.uint64) << np.uint64(50)
+    assert np.array_equal(oracle_lib.sort_perm128(ch, cl), np.lexsort((np.arange(4000), cl, ch)))
+
+
+def test_radix_tree128_reduces_to_64bit_and_keeps_invariants(oracle_lib):
+    g = np.random.default_rng(8)
+    lo = np.sort(g.integers(0, 2 ** 62, 300).astype(np.uint64))
+    want = oracle_lib.radix_tree(lo)
+    got = oracle_lib.radix_tree128(np.zeros(300, np.uint64), lo)
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)
+    # with duplicates in both words: the split bit of the augmented
+    # (hi, lo, position) key is 0 on the left and 1 on the right
+    hi = np.sort(g.integers(0, 4, 200).astype(np.uint64))
+    lw = g.integers(0, 3, 200).astype(np.uint64) << np.uint64(63)
+    o = np.lexsort((lw, hi))
+    hi, lw = hi[o], lw[o]
+    left, right, first, last = oracle_lib.radix_tree128(hi, lw)
+    n = len(hi)
+
+    def key(k):
+        return (int(hi[k]) << 96) | (int(lw[k]) << 32) | int(k)
+    for v in range(n - 1):
+        a, b = first[v], last[v]
+        lf = (left[v] - (n - 1),) * 2 if left[v] >= n - 1 else (first[left[v]], last[left[v]])
+        rt = (right[v] - (n - 1),) * 2 if right[v] >= n - 1 else (first[right[v]], last[right[v]])
+        assert lf[0] == a and rt[1] == b and lf[1] + 1 == rt[0]
+        bit = (key(a) ^ key(b)).bit_length() - 1
+        assert all(((key(k) >> bit) & 1) == 0 for k in range(lf[0], lf[1] + 1))
+        assert all(((key(k) >> bit) & 1) == 1 for k in range(rt[0], rt[1] + 1))
