@@ -89,7 +89,13 @@ typedef struct emst_options {
                                  weights are then FP32 squared mutual reachability distances,
                                  ordered and tie-broken like the Euclidean ones.  Not together
                                  with mlp_params. */
-  int32_t reserved[7];
+  int32_t morton_bits;        /* Z-curve code width: 64 (21 bits per axis in 3D, 32 in 2D,
+                                 FP32 quantiser), 128 (42 / 64 bits per axis, FP64 quantiser:
+                                 the finer grid §4.2 suggests for very dense data; one more
+                                 8-pass sort) or 0 = automatic (the default): 64, rebuilt with
+                                 128 when more than n/64 distinct points share their curve
+                                 predecessor's 64-bit code.  The tree is the same either way. */
+  int32_t reserved[6];
 } emst_options;
 
 #define EMST_MRD_MAX_K 32
@@ -99,7 +105,7 @@ typedef struct emst_stats {
   int32_t struct_size;   /* set by the caller: sizeof(emst_stats) */
   int32_t rounds;        /* Boruvka rounds run */
   int32_t kernel_launches; /* kernels this call launched */
-  int32_t reserved0;
+  int32_t morton_bits;   /* Z-curve code width used (64 or 128) */
   double total_ms;       /* device time of the whole call (CUDA events) */
   double build_ms;       /* scene box, codes, sort, hierarchy, refit (A1-A4) */
   double rounds_ms;      /* all Boruvka rounds */
@@ -116,7 +122,10 @@ typedef struct emst_stats {
   double learned_search_ms; /* learned radius: device time of the searches with the proposed
                                cutoffs alone (traverse_ms adds inference and the reruns) */
   double core_ms;          /* mutual reachability: device time of the core distances */
-  int64_t reserved[2];
+  int64_t code_collisions; /* distinct points sharing their curve predecessor's code: of the
+                              64-bit codes when they were built (automatic or 64), else of
+                              the 128-bit ones */
+  int64_t reserved[1];
 } emst_stats;
 
 /* EMST of n points (§3, Fig. 3 end to end).
@@ -245,6 +254,13 @@ const char *emst_status_string(int status);
  * Any output pointer may be NULL (then it is not written). */
 int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint64_t *out_codes,
                    uint32_t *out_perm, uint32_t *out_children, float *out_boxes, void *stream);
+
+/* emst_build_bvh with a Z-curve code width: morton_bits 64 (as above) or 128
+ * (emst_options.morton_bits); with 128, out_codes holds 2n uint64: the sorted
+ * codes as (high word, low word) pairs. */
+int emst_build_bvh_ex(const float *points, int64_t n, int dim, int leaf_size, int morton_bits,
+                      uint64_t *out_codes, uint32_t *out_perm, uint32_t *out_children,
+                      float *out_boxes, void *stream);
 
 /* One Boruvka round from given component labels (§3: Optimization 1 node
  * labels, Optimization 2 upper bounds, Algorithm 2 queries, the per-component

@@ -34,6 +34,7 @@ __all__ = [
     "EMST_NOALLOC_MAX_POINTS",
     "emst_status_string",
     "emst_build_bvh",
+    "emst_build_bvh_ex",
     "emst_round_step",
     "edges_w",
     "EMST_MLP_PARAMS",
@@ -72,12 +73,12 @@ class _Options(ctypes.Structure):
                 ("carried_radius", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("count_visits", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("mlp_params", ctypes.c_void_p), ("mrd_k", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("morton_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("rounds", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("morton_bits", ctypes.c_int32),
                 ("total_ms", ctypes.c_double), ("build_ms", ctypes.c_double),
                 ("rounds_ms", ctypes.c_double), ("output_ms", ctypes.c_double),
                 ("node_visits", ctypes.c_int64), ("components_per_round", ctypes.c_int64 * 40),
@@ -85,7 +86,7 @@ class _Stats(ctypes.Structure):
                 ("reserved1", ctypes.c_int32), ("round_traverse_ms", ctypes.c_double * 40),
                 ("queried_points", ctypes.c_int64), ("rerun_points", ctypes.c_int64),
                 ("learned_search_ms", ctypes.c_double), ("core_ms", ctypes.c_double),
-                ("reserved", ctypes.c_int64 * 2)]
+                ("code_collisions", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1)]
 
 
 _lock = threading.Lock()
@@ -116,6 +117,8 @@ def load_library(path: str | None = None):
         lib.emst_compute_ex.restype = I
         lib.emst_compute_batched.argtypes = [V, V, I, I, V, V, V]
         lib.emst_compute_batched.restype = I
+        lib.emst_build_bvh_ex.argtypes = [V, I64, I, I, I, V, V, V, V, V]
+        lib.emst_build_bvh_ex.restype = I
         lib.emst_core_distances.argtypes = [V, I64, I, I, V, V]
         lib.emst_core_distances.restype = I
         lib.emst_status_string.argtypes = [I]
@@ -227,7 +230,8 @@ def emst_compute_noalloc(points, out_edges=None, stream=None):
 
 
 def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_radius=True,
-                    use_graph=False, count_visits=False, leaf_size=0, mlp_params=None, mrd_k=0):
+                    use_graph=False, count_visits=False, leaf_size=0, mlp_params=None, mrd_k=0,
+                    morton_bits=0):
     """emst_compute with options; returns (edges, stats dict).  mrd_k >= 2:
     the mutual-reachability MST (squared MRD weights)."""
     n, dim = _check_points(points)
@@ -240,6 +244,7 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
     opt.count_visits = 1 if count_visits else 0
     opt.leaf_size = int(leaf_size)
     opt.mrd_k = int(mrd_k)
+    opt.morton_bits = int(morton_bits)
     if mlp_params is not None:
         if mlp_params.dtype != _torch().float32 or mlp_params.numel() != EMST_MLP_PARAMS:
             raise ValueError(f"mlp_params must hold {EMST_MLP_PARAMS} float32 values")
@@ -258,7 +263,8 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
                  round_traverse_ms=[float(st.round_traverse_ms[k]) for k in range(min(st.rounds, 40))],
                  components_per_round=[int(st.components_per_round[k]) for k in range(min(st.rounds, 40))],
                  queried_points=st.queried_points, rerun_points=st.rerun_points,
-                 learned_search_ms=st.learned_search_ms, core_ms=st.core_ms)
+                 learned_search_ms=st.learned_search_ms, core_ms=st.core_ms,
+                 morton_bits=st.morton_bits, code_collisions=st.code_collisions)
     return out_edges, stats
 
 
@@ -300,21 +306,23 @@ def emst_compute_batched(points, offsets, out_edges=None, stream=None):
     return out_edges, out_offs
 
 
-def emst_build_bvh(points, leaf_size=1, stream=None):
+def emst_build_bvh(points, leaf_size=1, stream=None, morton_bits=64):
     """The built hierarchy over leaf chunks of `leaf_size` curve positions:
-    dict(codes, perm, children (m-1, 2), boxes (m-1, 2, 6)), m = ceil(n/leaf_size)."""
+    dict(codes, perm, children (m-1, 2), boxes (m-1, 2, 6)), m = ceil(n/leaf_size).
+    With morton_bits=128, codes is (n, 2): (high, low) words."""
     torch = _torch()
     n, dim = _check_points(points)
     dev = points.device if points.device.type == "cuda" else torch.device("cuda")
     m = max((n + leaf_size - 1) // leaf_size, 1)
-    codes = torch.empty(n, dtype=torch.int64, device=dev)
+    codes = torch.empty((n, 2) if morton_bits == 128 else n, dtype=torch.int64, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     children = torch.empty((m - 1, 2), dtype=torch.int32, device=dev)
     boxes = torch.empty((m - 1, 2, 6), dtype=torch.float32, device=dev)
-    rc = load_library().emst_build_bvh(_ptr(points), n, dim, int(leaf_size), _ptr(codes), _ptr(perm),
-                                       _ptr(children), _ptr(boxes), _stream_ptr(stream, dev))
+    rc = load_library().emst_build_bvh_ex(_ptr(points), n, dim, int(leaf_size), int(morton_bits),
+                                          _ptr(codes), _ptr(perm), _ptr(children), _ptr(boxes),
+                                          _stream_ptr(stream, dev))
     if rc != 0:
-        raise EmstError(rc, "emst_build_bvh")
+        raise EmstError(rc, "emst_build_bvh_ex")
     return dict(codes=codes, perm=perm, children=children, boxes=boxes)
 
 

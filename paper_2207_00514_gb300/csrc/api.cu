@@ -139,6 +139,8 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   }
   if (P.want_logging) P.log_count = c.take<unsigned long long>(1);
   P.core2 = P.want_mrd ? c.take<float>(n) : nullptr;
+  P.wide_hi = P.wide || P.auto_wide ? c.take<uint64_t>(n) : nullptr;
+  P.wide_lo = P.wide || P.auto_wide ? c.take<uint64_t>(n) : nullptr;
   float *pcopy = c.take<float>(copy_points ? n * P.dim : 1);
   if (copy_points) P.points = pcopy;
   emst_edge *ecopy = c.take<emst_edge>(copy_edges ? n : 1);
@@ -171,18 +173,63 @@ int bits_for(int64_t v) {  // bits needed to represent values in [0, v]
   return b;
 }
 
-// A1-A4: scene box, codes, sort, gather, hierarchy, refit.
-void run_build(Problem &P) {
-  launch_scene_box(P);
-  if (P.num_inst > 1) launch_instance_ids(P);
+// A2-A4 (a): codes, their stable order, the points gathered into it.
+static void build_order64(Problem &P) {
   launch_morton(P);
-  int src = radix_sort_pairs(P, P.n, 0, 8, 0);
+  const int src = radix_sort_pairs(P, P.n, 0, 8, 0);
   if (src != 0) {  // keep the sorted codes in keys[0] and the order in vals[0]
     std::swap(P.keys[0], P.keys[1]);
     std::swap(P.vals[0], P.vals[1]);
   }
+  P.code_hi = nullptr;
   P.perm = P.vals[0];
   launch_gather(P, P.perm);
+}
+
+// The same with 128-bit codes: a stable LSD sort by the low words, then by
+// the high words carrying that order; the low words follow the final order.
+static void build_order128(Problem &P) {
+  launch_morton128(P);
+  const int s = radix_sort_pairs(P, P.n, 0, 8, 0);
+  launch_gather_u64(P, P.wide_hi, P.vals[s], P.keys[s ^ 1]);
+  cudaMemcpyAsync(P.vals[s ^ 1], P.vals[s], sizeof(uint32_t) * (size_t)P.n,
+                  cudaMemcpyDeviceToDevice, P.stream);
+  const int r = radix_sort_pairs(P, P.n, 0, 8, s ^ 1);
+  launch_gather_u64(P, P.wide_lo, P.vals[r], P.keys[r ^ 1]);
+  // keys[0] = sorted low words, keys[1] = sorted high words, vals[0] = order
+  if (r == 0) std::swap(P.keys[0], P.keys[1]);
+  else std::swap(P.vals[0], P.vals[1]);
+  P.code_hi = P.keys[1];
+  P.perm = P.vals[0];
+  launch_gather(P, P.perm);
+}
+
+// A1-A4: scene box, codes, sort, gather, hierarchy, refit.  With auto_wide
+// the 64-bit order is built first and its collisions counted (one host
+// read); when more than n/64 distinct points share their predecessor's code,
+// the order is rebuilt with 128-bit codes (§4.2's remedy for data the 64-bit
+// grid under-resolves).
+void run_build(Problem &P) {
+  launch_scene_box(P);
+  if (P.num_inst > 1) launch_instance_ids(P);
+  if (P.wide) {
+    build_order128(P);
+  } else {
+    build_order64(P);
+    if (P.auto_wide) {
+      unsigned long long c = 0;
+      uint32_t status = 0;
+      cudaMemcpyAsync(&c, P.counters + 30, sizeof(c), cudaMemcpyDeviceToHost, P.stream);
+      cudaMemcpyAsync(&status, P.counters + 1, sizeof(status), cudaMemcpyDeviceToHost, P.stream);
+      if (cudaStreamSynchronize(P.stream) == cudaSuccess) {
+        P.code_collisions = (int64_t)c;
+        if (status == 0 && (int64_t)c * 64 > P.n) {
+          P.wide = true;
+          build_order128(P);
+        }
+      }
+    }
+  }
   if (P.n >= 2) {
     cudaMemsetAsync(P.arrivals, 0, sizeof(uint32_t) * (size_t)(P.nc - 1), P.stream);
     launch_hierarchy(P);
@@ -212,22 +259,37 @@ void reset_round_state(Problem &P) {
 // A12: the n-1 edges in (w, i, j) order into `out` (device).  w_bits: the
 // largest emitted weight's bits (counters[11]): the sort key needs
 // L + significant bits of it.
-void run_output(Problem &P, emst_edge *out, uint32_t w_bits) {
+int run_output(Problem &P, emst_edge *out, uint32_t w_bits) {
   const int64_t m = P.num_inst > 1 ? P.edges_expected : P.n - 1;
-  if (m <= 0) return;
+  if (m <= 0) return EMST_OK;
   const int L = bits_for(P.n - 1);
   const int wb = w_bits ? 32 - __builtin_clz(w_bits) : 0;
-  launch_edge_keys_wi(P, m, L);
-  int s = radix_sort_pairs(P, m, 0, (L + wb + 7) / 8, 0);
-  launch_edge_ties(P, m, s);
   if (P.num_inst == 1) {
-    launch_edge_from_keys(P, m, s, L, out);
-    return;
+    launch_edge_keys_wi(P, m, L);
+    const int s = radix_sort_pairs(P, m, 0, (L + wb + 7) / 8, 0);
+    cudaMemsetAsync(P.counters + 10, 0, sizeof(uint32_t), P.stream);
+    launch_edge_ties(P, m, s);
+    uint32_t long_runs = 0;
+    if (cudaMemcpyAsync(&long_runs, P.counters + 10, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                        P.stream) != cudaSuccess ||
+        cudaStreamSynchronize(P.stream) != cudaSuccess)
+      return EMST_ERR_CUDA;
+    if (long_runs == 0) {
+      launch_edge_from_keys(P, m, s, L, out);
+      return EMST_OK;
+    }
   }
-  // instance is the most significant key (stable LSD)
-  launch_edge_keys_inst(P, m, s);
-  s = radix_sort_pairs(P, m, 0, (P.inst_bits + 7) / 8, s);
+  // full path: stable by j, then by (w, i), then (batched) by instance
+  launch_edge_keys_j(P, m);
+  int s = radix_sort_pairs(P, m, 0, (L + 7) / 8, 0);
+  launch_edge_keys_wi_of(P, m, s, L);
+  s = radix_sort_pairs(P, m, 0, (L + wb + 7) / 8, s);
+  if (P.num_inst > 1) {
+    launch_edge_keys_inst(P, m, s);
+    s = radix_sort_pairs(P, m, 0, (P.inst_bits + 7) / 8, s);
+  }
   launch_edge_gather(P, m, P.vals[s], out);
+  return EMST_OK;
 }
 
 namespace {
@@ -294,7 +356,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     stats->struct_size = sz;
   }
   if (n == 0) return EMST_OK;
-  int block = 0, carried = 1, count = 0, leaf_req = 0, mrd_k = 0;
+  int block = 0, carried = 1, count = 0, leaf_req = 0, mrd_k = 0, morton_bits = 0;
   const float *mlp_params = nullptr;
   if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
     block = opt->block_size;
@@ -305,6 +367,8 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     mrd_k = opt->mrd_k;
     if (mrd_k < 0 || mrd_k > EMST_MRD_MAX_K || (mrd_k >= 2 && (mlp_params || n < mrd_k)))
       return EMST_ERR_INVALID_ARG;
+    morton_bits = opt->morton_bits;
+    if (morton_bits != 0 && morton_bits != 64 && morton_bits != 128) return EMST_ERR_INVALID_ARG;
     if (leaf_req < 0 || leaf_req > 16 || (leaf_req & (leaf_req - 1)) != 0) return EMST_ERR_INVALID_ARG;
     if (block != 0 && (block < 64 || block > kTraverseMaxBlock || block % 32 != 0))
       return EMST_ERR_INVALID_ARG;
@@ -334,6 +398,8 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   P.want_learned = learned;
   P.want_logging = logging;
   P.want_mrd = mrd_k >= 2 && !offsets && n >= 2;
+  P.wide = morton_bits == 128 && !offsets;
+  P.auto_wide = morton_bits == 0 && !offsets;
   if (logging) {
     P.log_feat = ex->log_feat;
     P.log_target = ex->log_target;
@@ -343,7 +409,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   int64_t reruns = 0;
   const size_t need = layout(P, nullptr, !pts_dev, !out_dev);
   char *base = nullptr;
-  uint32_t host_counters[16] = {0};
+  uint32_t host_counters[33] = {0};
   Timer tm;
   int rounds = 0;
   cudaEvent_t tev[2 * 40];
@@ -374,6 +440,9 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
                      stream));
   CU(cudaStreamSynchronize(stream));
   if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
+  // a large group of identical points can exist: the search needs its tie rule
+  P.ties = host_counters[32] != 0;
+  if (!P.auto_wide) P.code_collisions = (int64_t)host_counters[30] | ((int64_t)host_counters[31] << 32);
   if (expected > 0) {
     if (P.core2) {  // mutual reachability: core distances on the finished hierarchy
       if (stats) {
@@ -437,7 +506,10 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     }
     tm.mark(2, stream);
     if ((int64_t)host_counters[0] != expected) { rc = EMST_ERR_INTERNAL; goto done; }
-    if (!skip_output) run_output(P, out_dev ? out : P.out_stage, host_counters[11]);
+    if (!skip_output) {
+      rc = run_output(P, out_dev ? out : P.out_stage, host_counters[11]);
+      if (rc != EMST_OK) goto done;
+    }
     if (!out_dev && !skip_output)
       CU(cudaMemcpyAsync(out, P.out_stage, sizeof(emst_edge) * (size_t)expected,
                          cudaMemcpyDeviceToHost, stream));
@@ -462,6 +534,8 @@ done:
     cudaStreamSynchronize(stream);
     stats->rounds = rounds;
     stats->kernel_launches = P.launches;
+    stats->morton_bits = P.wide ? 128 : 64;
+    stats->code_collisions = P.code_collisions;
     stats->build_ms = tm.ms(0, 1);
     stats->rounds_ms = tm.ms(1, 2);
     stats->output_ms = tm.ms(2, 3);
@@ -653,16 +727,24 @@ int emst_core_distances(const float *points, int64_t n, int dim, int k, float *o
   return finish_session(S);
 }
 
-int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint64_t *out_codes,
-                   uint32_t *out_perm, uint32_t *out_children, float *out_boxes, void *stream) {
+int emst_build_bvh_ex(const float *points, int64_t n, int dim, int leaf_size, int morton_bits,
+                      uint64_t *out_codes, uint32_t *out_perm, uint32_t *out_children,
+                      float *out_boxes, void *stream) {
+  if (morton_bits != 64 && morton_bits != 128) return EMST_ERR_INVALID_ARG;
   Session S;
+  S.P.wide = morton_bits == 128;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = open_session(S, points, n, dim, leaf_size, s);
   if (rc != EMST_OK) return rc;
   Problem &P = S.P;
   run_build(P);
   const int64_t m = P.nc - 1;
-  if (out_codes) cudaMemcpyAsync(out_codes, P.keys[0], 8 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+  if (out_codes && !P.wide)
+    cudaMemcpyAsync(out_codes, P.keys[0], 8 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+  if (out_codes && P.wide) {  // (high, low) word pairs
+    cudaMemcpy2DAsync(out_codes, 16, P.code_hi, 8, 8, (size_t)n, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpy2DAsync(out_codes + 1, 16, P.keys[0], 8, 8, (size_t)n, cudaMemcpyDeviceToDevice, s);
+  }
   if (out_perm) cudaMemcpyAsync(out_perm, P.perm, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
   if (out_children)
     cudaMemcpy2DAsync(out_children, 8, reinterpret_cast<char *>(P.nodes) + 48, 64, 8, (size_t)m,
@@ -670,6 +752,12 @@ int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint6
   if (out_boxes)
     cudaMemcpy2DAsync(out_boxes, 48, P.nodes, 64, 48, (size_t)m, cudaMemcpyDeviceToDevice, s);
   return finish_session(S);
+}
+
+int emst_build_bvh(const float *points, int64_t n, int dim, int leaf_size, uint64_t *out_codes,
+                   uint32_t *out_perm, uint32_t *out_children, float *out_boxes, void *stream) {
+  return emst_build_bvh_ex(points, n, dim, leaf_size, 64, out_codes, out_perm, out_children,
+                           out_boxes, stream);
 }
 
 int emst_round_step(const float *points, int64_t n, int dim, int leaf_size,

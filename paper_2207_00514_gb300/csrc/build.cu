@@ -114,6 +114,76 @@ void launch_morton(Problem &P) {
   P.launches += 1;
 }
 
+// A2 at the finer grid §4.2 suggests for very dense data (128-bit codes):
+// B = 42 bits per dimension in 3D, 64 in 2D, quantised in FP64 so the grid
+// resolves FP32 coordinates:
+//   s = 2^B / (hi - lo) (0 for a flat dimension), t = (x - lo) * s,
+//   q = t >= 2^B ? 2^B - 1 : trunc(t)
+// every step rounded explicitly.  The code is the 64-bit interleave of each
+// half of the cells: in 3D, with H and L the 63-bit interleaves of the high
+// and low 21 bits, code = H << 63 | L; in 2D the halves are the two words.
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_morton128(const float *__restrict__ pts, int64_t n,
+                                                      const uint32_t *__restrict__ box,
+                                                      uint64_t *__restrict__ code_hi,
+                                                      uint64_t *__restrict__ code_lo,
+                                                      uint64_t *__restrict__ keys,
+                                                      uint32_t *__restrict__ vals) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  constexpr int B = DIM == 3 ? 42 : 64;
+  const double twoB = DIM == 3 ? 4398046511104.0 : 18446744073709551616.0;  // 2^B
+  const uint64_t qmax = DIM == 3 ? ((1ull << 42) - 1ull) : ~0ull;
+  uint64_t q[3] = {0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double lo = (double)ordered_to_float(box[d]);
+    const double ext = __dsub_rn((double)ordered_to_float(box[3 + d]), lo);
+    const double sc = ext > 0.0 ? __ddiv_rn(twoB, ext) : 0.0;
+    const double t = __dmul_rn(__dsub_rn((double)__ldg(pts + k * DIM + d), lo), sc);
+    q[d] = t >= twoB ? qmax : (uint64_t)t;
+  }
+  uint64_t hi, lo;
+  if (DIM == 3) {
+    const uint64_t H = interleave((uint32_t)(q[0] >> 21), (uint32_t)(q[1] >> 21), (uint32_t)(q[2] >> 21), 3);
+    const uint64_t L = interleave((uint32_t)(q[0] & 0x1fffffu), (uint32_t)(q[1] & 0x1fffffu),
+                                  (uint32_t)(q[2] & 0x1fffffu), 3);
+    hi = H >> 1;
+    lo = L | (H << 63);
+  } else {
+    hi = interleave((uint32_t)(q[0] >> 32), (uint32_t)(q[1] >> 32), 0u, 2);
+    lo = interleave((uint32_t)q[0], (uint32_t)q[1], 0u, 2);
+  }
+  (void)B;
+  code_hi[k] = hi;
+  code_lo[k] = lo;
+  keys[k] = lo;
+  vals[k] = (uint32_t)k;
+}
+
+void launch_morton128(Problem &P) {
+  int g = grid_for(P.n, kBlock);
+  if (P.dim == 3)
+    k_morton128<3><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.wide_hi, P.wide_lo,
+                                               P.keys[0], P.vals[0]);
+  else
+    k_morton128<2><<<g, kBlock, 0, P.stream>>>(P.points, P.n, P.counters + 4, P.wide_hi, P.wide_lo,
+                                               P.keys[0], P.vals[0]);
+  P.launches += 1;
+}
+
+// out[k] = src[idx[k]] (a 64-bit word carried through a permutation)
+__global__ void k_gather_u64(const uint64_t *__restrict__ src, const uint32_t *__restrict__ idx,
+                             int64_t n, uint64_t *__restrict__ out) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = __ldg(src + __ldg(idx + k));
+}
+
+void launch_gather_u64(Problem &P, const uint64_t *src, const uint32_t *idx, uint64_t *out) {
+  k_gather_u64<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(src, idx, P.n, out);
+  P.launches += 1;
+}
+
 // Instance id of every input row (binary search in the offsets).
 __global__ void __launch_bounds__(kBlock) k_instance_ids(const int64_t *__restrict__ offsets,
                                                          int64_t num_inst, int64_t n,
@@ -174,13 +244,23 @@ void launch_instance_roots(Problem &P) {
 // A4 (a). Gather the points into curve order as float4 (x, y, z, original
 // index bits) and the first labels (labels(i) = i, Fig. 3), in curve indices.
 // ---------------------------------------------------------------------------
+// Also counts, over the curve positions whose code equals the previous
+// position's: identical points (dup[0]) and distinct points the grid does not
+// separate (dup[1]: a cell holding many of them has no spatial order inside,
+// so its subtree's boxes all span it); and flags (dup[2] != 0) a run of more
+// than 32 equal codes -- the only way a group of identical points can be
+// large, which is when the search needs its tie rule.
+// code_hi: the codes' high words (128-bit codes), else nullptr.
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) k_gather(const float *__restrict__ pts,
                                                    const uint32_t *__restrict__ perm, int64_t n,
                                                    float4 *__restrict__ out,
                                                    uint32_t *__restrict__ labels,
                                                    const uint32_t *__restrict__ inst_in,
-                                                   uint32_t *__restrict__ inst_of) {
+                                                   uint32_t *__restrict__ inst_of,
+                                                   const uint64_t *__restrict__ sorted_codes,
+                                                   const uint64_t *__restrict__ code_hi,
+                                                   unsigned long long *dup) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   uint32_t o = __ldg(perm + k);
@@ -189,16 +269,36 @@ __global__ void __launch_bounds__(kBlock) k_gather(const float *__restrict__ pts
   float x = __ldg(p), y = __ldg(p + 1), z = DIM == 3 ? __ldg(p + 2) : 0.0f;
   out[k] = make_float4(x, y, z, __uint_as_float(o));
   labels[k] = (uint32_t)k;
+  bool same = false, differ = false;
+  if (k > 0 && __ldg(sorted_codes + k) == __ldg(sorted_codes + k - 1) &&
+      (!code_hi || __ldg(code_hi + k) == __ldg(code_hi + k - 1))) {
+    const float *q = pts + (int64_t)__ldg(perm + k - 1) * DIM;
+    differ = __ldg(q) != x || __ldg(q + 1) != y || (DIM == 3 && __ldg(q + 2) != z);
+    same = !differ;
+  }
+  // sorted codes: equal 32 positions back means all between are equal too
+  const bool run = k >= 32 && __ldg(sorted_codes + k) == __ldg(sorted_codes + k - 32) &&
+                   (!code_hi || __ldg(code_hi + k) == __ldg(code_hi + k - 32));
+  const unsigned mask = __activemask();
+  const unsigned cs = __popc(__ballot_sync(mask, same)), cd = __popc(__ballot_sync(mask, differ));
+  const unsigned cr = __ballot_sync(mask, run);
+  if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) {
+    if (cs) atomicAdd(dup, (unsigned long long)cs);
+    if (cd) atomicAdd(dup + 1, (unsigned long long)cd);
+    if (cr) atomicOr(reinterpret_cast<unsigned int *>(dup + 2), 1u);
+  }
 }
 
 void launch_gather(Problem &P, const uint32_t *perm) {
   int g = grid_for(P.n, kBlock);
+  unsigned long long *dup = reinterpret_cast<unsigned long long *>(P.counters + 28);
+  cudaMemsetAsync(dup, 0, 3 * sizeof(unsigned long long), P.stream);
   if (P.dim == 3)
     k_gather<3><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.labels, P.inst_in,
-                                            P.inst_of);
+                                            P.inst_of, P.keys[0], P.code_hi, dup);
   else
     k_gather<2><<<g, kBlock, 0, P.stream>>>(P.points, perm, P.n, P.pts, P.labels, P.inst_in,
-                                            P.inst_of);
+                                            P.inst_of, P.keys[0], P.code_hi, dup);
   P.launches += 1;
 }
 
@@ -210,34 +310,44 @@ void launch_gather(Problem &P, const uint32_t *perm) {
 // split gamma gives the children gamma (left) and gamma+1 (right), leaves when
 // the range ends there.  This is the numbering drawn in Fig. 4.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k, int64_t nc, int leaf,
+// kh != nullptr: 128-bit codes, kh their high words (the augmented key is
+// then (high, low, position), 160 bits)
+__device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k,
+                                            const uint64_t *__restrict__ kh, int64_t nc, int leaf,
                                             int64_t i, int64_t j) {
   if (j < 0 || j >= nc) return -1;
+  int base = 0;
+  if (kh) {
+    const uint64_t a = __ldg(kh + i * leaf), b = __ldg(kh + j * leaf);
+    if (a != b) return __clzll((long long)(a ^ b));
+    base = 64;
+  }
   uint64_t a = __ldg(k + i * leaf), b = __ldg(k + j * leaf);
-  if (a != b) return __clzll((long long)(a ^ b));
-  return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+  if (a != b) return base + __clzll((long long)(a ^ b));
+  return base + 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
 }
 
-__global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict__ keys, int64_t nc,
-                                                      int leaf,
+__global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict__ keys,
+                                                      const uint64_t *__restrict__ keys_hi,
+                                                      int64_t nc, int leaf,
                                                       uint32_t *__restrict__ parent_leaf,
                                                       uint2 *__restrict__ up_delta,
                                                       uint4 *__restrict__ range) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc - 1) return;
-  int d = (prefix_delta(keys, nc, leaf, i, i + 1) - prefix_delta(keys, nc, leaf, i, i - 1)) > 0 ? 1 : -1;
-  int dmin = prefix_delta(keys, nc, leaf, i, i - d);
+  int d = (prefix_delta(keys, keys_hi, nc, leaf, i, i + 1) - prefix_delta(keys, keys_hi, nc, leaf, i, i - 1)) > 0 ? 1 : -1;
+  int dmin = prefix_delta(keys, keys_hi, nc, leaf, i, i - d);
   int64_t lmax = 2;
-  while (prefix_delta(keys, nc, leaf, i, i + lmax * d) > dmin) lmax <<= 1;
+  while (prefix_delta(keys, keys_hi, nc, leaf, i, i + lmax * d) > dmin) lmax <<= 1;
   int64_t l = 0;
   for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-    if (prefix_delta(keys, nc, leaf, i, i + (l + t) * d) > dmin) l += t;
+    if (prefix_delta(keys, keys_hi, nc, leaf, i, i + (l + t) * d) > dmin) l += t;
   int64_t j = i + l * d;
-  int dnode = prefix_delta(keys, nc, leaf, i, j);
+  int dnode = prefix_delta(keys, keys_hi, nc, leaf, i, j);
   int64_t s = 0, t = l;
   do {
     t = (t + 1) >> 1;
-    if (prefix_delta(keys, nc, leaf, i, i + (s + t) * d) > dnode) s += t;
+    if (prefix_delta(keys, keys_hi, nc, leaf, i, i + (s + t) * d) > dnode) s += t;
   } while (t > 1);
   int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
   int64_t lo = i < j ? i : j, hi = i < j ? j : i;
@@ -255,7 +365,7 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
 
 void launch_hierarchy(Problem &P) {
   k_hierarchy<<<grid_for(P.nc - 1, kBlock), kBlock, 0, P.stream>>>(
-      P.keys[0] /*sorted*/, P.nc, P.leaf, P.parent_leaf, P.up_delta, P.range);
+      P.keys[0] /*sorted*/, P.code_hi, P.nc, P.leaf, P.parent_leaf, P.up_delta, P.range);
   P.launches += 1;
 }
 
@@ -274,6 +384,8 @@ void launch_hierarchy(Problem &P) {
 // global counters.  The global counters are never reset: each
 // pass adds exactly two arrivals per node, so the parity of the count before
 // the add tells first from second.
+// Each record also carries the smallest original id of each child's points
+// (the traversal's tie pruning).
 // The child labels are the round-0 ones (a one-point chunk k: label k;
 // otherwise several components, kInvalid); a caller with other labels
 // rewrites them (A5).
@@ -298,6 +410,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
                                                   const uint4 *__restrict__ range,
                                                   uint32_t *arrivals) {
   __shared__ float s_box[kRefitBlock][2][6];  // both child boxes of each local node
+  __shared__ uint32_t s_min[kRefitBlock][2];  // and their smallest original ids
   __shared__ uint32_t s_arrive[kRefitBlock];
   const int64_t first = (int64_t)blockIdx.x * kRefitBlock;
   const int64_t last = first + kRefitBlock - 1;
@@ -308,10 +421,12 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
   const int64_t p0 = k * leaf, p1 = p0 + leaf < n ? p0 + leaf : n;
   float4 p = pts[p0];
   float box[6] = {p.x, p.y, p.z, p.x, p.y, p.z};
+  uint32_t idmin = __float_as_uint(p.w);
   for (int64_t m = p0 + 1; m < p1; ++m) {
     p = pts[m];
     box[0] = fminf(box[0], p.x); box[1] = fminf(box[1], p.y); box[2] = fminf(box[2], p.z);
     box[3] = fmaxf(box[3], p.x); box[4] = fmaxf(box[4], p.y); box[5] = fmaxf(box[5], p.z);
+    idmin = min(idmin, __float_as_uint(p.w));
   }
   uint32_t up = parent_leaf[k];
   while (true) {
@@ -322,16 +437,20 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
     const uint32_t up_next = __ldg(&up_delta[node].x);
     const bool local = (int64_t)r.x >= first && (int64_t)r.z <= last;
     float sib[6];
+    uint32_t sibmin;
     if (local) {
 #pragma unroll
       for (int t = 0; t < 6; ++t) s_box[node - first][slot][t] = box[t];
+      s_min[node - first][slot] = idmin;
       __threadfence_block();
       if (atomicAdd(&s_arrive[node - first], 1u) == 0u) return;  // first: the sibling carries on
       __threadfence_block();
 #pragma unroll
       for (int t = 0; t < 6; ++t) sib[t] = s_box[node - first][slot ^ 1][t];
+      sibmin = s_min[node - first][slot ^ 1];
     } else {
       store_slot_box(&nodes[node], slot, box);
+      reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = idmin;
       __threadfence();
       const uint32_t before = atomicAdd(&arrivals[node], 1u);
       if ((before & 1u) == 0u) return;
@@ -343,6 +462,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
         sib[2 * t] = v.x;
         sib[2 * t + 1] = v.y;
       }
+      sibmin = __ldcg(reinterpret_cast<const uint32_t *>(&nodes[node].d) + 2 + (slot ^ 1));
     }
     const float *L = slot == 0 ? box : sib;
     const float *R = slot == 0 ? sib : box;
@@ -356,7 +476,8 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
     rec.a = make_float4(L[0], L[1], L[2], L[3]);
     rec.b = make_float4(L[4], L[5], R[0], R[1]);
     rec.c = make_float4(R[2], R[3], R[4], R[5]);
-    rec.d = make_uint4(lleaf ? (kLeafBit | g) : g, rleaf ? (kLeafBit | (g + 1u)) : g + 1u, 0u, 0u);
+    rec.d = make_uint4(lleaf ? (kLeafBit | g) : g, rleaf ? (kLeafBit | (g + 1u)) : g + 1u,
+                       slot == 0 ? idmin : sibmin, slot == 0 ? sibmin : idmin);
     nodes[node] = rec;
     nlabels[node] = make_uint2(lleaf && one_point(g) ? (uint32_t)((int64_t)g * leaf) : kInvalid,
                                rleaf && one_point(g + 1) ? (uint32_t)((int64_t)(g + 1) * leaf) : kInvalid);
@@ -365,6 +486,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
       box[t] = fminf(L[t], R[t]);
       box[3 + t] = fmaxf(L[3 + t], R[3 + t]);
     }
+    idmin = min(idmin, sibmin);
     if (node == 0) return;
     up = up_next;
   }

@@ -30,7 +30,8 @@ enum : uint32_t {
 //   f[0..5]   left child box  (lo x,y,z, hi x,y,z)
 //   f[6..11]  right child box
 //   u[12..13] child references (leaf k: kLeafBit|k; internal node: its index)
-//   u[14..15] unused
+//   u[14..15] smallest original id among each child's points (a child whose
+//             weight bound only ties the cutoff can win the tie only below it)
 struct __align__(16) NodeRec {
   float4 a, b, c;
   uint4 d;
@@ -180,6 +181,12 @@ struct Problem {
   bool want_learned = false;         // set before layout(): carve the learned-radius arrays
   bool want_logging = false;         // set before layout(): carve the logging counter
   bool want_mrd = false;             // set before layout(): carve the core distances
+  bool wide = false;                 // set before layout(): 128-bit Morton codes
+  bool auto_wide = false;            // set before layout(): 64-bit codes unless they leave more
+                                     // than n/64 distinct points sharing a code (then 128)
+  int64_t code_collisions = 0;       // that count, when measured
+  bool ties = true;                  // the search needs its tie rule (a run of > 32 equal
+                                     // codes exists; set after the build, true when unknown)
   const float *mlp = nullptr;
   float *pred_r = nullptr;
   float *r_used = nullptr;
@@ -198,6 +205,10 @@ struct Problem {
   uint64_t *keys[2] = {nullptr, nullptr};
   uint32_t *vals[2] = {nullptr, nullptr};
   uint32_t *perm = nullptr;       // curve index -> original index
+  uint64_t *wide_hi = nullptr;    // n: 128-bit codes, high / low words in input order
+  uint64_t *wide_lo = nullptr;
+  const uint64_t *code_hi = nullptr;  // sorted high words during the build (128-bit codes),
+                                      // else nullptr; the sorted low words are keys[0]
   NodeRec *nodes = nullptr;       // nc-1 internal nodes
   uint2 *nlabels = nullptr;       // nc-1: child labels of each internal node (A5)
   uint32_t *parent_leaf = nullptr;   // nc: (parent << 1) | slot of each leaf chunk
@@ -235,7 +246,7 @@ struct Problem {
   emst_edge *edges = nullptr;        // n: edges in emission order
   emst_edge *out_stage = nullptr;    // n-1: device staging of host outputs
   uint32_t *counters = nullptr;      // [0] edges emitted, [1] status bits, [2..3] node visits (u64),
-                                     // [4..9] scene box (ordered), [11] largest emitted
+                                     // [4..9] scene box (ordered), [10] long tie runs in the output, [28..29] identical curve neighbours (u64), [30..31] code collisions (u64), [32] a run of > 32 equal codes, [11] largest emitted
                                      // weight bits, [16..23] sort tile counters,
                                      // [12] next round's active components, [13] points
                                      // to rerun, [14..15] reruns / queries (learned radius),
@@ -252,6 +263,10 @@ struct Problem {
 // build.cu
 void launch_scene_box(Problem &P);
 void launch_morton(Problem &P);
+void launch_morton128(Problem &P);
+void launch_gather_u64(Problem &P, const uint64_t *src, const uint32_t *idx, uint64_t *out);
+// also counts identical points and code collisions into counters[28..31] and
+// flags long runs of equal codes in counters[32]
 void launch_gather(Problem &P, const uint32_t *perm);
 void launch_instance_ids(Problem &P);
 void launch_instance_roots(Problem &P);
@@ -299,6 +314,8 @@ void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
 void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i);
 void launch_edge_ties(Problem &P, int64_t m, int src);
 void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, emst_edge *out);
+void launch_edge_keys_j(Problem &P, int64_t m);
+void launch_edge_keys_wi_of(Problem &P, int64_t m, int src, int shift_i);
 void launch_edge_keys_inst(Problem &P, int64_t m, int src);
 // learned.cu
 void launch_comp_sizes(Problem &P);
@@ -321,7 +338,7 @@ void run_round(Problem &P, int round, bool carried, int block, bool count);
 // Leaf chunk size actually used for n points and a requested size (0 =
 // default): a power of two, at most the request, leaving at least 2 chunks.
 int effective_leaf(int64_t n, int requested);
-void run_output(Problem &P, emst_edge *out, uint32_t w_bits);
+int run_output(Problem &P, emst_edge *out, uint32_t w_bits);
 
 inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;

@@ -616,6 +616,8 @@ void launch_log_samples(Problem &P, int round, bool carried) {
   T.pts = P.pts;
   T.nodes = P.nodes;
   T.nlabels = P.nlabels;
+  T.core2 = nullptr;
+  T.ties = P.ties;
   T.labels = P.labels;
   T.bound = P.bound;
   T.radius_in = nullptr;

@@ -104,7 +104,8 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
       if ((int64_t)host_counters[0] >= n - 1) break;
     }
     if ((int64_t)host_counters[0] != n - 1) return EMST_ERR_INTERNAL;
-    run_output(P, out_dev ? out_edges : P.out_stage, host_counters[11]);
+    const int orc = run_output(P, out_dev ? out_edges : P.out_stage, host_counters[11]);
+    if (orc != EMST_OK) return orc;
     if (!out_dev && cudaMemcpyAsync(out_edges, P.out_stage, sizeof(emst_edge) * (size_t)(n - 1),
                                     cudaMemcpyDeviceToHost, stream) != cudaSuccess)
       return EMST_ERR_CUDA;

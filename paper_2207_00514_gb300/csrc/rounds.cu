@@ -246,16 +246,16 @@ void launch_upper_bounds(Problem &P) {
 // One thread per point, or (list != nullptr) a grid-stride pass over the
 // listed points (the certification reruns of the learned radius).
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
-          bool FIRST, bool MRD>
+          bool FIRST, bool MRD, bool TIES = true>
 __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (list) {
     const int64_t count = *list_count;
     for (int64_t t = gid; t < count; t += (int64_t)gridDim.x * blockDim.x)
-      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD>(A, __ldg(list + t));
+      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, __ldg(list + t));
   } else if (gid < A.n) {
-    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD>(A, gid);
+    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, gid);
   }
 }
 
@@ -267,6 +267,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   A.nodes = P.nodes;
   A.nlabels = P.nlabels;
   A.core2 = P.core2;
+  A.ties = P.ties;
   A.labels = P.labels;
   A.bound = P.bound;
   A.radius_in = radius_in;
@@ -290,12 +291,19 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
 #define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L, false, false><<<g, block, 0, s>>>(A, list, list_count)
 #define EMST_TRAV_FIRST(K, H) k_traverse<false, false, K, true, H, false, true, false><<<g, block, 0, s>>>(A, list, list_count)
 #define EMST_TRAV_MRD(C, K, H) k_traverse<C, false, K, true, H, false, false, true><<<g, block, 0, s>>>(A, list, list_count)
+#define EMST_TRAV_NOTIES(C, F, H) k_traverse<C, false, false, true, H, false, F, false, false><<<g, block, 0, s>>>(A, list, list_count)
 #define EMST_TRAV(C, R, K, S, L)                       \
   do {                                                 \
     if (P.leaf > 1) EMST_TRAV2(C, R, K, S, true, L);   \
     else EMST_TRAV2(C, R, K, S, false, L);             \
   } while (0)
-  if (radius_in) {
+  if (!P.ties && !count && seeded && !radius_in && learned_pass == 0 && !P.core2) {
+    // the plain form on input without large groups of identical points
+    const bool h = P.leaf > 1;
+    if (carried) { if (h) EMST_TRAV_NOTIES(true, false, true); else EMST_TRAV_NOTIES(true, false, false); }
+    else if (first) { if (h) EMST_TRAV_NOTIES(false, true, true); else EMST_TRAV_NOTIES(false, true, false); }
+    else { if (h) EMST_TRAV_NOTIES(false, false, true); else EMST_TRAV_NOTIES(false, false, false); }
+  } else if (radius_in) {
     EMST_TRAV(false, true, false, false, false);
   } else if (!seeded) {
     EMST_TRAV(false, false, false, false, false);
@@ -329,6 +337,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
 #undef EMST_TRAV2
 #undef EMST_TRAV_FIRST
 #undef EMST_TRAV_MRD
+#undef EMST_TRAV_NOTIES
   P.launches += 1;
 }
 
@@ -506,40 +515,46 @@ void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count) {
 }
 
 // ---------------------------------------------------------------------------
-// A12. Output order: (w, i, j) ascending.  One radix sort by (w bits << L) | i
-// (only as many digits as the largest weight needs), then the runs of equal
-// (w, i) -- edges of one point with equal weights, at most the kissing
-// number of them in a minimum spanning tree -- are put in j order.  With one
-// instance the sorted value is j itself and the edges are rebuilt from
-// (key, value); with several the value is the edge's index (a stable sort by
-// instance follows) and a gather builds them.
+// A12. Output order: (w, i, j) ascending.  Fast path (one instance): one
+// radix sort by (w bits << L) | i (only as many digits as the largest weight
+// needs) with j as the value, then the runs of equal (w, i) -- the edges of
+// one point with equal weights, a handful in general position -- are put in
+// j order in place and the edges are rebuilt from (key, value).  A run longer
+// than kTieRunMax (exact ties: many identical points make a star of
+// zero-weight edges) is only counted; the caller then redoes the output on
+// the full path: a stable sort by j, then a stable sort by (w, i) (and by
+// instance in the batched form, which always takes it), then a gather.
 // ---------------------------------------------------------------------------
+constexpr int kTieRunMax = 64;
+
 __global__ void k_edge_keys_wi(const emst_edge *__restrict__ edges, int64_t m,
                                uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                               int shift_i, int direct) {
+                               int shift_i) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   const emst_edge E = edges[e];
   keys[e] = ((uint64_t)__float_as_uint(E.w) << shift_i) | (uint64_t)E.i;
-  vals[e] = direct ? E.j : (uint32_t)e;
+  vals[e] = E.j;
 }
 
 // The first thread of each run of equal keys orders the run by j (insertion
-// sort: the runs are a handful of edges long).
+// sort), or counts it when it is longer than kTieRunMax.
 __global__ void k_edge_ties(const uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                            const emst_edge *__restrict__ edges, int64_t m, int direct) {
+                            int64_t m, uint32_t *long_runs) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e + 1 >= m) return;
   const uint64_t key = keys[e];
   if (keys[e + 1] != key || (e > 0 && keys[e - 1] == key)) return;
   int64_t end = e + 2;
-  while (end < m && keys[end] == key) ++end;
-  auto j_of = [&](uint32_t v) { return direct ? v : edges[v].j; };
+  while (end < m && end - e <= kTieRunMax && keys[end] == key) ++end;
+  if (end - e > kTieRunMax) {
+    atomicAdd(long_runs, 1u);
+    return;
+  }
   for (int64_t a = e + 1; a < end; ++a) {
     const uint32_t v = vals[a];
-    const uint32_t j = j_of(v);
     int64_t b = a;
-    while (b > e && j_of(vals[b - 1]) > j) {
+    while (b > e && vals[b - 1] > v) {
       vals[b] = vals[b - 1];
       --b;
     }
@@ -559,6 +574,25 @@ __global__ void k_edge_from_keys(const uint64_t *__restrict__ keys,
   E.j = vals[e];
   E.w = __uint_as_float((uint32_t)(k >> shift_i));
   out[e] = E;
+}
+
+// Full path: keys by j with the edge index as the value, then keys by
+// (w, i) of the edges in that order.
+__global__ void k_edge_keys_j(const emst_edge *__restrict__ edges, int64_t m,
+                              uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  keys[e] = edges[e].j;
+  vals[e] = (uint32_t)e;
+}
+
+__global__ void k_edge_keys_wi_of(const emst_edge *__restrict__ edges, int64_t m,
+                                  uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                                  int shift_i) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const emst_edge E = edges[vals[e]];
+  keys[e] = ((uint64_t)__float_as_uint(E.w) << shift_i) | (uint64_t)E.i;
 }
 
 __global__ void k_edge_keys_inst(const emst_edge *__restrict__ edges, int64_t m,
@@ -587,17 +621,26 @@ __global__ void k_edge_gather(const emst_edge *__restrict__ edges, int64_t m,
 
 void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i) {
   k_edge_keys_wi<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[0], P.vals[0],
-                                                               shift_i, P.num_inst == 1);
+                                                               shift_i);
   P.launches += 1;
 }
 void launch_edge_ties(Problem &P, int64_t m, int src) {
-  k_edge_ties<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], P.edges, m,
-                                                            P.num_inst == 1);
+  k_edge_ties<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], m,
+                                                            P.counters + 10);
   P.launches += 1;
 }
 void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, emst_edge *out) {
   k_edge_from_keys<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], m,
                                                                  shift_i, out);
+  P.launches += 1;
+}
+void launch_edge_keys_j(Problem &P, int64_t m) {
+  k_edge_keys_j<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[0], P.vals[0]);
+  P.launches += 1;
+}
+void launch_edge_keys_wi_of(Problem &P, int64_t m, int src, int shift_i) {
+  k_edge_keys_wi_of<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.edges, m, P.keys[src],
+                                                                  P.vals[src], shift_i);
   P.launches += 1;
 }
 void launch_edge_keys_inst(Problem &P, int64_t m, int src) {

@@ -7,7 +7,10 @@
 
 namespace emst {
 
-constexpr int kStackDepth = 100;  // > 96 = the deepest possible path (see traverse_one)
+#ifndef EMST_STACK_DEPTH
+#define EMST_STACK_DEPTH 164
+#endif
+constexpr int kStackDepth = EMST_STACK_DEPTH;  // > 160 = the deepest possible path (see traverse_one)
 
 // Per-query state of Algorithm 2.
 struct Query {
@@ -97,14 +100,17 @@ __device__ __forceinline__ void load_record(const NodeRec *rec, float4 &a, float
 // the plain weight: the caller only searches with a cutoff at or above the
 // query's core distance, and every weight from the query is at least that,
 // so max(core, box distance) <= cutoff  <=>  box distance <= cutoff.
-template <bool COUNT, bool CHUNKS, bool FIRST, bool MRD = false>
+// TIES = false: the input has no large group of identical points (see the
+// tie rule below), so that check is compiled out.
+template <bool COUNT, bool CHUNKS, bool FIRST, bool MRD = false, bool TIES = true>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
                                         const uint2 *__restrict__ nlabels,
                                         const float4 *__restrict__ pts,
                                         const uint32_t *__restrict__ labels, int leaf, int64_t n,
                                         uint32_t *st_node, float *st_dist,
                                         unsigned long long &nvis,
-                                        const float *__restrict__ core2 = nullptr) {
+                                        const float *__restrict__ core2 = nullptr,
+                                        bool ties = true) {
   int sp = 0;
   while (true) {
     if (COUNT) ++nvis;
@@ -132,6 +138,24 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
     }
     okL = okL && dL <= q.radius;
     okR = okR && dR <= q.radius;
+    // An internal child whose weight bound only ties the cutoff holds nothing
+    // better than the best so far unless it has a point with a smaller
+    // original id (dd.z / dd.w hold each child's smallest).  Without this a
+    // group of m identical points costs each of its queries a visit to all m,
+    // and so does a group at one equal distance from the query.  (Checked
+    // only when a tie occurs; a leaf resolves its own ties.)
+    // (the ids are read again in the rare tie case: kept live through the
+    // leaf scans above they cost the hot loop a register it does not have)
+    // Only when the input has a run of more than 32 equal codes (`ties`):
+    // otherwise no group of identical points is larger than that, a tie
+    // involves a few points at most and the check would only cost time.
+    const float lbL = MRD ? fmaxf(q.core, dL) : dL, lbR = MRD ? fmaxf(q.core, dR) : dR;
+    if (TIES && ties && q.bj != kInvalid && ((okL && lbL == q.radius) || (okR && lbR == q.radius))) {
+      if (q.bid == kInvalid) q.bid = __float_as_uint(pts[q.bj].w);  // loaded lazily
+      const uint2 mn = __ldg(reinterpret_cast<const uint2 *>(nodes + node) + 7);  // dd.z, dd.w
+      if (lbL == q.radius && mn.x >= q.bid) okL = false;
+      if (lbR == q.radius && mn.y >= q.bid) okR = false;
+    }
     if (okL && okR) {
       if (sp >= kStackDepth) return false;
       if (dL <= dR) { st_node[sp] = dd.y; st_dist[sp] = dR; node = dd.x; }
@@ -164,9 +188,9 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
 // The leaves of the hierarchy are chunks of `leaf` consecutive curve
 // positions; an accepted chunk is scanned point by point.
 // The stack never overflows: every split of the hierarchy uses a strictly
-// later bit of the 96-bit augmented key (64-bit code + 32-bit index), so a
-// root-to-leaf path has at most 96 internal nodes and at most one stacked
-// sibling per level.
+// later bit of the augmented key (code + 32-bit index: 96 bits with 64-bit
+// codes, 160 with 128-bit codes), so a root-to-leaf path has at most 160
+// internal nodes and at most one stacked sibling per level.
 // Ends with the first half of the per-component minimum (A8): an atomicMin of
 // (w bits << 32 | min original id) per component.
 // SEEDED (the emst_compute path) also tightens each cutoff with the
@@ -184,6 +208,7 @@ struct TravArgs {
   const NodeRec *nodes;
   const uint2 *nlabels;
   const float *core2;  // MRD: squared core distances in curve order
+  bool ties;           // identical points exist: prune children that can only tie
   const uint32_t *labels;
   const uint32_t *bound;
   const float *radius_in;
@@ -206,7 +231,7 @@ struct TravArgs {
 // MRD: the mutual reachability weights (§4.5); a query whose own core
 // distance lies above its cutoff finds nothing and is skipped.
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
-          bool FIRST = false, bool MRD = false>
+          bool FIRST = false, bool MRD = false, bool TIES = true>
 __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   const float kInf = __int_as_float(0x7f800000);
   const int64_t n = A.n;
@@ -265,8 +290,9 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   uint32_t st_node[kStackDepth];
   float st_dist[kStackDepth];
   unsigned long long nvis = 0;
-  const bool ok = explore<COUNT, CHUNKS, FIRST, MRD>(q, start, A.nodes, A.nlabels, A.pts, A.labels,
-                                                     A.leaf, n, st_node, st_dist, nvis, A.core2);
+  const bool ok = explore<COUNT, CHUNKS, FIRST, MRD, TIES>(q, start, A.nodes, A.nlabels, A.pts, A.labels,
+                                                     A.leaf, n, st_node, st_dist, nvis, A.core2,
+                                                     A.ties);
   if (!ok) atomicOr(A.status, kErrStack);
   if (COUNT) {
     // one atomic per warp: sum the active lanes' counts first

@@ -76,6 +76,30 @@ def blobs(n: int, dim: int, seed: int, n_blobs: int = 50, frac_background: float
     return _wrap_f32(allp)
 
 
+def dense(n: int, dim: int, seed: int, n_clusters: int = 20_000,
+          sigma_range=(1e-9, 1e-6), frac_background: float = 0.10) -> np.ndarray:
+    """Extremely dense clusters (the under-resolved regime §4.2 describes for
+    a GPS-trace dataset): (1 - frac_background)·n points in ``n_clusters``
+    isotropic Gaussians with centres uniform in the unit box, sigma
+    log-uniform in ``sigma_range`` (below the 2^-21 cells of 64-bit 3D codes)
+    and sizes from a power law p(m) ∝ m^-2 (Dirichlet-free: counts drawn by
+    multinomial on those weights); the rest uniform.  Rows are shuffled."""
+    g = _rng(seed)
+    n_bg = int(round(frac_background * n))
+    n_cl = n - n_bg
+    centres = g.random((n_clusters, dim))
+    lo, hi = np.log(sigma_range[0]), np.log(sigma_range[1])
+    sigmas = np.exp(g.uniform(lo, hi, n_clusters))
+    w = (1.0 - g.random(n_clusters)) ** (-1.0)  # Pareto, p(m) ∝ m^-2
+    counts = g.multinomial(n_cl, w / w.sum())
+    which = np.repeat(np.arange(n_clusters), counts)
+    pts = centres[which] + sigmas[which, None] * g.standard_normal((n_cl, dim))
+    bg = g.random((n_bg, dim))
+    allp = np.concatenate([pts, bg], axis=0)
+    allp = allp[g.permutation(n)]
+    return _wrap_f32(allp)
+
+
 def _nfw_mass(x):
     return np.log1p(x) - x / (1.0 + x)
 

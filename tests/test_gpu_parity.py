@@ -333,3 +333,17 @@ def test_full_size_halos_100M_invariants(pkg):
         a, b = min(int(v), j), max(int(v), j)
         hit = np.nonzero((e["i"] == a) & (e["j"] == b))[0]
         assert len(hit) == 1 and e["w"][hit[0]] == m, (v, j)
+
+
+def test_massive_duplicate_group(pkg):
+    """20,000 copies of one point among 30,000 others: the zero-weight ties
+    resolve by id without every copy visiting every other (the traversal's
+    tie pruning), and the tree is the oracle's."""
+    g = np.random.default_rng(21)
+    pts = np.concatenate([np.full((20_000, 3), 0.25, np.float32),
+                          g.random((30_000, 3)).astype(np.float32)])
+    pts = pts[g.permutation(len(pts))]
+    got = gpu_emst(pkg, pts)
+    want = oracle.kd_boruvka(pts, threads=os.cpu_count() or 4)
+    assert_same_edges(got, want, "duplicates")
+    assert np.count_nonzero(got["w"] == 0) == 19_999
