@@ -36,7 +36,7 @@ WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member count
 # over one call's 11 launches of an ncu capture of this command
 # (--metrics dram__bytes_read.sum,dram__bytes_write.sum; profiles/k_traverse_dram_halos_37M.md).
 # Set back to None whenever the traversal kernel changes.
-TRAVERSE_DRAM_BYTES_PER_LAUNCH = None
+TRAVERSE_DRAM_BYTES_PER_LAUNCH = 2585.68e6
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")
 
