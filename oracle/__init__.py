@@ -74,6 +74,7 @@ def _load():
                 "oracle_sort_perm128": (None, [P, P, I64, P]),
                 "oracle_radix_tree128": (None, [P, P, I64, P, P, P, P]),
                 "oracle_count_components": (I64, [P, I64, I64, P]),
+                "oracle_dendrogram": (I, [P, I64, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -353,6 +354,24 @@ def count_components(edges, n):
     cyc = ctypes.c_int(0)
     comps = _load().oracle_count_components(_p(e), len(e), int(n), ctypes.byref(cyc))
     return int(comps), bool(cyc.value)
+
+
+LINKAGE_DTYPE = np.dtype([("a", np.uint32), ("b", np.uint32), ("w", np.float32), ("size", np.uint32)])
+
+
+def dendrogram(edges, n):
+    """Single-linkage hierarchy of a spanning tree given in merge order:
+    (linkage rows {a, b, w, size}, parent of each of the 2n - 1 clusters).
+    Raises ValueError on an invalid tree or a decreasing weight."""
+    e = np.ascontiguousarray(edges, dtype=EDGE_DTYPE)
+    n = int(n)
+    assert len(e) == max(n - 1, 0)
+    link = np.zeros(max(n - 1, 0), dtype=LINKAGE_DTYPE)
+    parent = np.zeros(max(2 * n - 1, 0), dtype=np.uint32)
+    rc = _load().oracle_dendrogram(_p(e), n, _p(link), _p(parent))
+    if rc != 0:
+        raise ValueError(f"not a spanning tree in weight order (rc {rc})")
+    return link, parent
 
 
 def bvh_reference(points, morton_bits: int = 64):

@@ -979,3 +979,62 @@ int64_t oracle_count_components(const oracle_edge *e, int64_t m, int64_t n, int 
   free(par);
   return comps;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Single-linkage dendrogram of a spanning tree.  The introduction names     */
+/* clustering (HDBSCAN*) as a consumer of the EMST, and §4.5 computes the    */
+/* mutual-reachability tree for it; the hierarchy those methods read off the */
+/* tree is defined here.                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* The single-linkage hierarchy of a tree is the sequence of merges that
+ * Kruskal's algorithm (§2, "MST computation") makes on the tree's own edges:
+ * take them in order of weight and join the two clusters each one connects.
+ * The given edge order is the merge order (weights must not decrease; among
+ * equal weights the order decides).  Cluster ids: point v is cluster v, the
+ * cluster made by the k-th edge is n + k.
+ *   e        m = n - 1 edges.
+ *   linkage  m rows of 4 words {a, b, w bits, size}: the two clusters merged
+ *            (a < b), the weight, the number of points in the new cluster.
+ *   parent   2n - 1 words: the cluster each cluster is merged into,
+ *            ORACLE_INVALID for the last one.
+ * Returns 0, or -1 when an id is >= n, an edge closes a cycle, a weight is
+ * NaN, or a weight is below the one before it. */
+int oracle_dendrogram(const oracle_edge *e, int64_t n, uint32_t *linkage, uint32_t *parent) {
+  if (n <= 0) return 0;
+  const int64_t m = n - 1;
+  uint32_t *par = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+  uint32_t *cluster = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+  uint32_t *size = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+  if (!par || !cluster || !size) { free(par); free(cluster); free(size); return -2; }
+  for (int64_t v = 0; v < n; ++v) {
+    par[v] = (uint32_t)v;
+    cluster[v] = (uint32_t)v;
+    size[v] = 1;
+  }
+  int rc = 0;
+  for (int64_t k = 0; k < m; ++k) {
+    if (e[k].i >= n || e[k].j >= n || e[k].w != e[k].w || (k > 0 && e[k].w < e[k - 1].w)) {
+      rc = -1;
+      break;
+    }
+    uint32_t ra = uf_find(par, e[k].i), rb = uf_find(par, e[k].j);
+    if (ra == rb) { rc = -1; break; }
+    uint32_t ca = cluster[ra], cb = cluster[rb];
+    uint32_t *row = linkage + 4 * k;
+    row[0] = ca < cb ? ca : cb;
+    row[1] = ca < cb ? cb : ca;
+    memcpy(&row[2], &e[k].w, 4);
+    row[3] = size[ra] + size[rb];
+    parent[ca] = parent[cb] = (uint32_t)(n + k);
+    uint32_t r = ra < rb ? ra : rb;
+    par[ra] = par[rb] = r;
+    cluster[r] = (uint32_t)(n + k);
+    size[r] = row[3];
+  }
+  parent[2 * n - 2] = ORACLE_INVALID;
+  free(par);
+  free(cluster);
+  free(size);
+  return rc;
+}

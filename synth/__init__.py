@@ -13,6 +13,9 @@ stand in for them with the same dimension, size and kind of structure:
                       duplicates: a tie-stress set (massive equal weights).
 * ``batched_sizes`` / ``batched_instances`` -- many independent instances of
                       uneven size.
+* ``tree_edges``   -- a random spanning tree of a given shape with weights,
+                      listed by non-decreasing weight (input for the
+                      single-linkage dendrogram; not point data).
 
 This module holds no arithmetic of the EMST method: it only draws numbers.
 Everything is generated in FP64 from ``numpy.random.Generator(PCG64(seed))``
@@ -24,6 +27,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
+    "tree_edges",
     "uniform",
     "blobs",
     "halos",
@@ -210,3 +214,51 @@ def config_points(config: int, n: int | None = None, seed: int | None = None) ->
     if config == 5:
         return halos(100_000_000 if n is None else n, 3 if seed is None else seed)
     raise ValueError(f"no single point set for config {config}")
+
+
+TREE_SHAPES = ("random", "path", "path_sorted", "star", "caterpillar", "binary")
+
+
+def tree_edges(n: int, seed: int, shape: str = "random", ties: int = 0) -> np.ndarray:
+    """A spanning tree on n vertices as an (n-1)-row structured array
+    (i, j: uint32 vertex ids, w: float32), listed by non-decreasing w with
+    equal weights in random order.
+
+    shape: "random" (each vertex k > 0 attaches to a uniform earlier vertex),
+    "path" (a random vertex order, random weights), "path_sorted" (a path whose
+    weights increase along it: the deepest possible hierarchy), "star" (one
+    centre), "caterpillar" (a path with a leaf on every vertex), "binary"
+    (vertex k attaches to (k-1)//2).  Vertex ids are shuffled.
+    ties: 0 for distinct weights (FP32 of uniform draws), else the weights are
+    drawn from that many distinct values."""
+    g = _rng(seed)
+    n = int(n)
+    m = max(n - 1, 0)
+    k = np.arange(1, n, dtype=np.int64)
+    if shape == "random":
+        parent = np.floor(g.random(m) * k).astype(np.int64)
+    elif shape in ("path", "path_sorted"):
+        parent = k - 1
+    elif shape == "star":
+        parent = np.zeros(m, dtype=np.int64)
+    elif shape == "caterpillar":
+        spine = (n + 1) // 2
+        parent = np.where(k < spine, k - 1, k - spine)
+    elif shape == "binary":
+        parent = (k - 1) // 2
+    else:
+        raise ValueError(shape)
+    if ties:
+        w = (g.integers(0, int(ties), size=m) + 1).astype(np.float64) / float(ties)
+    else:
+        w = g.random(m) + 1e-3
+    if shape == "path_sorted":
+        w = np.sort(w)
+    ids = g.permutation(n).astype(np.uint32)
+    e = np.zeros(m, dtype=[("i", np.uint32), ("j", np.uint32), ("w", np.float32)])
+    a, b = ids[parent], ids[k]
+    e["i"] = np.minimum(a, b)
+    e["j"] = np.maximum(a, b)
+    e["w"] = w.astype(np.float32)
+    order = np.lexsort((g.random(m), e["w"]))
+    return e[order]
