@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="halos37M",
-                    choices=["halos37M", "batched", "sweep", "mrd", "dense"],
+                    choices=["halos37M", "batched", "sweep", "mrd", "dense", "dendrogram"],
                     help="batched: 4,096 independent 3D instances (sizes log-uniform in [100, 1e6]) "
                          "in one emst_compute_batched call, against one emst_compute per instance")
     ap.add_argument("--instances", type=int, default=4096)
@@ -361,6 +361,68 @@ def run_dense(args, rank, world, local):
                           "mpoints_per_s": round(n / ms / 1e3, 2)}), flush=True)
 
 
+def run_dendrogram(args, rank, world, local):
+    """The single-linkage dendrogram (emst_dendrogram) of the trees the
+    library computes on the 37M halo workload -- the EMST and the
+    mutual-reachability tree for k_pts = 8 (HDBSCAN*'s hierarchy) -- and of a
+    seeded random tree of the same size: best and median device time of the
+    timed calls (edges and outputs resident on the device), against the
+    oracle's serial merge sequence on the same edges (one host core)."""
+    if rank != 0:
+        return
+    import torch
+    import synth
+    import oracle
+    import paper_2207_00514_gb300 as pkg
+
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    pts = torch.from_numpy(make_points(args.n, args.seed)).to(dev)
+    n = pts.shape[0]
+    trees = [("EMST of " + WORKLOAD, lambda: pkg.emst_compute(pts)),
+             ("mutual-reachability tree (k_pts = 8) of " + WORKLOAD,
+              lambda: pkg.emst_compute_ex(pts, mrd_k=8)[0]),
+             (f"random tree on {n:,} points (synth.tree_edges, seed 4)",
+              lambda: torch.from_numpy(np.ascontiguousarray(synth.tree_edges(n, 4, "random"))
+                                       .view(np.int32).reshape(-1, 3).copy()).to(dev))]
+    link = torch.empty((n - 1, 4), dtype=torch.int32, device=dev)
+    parent = torch.empty(2 * n - 1, dtype=torch.int32, device=dev)
+    peak, peak_kind = measured_peaks()
+    for name, make in trees:
+        edges = make()
+        torch.cuda.synchronize(dev)
+        for _ in range(max(args.warmup, 1)):
+            pkg.emst_dendrogram(edges, n, out_linkage=link, out_parent=parent, stream=stream)
+        torch.cuda.synchronize(dev)
+        times = []
+        for _ in range(max(args.steps, 3)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pkg.emst_dendrogram(edges, n, out_linkage=link, out_parent=parent, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+        e_np = pkg.edges_numpy(edges)
+        t0 = time.perf_counter()
+        oracle.dendrogram(e_np, n)
+        cpu_s = time.perf_counter() - t0
+        ms = min(times)
+        # compulsory traffic: read the edges (12 B), write the rows (16 B) and
+        # the parents (2 x 4 B) once per edge
+        alg = (n - 1) * 36.0
+        print(json.dumps({"workload": name, "n": n, "ms": round(ms, 3),
+                          "median_ms": round(float(np.median(times)), 3),
+                          "mpoints_per_s": round(n / ms / 1e3, 2),
+                          "roofline": {"bound": "hbm", "algorithmic_bytes": alg,
+                                       "achieved_gbs": round(alg / ms / 1e6, 1), "peak_gbs": peak,
+                                       "peak_kind": peak_kind, "frac": round(alg / ms / 1e6 / peak, 4)},
+                          "cpu_oracle_s": round(cpu_s, 3), "cpu_cores": 1}), flush=True)
+        del edges
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -378,6 +440,9 @@ def main():
         return
     if args.workload == "dense":
         run_dense(args, rank, world, local)
+        return
+    if args.workload == "dendrogram":
+        run_dendrogram(args, rank, world, local)
         return
 
     import torch

@@ -230,6 +230,40 @@ int emst_mlp_adam(float *params, float *grad, float *m1, float *m2, int step, fl
 int emst_learned_samples(const float *points, int64_t n, int dim, int every, float *out_features,
                          float *out_targets, int64_t capacity, int64_t *out_count, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Single-linkage dendrogram (the paper has no counterpart: the hierarchy   */
+/* that single-linkage clustering and HDBSCAN* read off the EMST, or off    */
+/* the mutual-reachability tree of §4.5 -- clustering is the first use of   */
+/* the EMST the introduction names).                                        */
+/* ---------------------------------------------------------------------- */
+/* One merge of the hierarchy: clusters a < b joined at weight w into a
+ * cluster of `size` points (16 bytes; the row layout of a linkage matrix). */
+typedef struct emst_linkage {
+  uint32_t a;
+  uint32_t b;
+  float w;
+  uint32_t size;
+} emst_linkage;
+
+/* The hierarchy is Kruskal's merge sequence over the tree's own edges (§2,
+ * "MST computation"), taken in the given order.  Cluster ids: point v is
+ * cluster v; the cluster made by edges[k] is n + k.
+ *   edges        n-1 edges of a spanning tree of points 0..n-1 in merge
+ *                order: weights not decreasing (emst_compute's output order
+ *                qualifies); equal weights merge in the given order.  Device
+ *                or host memory, read only.
+ *   n            0 <= n <= EMST_MAX_POINTS.
+ *   out_linkage  n-1 rows (device or host), or NULL: row k = the merge made
+ *                by edges[k] (a < b, w = edges[k].w).
+ *   out_parent   2n-1 uint32 (device or host), or NULL: the cluster each
+ *                cluster merges into; 0xFFFFFFFF for the last one (n + n-2,
+ *                or point 0 when n = 1).
+ * Returns EMST_OK, or EMST_ERR_INVALID_ARG when an id is >= n, an edge joins
+ * a point to itself or closes a cycle, a weight is NaN, or a weight is below
+ * the one before it (outputs then unspecified). */
+int emst_dendrogram(const emst_edge *edges, int64_t n, emst_linkage *out_linkage,
+                    uint32_t *out_parent, void *stream);
+
 /* Static string for a status code (never NULL). */
 const char *emst_status_string(int status);
 

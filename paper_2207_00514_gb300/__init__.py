@@ -45,6 +45,9 @@ __all__ = [
     "emst_learned_samples",
     "edges_numpy",
     "EDGE_DTYPE",
+    "emst_dendrogram",
+    "linkage_numpy",
+    "LINKAGE_DTYPE",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -55,6 +58,7 @@ EMST_MLP_PARAMS = 8981
 EMST_MLP_FEATURES = 8
 EMST_MRD_MAX_K = 32
 EDGE_DTYPE = np.dtype([("i", np.uint32), ("j", np.uint32), ("w", np.float32)])
+LINKAGE_DTYPE = np.dtype([("a", np.uint32), ("b", np.uint32), ("w", np.float32), ("size", np.uint32)])
 INVALID = 0xFFFFFFFF
 
 
@@ -120,6 +124,8 @@ def load_library(path: str | None = None):
         lib.emst_build_bvh_ex.argtypes = [V, I64, I, I, I, V, V, V, V, V]
         lib.emst_build_bvh_ex.restype = I
         lib.emst_core_distances.argtypes = [V, I64, I, I, V, V]
+        lib.emst_dendrogram.restype = I
+        lib.emst_dendrogram.argtypes = [V, I64, V, V, V]
         lib.emst_core_distances.restype = I
         lib.emst_status_string.argtypes = [I]
         lib.emst_status_string.restype = ctypes.c_char_p
@@ -354,6 +360,43 @@ def emst_round_step(points, labels, radius=None, leaf_size=1, stream=None):
 
 def edges_w(edges):
     return edges[:, 2].view(_torch().float32)
+
+
+def emst_dendrogram(edges, n=None, out_linkage=None, out_parent=None, stream=None,
+                    linkage=True, parent=True):
+    """Single-linkage dendrogram of a spanning tree given as (n-1, 3) int32
+    edges in merge order (weights not decreasing; emst_compute's output
+    qualifies), device or host.  Returns (linkage, parent): linkage is an
+    (n-1, 4) int32 tensor of rows {a, b, w bits, size} (linkage_numpy views
+    it), parent a (2n-1,) int32 tensor (-1 for the root); either is None when
+    not requested."""
+    torch = _torch()
+    if not isinstance(edges, torch.Tensor) or edges.dtype != torch.int32 or edges.dim() != 2 \
+            or edges.shape[1] != 3 or not edges.is_contiguous():
+        raise ValueError("edges must be a contiguous (m, 3) int32 tensor")
+    m = edges.shape[0]
+    n = m + 1 if n is None else int(n)
+    if m != max(n - 1, 0):
+        raise ValueError(f"a spanning tree of {n} points has {max(n - 1, 0)} edges, got {m}")
+    pin = edges.device.type == "cpu" and torch.cuda.is_available()
+    if linkage and out_linkage is None:
+        out_linkage = torch.empty((m, 4), dtype=torch.int32, device=edges.device, pin_memory=pin)
+    if parent and out_parent is None:
+        out_parent = torch.empty(max(2 * n - 1, 0), dtype=torch.int32, device=edges.device,
+                                 pin_memory=pin)
+    for t, shape in ((out_linkage, (m, 4)), (out_parent, (max(2 * n - 1, 0),))):
+        if t is not None and (t.dtype != torch.int32 or tuple(t.shape) != shape or not t.is_contiguous()):
+            raise ValueError(f"output must be a contiguous {shape} int32 tensor")
+    rc = load_library().emst_dendrogram(_ptr(edges), n, _ptr(out_linkage), _ptr(out_parent),
+                                        _stream_ptr(stream, edges.device))
+    if rc != 0:
+        raise EmstError(rc, "emst_dendrogram")
+    return out_linkage, out_parent
+
+
+def linkage_numpy(linkage) -> np.ndarray:
+    a = linkage.detach().cpu().contiguous().numpy()
+    return np.ascontiguousarray(a).view(LINKAGE_DTYPE).reshape(-1)
 
 
 def edges_numpy(edges) -> np.ndarray:

@@ -54,6 +54,21 @@ bool device_accessible(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool;
+  e = get_pool(dev, &pool);
+  if (e != cudaSuccess) return e;
+  e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+  }
+  return e;
+}
+
 struct Carver {
   char *base;
   size_t off = 0;
@@ -149,6 +164,7 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
 }
 
 int status_from_bits(uint32_t bits) {
+  if (bits & kErrBadInput) return EMST_ERR_INVALID_ARG;
   if (bits & kErrNonFinite) return EMST_ERR_NONFINITE;
   if (bits & (kErrStack | kErrSpin | kErrChain)) return EMST_ERR_INTERNAL;
   return EMST_OK;

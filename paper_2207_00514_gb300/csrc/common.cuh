@@ -20,6 +20,7 @@ enum : uint32_t {
   kErrStack = 1u << 1,
   kErrSpin = 1u << 2,
   kErrChain = 1u << 3,
+  kErrBadInput = 1u << 4,  // an input found invalid on the device (dendrogram)
 };
 
 // One internal node of the hierarchy, 64 bytes.  The boxes of both children
@@ -326,6 +327,9 @@ void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge 
 
 // api.cu: helpers of the orchestration
 bool device_accessible(const void *p);
+// Stream-ordered scratch from the library's pool on the current device
+// (release with cudaFreeAsync on the same stream).
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
 // Lays the scratch of one problem out from `base` (nullptr: only measures);
 // returns the bytes needed.
 size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges);

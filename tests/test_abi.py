@@ -17,7 +17,7 @@ def lib():
 def test_exports_every_declared_function(lib):
     names = pkg.declared_functions()
     assert {"emst_compute", "emst_compute_ex", "emst_compute_batched", "emst_status_string",
-            "emst_build_bvh", "emst_round_step"} <= set(names)
+            "emst_build_bvh", "emst_round_step", "emst_dendrogram"} <= set(names)
     for name in names:
         assert hasattr(lib, name), name
         assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
@@ -40,6 +40,11 @@ def test_argument_checks_without_gpu(lib):
     assert lib.emst_compute(V(0), 10, 3, dummy, V(0)) == -1
     assert lib.emst_compute(dummy, pkg.EMST_MAX_POINTS + 1, 3, dummy, V(0)) == -1
     assert lib.emst_compute(V(0), 0, 3, V(0), V(0)) == 0  # empty input: no work, no device
+    I64 = ctypes.c_int64
+    assert lib.emst_dendrogram(V(0), I64(-1), V(0), V(0), V(0)) == -1
+    assert lib.emst_dendrogram(V(0), I64(pkg.EMST_MAX_POINTS + 1), V(0), V(0), V(0)) == -1
+    assert lib.emst_dendrogram(V(0), I64(5), V(0), V(0), V(0)) == -1  # edges missing
+    assert lib.emst_dendrogram(V(0), I64(0), V(0), V(0), V(0)) == 0  # nothing to merge
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
