@@ -58,6 +58,8 @@ def parse():
                          "in one emst_compute_batched call, against one emst_compute per instance")
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--dense-n", type=int, default=24_000_000)
+    ap.add_argument("--dg-tree", default="all", choices=["all", "emst", "mrd", "random"],
+                    help="dendrogram workload: which tree(s) to time")
     return ap.parse_args()
 
 
@@ -381,12 +383,15 @@ def run_dendrogram(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     pts = torch.from_numpy(make_points(args.n, args.seed)).to(dev)
     n = pts.shape[0]
-    trees = [("EMST of " + WORKLOAD, lambda: pkg.emst_compute(pts)),
-             ("mutual-reachability tree (k_pts = 8) of " + WORKLOAD,
+    what = WORKLOAD if n == 37_000_000 else f"{n:,} points of the same halo generator (seed {args.seed})"
+    trees = [("EMST of " + what, lambda: pkg.emst_compute(pts)),
+             ("mutual-reachability tree (k_pts = 8) of " + what,
               lambda: pkg.emst_compute_ex(pts, mrd_k=8)[0]),
              (f"random tree on {n:,} points (synth.tree_edges, seed 4)",
               lambda: torch.from_numpy(np.ascontiguousarray(synth.tree_edges(n, 4, "random"))
                                        .view(np.int32).reshape(-1, 3).copy()).to(dev))]
+    if args.dg_tree != "all":
+        trees = [trees[["emst", "mrd", "random"].index(args.dg_tree)]]
     link = torch.empty((n - 1, 4), dtype=torch.int32, device=dev)
     parent = torch.empty(2 * n - 1, dtype=torch.int32, device=dev)
     peak, peak_kind = measured_peaks()

@@ -20,20 +20,25 @@
 //    in B's light half, p in its heavy half, C(k) is k's light component K,
 //    k is K's top (largest rank) edge and p is the lowest-ranked heavy edge
 //    touching K.  One level finds those (k, p) for every block at once.
-//  - Blocks of kBaseEdges edges finish with the serial merge sequence in
-//    shared memory, one warp each, which also gives every cluster's size.
+//  - Blocks of kLocalEdges edges and less run their levels in shared
+//    memory, one CTA each, and finish with the serial merge sequence over
+//    blocks of kSerialEdges edges, which also gives every cluster's size.
 // A contracted vertex is named by an endpoint slot 2k + side of the
 // lowest-ranked edge of its block that touches it.  The blocks of one level
 // own disjoint slot ranges, so one union-find over all 2m slots serves every
 // block of a level at once.
+#include <utility>
+
 #include "common.cuh"
 
 namespace emst {
 namespace {
 
-constexpr int kBaseEdges = 256;  // edges per block of the serial finish
-constexpr int kBaseWarps = 4;    // serial blocks per CTA (one warp each)
+constexpr int kLocalEdges = 2048;   // edges per block of the shared-memory levels
+constexpr int kLocalThreads = 512;
+constexpr int kSerialEdges = 32;    // edges per serial finish (one thread each)
 constexpr int kDgBlock = 256;
+constexpr size_t kLocalSmem = (size_t)2 * kLocalEdges * (5 * 4 + 2);
 
 // A bijective mix of a slot name (the MurmurHash3 32-bit finaliser): the
 // union-find hooks the root of higher priority under the other, so trees
@@ -48,34 +53,75 @@ __device__ __forceinline__ uint32_t prio(uint32_t x) {
   return x;
 }
 
-// Root of x with path halving.  Every parent has a lower priority than its
-// child and a parent is only ever replaced by an ancestor, so concurrent
-// walks and hooks keep each walk strictly descending: it ends.
-__device__ __forceinline__ uint32_t uf_find(uint32_t *uf, uint32_t x) {
-  volatile uint32_t *u = uf;
+// Root of x, optionally halving the path.  Every parent has a lower
+// priority than its child and a parent is only ever replaced by an
+// ancestor, so a walk is strictly descending and ends even when it reads
+// stale (cached) entries: a stale entry is still an ancestor.  A stale root
+// is caught by the hook's compare-and-swap in uf_unite.
+template <bool HALVE, class T>
+__device__ __forceinline__ uint32_t uf_find(T *uf, uint32_t x) {
   for (;;) {
-    const uint32_t p = u[x];
+    const uint32_t p = uf[x];
     if (p == x) return x;
-    const uint32_t g = u[p];
+    const uint32_t g = uf[p];
     if (g == p) return p;
-    u[x] = g;
+    if (HALVE) uf[x] = g;
     x = g;
   }
 }
 
-// Joins the sets of a and b (lock-free: a failed hook means another thread
-// hooked that root first; retry from the new roots).  False only if the
-// retry bound runs out.
-__device__ __forceinline__ bool uf_unite(uint32_t *uf, uint32_t a, uint32_t b) {
+// Joins the sets of a and b, lock-free.  A failed hook returns the hooked
+// root's actual parent, and the walk resumes there, so each retry climbs the
+// real chain.  Hooking the higher-priority root under the other cannot close
+// a cycle even when the other is stale: its actual root has a still lower
+// priority.  False only if the retry bound runs out.
+template <class T>
+__device__ __forceinline__ bool uf_unite(T *uf, uint32_t a, uint32_t b) {
+  a = uf_find<true>(uf, a);
+  b = uf_find<true>(uf, b);
   for (int it = 0; it < (1 << 22); ++it) {
-    a = uf_find(uf, a);
-    b = uf_find(uf, b);
     if (a == b) return true;
-    uint32_t hi = a, lo = b;
-    if (prio(a) < prio(b)) { hi = b; lo = a; }
-    if (atomicCAS(uf + hi, hi, lo) == hi) return true;
+    const bool ah = prio(a) > prio(b);
+    const uint32_t hi = ah ? a : b, lo = ah ? b : a;
+    const uint32_t old = atomicCAS((uint32_t *)uf + hi, hi, lo);
+    if (old == hi) return true;
+    if (ah) a = uf_find<true>(uf, old);
+    else b = uf_find<true>(uf, old);
   }
   return false;
+}
+
+// Atomics on a[idx] from a warp.  In up to two rounds, the lanes that share
+// the target of the lowest remaining lane (the lanes of one large
+// component) combine their values and one of them updates, after a cached
+// look at the entry (max and min only; values only move one way, so a stale
+// look can only cause an unneeded update).  Lanes left after two rounds
+// update on their own.  Every lane of the warp calls; `want` selects the
+// participants.
+template <int OP>  // 0 max, 1 min, 2 add
+__device__ __forceinline__ void warp_update(uint32_t *a, uint32_t idx, uint32_t v, bool want) {
+  unsigned act = __ballot_sync(0xffffffffu, want);
+  if (!want) return;
+  const int lane = (int)(threadIdx.x & 31);
+#pragma unroll
+  for (int round = 0; round < 2; ++round) {
+    const int leader = __ffs(act) - 1;
+    const uint32_t lead_idx = __shfl_sync(act, idx, leader);
+    const unsigned same = __ballot_sync(act, idx == lead_idx);
+    if (idx == lead_idx) {
+      const uint32_t r = OP == 0 ? __reduce_max_sync(same, v)
+                       : OP == 1 ? __reduce_min_sync(same, v) : __reduce_add_sync(same, v);
+      if (lane != leader) return;
+      if (OP == 0 && a[idx] < r) atomicMax(a + idx, r);
+      if (OP == 1 && a[idx] > r) atomicMin(a + idx, r);
+      if (OP == 2) atomicAdd(a + idx, r);
+      return;
+    }
+    act &= ~same;
+  }
+  if (OP == 0) atomicMax(a + idx, v);
+  if (OP == 1) atomicMin(a + idx, v);
+  if (OP == 2) atomicAdd(a + idx, v);
 }
 
 __device__ __forceinline__ uint32_t slot_vertex(const emst_edge *e, uint32_t s) {
@@ -95,30 +141,34 @@ __global__ void k_dg_check(const emst_edge *__restrict__ e, int64_t m, int64_t n
   if (bad) atomicOr(status, kErrBadInput);
 }
 
-// vslot[v] = the lowest slot touching point v (its parent edge is vslot>>1).
+// vslot[v] = the lowest slot touching point v: slot 2p + side says that v
+// hangs under edge p, on that side.
 __global__ void k_dg_first_slot(const emst_edge *__restrict__ e, int64_t m2,
                                 uint32_t *__restrict__ vslot) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= m2) return;
-  atomicMin(vslot + slot_vertex(e, (uint32_t)s), (uint32_t)s);
+  const uint32_t v = slot_vertex(e, (uint32_t)s);
+  if (vslot[v] > (uint32_t)s) atomicMin(vslot + v, (uint32_t)s);
 }
 
-// Top level: every vertex is a point, named by its lowest slot, size 1.
-__global__ void k_dg_init(const emst_edge *__restrict__ e, int64_t m2,
-                          const uint32_t *__restrict__ vslot, uint32_t *__restrict__ rep,
-                          uint32_t *__restrict__ sz) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= m2) return;
-  rep[s] = vslot[slot_vertex(e, (uint32_t)s)];
-  sz[s] = 1;
-}
-
+// The per-level union-find and per-component values come in two sets: a
+// level reads one and, in its last kernel, clears the other for the next
+// level.  Only slots that name a vertex are ever read there (every walk
+// starts at a name and hooks join names), so only those are cleared.
 struct Level {
   uint32_t *rep, *sz, *uf, *top, *minh, *csz, *parent;
+  uint32_t *nuf, *ntop, *nminh, *ncsz;  // the next level's set
   int64_t m;
   uint32_t mask, half;  // block size - 1, half the block size
   uint32_t *status;
 };
+
+__device__ __forceinline__ void clear_name(const Level &L, uint32_t s) {
+  L.nuf[s] = s;
+  L.ntop[s] = 0;
+  L.nminh[s] = kInvalid;
+  L.ncsz[s] = 0;
+}
 
 __device__ __forceinline__ bool block_split(const Level &L, uint32_t k, bool &light) {
   const uint32_t start = k & ~L.mask;
@@ -126,13 +176,21 @@ __device__ __forceinline__ bool block_split(const Level &L, uint32_t k, bool &li
   return (int64_t)start + L.half < L.m;  // the block has a heavy half
 }
 
-__global__ void k_dg_reset(Level L) {
+// Top level: every vertex is a point, named by its lowest slot, size 1.
+// The slot that names point v also records v as the child on that side of
+// its edge (the cluster a point starts in) and clears the first level's set
+// there.
+__global__ void k_dg_init(Level L, const emst_edge *__restrict__ e,
+                          const uint32_t *__restrict__ vslot, uint32_t *__restrict__ child) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= 2 * L.m) return;
-  L.uf[s] = (uint32_t)s;
-  L.top[s] = 0;
-  L.minh[s] = kInvalid;
-  L.csz[s] = 0;
+  const uint32_t v = slot_vertex(e, (uint32_t)s);
+  const uint32_t r = vslot[v];
+  L.rep[s] = r;
+  L.sz[s] = 1;
+  if (r != (uint32_t)s) return;
+  if (child) child[s] = v;
+  clear_name(L, (uint32_t)s);
 }
 
 // Light components: unite the two vertices of every light edge.
@@ -146,126 +204,234 @@ __global__ void k_dg_unite(Level L) {
 
 // Per light component (by root): its top edge (rank + 1), its size (the sum
 // over its vertices, each counted at the slot that names it) and the lowest
-// heavy slot touching it.
+// heavy slot touching it.  A warp covers 32 edges of one half.  Light halves
+// are visited from the top rank down, so the first value to reach a
+// component's top is usually its maximum and later lanes skip the atomic.
 __global__ void k_dg_classify(Level L) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= L.m) return;
-  bool light;
-  if (!block_split(L, (uint32_t)k, light)) return;
-  const uint32_t s0 = 2 * (uint32_t)k;
-  const uint32_t r0 = L.rep[s0], r1 = L.rep[s0 + 1];
-  if (light) {
-    atomicMax(L.top + uf_find(L.uf, r0), (uint32_t)k + 1);
-  } else {
-    atomicMin(L.minh + uf_find(L.uf, r0), s0);
-    atomicMin(L.minh + uf_find(L.uf, r1), s0 + 1);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool light = false;
+  const bool act = t < L.m && block_split(L, (uint32_t)t, light);
+  uint32_t k = (uint32_t)t;
+  if (act && light) {
+    const uint32_t start = k & ~L.mask;
+    k = start + L.half - 1 - (k - start);
   }
-  if (r0 == s0) atomicAdd(L.csz + uf_find(L.uf, s0), L.sz[s0]);
-  if (r1 == s0 + 1) atomicAdd(L.csz + uf_find(L.uf, s0 + 1), L.sz[s0 + 1]);
+  const uint32_t s0 = 2 * k;
+  uint32_t r0 = 0, r1 = 0, x0 = 0, x1 = 0;
+  if (act) {
+    r0 = L.rep[s0];
+    r1 = L.rep[s0 + 1];
+    x0 = uf_find<true>(L.uf, r0);
+    x1 = light ? x0 : uf_find<true>(L.uf, r1);  // a light edge's ends share a root
+  }
+  warp_update<0>(L.top, x0, k + 1, act && light);
+  warp_update<1>(L.minh, x0, s0, act && !light);
+  warp_update<1>(L.minh, x1, s0 + 1, act && !light);
+  const bool self0 = act && r0 == s0, self1 = act && r1 == s0 + 1;
+  warp_update<2>(L.csz, x0, self0 ? L.sz[s0] : 0u, self0);
+  warp_update<2>(L.csz, x1, self1 ? L.sz[s0 + 1] : 0u, self1);
 }
 
-// The top edge of each light component takes the lowest heavy edge touching
-// it as its parent, and hands the component's size to the slot that names
-// the component in the heavy half; heavy slots are renamed to that slot.
+// The top edge of each light component takes the lowest heavy slot touching
+// it as its parent (2p + side: edge p, on that side), and hands the
+// component's size to that slot, which names the component in the heavy
+// half; heavy slots are renamed to it.
 __global__ void k_dg_stitch(Level L) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= L.m) return;
   bool light;
-  if (!block_split(L, (uint32_t)k, light)) return;
+  const bool split = block_split(L, (uint32_t)k, light);
   const uint32_t s0 = 2 * (uint32_t)k;
-  if (light) {
-    const uint32_t r = uf_find(L.uf, L.rep[s0]);
+  uint32_t r0 = L.rep[s0], r1 = L.rep[s0 + 1];
+  if (split && light) {
+    const uint32_t r = uf_find<false>(L.uf, r0);
     const uint32_t h = L.minh[r];
     if (L.top[r] == (uint32_t)k + 1 && h != kInvalid) {
-      L.parent[k] = h >> 1;
+      L.parent[k] = h;
       L.sz[h] = L.csz[r];
     }
-  } else {
-    L.rep[s0] = L.minh[uf_find(L.uf, L.rep[s0])];
-    L.rep[s0 + 1] = L.minh[uf_find(L.uf, L.rep[s0 + 1])];
+  } else if (split) {
+    r0 = L.minh[uf_find<false>(L.uf, r0)];
+    r1 = L.minh[uf_find<false>(L.uf, r1)];
+    L.rep[s0] = r0;
+    L.rep[s0 + 1] = r1;
   }
+  if (r0 == s0) clear_name(L, s0);
+  if (r1 == s0 + 1) clear_name(L, s0 + 1);
 }
 
-// The serial finish: one warp per block of kBaseEdges edges.  The lanes
-// stage the block's vertex names (local slot numbers) and sizes in shared
-// memory; lane 0 then runs the merge sequence over them.
-__global__ void __launch_bounds__(32 * kBaseWarps)
-    k_dg_base(int64_t m, const uint32_t *__restrict__ rep, const uint32_t *__restrict__ sz,
-              uint32_t *__restrict__ parent, uint32_t *__restrict__ size_out, uint32_t *status) {
-  __shared__ uint16_t s_rep[kBaseWarps][2 * kBaseEdges];
-  __shared__ uint16_t s_uf[kBaseWarps][2 * kBaseEdges];
-  __shared__ uint16_t s_top[kBaseWarps][2 * kBaseEdges];
-  __shared__ uint32_t s_size[kBaseWarps][2 * kBaseEdges];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t b0 = ((int64_t)blockIdx.x * kBaseWarps + w) * kBaseEdges;
-  if (b0 >= m) return;
-  const int cnt = (int)(m - b0 < kBaseEdges ? m - b0 : kBaseEdges);
-  uint16_t *lrep = s_rep[w], *uf = s_uf[w], *top = s_top[w];
-  uint32_t *csize = s_size[w];
+// The levels of blocks of kLocalEdges edges and less, in shared memory, one
+// CTA per block: the same four steps per level as the global kernels, then
+// the serial merge sequence over blocks of kSerialEdges edges, one thread
+// each, which also gives every cluster's size.  Vertex names are local slot
+// numbers (slot - 2 * block start); the serial finish checks that each stays
+// inside its block (it does for any input with valid ids).
+__global__ void __launch_bounds__(kLocalThreads)
+    k_dg_local(int64_t m, const uint32_t *__restrict__ rep, const uint32_t *__restrict__ sz,
+               uint32_t *__restrict__ parent, uint32_t *__restrict__ size_out, uint32_t *status) {
+  constexpr int SL = 2 * kLocalEdges;
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t *uf = smem, *top = uf + SL, *minh = top + SL, *csz = minh + SL, *szl = csz + SL;
+  uint16_t *lrep = reinterpret_cast<uint16_t *>(szl + SL);
+  volatile uint32_t *vuf = uf;
+  const int tid = threadIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.x * kLocalEdges;
+  const int cnt = (int)(m - b0 < kLocalEdges ? m - b0 : kLocalEdges);
+  const uint32_t g0 = (uint32_t)(2 * b0);  // global slot of local slot 0
   bool bad = false;
-  for (int l = lane; l < 2 * cnt; l += 32) {
-    const uint32_t s = (uint32_t)(2 * b0) + l;
-    const uint32_t r = rep[s];
-    const int64_t lr = (int64_t)r - 2 * b0;
-    if (lr < 0 || lr >= 2 * cnt) bad = true;
-    lrep[l] = bad ? (uint16_t)l : (uint16_t)lr;
-    uf[l] = (uint16_t)l;
-    top[l] = 0;
-    csize[l] = r == s ? sz[s] : 0;
+  if (cnt == kLocalEdges) {  // a full block: 16-byte loads, all in flight at once
+    constexpr int kVec = SL / 4 / kLocalThreads;
+    uint4 vr[kVec], vs[kVec];
+#pragma unroll
+    for (int i = 0; i < kVec; ++i) {
+      vr[i] = reinterpret_cast<const uint4 *>(rep + g0)[tid + i * kLocalThreads];
+      vs[i] = reinterpret_cast<const uint4 *>(sz + g0)[tid + i * kLocalThreads];
+    }
+#pragma unroll
+    for (int i = 0; i < kVec; ++i) {
+      const int l = 4 * (tid + i * kLocalThreads);
+      const uint32_t r[4] = {vr[i].x, vr[i].y, vr[i].z, vr[i].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t lr = (int64_t)r[j] - g0;
+        const bool out = lr < 0 || lr >= SL;
+        bad |= out;
+        lrep[l + j] = out ? (uint16_t)(l + j) : (uint16_t)lr;
+      }
+      reinterpret_cast<uint4 *>(szl)[tid + i * kLocalThreads] = vs[i];
+    }
+  } else {
+    for (int l = tid; l < 2 * cnt; l += kLocalThreads) {
+      const int64_t lr = (int64_t)rep[g0 + l] - g0;
+      const bool out = lr < 0 || lr >= 2 * cnt;
+      bad |= out;
+      lrep[l] = out ? (uint16_t)l : (uint16_t)lr;
+      szl[l] = sz[g0 + l];
+    }
   }
-  if (__any_sync(0xffffffffu, bad)) {
-    if (lane == 0) atomicOr(status, kErrChain);
+  if (__syncthreads_or(bad)) {
+    if (tid == 0) atomicOr(status, kErrChain);
     return;
   }
-  __syncwarp();
-  if (lane != 0) return;
-  for (int t = 0; t < cnt; ++t) {
-    uint32_t a = lrep[2 * t], b = lrep[2 * t + 1];
+  for (int S = kLocalEdges; S > kSerialEdges; S >>= 1) {
+    const int half = S >> 1;
+    for (int l = tid; l < 2 * cnt; l += kLocalThreads) {
+      uf[l] = (uint32_t)l;
+      top[l] = 0;
+      minh[l] = kInvalid;
+      csz[l] = 0;
+    }
+    __syncthreads();
+    for (int t = tid; t < cnt; t += kLocalThreads) {
+      const int start = t & ~(S - 1);
+      if ((t & (S - 1)) < half && start + half < cnt && !uf_unite(vuf, lrep[2 * t], lrep[2 * t + 1]))
+        atomicOr(status, kErrSpin);
+    }
+    __syncthreads();
+    for (int t = tid; t < cnt; t += kLocalThreads) {
+      const int start = t & ~(S - 1);
+      if (start + half >= cnt) continue;
+      const uint32_t s0 = 2 * t, r0 = lrep[s0], r1 = lrep[s0 + 1];
+      const uint32_t x0 = uf_find<true>(vuf, r0);
+      if ((t & (S - 1)) < half) {
+        atomicMax(top + x0, (uint32_t)t + 1);
+        if (r0 == s0) atomicAdd(csz + x0, szl[s0]);
+        if (r1 == s0 + 1) atomicAdd(csz + x0, szl[s0 + 1]);
+      } else {
+        const uint32_t x1 = uf_find<true>(vuf, r1);
+        atomicMin(minh + x0, s0);
+        atomicMin(minh + x1, s0 + 1);
+        if (r0 == s0) atomicAdd(csz + x0, szl[s0]);
+        if (r1 == s0 + 1) atomicAdd(csz + x1, szl[s0 + 1]);
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < cnt; t += kLocalThreads) {
+      const int start = t & ~(S - 1);
+      if (start + half >= cnt) continue;
+      const uint32_t s0 = 2 * t;
+      if ((t & (S - 1)) < half) {
+        const uint32_t r = uf_find<false>(vuf, lrep[s0]);
+        const uint32_t h = minh[r];
+        if (top[r] == (uint32_t)t + 1 && h != kInvalid) {
+          parent[b0 + t] = g0 + h;
+          szl[h] = csz[r];
+        }
+      } else {
+        lrep[s0] = (uint16_t)minh[uf_find<false>(vuf, lrep[s0])];
+        lrep[s0 + 1] = (uint16_t)minh[uf_find<false>(vuf, lrep[s0 + 1])];
+      }
+    }
+    __syncthreads();
+  }
+  // Serial finish: thread j merges local edges [j * kSerialEdges, ...).  Its
+  // slots are laid out transposed (slot o of sub-block j at o * kSubSlots +
+  // j), so the lanes of a warp, at the same step of their own sub-blocks,
+  // touch 32 different banks.  pn holds each slot's name, transposed too.
+  constexpr int kSubSlots = 2 * kSerialEdges;
+  constexpr int kSubs = SL / kSubSlots;
+  static_assert(kSubs == kSubSlots, "square transposition");
+  uint32_t *pn = minh;
+  for (int l = tid; l < 2 * cnt; l += kLocalThreads) {
+    const uint32_t r = lrep[l];
+    if (r / kSubSlots != (uint32_t)l / kSubSlots) bad = true;  // a name outside its sub-block
+    const uint32_t pl = (l % kSubSlots) * kSubs + l / kSubSlots;
+    pn[pl] = (r % kSubSlots) * kSubs + r / kSubSlots;
+    uf[pl] = pl;
+    top[pl] = 0;
+    csz[pl] = r == (uint32_t)l ? szl[l] : 0u;
+  }
+  if (__syncthreads_or(bad)) {
+    if (tid == 0) atomicOr(status, kErrChain);
+    return;
+  }
+  const int j = tid, t0 = j * kSerialEdges;
+  if (t0 >= cnt) return;
+  const int ne = cnt - t0 < kSerialEdges ? cnt - t0 : kSerialEdges;
+  for (int i = 0; i < ne; ++i) {
+    uint32_t a = pn[(2 * i) * kSubs + j], b = pn[(2 * i + 1) * kSubs + j];
     while (uf[a] != a) { uf[a] = uf[uf[a]]; a = uf[a]; }
     while (uf[b] != b) { uf[b] = uf[uf[b]]; b = uf[b]; }
     if (a == b) {  // the edge closes a cycle: not a tree
       atomicOr(status, kErrBadInput);
       return;
     }
-    const uint32_t k = (uint32_t)b0 + t;
-    if (top[a]) parent[b0 + top[a] - 1] = k;
-    if (top[b]) parent[b0 + top[b] - 1] = k;
-    const uint32_t size = csize[a] + csize[b];
+    const uint32_t k = (uint32_t)(b0 + t0 + i);
+    if (top[a]) parent[b0 + t0 + top[a] - 1] = 2 * k;
+    if (top[b]) parent[b0 + t0 + top[b] - 1] = 2 * k + 1;
+    const uint32_t size = csz[a] + csz[b];
     size_out[k] = size;
     const uint32_t r = a < b ? a : b;
-    uf[a ^ b ^ r] = (uint16_t)r;
-    top[r] = (uint16_t)(t + 1);
-    csize[r] = size;
+    uf[a ^ b ^ r] = r;
+    top[r] = (uint32_t)i + 1;
+    csz[r] = size;
   }
 }
 
-// Linkage rows {a, b, w, size}: w and size now, the children (a < b) by
-// min/max scatter from both sides in k_dg_children.
-__global__ void k_dg_rows(const emst_edge *__restrict__ e, int64_t m,
-                          const uint32_t *__restrict__ size_out, uint4 *__restrict__ link) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= m) return;
-  link[k] = make_uint4(kInvalid, 0u, __float_as_uint(e[k].w), size_out[k]);
-}
-
-// Every cluster names its parent: point v (id v) hangs under its lowest
-// edge, edge f (id n + f) under parent[f].  Each row receives exactly two
-// children, so a min and a max order them.
+// Every cluster names its parent: point v (id v) the edge of its lowest
+// slot, edge f (id n + f) the edge of slot parent[f], the root none.  Slot
+// 2p + side receives exactly one child, the cluster on that side of edge p
+// (points were placed there by k_dg_init).
 __global__ void k_dg_children(int64_t n, int64_t m, const uint32_t *__restrict__ vslot,
-                              const uint32_t *__restrict__ eparent, uint4 *link,
+                              const uint32_t *__restrict__ eparent, uint32_t *__restrict__ child,
                               uint32_t *__restrict__ out_parent) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n + m) return;
   // (a point with no edge exists only when the input has a cycle, which
   // the serial finish reports)
-  uint32_t p = kInvalid;
-  if (c < n) p = vslot[c] == kInvalid ? kInvalid : vslot[c] >> 1;
-  else p = eparent[c - n];
-  if (out_parent) out_parent[c] = p == kInvalid ? kInvalid : (uint32_t)n + p;
-  if (link && p != kInvalid) {
-    atomicMin(&link[p].x, (uint32_t)c);
-    atomicMax(&link[p].y, (uint32_t)c);
-  }
+  const uint32_t ps = c < n ? vslot[c] : eparent[c - n];
+  if (out_parent) out_parent[c] = ps == kInvalid ? kInvalid : (uint32_t)n + (ps >> 1);
+  if (child && c >= n && ps != kInvalid) child[ps] = (uint32_t)c;
+}
+
+// Linkage rows {a, b, w, size}, the two children ordered a < b.
+__global__ void k_dg_rows(const emst_edge *__restrict__ e, int64_t m,
+                          const uint32_t *__restrict__ size_out, const uint2 *__restrict__ child,
+                          uint4 *__restrict__ link) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const uint2 c = child[k];
+  link[k] = make_uint4(min(c.x, c.y), max(c.x, c.y), __float_as_uint(e[k].w), size_out[k]);
 }
 
 }  // namespace
@@ -300,8 +466,8 @@ int dendrogram_impl(const emst_edge *edges, int64_t n, uint4 *out_link, uint32_t
   };
   const size_t o_status = take(64);
   const size_t o_vslot = take(4 * (size_t)n);
-  size_t o_slot[6];
-  for (int i = 0; i < 6; ++i) o_slot[i] = take(4 * (size_t)m2);
+  size_t o_slot[11];  // rep, sz, two sets of (uf, top, minh, csz), child
+  for (int i = 0; i < 11; ++i) o_slot[i] = take(4 * (size_t)m2);
   const size_t o_par = take(4 * (size_t)m);
   const size_t o_size = take(4 * (size_t)m);
   const size_t o_edges = edges_dev ? 0 : take(sizeof(emst_edge) * (size_t)m);
@@ -323,6 +489,10 @@ int dendrogram_impl(const emst_edge *edges, int64_t n, uint4 *out_link, uint32_t
   L.top = U(o_slot[3]);
   L.minh = U(o_slot[4]);
   L.csz = U(o_slot[5]);
+  L.nuf = U(o_slot[6]);
+  L.ntop = U(o_slot[7]);
+  L.nminh = U(o_slot[8]);
+  L.ncsz = U(o_slot[9]);
   L.parent = eparent;
   L.m = m;
   L.status = status;
@@ -341,22 +511,36 @@ int dendrogram_impl(const emst_edge *edges, int64_t n, uint4 *out_link, uint32_t
     cudaMemsetAsync(vslot, 0xff, 4 * (size_t)n, s);
     cudaMemsetAsync(eparent, 0xff, 4 * (size_t)m, s);
     k_dg_first_slot<<<gs, kDgBlock, 0, s>>>(e, m2, vslot);
-    k_dg_init<<<gs, kDgBlock, 0, s>>>(e, m2, vslot, L.rep, L.sz);
-    int64_t S = kBaseEdges;
+    uint32_t *child = link ? U(o_slot[10]) : nullptr;
+    int64_t S = kLocalEdges;
     while (S < m) S *= 2;
-    for (; S > kBaseEdges; S /= 2) {
+    // the first level reads the set k_dg_init clears (the "next" one here)
+    std::swap(L.uf, L.nuf);
+    std::swap(L.top, L.ntop);
+    std::swap(L.minh, L.nminh);
+    std::swap(L.csz, L.ncsz);
+    k_dg_init<<<gs, kDgBlock, 0, s>>>(L, e, vslot, child);
+    std::swap(L.uf, L.nuf);
+    std::swap(L.top, L.ntop);
+    std::swap(L.minh, L.nminh);
+    std::swap(L.csz, L.ncsz);
+    for (; S > kLocalEdges; S /= 2) {
       L.mask = (uint32_t)(S - 1);
       L.half = (uint32_t)(S / 2);
-      k_dg_reset<<<gs, kDgBlock, 0, s>>>(L);
       k_dg_unite<<<gm, kDgBlock, 0, s>>>(L);
       k_dg_classify<<<gm, kDgBlock, 0, s>>>(L);
       k_dg_stitch<<<gm, kDgBlock, 0, s>>>(L);
+      std::swap(L.uf, L.nuf);
+      std::swap(L.top, L.ntop);
+      std::swap(L.minh, L.nminh);
+      std::swap(L.csz, L.ncsz);
     }
-    const int64_t blocks = (m + kBaseEdges - 1) / kBaseEdges;
-    k_dg_base<<<grid_for(blocks, kBaseWarps), 32 * kBaseWarps, 0, s>>>(m, L.rep, L.sz, eparent,
-                                                                       size, status);
-    if (link) k_dg_rows<<<gm, kDgBlock, 0, s>>>(e, m, size, link);
-    k_dg_children<<<grid_for(n + m, kDgBlock), kDgBlock, 0, s>>>(n, m, vslot, eparent, link, pout);
+    cudaFuncSetAttribute(k_dg_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLocalSmem);
+    k_dg_local<<<grid_for(m, kLocalEdges), kLocalThreads, kLocalSmem, s>>>(m, L.rep, L.sz, eparent,
+                                                                           size, status);
+    k_dg_children<<<grid_for(n + m, kDgBlock), kDgBlock, 0, s>>>(n, m, vslot, eparent, child, pout);
+    if (link)
+      k_dg_rows<<<gm, kDgBlock, 0, s>>>(e, m, size, reinterpret_cast<const uint2 *>(child), link);
     if (cudaPeekAtLastError() != cudaSuccess) rc = EMST_ERR_CUDA;
     if (out_link && !link_dev)
       cudaMemcpyAsync(out_link, link, 16 * (size_t)m, cudaMemcpyDeviceToHost, s);
