@@ -154,7 +154,10 @@ __global__ void k_dg_first_slot(const emst_edge *__restrict__ e, int64_t m2,
 // The per-level union-find and per-component values come in two sets: a
 // level reads one and, in its last kernel, clears the other for the next
 // level.  Only slots that name a vertex are ever read there (every walk
-// starts at a name and hooks join names), so only those are cleared.
+// starts at a name and hooks join names), but every slot is cleared: whole
+// coalesced sectors, where clearing the scattered names alone made each
+// sector a partial write that DRAM had to fill first (measured 4.2 GB per
+// stitch launch at 37M points, HBM-bound).
 struct Level {
   uint32_t *rep, *sz, *uf, *top, *minh, *csz, *parent;
   uint32_t *nuf, *ntop, *nminh, *ncsz;  // the next level's set
@@ -163,11 +166,11 @@ struct Level {
   uint32_t *status;
 };
 
-__device__ __forceinline__ void clear_name(const Level &L, uint32_t s) {
-  L.nuf[s] = s;
-  L.ntop[s] = 0;
-  L.nminh[s] = kInvalid;
-  L.ncsz[s] = 0;
+__device__ __forceinline__ void clear_pair(const Level &L, uint32_t s0) {
+  reinterpret_cast<uint2 *>(L.nuf)[s0 >> 1] = make_uint2(s0, s0 + 1);
+  reinterpret_cast<uint2 *>(L.ntop)[s0 >> 1] = make_uint2(0u, 0u);
+  reinterpret_cast<uint2 *>(L.nminh)[s0 >> 1] = make_uint2(kInvalid, kInvalid);
+  reinterpret_cast<uint2 *>(L.ncsz)[s0 >> 1] = make_uint2(0u, 0u);
 }
 
 __device__ __forceinline__ bool block_split(const Level &L, uint32_t k, bool &light) {
@@ -178,8 +181,8 @@ __device__ __forceinline__ bool block_split(const Level &L, uint32_t k, bool &li
 
 // Top level: every vertex is a point, named by its lowest slot, size 1.
 // The slot that names point v also records v as the child on that side of
-// its edge (the cluster a point starts in) and clears the first level's set
-// there.
+// its edge (the cluster a point starts in); the even slot of each edge
+// clears the first level's set for the edge's two slots.
 __global__ void k_dg_init(Level L, const emst_edge *__restrict__ e,
                           const uint32_t *__restrict__ vslot, uint32_t *__restrict__ child) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,9 +191,8 @@ __global__ void k_dg_init(Level L, const emst_edge *__restrict__ e,
   const uint32_t r = vslot[v];
   L.rep[s] = r;
   L.sz[s] = 1;
-  if (r != (uint32_t)s) return;
-  if (child) child[s] = v;
-  clear_name(L, (uint32_t)s);
+  if ((s & 1) == 0) clear_pair(L, (uint32_t)s);
+  if (child) child[s] = r == (uint32_t)s ? v : kInvalid;  // the rest come from k_dg_children
 }
 
 // Light components: unite the two vertices of every light edge.
@@ -256,8 +258,7 @@ __global__ void k_dg_stitch(Level L) {
     L.rep[s0] = r0;
     L.rep[s0 + 1] = r1;
   }
-  if (r0 == s0) clear_name(L, s0);
-  if (r1 == s0 + 1) clear_name(L, s0 + 1);
+  clear_pair(L, s0);
 }
 
 // The levels of blocks of kLocalEdges edges and less, in shared memory, one
