@@ -59,6 +59,9 @@ def parse():
                          "in one emst_compute_batched call, against one emst_compute per instance")
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--dense-n", type=int, default=24_000_000)
+    ap.add_argument("--clocks-dir", default=None,
+                    help="keep the raw nvidia-smi clock samples of the timed region there "
+                         "(default: a temporary file; the JSON line carries their summary)")
     ap.add_argument("--dg-tree", default="all", choices=["all", "emst", "mrd", "random"],
                     help="dendrogram workload: which tree(s) to time")
     return ap.parse_args()
@@ -77,10 +80,12 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, keep_dir: str | None = None):
+        import tempfile
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        d = keep_dir or tempfile.gettempdir()
+        self.path = os.path.join(d, f"emst_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -495,7 +500,7 @@ def main():
         step()
     torch.cuda.synchronize(dev)
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_dir)
     clocks.start()
     time.sleep(0.3)
     shard.barrier(dev)
