@@ -59,6 +59,8 @@ def parse():
                          "in one emst_compute_batched call, against one emst_compute per instance")
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--dense-n", type=int, default=24_000_000)
+    ap.add_argument("--mrd-k", default="1,2,4,8,16",
+                    help="mrd workload: the k_pts values to time, comma-separated")
     ap.add_argument("--clocks-dir", default=None,
                     help="keep the raw nvidia-smi clock samples of the timed region there "
                          "(default: a temporary file; the JSON line carries their summary)")
@@ -321,7 +323,7 @@ def run_mrd(args, rank, world, local):
     pts = torch.from_numpy(make_points(args.n, args.seed)).to(dev)
     n = pts.shape[0]
     out = torch.empty((n - 1, 3), dtype=torch.int32, device=dev)
-    for k in (1, 2, 4, 8, 16):
+    for k in [int(x) for x in args.mrd_k.split(",")]:
         for _ in range(max(args.warmup, 1)):
             pkg.emst_compute_ex(pts, out_edges=out, stream=stream, mrd_k=k)
         torch.cuda.synchronize(dev)
