@@ -58,3 +58,17 @@ def test_oracle_is_not_imported_by_the_product():
     for f in list(root.rglob("*.py")) + list(root.rglob("*.cu")) + list(root.rglob("*.cuh")):
         txt = f.read_text()
         assert "import oracle" not in txt and "from oracle" not in txt and "emst_oracle" not in txt, f
+
+
+def test_dendrogram_binding_rejects_bad_shapes_without_gpu():
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        pkg.emst_dendrogram(torch.zeros((5, 2), dtype=torch.int32))      # not (m, 3)
+    with pytest.raises(ValueError):
+        pkg.emst_dendrogram(torch.zeros((5, 3), dtype=torch.int64))      # not int32
+    with pytest.raises(ValueError):
+        pkg.emst_dendrogram(torch.zeros((5, 3), dtype=torch.int32), n=9)  # a tree of 9 points has 8 edges
+    with pytest.raises(ValueError):
+        pkg.emst_dendrogram(torch.zeros((3, 3), dtype=torch.int32),
+                            out_linkage=torch.zeros((3, 3), dtype=torch.int32))
+    assert pkg.LINKAGE_DTYPE.itemsize == 16
