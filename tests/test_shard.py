@@ -6,7 +6,6 @@ GPU; the GPU path runs the same steps with emst_compute_batched."""
 from __future__ import annotations
 
 import os
-import socket
 
 import numpy as np
 import pytest
@@ -47,15 +46,15 @@ def test_local_batch_slices_instances():
     assert len(sub) == 0 and list(so) == [0]
 
 
-def _solve_share(rank, world, port, out_dir):
+def _solve_share(rank, world, out_dir):
     """One rank: the batched flow with the oracle standing in for the GPU."""
     import torch.distributed as dist
 
     import oracle
     import synth
-    os.environ["MASTER_ADDR"] = "127.0.0.1"
-    os.environ["MASTER_PORT"] = str(port)
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rendezvous through a file: no port to race for
+    dist.init_process_group("gloo", init_method="file://" + os.path.join(out_dir, "rendezvous"),
+                            rank=rank, world_size=world)
     try:
         sizes = synth.batched_sizes(24, seed=7, lo=2, hi=300)
         pts, offs = synth.batched_instances(sizes, seed=7)
@@ -78,19 +77,13 @@ def _solve_share(rank, world, port, out_dir):
         dist.destroy_process_group()
 
 
-def _free_port():
-    with socket.socket() as s:
-        s.bind(("127.0.0.1", 0))
-        return s.getsockname()[1]
-
-
 def test_world_size_2_gloo_batched_flow(tmp_path):
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as mp
 
     import oracle
     import synth
-    mp.start_processes(_solve_share, args=(2, _free_port(), str(tmp_path)), nprocs=2,
+    mp.start_processes(_solve_share, args=(2, str(tmp_path)), nprocs=2,
                        join=True, start_method="spawn")
     for r in range(2):
         assert float(np.load(tmp_path / f"max_{r}.npy")[0]) == 2.5
