@@ -167,3 +167,20 @@ def test_invalid_inputs():
     bad[0]["w"] = np.nan
     with pytest.raises(ValueError):
         oracle.dendrogram(bad, 50)
+
+
+@pytest.mark.parametrize("shape", synth.TREE_SHAPES)
+def test_tree_generator_gives_spanning_trees_in_merge_order(shape):
+    for n, ties in ((1, 0), (2, 0), (257, 0), (1000, 3)):
+        e = synth.tree_edges(n, n + ties, shape, ties=ties)
+        assert len(e) == max(n - 1, 0)
+        if n < 2:
+            continue
+        assert np.all(e["i"] < e["j"]) and np.all(e["j"] < n)
+        assert np.all(np.diff(e["w"].astype(np.float64)) >= 0)
+        comps, cycle = oracle.count_components(e, n)
+        assert comps == 1 and not cycle
+    # the deep case: along the path the weights rise, so every merge adds one point
+    e = synth.tree_edges(300, 5, "path_sorted")
+    link, _ = oracle.dendrogram(e, 300)
+    assert list(link["size"]) == list(range(2, 301))
