@@ -91,7 +91,7 @@ typedef struct emst_options {
                                  with mlp_params. */
   int32_t morton_bits;        /* Z-curve code width: 64 (21 bits per axis in 3D, 32 in 2D,
                                  FP32 quantiser), 128 (42 / 64 bits per axis, FP64 quantiser:
-                                 the finer grid §4.2 suggests for very dense data; one more
+                                 the finer grid §4.1 suggests for very dense data; one more
                                  8-pass sort) or 0 = automatic (the default): 64, rebuilt with
                                  128 when more than n/64 distinct points share their curve
                                  predecessor's 64-bit code.  The tree is the same either way. */
@@ -170,6 +170,9 @@ int emst_core_distances(const float *points, int64_t n, int dim, int k, float *o
  * allocate, a process under a device-memory budget it does not own, or a
  * latency-critical loop that cannot take an allocator's implicit
  * synchronisation.  Same arguments, result and output order as emst_compute.
+ *   - Codes: always 64-bit Z-curve codes (emst_compute switches to 128-bit
+ *     codes on very dense data, see emst_options.morton_bits).  The tree is
+ *     the same either way; only the search on very dense input is slower.
  *   - Scratch: one fixed 16 MiB array in the library's device memory, held by
  *     every GPU that loads the library until the process exits; no cudaMalloc,
  *     cudaFree or pool allocation happens in the call.

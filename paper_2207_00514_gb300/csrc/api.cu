@@ -54,6 +54,21 @@ bool device_accessible(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 1;
+    }
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
 cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -223,7 +238,7 @@ static void build_order128(Problem &P) {
 // A1-A4: scene box, codes, sort, gather, hierarchy, refit.  With auto_wide
 // the 64-bit order is built first and its collisions counted (one host
 // read); when more than n/64 distinct points share their predecessor's code,
-// the order is rebuilt with 128-bit codes (§4.2's remedy for data the 64-bit
+// the order is rebuilt with 128-bit codes (§4.1's remedy for data the 64-bit
 // grid under-resolves).
 void run_build(Problem &P) {
   launch_scene_box(P);

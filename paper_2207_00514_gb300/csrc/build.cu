@@ -65,7 +65,7 @@ __global__ void k_box_init(uint32_t *box) {
 void launch_scene_box(Problem &P) {
   uint32_t *box = P.counters + 4;
   k_box_init<<<1, 32, 0, P.stream>>>(box);
-  int grid = 152 * 4;
+  int grid = sm_count() * 4;
   int64_t need = (P.n + kBlock - 1) / kBlock;
   if (need < grid) grid = (int)(need < 1 ? 1 : need);
   if (P.dim == 3)
@@ -114,7 +114,7 @@ void launch_morton(Problem &P) {
   P.launches += 1;
 }
 
-// A2 at the finer grid §4.2 suggests for very dense data (128-bit codes):
+// A2 at the finer grid §4.1 suggests for very dense data (128-bit codes):
 // B = 42 bits per dimension in 3D, 64 in 2D, quantised in FP64 so the grid
 // resolves FP32 coordinates:
 //   s = 2^B / (hi - lo) (0 for a flat dimension), t = (x - lo) * s,

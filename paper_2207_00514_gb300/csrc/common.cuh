@@ -327,6 +327,9 @@ void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge 
 
 // api.cu: helpers of the orchestration
 bool device_accessible(const void *p);
+// Streaming multiprocessors of the current device (queried once per device):
+// grid caps of grid-stride kernels are multiples of it.
+int sm_count();
 // Stream-ordered scratch from the library's pool on the current device
 // (release with cudaFreeAsync on the same stream).
 cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);

@@ -599,7 +599,7 @@ void launch_predict(Problem &P, bool carried) {
   set_mlp_attrs();
   const int64_t tiles = (P.n + 31) / 32;
   int64_t g = (tiles + 7) / 8;
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > sm_count() * 8) g = sm_count() * 8;
   k_predict<<<(unsigned)g, 256, sizeof(MlpSmem), P.stream>>>(feat_args(P, carried), P.mlp, P.pred_r);
   P.launches += 1;
 }
@@ -651,7 +651,7 @@ int emst_mlp_forward(const float *features, int64_t m, const float *params, floa
   set_mlp_attrs();
   const int64_t tiles = (m + 31) / 32;
   int64_t g = (tiles + 7) / 8;
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > sm_count() * 8) g = sm_count() * 8;
   k_mlp_forward<<<(unsigned)g, 256, sizeof(MlpSmem), (cudaStream_t)stream>>>(features, m, params,
                                                                             out_log2w);
   return cudaGetLastError() == cudaSuccess ? EMST_OK : EMST_ERR_CUDA;

@@ -51,6 +51,17 @@ cudaError_t scratch_address(int dev, void **out) {
 
 using namespace emst;
 
+// A CUDA failure: read and clear the runtime's last error (as emst_compute
+// does), so the caller's next runtime call does not report this call's error.
+static int cuda_failure() {
+  cudaGetLastError();
+  return EMST_ERR_CUDA;
+}
+
+// Codes are always 64-bit here (emst_compute may rebuild with 128-bit codes
+// on very dense data; the 128-bit arrays would not fit the fixed scratch at
+// the size limit).  The tree does not depend on the code width, only the
+// search time on very dense input does.
 extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, emst_edge *out_edges,
                                     void *stream_) {
   int rc = check_args(points, n, dim);
@@ -60,12 +71,9 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
   if (n == 0) return EMST_OK;
   cudaStream_t stream = (cudaStream_t)stream_;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return EMST_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cuda_failure();
   char *base = nullptr;
-  if (scratch_address(dev, (void **)&base) != cudaSuccess) {
-    cudaGetLastError();
-    return EMST_ERR_CUDA;
-  }
+  if (scratch_address(dev, (void **)&base) != cudaSuccess) return cuda_failure();
   const bool pts_dev = device_accessible(points);
   const bool out_dev = n < 2 || device_accessible(out_edges);
   Problem P;
@@ -78,19 +86,22 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
   layout(P, base, !pts_dev, !out_dev);
 
   uint32_t host_counters[16] = {0};
+  // Launch errors first: a failed launch must not read as a round without edges.
   auto sync_counters = [&]() -> bool {
+    if (cudaPeekAtLastError() != cudaSuccess) return false;
     if (cudaMemcpyAsync(host_counters, P.counters, sizeof(host_counters), cudaMemcpyDeviceToHost,
                         stream) != cudaSuccess)
       return false;
     return cudaStreamSynchronize(stream) == cudaSuccess;
   };
   // Counters (edge count, status word, box) start from zero every call.
-  if (cudaMemsetAsync(P.counters, 0, sizeof(uint32_t) * 64, stream) != cudaSuccess) return EMST_ERR_CUDA;
+  if (cudaMemsetAsync(P.counters, 0, sizeof(uint32_t) * 64, stream) != cudaSuccess)
+    return cuda_failure();
   if (!pts_dev && cudaMemcpyAsync((void *)P.points, points, sizeof(float) * (size_t)n * dim,
                                   cudaMemcpyHostToDevice, stream) != cudaSuccess)
-    return EMST_ERR_CUDA;
+    return cuda_failure();
   run_build(P);  // clears its own histograms, tile counters, look-back and arrivals
-  if (!sync_counters()) return EMST_ERR_CUDA;
+  if (!sync_counters()) return cuda_failure();
   if (host_counters[1] != 0) return status_from_bits(host_counters[1]);
   if (n >= 2) {
     reset_round_state(P);  // bounds and per-component minima back to their sentinels
@@ -98,19 +109,20 @@ extern "C" int emst_compute_noalloc(const float *points, int64_t n, int dim, ems
     for (int round = 0;; ++round) {
       if (round >= limit) return EMST_ERR_ROUND_LIMIT;
       run_round(P, round, true, 0, false);
-      if (!sync_counters()) return EMST_ERR_CUDA;
+      if (!sync_counters()) return cuda_failure();
       if (host_counters[1] != 0) return status_from_bits(host_counters[1]);
       advance_round(P, (int64_t)host_counters[12]);
       if ((int64_t)host_counters[0] >= n - 1) break;
     }
     if ((int64_t)host_counters[0] != n - 1) return EMST_ERR_INTERNAL;
     const int orc = run_output(P, out_dev ? out_edges : P.out_stage, host_counters[11]);
+    if (orc == EMST_ERR_CUDA) return cuda_failure();
     if (orc != EMST_OK) return orc;
     if (!out_dev && cudaMemcpyAsync(out_edges, P.out_stage, sizeof(emst_edge) * (size_t)(n - 1),
                                     cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-      return EMST_ERR_CUDA;
+      return cuda_failure();
   }
-  if (!sync_counters()) return EMST_ERR_CUDA;
+  if (!sync_counters()) return cuda_failure();
   if (cudaGetLastError() != cudaSuccess) return EMST_ERR_CUDA;
   return status_from_bits(host_counters[1]);
 }

@@ -286,7 +286,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   // listed points with the plain cutoff
   const uint32_t *list = learned_pass == 2 ? P.rerun_list : nullptr;
   const uint32_t *list_count = learned_pass == 2 ? P.counters + 13 : nullptr;
-  const int g = learned_pass == 2 ? 152 * 8 : grid_for(P.n, block);
+  const int g = learned_pass == 2 ? sm_count() * 8 : grid_for(P.n, block);
   cudaStream_t s = P.stream;
 #define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L, false, false><<<g, block, 0, s>>>(A, list, list_count)
 #define EMST_TRAV_FIRST(K, H) k_traverse<false, false, K, true, H, false, true, false><<<g, block, 0, s>>>(A, list, list_count)

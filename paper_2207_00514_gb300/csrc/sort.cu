@@ -230,7 +230,7 @@ int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int 
   cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 8 * kRadix, s);
   cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t) * 8, s);
   int hgrid = (int)((n + 511) / 512);
-  if (hgrid > 152 * 4) hgrid = 152 * 4;
+  if (hgrid > sm_count() * 4) hgrid = sm_count() * 4;
   k_sort_hist<<<hgrid, 512, 0, s>>>(P.keys[src], n, digit_begin, digit_end, hist);
   k_sort_scan<<<8, kRadix, 0, s>>>(hist);
   P.launches += 2;

@@ -82,7 +82,7 @@ def blobs(n: int, dim: int, seed: int, n_blobs: int = 50, frac_background: float
 
 def dense(n: int, dim: int, seed: int, n_clusters: int = 20_000,
           sigma_range=(1e-9, 1e-6), frac_background: float = 0.10) -> np.ndarray:
-    """Extremely dense clusters (the under-resolved regime §4.2 describes for
+    """Extremely dense clusters (the under-resolved regime §4.1 describes for
     a GPS-trace dataset): (1 - frac_background)·n points in ``n_clusters``
     isotropic Gaussians with centres uniform in the unit box, sigma
     log-uniform in ``sigma_range`` (below the 2^-21 cells of 64-bit 3D codes)

@@ -81,3 +81,46 @@ def test_batched_rejects_bad_offsets(pkg):
         pkg.emst_compute_batched(pts, np.array([0, 5, 4, 10]))
     with pytest.raises(ValueError):
         pkg.emst_compute_batched(pts, np.array([0, 5, 9]))
+
+
+def test_full_config4_batch_vs_oracle(pkg):
+    """The whole batched workload at full size -- 4,096 independent 3D
+    instances (sizes log-uniform in [100, 1e6], seed 4: 460.6M points) -- in
+    ONE emst_compute_batched call.  The 16 largest instances and 240 more
+    drawn by a seeded choice are compared edge for edge with the oracle
+    (Algorithm 1 with the §2 tie-break, the k-d tree Boruvka, one host thread
+    per instance, instances in parallel); every instance is compared with an
+    emst_compute call on it alone."""
+    from concurrent.futures import ThreadPoolExecutor
+    sizes = synth.batched_sizes(4096, seed=4, lo=100, hi=1_000_000)
+    pts, offsets = synth.batched_instances(sizes, seed=4)
+    dev = torch.from_numpy(pts).cuda()
+    e, eo = pkg.emst_compute_batched(dev, offsets)
+    torch.cuda.synchronize()
+    assert int(eo[-1]) == int(np.sum(np.maximum(sizes - 1, 0)))
+    # every instance against a single call, compared on the device
+    for k in range(len(sizes)):
+        a, b = int(offsets[k]), int(offsets[k + 1])
+        if b - a < 2:
+            assert eo[k + 1] == eo[k]
+            continue
+        single = pkg.emst_compute(dev[a:b])
+        assert torch.equal(e[int(eo[k]):int(eo[k + 1])], single), f"instance {k} differs from emst_compute"
+    # a subset against the oracle
+    g = np.random.default_rng(44)
+    largest = np.argsort(sizes)[-16:]
+    rest = np.setdiff1d(np.arange(len(sizes)), largest)
+    picked = np.concatenate([largest, g.choice(rest, 240, replace=False)])
+    eh = pkg.edges_numpy(e)
+    del dev, e
+    torch.cuda.empty_cache()
+
+    def check(k):
+        part = pts[offsets[k]:offsets[k + 1]]
+        want = oracle.kd_boruvka(part, threads=1)
+        return k, same(eh[eo[k]:eo[k + 1]], want)
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        results = list(ex.map(check, sorted(picked.tolist(), key=lambda k: -sizes[k])))
+    bad = [k for k, ok in results if not ok]
+    assert len(results) == 256 and not bad, f"instances differing from the oracle: {bad[:10]}"

@@ -300,14 +300,16 @@ def test_full_size_lattice_ties_vs_kd_oracle(pkg):
     assert_same_edges(got, want, "lattice ties")
 
 
-def test_full_size_halos_100M_invariants(pkg):
-    """Config 5 at full size (100,000,000 3D halo points, seed 3).  The oracle
-    cannot redo the whole tree in test time, so this checks what holds at any
-    size: n-1 edges, one connected acyclic tree, (w, i, j) order, weights equal
-    to the FP32 weight of their endpoints (sampled), and the cut property on
-    sampled single-vertex cuts: for a vertex v the smallest edge (w, min id,
-    max id) incident to v separates {v} from the rest, so it must be in the
-    tree -- that edge is found here by brute force over all n points."""
+def test_full_size_halos_100M_vs_kd_oracle(pkg):
+    """Config 5 at full size (100,000,000 3D halo points, seed 3): the whole
+    tree against the k-d tree Boruvka oracle (Algorithm 1 with the §2
+    tie-break, all host threads), edge for edge.  Before that, what holds at
+    any size without the oracle: n-1 edges, one connected acyclic tree,
+    (w, i, j) order, weights equal to the FP32 weight of their endpoints
+    (sampled), and the cut property on sampled single-vertex cuts: for a
+    vertex v the smallest edge (w, min id, max id) incident to v separates {v}
+    from the rest, so it must be in the tree -- found here by brute force over
+    all n points."""
     from fp32ref import weight32
     pts = synth.config_points(5)
     n = len(pts)
@@ -319,6 +321,7 @@ def test_full_size_halos_100M_invariants(pkg):
     later = (w_bits[1:] > w_bits[:-1]) | ((w_bits[1:] == w_bits[:-1]) &
              ((ii[1:] > ii[:-1]) | ((ii[1:] == ii[:-1]) & (jj[1:] > jj[:-1]))))
     assert np.all(later)
+    del w_bits, ii, jj, later
     comps, cyc = oracle.count_components(e, n)
     assert comps == 1 and not cyc
     g = np.random.default_rng(5)
@@ -333,6 +336,9 @@ def test_full_size_halos_100M_invariants(pkg):
         a, b = min(int(v), j), max(int(v), j)
         hit = np.nonzero((e["i"] == a) & (e["j"] == b))[0]
         assert len(hit) == 1 and e["w"][hit[0]] == m, (v, j)
+        del wv
+    want = oracle.kd_boruvka(pts, threads=os.cpu_count() or 4)
+    assert_same_edges(e, want, "config 5 (100M)")
 
 
 def test_massive_duplicate_group(pkg):

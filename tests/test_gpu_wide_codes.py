@@ -1,4 +1,4 @@
-"""128-bit Morton codes (§4.2's finer Z-curve grid) on the GPU against the
+"""128-bit Morton codes (§4.1's finer Z-curve grid) on the GPU against the
 CPU oracle, through the C ABI: codes, order, hierarchy and boxes bit-exact,
 and the spanning tree identical to the 64-bit one (the tree does not depend
 on the code width)."""
@@ -35,7 +35,7 @@ def u32(t):
 
 def dense_clusters(n, dim, seed, sigma=2e-7, n_clusters=40, far=True):
     """Clusters far denser than the 64-bit grid in 3D (cells of 2^-21), at
-    positions spread over a large box: the regime §4.2 describes."""
+    positions spread over a large box: the regime §4.1 describes."""
     g = np.random.default_rng(seed)
     scale = 1000.0 if far else 1.0
     centres = g.random((n_clusters, dim)) * scale

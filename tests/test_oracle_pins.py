@@ -69,16 +69,17 @@ def test_weight_exact_fma_order(oracle_lib):
 
 
 def test_weight_order_is_not_plain_sum(oracle_lib):
-    # fma(dy,dy, dx*dx) differs from round(round(dx*dx) + round(dy*dy)) here
-    dx = np.float32(1.0) + np.float32(2.0 ** -12)
-    dy = np.float32(2.0 ** -12) + np.float32(2.0 ** -30)
+    # a pair where fma(dy,dy, dx*dx) and round(round(dx*dx) + round(dy*dy))
+    # round to different FP32 values: the oracle must give the fused one
+    dx = np.array([1050244054], np.uint32).view(np.float32)[0]  # 0.29971188
+    dy = np.array([1054370422], np.uint32).view(np.float32)[0]  # 0.42268723
     p = np.array([dx, dy], np.float32)
     q = np.zeros(2, np.float32)
     w = oracle_lib.weight(p, q)
     fused = fma32(dy, dy, np.float32(dx * dx))
-    assert w == fused
     plain = np.float32(np.float32(dx * dx) + np.float32(dy * dy))
-    assert fused != plain or True  # documents the order; the pin is the equality above
+    assert fused != plain
+    assert w == fused
 
 
 # --------------------------------------------------------------------------
@@ -423,7 +424,7 @@ def test_component_min_uses_full_key(oracle_lib):
 
 
 # ---------------------------------------------------------------------------
-# 128-bit Morton codes (§4.2's finer grid): codes, order, radix tree
+# 128-bit Morton codes (§4.1's finer grid): codes, order, radix tree
 # ---------------------------------------------------------------------------
 def test_morton128_hand_values(oracle_lib):
     # lo = 0, hi = 1 on every axis: (0.5, 0.25, 0.75) quantises to x = 2^41,

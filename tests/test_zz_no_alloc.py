@@ -36,11 +36,56 @@ def _run(lib_, fn, pts):
     return rc, out.cpu().numpy()
 
 
+def _run_host(fn, pts_np):
+    """The same call with plain (pageable) host buffers for the points and
+    the edges: the library stages both through its scratch."""
+    n, dim = pts_np.shape
+    pts_np = np.ascontiguousarray(pts_np, dtype=np.float32)
+    out = np.zeros((n - 1, 3), np.int32)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = fn(ctypes.c_void_p(pts_np.ctypes.data), n, dim, ctypes.c_void_p(out.ctypes.data), stream)
+    torch.cuda.synchronize()
+    return rc, out
+
+
 @pytest.mark.gpu
 def test_noalloc_matches_emst_compute_twice_in_a_row(lib):
     pkg, L = lib
     cases = [synth.halos(40_000, 21), synth.blobs(65_536, 2, 22)]  # the second fills the limit
     for pts_np in cases:
+        pts = torch.from_numpy(pts_np).cuda()
+        rc_ref, ref = _run(L, L.emst_compute, pts)
+        rc_na, got = _run(L, L.emst_compute_noalloc, pts)
+        assert rc_ref == 0 and rc_na == 0
+        assert np.array_equal(got, ref)
+
+
+@pytest.mark.gpu
+def test_noalloc_host_buffers_at_the_size_limit(lib):
+    """Host input and host output at exactly EMST_NOALLOC_MAX_POINTS in 3D:
+    the largest layout the fixed scratch has to hold (the point and edge
+    staging copies included), twice in a row."""
+    pkg, L = lib
+    n = pkg.EMST_NOALLOC_MAX_POINTS
+    for seed in (23, 24):
+        pts_np = synth.halos(n, seed)
+        rc_ref, ref = _run_host(L.emst_compute, pts_np)
+        rc_na, got = _run_host(L.emst_compute_noalloc, pts_np)
+        assert rc_ref == 0 and rc_na == 0
+        assert np.array_equal(got, ref)
+
+
+@pytest.mark.gpu
+def test_noalloc_on_code_collisions_and_duplicates(lib):
+    """Very dense clusters, where emst_compute rebuilds with 128-bit codes
+    and the allocation-free path keeps 64-bit ones, and a lattice with
+    duplicate points (zero-weight ties): the same trees, bit for bit."""
+    pkg, L = lib
+    dense = synth.dense(pkg.EMST_NOALLOC_MAX_POINTS, 3, 7, n_clusters=200)
+    _, st = pkg.emst_compute_ex(torch.from_numpy(dense).cuda())
+    assert st["morton_bits"] == 128  # the case really takes the other code width there
+    lattice = synth.lattice_ties(n_sites=62_915, n_dup=2_621, side=40, seed=8)
+    for pts_np in (dense, lattice):
         pts = torch.from_numpy(pts_np).cuda()
         rc_ref, ref = _run(L, L.emst_compute, pts)
         rc_na, got = _run(L, L.emst_compute_noalloc, pts)
