@@ -32,11 +32,11 @@ sys.path.insert(0, ROOT)
 METRIC = "EMST Mpoints/s at 37M 3D clustered, plain vs learned-radius; % HBM roofline"
 WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member counts m^-1.9 on "
             "[10, 1e5], c = 5, r_vir = 0.01 (m/1e5)^(1/3)), 20% uniform, unit box, seed 2")
-# DRAM bytes (read + write) per k_traverse launch on this workload: the average
-# over one call's 11 launches of an ncu capture of this command
-# (--metrics dram__bytes_read.sum,dram__bytes_write.sum; profiles/k_traverse_dram_halos_37M.md).
-# Set back to None whenever the traversal kernel changes.
-TRAVERSE_DRAM_BYTES_PER_LAUNCH = 2585.68e6
+# DRAM bytes (read + write) per launch of the traversal kernel on this
+# workload, averaged over one call's launches, from an ncu capture
+# (--metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none);
+# None until a capture of the kernel as it is now exists.
+TRAVERSE_DRAM_BYTES_PER_LAUNCH = None
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")
 
@@ -49,8 +49,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=37_000_000)
     ap.add_argument("--seed", type=int, default=2)
-    ap.add_argument("--cpu-sample", type=int, default=10_000_000,
-                    help="points in the oracle's bounded sample (about 10 s on 16 host cores)")
+    ap.add_argument("--cpu-sample", type=int, default=3_000_000,
+                    help="reference arm: points per step in the oracle's spatial-window sample")
+    ap.add_argument("--cpu-full", type=int, default=1,
+                    help="cpu_baseline: 1 = the oracle on the whole workload (all host threads)")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-batched-summary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="halos37M",
@@ -139,12 +143,33 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traversal_algorithmic_bytes(n: int) -> float:
-    """Bytes one traversal launch must move at least: per query point its
-    record (16 B), label (4), bound (4), the component's best so far (8), its
-    result (8) and the component minimum atomic (8); plus every internal node
-    record once (64 B): the early rounds touch essentially the whole tree."""
-    return n * (16 + 4 + 4 + 8 + 8 + 8) + (n - 1) * 64.0
+# Algorithmic bytes of one traversal launch (Algorithm 2 over every point), by
+# what the method must read or write at least once:
+#  round 0 (every label is the point's own index, every query searches):
+#    per query 48 B -- its point (16), label (4), component bound (4), the
+#    component's best so far (8), its result (8), the component-minimum
+#    atomic (8) -- and per distinct internal node visited its 64-B record;
+#  later rounds: per point 32 B to decide whether to search at all -- label
+#    (4), component bound (4) and best so far (8), its previous result (8),
+#    its new result (8) -- plus per query that searches 28 B -- its point
+#    (16), its previous neighbour's label (4), the atomic (8) -- and per
+#    distinct internal node visited 72 B: the record (64) and its child
+#    labels (8).
+BYTES_FIRST_QUERY = 48
+BYTES_POINT = 32
+BYTES_SEARCH = 28
+BYTES_RECORD_FIRST = 64
+BYTES_RECORD = 72
+
+
+def traversal_round_bytes(n: int, queries, distinct):
+    out = []
+    for r, (q, d) in enumerate(zip(queries, distinct)):
+        if r == 0:
+            out.append(float(q * BYTES_FIRST_QUERY + d * BYTES_RECORD_FIRST))
+        else:
+            out.append(float(n * BYTES_POINT + q * BYTES_SEARCH + d * BYTES_RECORD))
+    return out
 
 
 def cpu_oracle_run(pts_sample, threads):
@@ -165,8 +190,29 @@ def workload_name(n: int, seed: int) -> str:
     return f"{n:,} FP32 3D points of the same halo generator (seed {seed})"
 
 
+def config_of(n: int, seed: int) -> dict:
+    """The workload, the same for both arms of the benchmark."""
+    return {"workload": workload_name(n, seed), "n": n, "dim": 3,
+            "l2": "inputs and working set larger than L2 (no flush between steps)"}
+
+
+def window_sample(pts, m, g):
+    """A spatial window of the point set: the points inside a sub-cube of the
+    unit box expected to hold about m of them, at a seeded random place.
+    Unlike a random subsample it keeps the set's local density and
+    clustering, so the oracle's rate on it stands for its rate on the whole
+    set."""
+    n = len(pts)
+    side = min(1.0, (m / n) ** (1.0 / 3.0))
+    o = g.random(3) * (1.0 - side)
+    inside = np.all((pts >= o) & (pts < o + side), axis=1)
+    return np.ascontiguousarray(pts[inside])
+
+
 def run_reference(args, rank, world):
-    """The oracle as it stands, on the host cores, on a bounded sample."""
+    """The oracle as it stands, on the host cores: each step one spatial
+    window of the workload (about --cpu-sample points; the untimed warm-up
+    steps a tenth of that), all host threads."""
     if rank != 0:
         return
     import oracle
@@ -174,24 +220,25 @@ def run_reference(args, rank, world):
     pts = make_points(args.n, args.seed)
     g = np.random.default_rng(12345)
     threads = os.cpu_count() or 1
-    times = []
-    ns = min(args.cpu_sample, args.n)
+    done, secs = 0, 0.0
     for step in range(args.warmup + args.steps):
-        sample = pts[np.sort(g.choice(len(pts), ns, replace=False))]
+        m = args.cpu_sample if step >= args.warmup else max(args.cpu_sample // 10, 1000)
+        sample = window_sample(pts, m, g)
         dt = cpu_oracle_run(sample, threads)
         if step >= args.warmup:
-            times.append(dt)
-    t = float(np.mean(times))
-    value = ns / t / 1e6
-    sample_desc = (f"random subsample of {ns} of the {args.n} points per step (k-d tree Boruvka, "
-                   f"{threads} threads)")
+            done += len(sample)
+            secs += dt
+    value = done / secs / 1e6
+    sample_desc = (f"per step the points of a seeded random sub-cube of the unit box holding about "
+                   f"{args.cpu_sample:,} of the {args.n:,} points (same density and clustering); "
+                   f"k-d tree Boruvka, {threads} threads; {done:,} points in {secs:.1f} s over "
+                   f"{args.steps} steps")
     line = {
         "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": workload_name(args.n, args.seed), "n": args.n, "dim": 3,
-                   "sample_points": ns},
+        "config": config_of(args.n, args.seed),
         "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": threads, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -493,124 +540,133 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
 
-    pts_np = make_points(args.n, args.seed + 1000 * rank if world > 1 else args.seed)
+    seed = args.seed + 1000 * rank if world > 1 else args.seed
+    pts_np = make_points(args.n, seed)
     n = len(pts_np)
     pts = torch.from_numpy(pts_np).to(dev)
     out = torch.empty((n - 1, 3), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    params = None
+    if not args.no_learned:
+        try:
+            from paper_2207_00514_gb300 import learned
+            params = learned.load(device=dev)
+        except FileNotFoundError:
+            params = None
 
-    def step(stats=False):
-        if stats:
-            return pkg.emst_compute_ex(pts, out_edges=out, stream=stream)[1]
-        pkg.emst_compute(pts, out_edges=out, stream=stream)
-        return None
+    def timed(call, steps):
+        """Run `call` (returning a stats dict) `steps` times between CUDA
+        events on the launching stream, after a barrier; max over ranks."""
+        shard.barrier(dev)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sts = [call() for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        shard.barrier(dev)
+        return shard.max_over_ranks(e0.elapsed_time(e1) / steps, device=dev), sts
 
+    plain = lambda: pkg.emst_compute_ex(pts, out_edges=out, stream=stream)[1]
     for _ in range(args.warmup):
-        step()
+        plain()
     torch.cuda.synchronize(dev)
 
     clocks = ClockSampler(local, args.clocks_dir)
     clocks.start()
     time.sleep(0.3)
-    shard.barrier(dev)
-    torch.cuda.synchronize(dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    launches = 0
-    trav_ms, trav_launches, rounds = 0.0, 0, []
-    phases = {"build": 0.0, "rounds": 0.0, "output": 0.0, "traverse": 0.0}
-    round_trav = None
-    for _ in range(args.steps):
-        st = step(stats=True)
-        launches += st["kernel_launches"]
-        trav_ms += st["traverse_ms"]
-        trav_launches += st["traverse_launches"]
-        rounds.append(st["rounds"])
-        for k in ("build", "rounds", "output", "traverse"):
-            phases[k] += st[k + "_ms"] / args.steps
-        round_trav = st["round_traverse_ms"]
-        comps = st["components_per_round"]
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    shard.barrier(dev)
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms, sts = timed(plain, args.steps)
     clk = clocks.stop()
-    ms = shard.max_over_ranks(ms, device=dev)
     value = world * n / (ms / 1e3) / 1e6
+    launches = sum(st["kernel_launches"] for st in sts)
+    rounds = sts[-1]["rounds"]
+    phases = {k: float(np.mean([st[k + "_ms"] for st in sts])) for k in ("build", "rounds", "output", "traverse")}
+    round_ms = [float(np.mean([st["round_traverse_ms"][r] for st in sts])) for r in range(rounds)]
+    ref_edges = out.clone()
+
+    # the learned-radius form (committed network) in its own timed region
+    learned_form = None
+    if params is not None:
+        lcall = lambda: pkg.emst_compute_ex(pts, out_edges=out, stream=stream, mlp_params=params)[1]
+        for _ in range(max(args.warmup, 1)):
+            lcall()
+        lms, lsts = timed(lcall, args.steps)
+        launches += sum(st["kernel_launches"] for st in lsts)
+        same = bool(torch.equal(out, ref_edges))
+        lst = lsts[-1]
+        learned_form = {"value": world * n / (lms / 1e3) / 1e6, "unit": "Mpoints/s", "ms_per_step": lms,
+                        "vs_plain": ms / lms, "identical_tree": same,
+                        "traverse_ms": round(float(np.mean([x["traverse_ms"] for x in lsts])), 3),
+                        "search_with_proposed_cutoffs_ms": round(float(np.mean([x["learned_search_ms"] for x in lsts])), 3),
+                        "rerun_fraction": lst["rerun_points"] / max(lst["queried_points"], 1)}
 
     # end to end through the C ABI with pinned host buffers (copies inside)
     e2e = None
     if not args.no_e2e:
         hpts = torch.from_numpy(pts_np).pin_memory()
         hout = torch.empty((n - 1, 3), dtype=torch.int32).pin_memory()
-        pkg.emst_compute(hpts, out_edges=hout, stream=stream)
-        torch.cuda.synchronize(dev)
-        shard.barrier(dev)
-        t0 = time.perf_counter()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            pkg.emst_compute(hpts, out_edges=hout, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ems = e0.elapsed_time(e1) / args.steps
-        ems = shard.max_over_ranks(ems, device=dev)
+        hcall = lambda: pkg.emst_compute_ex(hpts, out_edges=hout, stream=stream)[1]
+        hcall()
+        ems, ests = timed(hcall, args.steps)
+        launches += sum(st["kernel_launches"] for st in ests)
         e2e = {"value": world * n / (ems / 1e3) / 1e6, "unit": "Mpoints/s",
                "h2d_bytes_per_step": int(n * 3 * 4), "d2h_bytes_per_step": int((n - 1) * 12),
                "ms_per_step": ems}
 
-    # node visits per query (one extra, untimed call with counting on)
+    # per-round counts of the traversal (one extra, untimed call with counting on)
     vis = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, count_visits=True)[1]
     torch.cuda.synchronize(dev)
-    visits_per_query_round = vis["node_visits"] / float(n * max(vis["rounds"], 1))
-    # the learned-radius form on the same input (committed network), untimed
-    learned_form = None
-    try:
-        from paper_2207_00514_gb300 import learned
-        params = learned.load(device=dev)
-        for _ in range(2):
-            lst = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, mlp_params=params)[1]
-        torch.cuda.synchronize(dev)
-        learned_form = {"total_ms": round(lst["total_ms"], 3), "traverse_ms": round(lst["traverse_ms"], 3),
-                        "search_with_proposed_cutoffs_ms": round(lst["learned_search_ms"], 3),
-                        "rerun_fraction": lst["rerun_points"] / max(lst["queried_points"], 1),
-                        "mpoints_per_s": n / lst["total_ms"] / 1e3}
-    except FileNotFoundError:
-        learned_form = None
-    # other leaf chunk sizes, untimed, for comparison
-    leaf_sweep = {}
-    for leaf in (2, 4, 8):
-        lv = pkg.emst_compute_ex(pts, out_edges=out, stream=stream, leaf_size=leaf)[1]
-        torch.cuda.synchronize(dev)
-        leaf_sweep[str(leaf)] = {"total_ms": round(lv["total_ms"], 3), "traverse_ms": round(lv["traverse_ms"], 3)}
-
+    same_counted = bool(torch.equal(out, ref_edges))
     peak, peak_kind = measured_peaks()
-    avg_trav = trav_ms / max(trav_launches, 1)
-    alg = traversal_algorithmic_bytes(n)
-    achieved = alg / (avg_trav / 1e3) / 1e9 if avg_trav > 0 else 0.0
-    # DRAM bytes per k_traverse launch from an ncu capture of this workload
-    # (profiles/k_traverse_dram_halos_37M.md); None until one is taken for the
-    # kernel as it is now.
+    rb = traversal_round_bytes(n, vis["round_queries"], vis["round_distinct_nodes"])
+    rr = min(len(rb), len(round_ms))
+    tot_bytes, tot_ms = sum(rb[:rr]), sum(round_ms[:rr])
+    achieved = tot_bytes / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
+    per_round = {
+        "ms": [round(x, 4) for x in round_ms[:rr]],
+        "algorithmic_bytes": rb[:rr],
+        "achieved_gbs": [round(b / (t / 1e3) / 1e9, 1) if t > 0 else None for b, t in zip(rb, round_ms)],
+        "frac": [round(b / (t / 1e3) / 1e9 / peak, 4) if t > 0 else None for b, t in zip(rb, round_ms)],
+        "queries": vis["round_queries"][:rr],
+        "distinct_nodes": vis["round_distinct_nodes"][:rr],
+        "visits": vis["round_visits"][:rr],
+    }
     traffic = TRAVERSE_DRAM_BYTES_PER_LAUNCH if n == 37_000_000 else None
-    roofline = {"bound": "hbm", "kernel": "k_traverse (Algorithm 2 queries)", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs copy)" if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "avg_launch_ms": avg_trav, "launches": trav_launches,
-                "algorithmic_bytes_per_launch": alg}
+    roofline = {"bound": "hbm", "kernel": "k_traverse_queue (Algorithm 2 queries, persistent work queue)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "peak_kind": (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs copy)" if peak_kind == "measured"
+                              else "fallback 6.8 TB/s"),
+                "avg_launch_ms": tot_ms / max(rr, 1), "launches": rr,
+                "algorithmic_bytes_per_launch": tot_bytes / max(rr, 1),
+                "bytes_model": (f"round 0: {BYTES_FIRST_QUERY} B per query + {BYTES_RECORD_FIRST} B per distinct "
+                                f"internal node visited; later rounds: {BYTES_POINT} B per point + "
+                                f"{BYTES_SEARCH} B per query that searches + {BYTES_RECORD} B per distinct "
+                                "internal node visited (counted by an instrumented call); time = the "
+                                "round's traversal CUDA events in the timed calls"),
+                "per_round": per_round}
+
+    # the batched form (4,096 instances), one call, against one call per instance
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched_summary:
+        batched = batched_summary(args, pkg, torch, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        g = np.random.default_rng(12345)
-        ns = min(args.cpu_sample, n)
-        sample = pts_np[np.sort(g.choice(n, ns, replace=False))]
         threads = os.cpu_count() or 1
-        dt = cpu_oracle_run(sample, threads)
-        cpu = {"value": ns / dt / 1e6, "unit": "Mpoints/s", "cores": threads, "kind": "oracle",
-               "sample": f"random subsample of {ns} of the {n} points, k-d tree Boruvka, {threads} threads, {dt:.1f} s"}
+        if args.cpu_full:
+            dt = cpu_oracle_run(pts_np, threads)
+            cpu = {"value": n / dt / 1e6, "unit": "Mpoints/s", "cores": threads, "kind": "oracle",
+                   "sample": f"the whole workload ({n:,} points), k-d tree Boruvka, {threads} threads, {dt:.1f} s"}
+        else:
+            g = np.random.default_rng(12345)
+            sample = window_sample(pts_np, args.cpu_sample, g)
+            dt = cpu_oracle_run(sample, threads)
+            cpu = {"value": len(sample) / dt / 1e6, "unit": "Mpoints/s", "cores": threads, "kind": "oracle",
+                   "sample": f"a spatial window of {len(sample):,} points, k-d tree Boruvka, {threads} threads, {dt:.1f} s"}
 
     if rank == 0:
         line = {
@@ -618,18 +674,16 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "dim": 3, "form": "plain",
-                       "inputs": "resident in HBM; working set ~6 GB and input 444 MB, both larger than L2 (no flush)",
-                       "parallelism": f"{world} independent replica(s)" if world > 1 else "1 GPU",
-                       "rounds": rounds[-1] if rounds else None,
-                       "phases_ms": {k: round(v, 3) for k, v in phases.items()},
-                       "round_traverse_ms": [round(x, 3) for x in (round_trav or [])],
-                       "components_per_round": comps,
-                       "node_visits_per_query_per_round": round(visits_per_query_round, 2),
-                       "leaf_size": 1,
-                       "learned_radius_form_untimed": learned_form,
-                       "other_leaf_sizes_untimed": leaf_sweep,
-                       "mfeatures_per_s": value * 3},
+            "config": config_of(args.n, args.seed),
+            "form": "plain",
+            "parallelism": f"{world} independent replica(s)" if world > 1 else "1 GPU",
+            "detail": {"rounds": rounds, "phases_ms": {k: round(v, 3) for k, v in phases.items()},
+                       "components_per_round": sts[-1]["components_per_round"],
+                       "node_visits_per_query_per_round": round(vis["node_visits"] / float(n * max(vis["rounds"], 1)), 2),
+                       "counted_call_identical_tree": same_counted,
+                       "mfeatures_per_s": value * 3, "leaf_size": 1},
+            "learned_form": learned_form,
+            "batched_form": batched,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -640,6 +694,45 @@ def main():
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def batched_summary(args, pkg, torch, dev, stream):
+    """The batched workload (4,096 independent 3D instances, sizes
+    log-uniform in [100, 1e6], seed 4) in one emst_compute_batched call,
+    against one emst_compute call per instance on the same device-resident
+    points (identical output checked); CUDA events on the stream."""
+    import synth
+    sizes = synth.batched_sizes(args.instances, seed=4, lo=100, hi=1_000_000)
+    pts_np, offs = synth.batched_instances(sizes, seed=4, workers=os.cpu_count() or 4)
+    pts = torch.from_numpy(pts_np).to(dev)
+    del pts_np
+    pkg.emst_compute_batched(pts, offs, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        eb, eo = pkg.emst_compute_batched(pts, offs, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    singles = []
+    for k in range(len(sizes)):
+        a, b = int(offs[k]), int(offs[k + 1])
+        singles.append(pkg.emst_compute(pts[a:b], stream=stream) if b - a > 1 else None)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_seq = e0.elapsed_time(e1)
+    same = all(s is None or torch.equal(eb[int(eo[k]):int(eo[k + 1])], s) for k, s in enumerate(singles))
+    npts = int(offs[-1])
+    del pts, eb, singles
+    torch.cuda.empty_cache()
+    return {"workload": f"{len(sizes):,} instances, sizes log-uniform [100, 1e6] (seed 4), each 20 "
+                        "Gaussian blobs (sigma log-U[1e-3, 5e-2]) + 10% uniform",
+            "points": npts, "ms": ms, "mpoints_per_s": npts / ms / 1e3,
+            "one_call_per_instance_ms": ms_seq, "speedup_over_one_call_per_instance": ms_seq / ms,
+            "identical_output": same}
 
 
 if __name__ == "__main__":

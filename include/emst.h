@@ -95,12 +95,18 @@ typedef struct emst_options {
                                  8-pass sort) or 0 = automatic (the default): 64, rebuilt with
                                  128 when more than n/64 distinct points share their curve
                                  predecessor's 64-bit code.  The tree is the same either way. */
-  int32_t reserved[6];
+  int32_t traversal;          /* the Algorithm 2 kernel: 0 = default (the persistent
+                                 work-queue kernel where it applies), 1 = one thread per
+                                 point, 2 = persistent work queue (plain rounds on one-point
+                                 leaves; other forms fall back to one thread per point).
+                                 The tree is the same either way. */
+  int32_t reserved[5];
 } emst_options;
 
 #define EMST_MRD_MAX_K 32
 
-/* Per-call statistics filled by emst_compute_ex when `stats` is not NULL. */
+/* Per-call statistics filled by emst_compute_ex when `stats` is not NULL
+ * (struct_size must be at least sizeof(emst_stats), else EMST_ERR_INVALID_ARG). */
 typedef struct emst_stats {
   int32_t struct_size;   /* set by the caller: sizeof(emst_stats) */
   int32_t rounds;        /* Boruvka rounds run */
@@ -126,6 +132,11 @@ typedef struct emst_stats {
                               64-bit codes when they were built (automatic or 64), else of
                               the 128-bit ones */
   int64_t reserved[1];
+  /* count_visits = 1 only (else 0), per round of the plain form: */
+  int64_t round_visits[40];   /* internal-node visits of the round's searches */
+  int64_t round_queries[40];  /* queries that searched (the others were skipped by their
+                                 lower bound before any node visit) */
+  int64_t round_distinct_nodes[40]; /* distinct internal nodes those searches visited */
 } emst_stats;
 
 /* EMST of n points (§3, Fig. 3 end to end).

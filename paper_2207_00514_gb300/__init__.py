@@ -77,7 +77,8 @@ class _Options(ctypes.Structure):
                 ("carried_radius", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("count_visits", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("mlp_params", ctypes.c_void_p), ("mrd_k", ctypes.c_int32),
-                ("morton_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("morton_bits", ctypes.c_int32), ("traversal", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class _Stats(ctypes.Structure):
@@ -90,7 +91,9 @@ class _Stats(ctypes.Structure):
                 ("reserved1", ctypes.c_int32), ("round_traverse_ms", ctypes.c_double * 40),
                 ("queried_points", ctypes.c_int64), ("rerun_points", ctypes.c_int64),
                 ("learned_search_ms", ctypes.c_double), ("core_ms", ctypes.c_double),
-                ("code_collisions", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1)]
+                ("code_collisions", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1),
+                ("round_visits", ctypes.c_int64 * 40), ("round_queries", ctypes.c_int64 * 40),
+                ("round_distinct_nodes", ctypes.c_int64 * 40)]
 
 
 _lock = threading.Lock()
@@ -237,9 +240,10 @@ def emst_compute_noalloc(points, out_edges=None, stream=None):
 
 def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_radius=True,
                     use_graph=False, count_visits=False, leaf_size=0, mlp_params=None, mrd_k=0,
-                    morton_bits=0):
+                    morton_bits=0, traversal=0):
     """emst_compute with options; returns (edges, stats dict).  mrd_k >= 2:
-    the mutual-reachability MST (squared MRD weights)."""
+    the mutual-reachability MST (squared MRD weights).  traversal: 0 default,
+    1 one thread per point, 2 persistent work queue."""
     n, dim = _check_points(points)
     out_edges = _edges_out(n, points, out_edges)
     opt = _Options()
@@ -251,6 +255,7 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
     opt.leaf_size = int(leaf_size)
     opt.mrd_k = int(mrd_k)
     opt.morton_bits = int(morton_bits)
+    opt.traversal = int(traversal)
     if mlp_params is not None:
         if mlp_params.dtype != _torch().float32 or mlp_params.numel() != EMST_MLP_PARAMS:
             raise ValueError(f"mlp_params must hold {EMST_MLP_PARAMS} float32 values")
@@ -270,7 +275,11 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
                  components_per_round=[int(st.components_per_round[k]) for k in range(min(st.rounds, 40))],
                  queried_points=st.queried_points, rerun_points=st.rerun_points,
                  learned_search_ms=st.learned_search_ms, core_ms=st.core_ms,
-                 morton_bits=st.morton_bits, code_collisions=st.code_collisions)
+                 morton_bits=st.morton_bits, code_collisions=st.code_collisions,
+                 round_visits=[int(st.round_visits[k]) for k in range(min(st.rounds, 40))],
+                 round_queries=[int(st.round_queries[k]) for k in range(min(st.rounds, 40))],
+                 round_distinct_nodes=[int(st.round_distinct_nodes[k])
+                                       for k in range(min(st.rounds, 40))])
     return out_edges, stats
 
 

@@ -54,6 +54,20 @@ bool device_accessible(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+#ifndef EMST_MAPPED_HOST
+#define EMST_MAPPED_HOST 1
+#endif
+void *mapped_host(const void *p) {
+  if (!EMST_MAPPED_HOST || !p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost) return nullptr;
+  return a.devicePointer;
+}
+
 int sm_count() {
   static int cached[64] = {0};
   int dev = 0;
@@ -168,6 +182,7 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
     P.mlp = c.take<float>(EMST_MLP_PARAMS);
   }
   if (P.want_logging) P.log_count = c.take<unsigned long long>(1);
+  P.seen = P.want_count ? c.take<uint32_t>((nc - 1 + 31) / 32) : nullptr;
   P.core2 = P.want_mrd ? c.take<float>(n) : nullptr;
   P.wide_hi = P.wide || P.auto_wide ? c.take<uint64_t>(n) : nullptr;
   P.wide_lo = P.wide || P.auto_wide ? c.take<uint64_t>(n) : nullptr;
@@ -383,11 +398,12 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   if (expected > 0 && !out && !skip_output) return EMST_ERR_INVALID_ARG;
   if (stats) {
     int32_t sz = stats->struct_size;
+    if (sz < (int32_t)sizeof(emst_stats)) return EMST_ERR_INVALID_ARG;
     std::memset(stats, 0, sizeof(emst_stats));
     stats->struct_size = sz;
   }
   if (n == 0) return EMST_OK;
-  int block = 0, carried = 1, count = 0, leaf_req = 0, mrd_k = 0, morton_bits = 0;
+  int block = 0, carried = 1, count = 0, leaf_req = 0, mrd_k = 0, morton_bits = 0, traversal = 0;
   const float *mlp_params = nullptr;
   if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
     block = opt->block_size;
@@ -399,6 +415,8 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     if (mrd_k < 0 || mrd_k > EMST_MRD_MAX_K || (mrd_k >= 2 && (mlp_params || n < mrd_k)))
       return EMST_ERR_INVALID_ARG;
     morton_bits = opt->morton_bits;
+    traversal = opt->traversal;
+    if (traversal < 0 || traversal > 2) return EMST_ERR_INVALID_ARG;
     if (morton_bits != 0 && morton_bits != 64 && morton_bits != 128) return EMST_ERR_INVALID_ARG;
     if (leaf_req < 0 || leaf_req > 16 || (leaf_req & (leaf_req - 1)) != 0) return EMST_ERR_INVALID_ARG;
     if (block != 0 && (block < 64 || block > kTraverseMaxBlock || block % 32 != 0))
@@ -413,6 +431,10 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   if (get_pool(dev, &pool) != cudaSuccess) return EMST_ERR_CUDA;
   const bool pts_dev = device_accessible(points);
   const bool out_dev = expected == 0 || skip_output || device_accessible(out);
+  // pinned host buffers are read / written in place by the first and last
+  // passes (no separate copies); pageable ones are staged through scratch
+  const float *pts_map = pts_dev ? nullptr : static_cast<const float *>(mapped_host(points));
+  emst_edge *out_map = out_dev ? nullptr : static_cast<emst_edge *>(mapped_host(out));
   const bool learned = mlp_params != nullptr;
   const bool logging = ex && ex->log_feat;
 
@@ -431,6 +453,8 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   P.want_mrd = mrd_k >= 2 && !offsets && n >= 2;
   P.wide = morton_bits == 128 && !offsets;
   P.auto_wide = morton_bits == 0 && !offsets;
+  P.persistent = traversal != 1;
+  P.want_count = count != 0;
   if (logging) {
     P.log_feat = ex->log_feat;
     P.log_target = ex->log_target;
@@ -438,9 +462,10 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     P.log_every = ex->log_every < 1 ? 1 : ex->log_every;
   }
   int64_t reruns = 0;
-  const size_t need = layout(P, nullptr, !pts_dev, !out_dev);
+  const size_t need = layout(P, nullptr, !pts_dev, !out_dev && !out_map);
   char *base = nullptr;
-  uint32_t host_counters[33] = {0};
+  uint32_t host_counters[40] = {0};
+  uint64_t prev_visits = 0, prev_queries = 0, prev_distinct = 0;
   Timer tm;
   int rounds = 0;
   cudaEvent_t tev[2 * 40];
@@ -451,10 +476,11 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     cudaGetLastError();
     return EMST_ERR_OOM;
   }
-  layout(P, base, !pts_dev, !out_dev);
+  layout(P, base, !pts_dev, !out_dev && !out_map);
   if (stats) tm.start(stream);
   CU(cudaMemsetAsync(P.counters, 0, sizeof(uint32_t) * 64, stream));
-  if (!pts_dev)
+  if (pts_map) P.points_mapped = pts_map;  // copied by the scene-box pass
+  else if (!pts_dev)
     CU(cudaMemcpyAsync((void *)P.points, points, sizeof(float) * (size_t)n * dim,
                        cudaMemcpyHostToDevice, stream));
   if (num_inst > 1)
@@ -464,6 +490,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     CU(cudaMemcpyAsync((void *)P.mlp, mlp_params, sizeof(float) * EMST_MLP_PARAMS,
                        cudaMemcpyDefault, stream));
   if (logging) CU(cudaMemsetAsync(P.log_count, 0, sizeof(unsigned long long), stream));
+  if (P.seen) CU(cudaMemsetAsync(P.seen, 0, sizeof(uint32_t) * (size_t)((P.nc - 1 + 31) / 32), stream));
   run_build(P);
   tm.mark(1, stream);
   // Non-finite input is reported before any round runs.
@@ -524,6 +551,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
         cudaEventRecord(tev[2 * rounds + 1], stream);
         n_tev = rounds + 1;
       }
+      if (count) launch_count_seen(P);
       launch_reduce(P);
       launch_merge(P);
       CU(cudaPeekAtLastError());  // a launch that failed must not read as a round without edges
@@ -532,16 +560,25 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
       CU(cudaStreamSynchronize(stream));
       if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
       if (learned) reruns += host_counters[13];
+      if (count && stats && rounds < 40) {
+        auto u64 = [&](int k) { return (uint64_t)host_counters[k] | ((uint64_t)host_counters[k + 1] << 32); };
+        stats->round_visits[rounds] = (int64_t)(u64(2) - prev_visits);
+        stats->round_queries[rounds] = (int64_t)(u64(34) - prev_queries);
+        stats->round_distinct_nodes[rounds] = (int64_t)(u64(38) - prev_distinct);
+        prev_visits = u64(2);
+        prev_queries = u64(34);
+        prev_distinct = u64(38);
+      }
       advance_round(P, (int64_t)host_counters[12]);
       if ((int64_t)host_counters[0] >= expected) { ++rounds; break; }
     }
     tm.mark(2, stream);
     if ((int64_t)host_counters[0] != expected) { rc = EMST_ERR_INTERNAL; goto done; }
     if (!skip_output) {
-      rc = run_output(P, out_dev ? out : P.out_stage, host_counters[11]);
+      rc = run_output(P, out_dev ? out : (out_map ? out_map : P.out_stage), host_counters[11]);
       if (rc != EMST_OK) goto done;
     }
-    if (!out_dev && !skip_output)
+    if (!out_dev && !out_map && !skip_output)
       CU(cudaMemcpyAsync(out, P.out_stage, sizeof(emst_edge) * (size_t)expected,
                          cudaMemcpyDeviceToHost, stream));
   } else {

@@ -11,10 +11,14 @@ constexpr int kBlock = 256;
 // A1. Scene box: per-dimension min / max of all coordinates, plus a flag for
 // any non-finite coordinate.  box[0..2] = ordered min, box[3..5] = ordered max.
 // ---------------------------------------------------------------------------
-template <int DIM>
+// COPY: the points are read from pinned host memory through its device
+// mapping and written to `copy` (device) on the way, so the host-to-device
+// transfer of a host input is this pass itself.
+template <int DIM, bool COPY>
 __global__ void __launch_bounds__(kBlock) k_scene_box(const float *__restrict__ pts, int64_t n,
                                                       uint32_t *__restrict__ box,
-                                                      uint32_t *__restrict__ status) {
+                                                      uint32_t *__restrict__ status,
+                                                      float *__restrict__ copy) {
   float lo[3] = {INFINITY, INFINITY, INFINITY};
   float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   bool bad = false;
@@ -22,7 +26,8 @@ __global__ void __launch_bounds__(kBlock) k_scene_box(const float *__restrict__ 
   auto take = [&](int64_t k) {
 #pragma unroll
     for (int q = 0; q < DIM; ++q) {
-      const float x = __ldg(pts + k * DIM + q);
+      const float x = COPY ? pts[k * DIM + q] : __ldg(pts + k * DIM + q);
+      if (COPY) copy[k * DIM + q] = x;
       if (!isfinite(x)) { bad = true; continue; }
       lo[q] = fminf(lo[q], x);
       hi[q] = fmaxf(hi[q], x);
@@ -68,10 +73,17 @@ void launch_scene_box(Problem &P) {
   int grid = sm_count() * 4;
   int64_t need = (P.n + kBlock - 1) / kBlock;
   if (need < grid) grid = (int)(need < 1 ? 1 : need);
-  if (P.dim == 3)
-    k_scene_box<3><<<grid, kBlock, 0, P.stream>>>(P.points, P.n, box, P.counters + 1);
-  else
-    k_scene_box<2><<<grid, kBlock, 0, P.stream>>>(P.points, P.n, box, P.counters + 1);
+  float *copy = const_cast<float *>(P.points);
+  if (P.points_mapped) {  // read the host input through its mapping, keep a device copy
+    if (P.dim == 3)
+      k_scene_box<3, true><<<grid, kBlock, 0, P.stream>>>(P.points_mapped, P.n, box, P.counters + 1, copy);
+    else
+      k_scene_box<2, true><<<grid, kBlock, 0, P.stream>>>(P.points_mapped, P.n, box, P.counters + 1, copy);
+  } else if (P.dim == 3) {
+    k_scene_box<3, false><<<grid, kBlock, 0, P.stream>>>(P.points, P.n, box, P.counters + 1, nullptr);
+  } else {
+    k_scene_box<2, false><<<grid, kBlock, 0, P.stream>>>(P.points, P.n, box, P.counters + 1, nullptr);
+  }
   P.launches += 2;
 }
 

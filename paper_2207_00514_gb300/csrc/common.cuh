@@ -186,6 +186,9 @@ struct Problem {
   bool auto_wide = false;            // set before layout(): 64-bit codes unless they leave more
                                      // than n/64 distinct points sharing a code (then 128)
   int64_t code_collisions = 0;       // that count, when measured
+  bool persistent = false;           // A7 by the persistent work-queue kernel
+  bool want_count = false;           // set before layout(): carve the visited-node bitmap
+  uint32_t *seen = nullptr;          // count runs: bitmap of the internal nodes visited this round
   bool ties = true;                  // the search needs its tie rule (a run of > 32 equal
                                      // codes exists; set after the build, true when unknown)
   const float *mlp = nullptr;
@@ -202,6 +205,8 @@ struct Problem {
   cudaStream_t stream = nullptr;
 
   const float *points = nullptr;  // n x dim, device
+  const float *points_mapped = nullptr;  // a pinned host input through its device mapping: the
+                                         // scene-box pass reads it and writes `points`
   float4 *pts = nullptr;          // n, curve order, .w = original index bits
   uint64_t *keys[2] = {nullptr, nullptr};
   uint32_t *vals[2] = {nullptr, nullptr};
@@ -251,7 +256,10 @@ struct Problem {
                                      // weight bits, [16..23] sort tile counters,
                                      // [12] next round's active components, [13] points
                                      // to rerun, [14..15] reruns / queries (learned radius),
-                                     // [24] scan tiles finished
+                                     // [24] scan tiles finished, [34..35] queries that
+                                     // searched (u64), [36..37] the work queue of the
+                                     // persistent traversal (u64), [38..39] distinct internal
+                                     // nodes visited (u64)
   uint32_t *sort_hist = nullptr;     // 8 x 256
   uint32_t *sort_lookback = nullptr; // tiles x 256
   int64_t sort_tiles = 0;
@@ -311,6 +319,9 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
 void launch_reduce(Problem &P);
 void launch_merge(Problem &P);
 void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
+// count runs: adds the bits of the visited-node bitmap to counters[38..39]
+// and clears it for the next round
+void launch_count_seen(Problem &P);
 // output
 void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i);
 void launch_edge_ties(Problem &P, int64_t m, int src);
@@ -327,6 +338,9 @@ void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge 
 
 // api.cu: helpers of the orchestration
 bool device_accessible(const void *p);
+// The device address of page-locked (pinned) host memory that kernels can
+// read and write directly (over the chip-to-chip link), else nullptr.
+void *mapped_host(const void *p);
 // Streaming multiprocessors of the current device (queried once per device):
 // grid caps of grid-stride kernels are multiples of it.
 int sm_count();

@@ -514,10 +514,10 @@ __global__ void __launch_bounds__(128) k_log_samples(FeatArgs F, TravArgs T, int
   q.best = q.radius;
   q.bj = kInvalid;
   q.bid = kInvalid;
-  uint32_t st_node[kStackDepth];
-  float st_dist[kStackDepth];
+  LocalStack stk;
+  stk.init(nullptr, 0);
   unsigned long long nv = 0;
-  if (!explore<false, false, false>(q, start, T.nodes, T.nlabels, T.pts, T.labels, 1, F.n, st_node, st_dist, nv)) {
+  if (!explore<false, false, false>(q, start, T.nodes, T.nlabels, T.pts, T.labels, 1, F.n, stk, nv)) {
     atomicOr(T.status, kErrStack);
     return;
   }
@@ -630,6 +630,8 @@ void launch_log_samples(Problem &P, int round, bool carried) {
   T.n = P.n;
   T.status = P.counters + 1;
   T.visits = nullptr;
+  T.queries = nullptr;
+  T.seen = nullptr;
   T.pred_r = nullptr;
   T.r_used = nullptr;
   k_log_samples<<<grid_for(P.n, 128), 128, 0, P.stream>>>(feat_args(P, carried), T, round,

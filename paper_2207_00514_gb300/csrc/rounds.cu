@@ -244,19 +244,178 @@ void launch_upper_bounds(Problem &P) {
 }
 
 // One thread per point, or (list != nullptr) a grid-stride pass over the
-// listed points (the certification reruns of the learned radius).
+// listed points (the certification reruns of the learned radius).  Dynamic
+// shared memory: the stack rings, kRingSlots 8-byte slots per thread.
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
           bool FIRST, bool MRD, bool TIES = true>
 __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
+  extern __shared__ uint2 s_ring[];
+  uint2 *ring = s_ring + threadIdx.x;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (list) {
     const int64_t count = *list_count;
     for (int64_t t = gid; t < count; t += (int64_t)gridDim.x * blockDim.x)
-      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, __ldg(list + t));
+      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, __ldg(list + t), ring);
   } else if (gid < A.n) {
-    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, gid);
+    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, gid, ring);
   }
+}
+
+// ---------------------------------------------------------------------------
+// A7, persistent form: a resident grid whose warps take queries from a
+// global work queue (the curve positions in order, handed out in chunks of
+// kQueueChunk consecutive positions per warp, so the queries a warp holds
+// stay close on the curve and share node records in L1) and refill a lane as
+// soon as its search ends, instead of holding 32 queries until the longest
+// one finishes.  Each loop iteration: when at least kRefillLanes lanes are
+// idle (or all are), they take the next positions of the warp's chunk and
+// start them (a query skipped by its lower bound finishes at once and leaves
+// its lane idle); then every lane with a search in progress makes one node
+// visit (or pops).  Same per-query arithmetic as traverse_one, so the same
+// results.  One-point leaves, no learned cutoff, no mutual reachability.
+// ---------------------------------------------------------------------------
+#ifndef EMST_QUEUE_CHUNK
+#define EMST_QUEUE_CHUNK 64
+#endif
+#ifndef EMST_REFILL_LANES
+#define EMST_REFILL_LANES 8
+#endif
+#ifndef EMST_PERSIST_BLOCK
+#define EMST_PERSIST_BLOCK 128
+#endif
+#ifndef EMST_PERSIST_MIN_BLOCKS
+#define EMST_PERSIST_MIN_BLOCKS 12
+#endif
+#ifndef EMST_PERSIST_RING
+#define EMST_PERSIST_RING 8
+#endif
+constexpr int kQueueChunk = EMST_QUEUE_CHUNK;
+static_assert(kQueueChunk >= 32, "a refill takes at most 32 positions, from at most two chunks");
+constexpr int kRefillLanes = EMST_REFILL_LANES;
+constexpr int kPersistBlock = EMST_PERSIST_BLOCK;
+using PersistStack = StackOf<EMST_PERSIST_RING>::type;
+
+template <bool CARRIED, bool FIRST, bool TIES, bool COUNT>
+__global__ void __launch_bounds__(kPersistBlock, EMST_PERSIST_MIN_BLOCKS)
+    k_traverse_queue(TravArgs A, unsigned long long *queue) {
+  extern __shared__ uint2 s_ring[];
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t n = A.n;
+  PersistStack stk;
+  stk.init(s_ring + threadIdx.x, blockDim.x);
+  Query q;
+  uint32_t node = 0, i = 0;
+  float r0 = 0.0f;
+  bool live = false;
+  unsigned long long nvis = 0, nq = 0;
+  // this warp's current chunk [next, end) of curve positions (warp-uniform)
+  int64_t next = 0, end = 0;
+  bool drained = false;
+  while (true) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !live);
+    if (idle == 0xffffffffu && drained) break;
+    if (!drained && __popc(idle) >= (idle == 0xffffffffu ? 1 : kRefillLanes)) {
+      const int need = __popc(idle);
+      const int64_t avail = end - next;
+      int64_t fresh = 0;
+      if (avail < need) {
+        if (lane == 0) fresh = (int64_t)atomicAdd(queue, (unsigned long long)kQueueChunk);
+        fresh = __shfl_sync(0xffffffffu, fresh, 0);
+      }
+      if (!live) {
+        const int rank = __popc(idle & lt);
+        const int64_t t = rank < avail ? next + rank : fresh + (rank - avail);
+        if (t < n) {
+          i = (uint32_t)t;
+          uint32_t start;
+          live = start_query<CARRIED, false, true, false, false>(A, t, q, start, r0);
+          if (live) {
+            node = start;
+            stk.init(s_ring + threadIdx.x, blockDim.x);
+            if (COUNT) ++nq;
+          }
+        }
+      }
+      if (avail < need) {
+        next = fresh + (need - avail);
+        end = fresh + kQueueChunk;
+      } else {
+        next += need;
+      }
+      // chunks leave the queue in increasing order, so once this warp's next
+      // position is past the end no later chunk holds a query either
+      drained = next >= n;
+    }
+    if (live) {
+      if (COUNT) {
+        ++nvis;
+        if (A.seen) atomicOr(A.seen + (node >> 5), 1u << (node & 31));
+      }
+      bool overflow = false;
+      uint32_t nxt = visit<false, FIRST, false, TIES>(q, node, A.nodes, A.nlabels, A.pts, A.labels,
+                                                      1, n, stk, overflow, nullptr, A.ties);
+      if (overflow) atomicOr(A.status, kErrStack);
+      if (nxt == kInvalid && !overflow) nxt = pop_next(q, stk);
+      if (nxt == kInvalid || overflow) {
+        finish_query<true>(A, i, q, r0);
+        live = false;
+      } else {
+        node = nxt;
+      }
+    }
+  }
+  if (COUNT) {
+    const unsigned long long v = __reduce_add_sync(0xffffffffu, (unsigned)nvis);
+    const unsigned long long c = __reduce_add_sync(0xffffffffu, (unsigned)nq);
+    if (lane == 0) {
+      atomicAdd(A.visits, v);
+      atomicAdd(A.queries, c);
+    }
+  }
+}
+
+template <bool CARRIED, bool FIRST, bool TIES, bool COUNT>
+static void queue_launch(Problem &P, const TravArgs &A) {
+  static int blocks_per_sm[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t sm = sizeof(uint2) * (size_t)EMST_PERSIST_RING * kPersistBlock;
+  auto kern = k_traverse_queue<CARRIED, FIRST, TIES, COUNT>;
+  if (dev >= 0 && dev < 64 && blocks_per_sm[dev] == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kPersistBlock, sm) != cudaSuccess || b < 1) {
+      cudaGetLastError();
+      b = 1;
+    }
+    blocks_per_sm[dev] = b;
+  }
+  const int per_sm = (dev >= 0 && dev < 64) ? blocks_per_sm[dev] : 1;
+  // no more warps than there are chunks of queries
+  const int64_t warps_needed = (A.n + kQueueChunk - 1) / kQueueChunk;
+  int64_t g = (int64_t)sm_count() * per_sm;
+  const int64_t g_need = (warps_needed + kPersistBlock / 32 - 1) / (kPersistBlock / 32);
+  if (g > g_need) g = g_need;
+  if (g < 1) g = 1;
+  kern<<<(unsigned)g, kPersistBlock, sm, P.stream>>>(A, reinterpret_cast<unsigned long long *>(P.counters + 36));
+}
+
+static void launch_traverse_queue(Problem &P, const TravArgs &A, bool carried, bool first, bool count) {
+  cudaMemsetAsync(P.counters + 36, 0, sizeof(unsigned long long), P.stream);
+  const bool ties = P.ties;
+#define EMST_Q(C, F, T, K) queue_launch<C, F, T, K>(P, A)
+  if (count) {
+    if (carried) { if (ties) EMST_Q(true, false, true, true); else EMST_Q(true, false, false, true); }
+    else if (first) { if (ties) EMST_Q(false, true, true, true); else EMST_Q(false, true, false, true); }
+    else { if (ties) EMST_Q(false, false, true, true); else EMST_Q(false, false, false, true); }
+  } else {
+    if (carried) { if (ties) EMST_Q(true, false, true, false); else EMST_Q(true, false, false, false); }
+    else if (first) { if (ties) EMST_Q(false, true, true, false); else EMST_Q(false, true, false, false); }
+    else { if (ties) EMST_Q(false, false, true, false); else EMST_Q(false, false, false, false); }
+  }
+#undef EMST_Q
+  P.launches += 1;
 }
 
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
@@ -280,18 +439,26 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   A.n = P.n;
   A.status = P.counters + 1;
   A.visits = reinterpret_cast<unsigned long long *>(P.counters + 2);
+  A.queries = reinterpret_cast<unsigned long long *>(P.counters + 34);
+  A.seen = P.seen;
   A.pred_r = P.pred_r;
   A.r_used = P.r_used;
   // learned_pass: 0 = plain, 1 = with the proposed radii, 2 = rerun of the
   // listed points with the plain cutoff
+  // the persistent work-queue form serves the plain rounds on one-point leaves
+  if (P.persistent && seeded && !radius_in && learned_pass == 0 && !P.core2 && P.leaf == 1) {
+    launch_traverse_queue(P, A, carried, first, count);
+    return;
+  }
   const uint32_t *list = learned_pass == 2 ? P.rerun_list : nullptr;
   const uint32_t *list_count = learned_pass == 2 ? P.counters + 13 : nullptr;
   const int g = learned_pass == 2 ? sm_count() * 8 : grid_for(P.n, block);
+  const size_t sm = sizeof(uint2) * (size_t)kRingSlots * (size_t)block;
   cudaStream_t s = P.stream;
-#define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L, false, false><<<g, block, 0, s>>>(A, list, list_count)
-#define EMST_TRAV_FIRST(K, H) k_traverse<false, false, K, true, H, false, true, false><<<g, block, 0, s>>>(A, list, list_count)
-#define EMST_TRAV_MRD(C, K, H) k_traverse<C, false, K, true, H, false, false, true><<<g, block, 0, s>>>(A, list, list_count)
-#define EMST_TRAV_NOTIES(C, F, H) k_traverse<C, false, false, true, H, false, F, false, false><<<g, block, 0, s>>>(A, list, list_count)
+#define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L, false, false><<<g, block, sm, s>>>(A, list, list_count)
+#define EMST_TRAV_FIRST(K, H) k_traverse<false, false, K, true, H, false, true, false><<<g, block, sm, s>>>(A, list, list_count)
+#define EMST_TRAV_MRD(C, K, H) k_traverse<C, false, K, true, H, false, false, true><<<g, block, sm, s>>>(A, list, list_count)
+#define EMST_TRAV_NOTIES(C, F, H) k_traverse<C, false, false, true, H, false, F, false, false><<<g, block, sm, s>>>(A, list, list_count)
 #define EMST_TRAV(C, R, K, S, L)                       \
   do {                                                 \
     if (P.leaf > 1) EMST_TRAV2(C, R, K, S, true, L);   \
@@ -501,6 +668,29 @@ void advance_round(Problem &P, int64_t n_active) {
   P.active_list = P.next_list;
   P.next_list = t;
   P.n_active = n_active;
+}
+
+// Count runs only: the distinct internal nodes of this round's searches (the
+// bits of the visited bitmap), added to a 64-bit counter; the bitmap is
+// cleared for the next round.
+__global__ void __launch_bounds__(kBlock) k_count_seen(uint32_t *seen, int64_t words,
+                                                       unsigned long long *total) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned c = 0;
+  if (k < words) {
+    c = __popc(seen[k]);
+    seen[k] = 0u;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(total, (unsigned long long)c);
+}
+
+void launch_count_seen(Problem &P) {
+  if (!P.seen || P.nc < 2) return;
+  const int64_t words = (P.nc - 1 + 31) / 32;
+  k_count_seen<<<grid_for(words, kBlock), kBlock, 0, P.stream>>>(
+      P.seen, words, reinterpret_cast<unsigned long long *>(P.counters + 38));
+  P.launches += 1;
 }
 
 __global__ void k_fill_u32(uint32_t *p, uint32_t v, int64_t count) {

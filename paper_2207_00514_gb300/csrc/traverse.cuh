@@ -77,11 +77,6 @@ __device__ __forceinline__ void scan_chunk(Query &q, uint32_t c, float d1, int l
   }
 }
 
-// Depth-first search of the subtree of internal node `node`, whose own box
-// the caller has already accepted: test both children of every visited
-// record, scan accepted leaf chunks, descend into the nearer accepted
-// internal child and stack the farther one with its box distance (re-tested
-// when popped).
 // One node record in two 32-byte loads (the record is 64-byte aligned).
 __device__ __forceinline__ void load_record(const NodeRec *rec, float4 &a, float4 &b, float4 &c,
                                             uint4 &dd) {
@@ -93,6 +88,87 @@ __device__ __forceinline__ void load_record(const NodeRec *rec, float4 &a, float
       : "l"(reinterpret_cast<const char *>(rec) + 32));
 }
 
+// ---------------------------------------------------------------------------
+// The search stack of one query (Algorithm 2's stack of nodes still to
+// examine, each with the weight bound of its box, re-tested when popped).
+// An entry is one 8-byte (node, bound bits) pair.
+//  - LocalStack: every entry in a per-thread local array.
+//  - RingStack<K>: the top K entries in shared memory, a ring of K slots per
+//    thread stored slot-major (slot s of thread t at ring[s * stride + t]), so
+//    the lanes of a warp touch distinct banks whatever their depths and one
+//    warp-wide push or pop is one or two shared wavefronts instead of one L1
+//    sector per lane; deeper entries are spilled to the local array.
+// Both hold kStackDepth entries in all (the deepest possible path, see
+// traverse_one); push reports an overflow instead of writing past it.
+// ---------------------------------------------------------------------------
+struct LocalStack {
+  uint2 e[kStackDepth];
+  int sp;
+  __device__ __forceinline__ void init(uint2 *, int) { sp = 0; }
+  __device__ __forceinline__ bool push(uint32_t node, float d) {
+    if (sp >= kStackDepth) return false;
+    e[sp++] = make_uint2(node, __float_as_uint(d));
+    return true;
+  }
+  __device__ __forceinline__ bool pop(uint2 &x) {
+    if (sp == 0) return false;
+    x = e[--sp];
+    return true;
+  }
+};
+
+template <int K>
+struct RingStack {
+  static_assert(K > 0 && (K & (K - 1)) == 0, "ring size: a power of two");
+  uint2 *ring;   // this thread's slot 0 in shared memory
+  int stride;    // threads of the CTA
+  int sp;        // entries in all
+  int cnt;       // of those, in the ring (the newest cnt)
+  uint2 spill[kStackDepth];
+  __device__ __forceinline__ void init(uint2 *mine, int stride_) {
+    ring = mine;
+    stride = stride_;
+    sp = 0;
+    cnt = 0;
+  }
+  __device__ __forceinline__ bool push(uint32_t node, float d) {
+    if (sp >= kStackDepth) return false;
+    uint2 *slot = ring + (sp & (K - 1)) * stride;
+    if (cnt == K) spill[sp - K] = *slot;  // the oldest ring entry moves to local memory
+    else ++cnt;
+    *slot = make_uint2(node, __float_as_uint(d));
+    ++sp;
+    return true;
+  }
+  __device__ __forceinline__ bool pop(uint2 &x) {
+    if (sp == 0) return false;
+    --sp;
+    if (cnt > 0) {
+      --cnt;
+      x = ring[(sp & (K - 1)) * stride];
+    } else {
+      x = spill[sp];
+    }
+    return true;
+  }
+};
+
+// Shared-memory ring slots per thread of the classic traversal kernel (0 =
+// local stack only).
+#ifndef EMST_RING_SLOTS
+#define EMST_RING_SLOTS 8
+#endif
+constexpr int kRingSlots = EMST_RING_SLOTS;
+template <int K> struct StackOf { using type = RingStack<K>; };
+template <> struct StackOf<0> { using type = LocalStack; };
+using TravStack = StackOf<kRingSlots>::type;
+
+// One visit of internal node `node` of Algorithm 2, whose own box the caller
+// has already accepted: test both children from the node's record, scan
+// accepted leaf chunks, and return the nearer accepted internal child (the
+// farther one is pushed with its box bound), or kInvalid when no internal
+// child is accepted (the caller pops).  `overflow` is set if a push found
+// the stack full (cannot happen, see traverse_one).
 // FIRST: the first round, where every label is the point's own curve index,
 // so no internal child is single-component and the only one-point leaf to
 // skip is the query itself: no label load.
@@ -102,75 +178,101 @@ __device__ __forceinline__ void load_record(const NodeRec *rec, float4 &a, float
 // so max(core, box distance) <= cutoff  <=>  box distance <= cutoff.
 // TIES = false: the input has no large group of identical points (see the
 // tie rule below), so that check is compiled out.
-template <bool COUNT, bool CHUNKS, bool FIRST, bool MRD = false, bool TIES = true>
+template <bool CHUNKS, bool FIRST, bool MRD, bool TIES, class Stack>
+__device__ __forceinline__ uint32_t visit(Query &q, uint32_t node,
+                                          const NodeRec *__restrict__ nodes,
+                                          const uint2 *__restrict__ nlabels,
+                                          const float4 *__restrict__ pts,
+                                          const uint32_t *__restrict__ labels, int leaf,
+                                          int64_t n, Stack &stk, bool &overflow,
+                                          const float *__restrict__ core2, bool ties) {
+  float4 a, b, c;
+  uint4 dd;
+  load_record(nodes + node, a, b, c, dd);
+  uint2 lab;
+  if (FIRST) {
+    lab.x = (!CHUNKS && (dd.x & kLeafBit)) ? (dd.x & ~kLeafBit) : kInvalid;
+    lab.y = (!CHUNKS && (dd.y & kLeafBit)) ? (dd.y & ~kLeafBit) : kInvalid;
+  } else {
+    lab = __ldg(nlabels + node);
+  }
+  const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
+  const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
+  bool okL = (lab.x != q.me) && (dL <= q.radius);
+  bool okR = (lab.y != q.me) && (dR <= q.radius);
+  if (okL && (dd.x & kLeafBit)) {
+    scan_chunk<CHUNKS, MRD>(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels, core2);
+    okL = false;
+  }
+  if (okR && (dd.y & kLeafBit)) {
+    if (dR <= q.radius) scan_chunk<CHUNKS, MRD>(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels, core2);
+    okR = false;
+  }
+  okL = okL && dL <= q.radius;
+  okR = okR && dR <= q.radius;
+  // An internal child whose weight bound only ties the cutoff holds nothing
+  // better than the best so far unless it has a point with a smaller
+  // original id (dd.z / dd.w hold each child's smallest).  Without this a
+  // group of m identical points costs each of its queries a visit to all m,
+  // and so does a group at one equal distance from the query.  (Checked
+  // only when a tie occurs; a leaf resolves its own ties.)
+  // (the ids are read again in the rare tie case: kept live through the
+  // leaf scans above they cost the hot loop a register it does not have)
+  // Only when the input has a run of more than 32 equal codes (`ties`):
+  // otherwise no group of identical points is larger than that, a tie
+  // involves a few points at most and the check would only cost time.
+  const float lbL = MRD ? fmaxf(q.core, dL) : dL, lbR = MRD ? fmaxf(q.core, dR) : dR;
+  if (TIES && ties && q.bj != kInvalid && ((okL && lbL == q.radius) || (okR && lbR == q.radius))) {
+    if (q.bid == kInvalid) q.bid = __float_as_uint(pts[q.bj].w);  // loaded lazily
+    const uint2 mn = __ldg(reinterpret_cast<const uint2 *>(nodes + node) + 7);  // dd.z, dd.w
+    if (lbL == q.radius && mn.x >= q.bid) okL = false;
+    if (lbR == q.radius && mn.y >= q.bid) okR = false;
+  }
+  if (okL && okR) {
+    const bool left_first = dL <= dR;
+    if (!stk.push(left_first ? dd.y : dd.x, left_first ? dR : dL)) overflow = true;
+    return left_first ? dd.x : dd.y;
+  }
+  if (okL) return dd.x;
+  if (okR) return dd.y;
+  return kInvalid;
+}
+
+// The next stacked node whose bound is still within the cutoff (the cutoff
+// only shrinks, so entries above it are dropped), or kInvalid.
+template <class Stack>
+__device__ __forceinline__ uint32_t pop_next(const Query &q, Stack &stk) {
+  uint2 e;
+  while (stk.pop(e))
+    if (__uint_as_float(e.y) <= q.radius) return e.x;
+  return kInvalid;
+}
+
+// Depth-first search of the subtree of internal node `node`, whose own box
+// the caller has already accepted (Algorithm 2): visit, descend into the
+// nearer accepted child, pop when none.  COUNT: count the visits (nvis) and,
+// with a bitmap `seen` of the internal nodes, mark each node visited.
+// Returns false on a stack overflow.
+template <bool COUNT, bool CHUNKS, bool FIRST, bool MRD = false, bool TIES = true, class Stack>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
                                         const uint2 *__restrict__ nlabels,
                                         const float4 *__restrict__ pts,
                                         const uint32_t *__restrict__ labels, int leaf, int64_t n,
-                                        uint32_t *st_node, float *st_dist,
-                                        unsigned long long &nvis,
+                                        Stack &stk, unsigned long long &nvis,
                                         const float *__restrict__ core2 = nullptr,
-                                        bool ties = true) {
-  int sp = 0;
+                                        bool ties = true, uint32_t *seen = nullptr) {
+  bool overflow = false;
   while (true) {
-    if (COUNT) ++nvis;
-    float4 a, b, c;
-    uint4 dd;
-    load_record(nodes + node, a, b, c, dd);
-    uint2 lab;
-    if (FIRST) {
-      lab.x = (!CHUNKS && (dd.x & kLeafBit)) ? (dd.x & ~kLeafBit) : kInvalid;
-      lab.y = (!CHUNKS && (dd.y & kLeafBit)) ? (dd.y & ~kLeafBit) : kInvalid;
-    } else {
-      lab = __ldg(nlabels + node);
+    if (COUNT) {
+      ++nvis;
+      if (seen) atomicOr(seen + (node >> 5), 1u << (node & 31));
     }
-    const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
-    const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
-    bool okL = (lab.x != q.me) && (dL <= q.radius);
-    bool okR = (lab.y != q.me) && (dR <= q.radius);
-    if (okL && (dd.x & kLeafBit)) {
-      scan_chunk<CHUNKS, MRD>(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels, core2);
-      okL = false;
-    }
-    if (okR && (dd.y & kLeafBit)) {
-      if (dR <= q.radius) scan_chunk<CHUNKS, MRD>(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels, core2);
-      okR = false;
-    }
-    okL = okL && dL <= q.radius;
-    okR = okR && dR <= q.radius;
-    // An internal child whose weight bound only ties the cutoff holds nothing
-    // better than the best so far unless it has a point with a smaller
-    // original id (dd.z / dd.w hold each child's smallest).  Without this a
-    // group of m identical points costs each of its queries a visit to all m,
-    // and so does a group at one equal distance from the query.  (Checked
-    // only when a tie occurs; a leaf resolves its own ties.)
-    // (the ids are read again in the rare tie case: kept live through the
-    // leaf scans above they cost the hot loop a register it does not have)
-    // Only when the input has a run of more than 32 equal codes (`ties`):
-    // otherwise no group of identical points is larger than that, a tie
-    // involves a few points at most and the check would only cost time.
-    const float lbL = MRD ? fmaxf(q.core, dL) : dL, lbR = MRD ? fmaxf(q.core, dR) : dR;
-    if (TIES && ties && q.bj != kInvalid && ((okL && lbL == q.radius) || (okR && lbR == q.radius))) {
-      if (q.bid == kInvalid) q.bid = __float_as_uint(pts[q.bj].w);  // loaded lazily
-      const uint2 mn = __ldg(reinterpret_cast<const uint2 *>(nodes + node) + 7);  // dd.z, dd.w
-      if (lbL == q.radius && mn.x >= q.bid) okL = false;
-      if (lbR == q.radius && mn.y >= q.bid) okR = false;
-    }
-    if (okL && okR) {
-      if (sp >= kStackDepth) return false;
-      if (dL <= dR) { st_node[sp] = dd.y; st_dist[sp] = dR; node = dd.x; }
-      else { st_node[sp] = dd.x; st_dist[sp] = dL; node = dd.y; }
-      ++sp;
-      continue;
-    }
-    if (okL) { node = dd.x; continue; }
-    if (okR) { node = dd.y; continue; }
-    bool found = false;
-    while (sp > 0) {
-      --sp;
-      if (st_dist[sp] <= q.radius) { node = st_node[sp]; found = true; break; }
-    }
-    if (!found) return true;
+    uint32_t nxt = visit<CHUNKS, FIRST, MRD, TIES>(q, node, nodes, nlabels, pts, labels, leaf, n,
+                                                   stk, overflow, core2, ties);
+    if (overflow) return false;
+    if (nxt == kInvalid) nxt = pop_next(q, stk);
+    if (nxt == kInvalid) return true;
+    node = nxt;
   }
 }
 
@@ -220,34 +322,40 @@ struct TravArgs {
   uint64_t *comp_key;
   int64_t n;
   uint32_t *status;
-  unsigned long long *visits;
+  unsigned long long *visits;   // COUNT: node visits
+  unsigned long long *queries;  // COUNT: queries that searched (not skipped)
+  uint32_t *seen;               // COUNT: bitmap of the internal nodes visited
   const float *pred_r;  // LEARNED: proposed cutoff of each point
   float *r_used;        // LEARNED: cutoff each query was exact within (+inf: skipped)
 };
 
+// The first half of a query: its cutoff, and whether it needs a search at all.
+// Returns false when the query is already finished (its result written):
+// a one-point instance, a point whose lower bound exceeds its component's
+// cutoff, or (MRD) a core distance above the cutoff.  Otherwise q holds the
+// query, `start` the node to search from and r0 the cutoff the search is
+// exact within.
 // LEARNED also tightens the cutoff with the proposed radius pred_r[i] (any
 // value: exactness is restored afterwards by rerunning every point whose
 // cutoff fell below its component's found minimum) and records it in r_used.
 // MRD: the mutual reachability weights (§4.5); a query whose own core
 // distance lies above its cutoff finds nothing and is skipped.
-template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
-          bool FIRST = false, bool MRD = false, bool TIES = true>
-__device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
+template <bool CARRIED, bool RADIUS_IN, bool SEEDED, bool LEARNED, bool MRD>
+__device__ __forceinline__ bool start_query(const TravArgs &A, int64_t i, Query &q,
+                                            uint32_t &start, float &r0) {
   const float kInf = __int_as_float(0x7f800000);
-  const int64_t n = A.n;
   // Batched form: search only this point's instance (its subtree).
-  uint32_t start = 0u;
+  start = 0u;
   if (A.inst_of) {
     const uint32_t I = __ldg(A.inst_of + i);
     start = __ldg(A.inst_root + I);
     if (start == kInvalid) {  // a one-point instance: nothing to find
       A.res[i] = make_uint2(0u, kInvalid);
       if (LEARNED) A.r_used[i] = kInf;
-      return;
+      return false;
     }
   }
   const float4 p = A.pts[i];
-  Query q;
   q.px = p.x;
   q.py = p.y;
   q.pz = p.z;
@@ -273,7 +381,7 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
     if (CARRIED && __uint_as_float(prev.x) > q.radius) {
       A.res[i] = make_uint2(prev.x, kInvalid);
       if (LEARNED) A.r_used[i] = kInf;
-      return;
+      return false;
     }
   }
   // The previous round's neighbour, if still in another component, is a real
@@ -281,29 +389,24 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   if (CARRIED && prev.y != kInvalid && A.labels[prev.y] != q.me)
     q.radius = fminf(q.radius, __uint_as_float(prev.x));
   if (LEARNED) q.radius = fminf(q.radius, __ldg(A.pred_r + i));
-  const float r0 = q.radius;  // the search is exact within this cutoff
+  r0 = q.radius;  // the search is exact within this cutoff
   if (LEARNED) A.r_used[i] = r0;
   if (MRD && q.core > r0) {  // every weight from this point is at least its core distance
     A.res[i] = make_uint2(__float_as_uint(q.core), kInvalid);
-    return;
+    return false;
   }
-  uint32_t st_node[kStackDepth];
-  float st_dist[kStackDepth];
-  unsigned long long nvis = 0;
-  const bool ok = explore<COUNT, CHUNKS, FIRST, MRD, TIES>(q, start, A.nodes, A.nlabels, A.pts, A.labels,
-                                                     A.leaf, n, st_node, st_dist, nvis, A.core2,
-                                                     A.ties);
-  if (!ok) atomicOr(A.status, kErrStack);
-  if (COUNT) {
-    // one atomic per warp: sum the active lanes' counts first
-    const unsigned mask = __activemask();
-    const unsigned v = __reduce_add_sync(mask, (unsigned)nvis);
-    if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) atomicAdd(A.visits, (unsigned long long)v);
-  }
+  return true;
+}
+
+// The second half: the query's result and the first stage of its
+// component's minimum (A8): an atomicMin of (w bits << 32 | min original id).
+// SEEDED reports only the exact nearest neighbour within r0 (a seed beyond r0
+// is dropped) and keeps in res.x a lower bound for the next round: the found
+// weight, or r0 when nothing lies within it.
+template <bool SEEDED>
+__device__ __forceinline__ void finish_query(const TravArgs &A, int64_t i, Query &q, float r0) {
+  const float kInf = __int_as_float(0x7f800000);
   if (SEEDED) {
-    // Report only the exact nearest neighbour within r0 (a seed beyond r0 is
-    // dropped); keep in res.x a lower bound for the next round: the found
-    // weight, or r0 when nothing lies within it.
     const bool found = q.bj != kInvalid && q.best <= r0;
     if (!found) q.bj = kInvalid;
     const float lb = found ? q.best : (r0 < kInf ? r0 : 0.0f);
@@ -312,14 +415,43 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
     A.res[i] = make_uint2(__float_as_uint(q.best), q.bj);
   }
   if (q.bj != kInvalid) {
-    const uint32_t oi = __float_as_uint(p.w);
-    const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(A.pts[q.bj].w);
+    const uint32_t oi = __float_as_uint(__ldg(&A.pts[i].w));
+    const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(__ldg(&A.pts[q.bj].w));
     const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
     // (many points of a large component find edges: only one that improves
     // on the value seen now needs the atomic)
     unsigned long long *ck = reinterpret_cast<unsigned long long *>(A.comp_key + q.me);
     if ((unsigned long long)key < __ldcg(ck)) atomicMin(ck, (unsigned long long)key);
   }
+}
+
+// One query, start to finish (the classic one-thread-per-point form).
+// `ring`: this thread's slot 0 of the shared-memory stack ring (unused with
+// the local stack).
+template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
+          bool FIRST = false, bool MRD = false, bool TIES = true>
+__device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i, uint2 *ring) {
+  Query q;
+  uint32_t start;
+  float r0;
+  if (!start_query<CARRIED, RADIUS_IN, SEEDED, LEARNED, MRD>(A, i, q, start, r0)) return;
+  TravStack stk;
+  stk.init(ring, blockDim.x);
+  unsigned long long nvis = 0;
+  const bool ok = explore<COUNT, CHUNKS, FIRST, MRD, TIES>(q, start, A.nodes, A.nlabels, A.pts,
+                                                           A.labels, A.leaf, A.n, stk, nvis, A.core2,
+                                                           A.ties, COUNT ? A.seen : nullptr);
+  if (!ok) atomicOr(A.status, kErrStack);
+  if (COUNT) {
+    // one atomic per warp: sum the active lanes' counts first
+    const unsigned mask = __activemask();
+    const unsigned v = __reduce_add_sync(mask, (unsigned)nvis);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) {
+      atomicAdd(A.visits, (unsigned long long)v);
+      atomicAdd(A.queries, (unsigned long long)__popc(mask));
+    }
+  }
+  finish_query<SEEDED>(A, i, q, r0);
 }
 
 }  // namespace emst

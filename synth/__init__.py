@@ -190,16 +190,58 @@ def batched_sizes(num_instances: int, seed: int, lo: int = 100, hi: int = 1_000_
     return np.floor(s).astype(np.int64)
 
 
-def batched_instances(sizes, seed: int, n_blobs: int = 20, frac_background: float = 0.10):
+def _fill_instances(job):
+    """Worker of batched_instances: draw instances [k0, k1) into the shared
+    output buffer (each instance has its own seed, so the result does not
+    depend on how the work is split)."""
+    from multiprocessing import shared_memory
+    name, total, sizes, offsets, k0, k1, seed, n_blobs, frac_background = job
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        out = np.ndarray((total, 3), dtype=np.float32, buffer=shm.buf)
+        for k in range(k0, k1):
+            out[offsets[k]:offsets[k + 1]] = blobs(int(sizes[k]), 3, seed * 1_000_003 + k,
+                                                   n_blobs=n_blobs, frac_background=frac_background)
+        del out
+    finally:
+        shm.close()
+    return k1 - k0
+
+
+def batched_instances(sizes, seed: int, n_blobs: int = 20, frac_background: float = 0.10,
+                      workers: int = 1):
     """Concatenated 3D instances (blobs generator, 20 blobs, 10 % uniform) and
-    the int64 offsets array of length len(sizes)+1."""
+    the int64 offsets array of length len(sizes)+1.  Instance k is drawn with
+    seed ``seed * 1_000_003 + k``; ``workers`` > 1 draws the instances in that
+    many processes (spawned, so it is safe after CUDA is initialised) with the
+    same result."""
     sizes = np.asarray(sizes, dtype=np.int64)
     offsets = np.zeros(len(sizes) + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(sizes)
-    out = np.empty((int(offsets[-1]), 3), dtype=np.float32)
-    for k, s in enumerate(sizes):
-        out[offsets[k]:offsets[k + 1]] = blobs(int(s), 3, seed * 1_000_003 + k, n_blobs=n_blobs,
-                                               frac_background=frac_background)
+    total = int(offsets[-1])
+    if workers <= 1 or len(sizes) < 2 or total == 0:
+        out = np.empty((total, 3), dtype=np.float32)
+        for k, s in enumerate(sizes):
+            out[offsets[k]:offsets[k + 1]] = blobs(int(s), 3, seed * 1_000_003 + k, n_blobs=n_blobs,
+                                                   frac_background=frac_background)
+        return out, offsets
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(create=True, size=total * 3 * 4)
+    try:
+        # contiguous runs of instances with about equal point counts
+        bounds = np.searchsorted(offsets, np.linspace(0, total, 4 * workers + 1)[1:-1])
+        cuts = np.unique(np.concatenate([[0], bounds, [len(sizes)]]))
+        jobs = [(shm.name, total, sizes, offsets, int(a), int(b), seed, n_blobs, frac_background)
+                for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            done = sum(ex.map(_fill_instances, jobs))
+        assert done == len(sizes)
+        out = np.ndarray((total, 3), dtype=np.float32, buffer=shm.buf).copy()
+    finally:
+        shm.close()
+        shm.unlink()
     return out, offsets
 
 

@@ -1,7 +1,7 @@
 """bench.py's reference arm (the oracle on the host cores) keeps the JSON
-contract: one line with the metric, a positive value, impl "reference", a
-cpu_baseline describing the run and an e2e block with no copies.  Runs on a
-small sample, no GPU."""
+contract: one line with the metric, a positive value, impl "reference", the
+same config as the GPU arm, a cpu_baseline describing the run and an e2e
+block with no copies.  Runs on a small sample, no GPU."""
 from __future__ import annotations
 
 import json
@@ -26,7 +26,9 @@ def test_reference_arm_json_line():
         assert k in d, k
     assert d["value"] > 0 and d["higher_is_better"] is True
     assert d["steps"] == 2 and d["warmup"] == 1
-    assert d["config"]["n"] == 30000 and d["config"]["sample_points"] == 8000
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.config_of(30000, 2)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]

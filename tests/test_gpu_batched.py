@@ -93,7 +93,7 @@ def test_full_config4_batch_vs_oracle(pkg):
     emst_compute call on it alone."""
     from concurrent.futures import ThreadPoolExecutor
     sizes = synth.batched_sizes(4096, seed=4, lo=100, hi=1_000_000)
-    pts, offsets = synth.batched_instances(sizes, seed=4)
+    pts, offsets = synth.batched_instances(sizes, seed=4, workers=os.cpu_count() or 4)
     dev = torch.from_numpy(pts).cuda()
     e, eo = pkg.emst_compute_batched(dev, offsets)
     torch.cuda.synchronize()
