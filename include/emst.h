@@ -95,10 +95,11 @@ typedef struct emst_options {
                                  8-pass sort) or 0 = automatic (the default): 64, rebuilt with
                                  128 when more than n/64 distinct points share their curve
                                  predecessor's 64-bit code.  The tree is the same either way. */
-  int32_t traversal;          /* the Algorithm 2 kernel: 0 = default (the persistent
-                                 work-queue kernel where it applies), 1 = one thread per
-                                 point, 2 = persistent work queue (plain rounds on one-point
-                                 leaves; other forms fall back to one thread per point).
+  int32_t traversal;          /* the Algorithm 2 kernel: 0 = default (one thread per point,
+                                 the fastest measured), 1 = one thread per point, 2 = a
+                                 persistent grid whose warps take queries from a global work
+                                 queue and refill lanes as searches end (plain rounds on
+                                 one-point leaves; other forms use one thread per point).
                                  The tree is the same either way. */
   int32_t reserved[5];
 } emst_options;
@@ -155,13 +156,23 @@ int emst_compute_ex(const float *points, int64_t n, int dim, emst_edge *out_edge
  * independent problems, each solved exactly as emst_compute would).
  *   points        all instances' points concatenated, sum(n_k) x dim FP32.
  *   offsets       num_instances+1 int64, offsets[0] = 0, non-decreasing,
- *                 instance k = rows [offsets[k], offsets[k+1]); host memory.
+ *                 instance k = rows [offsets[k], offsets[k+1]); host or
+ *                 device memory (device: read back once, they size the call).
  *   out_edges     room for sum(max(n_k-1, 0)) edges; instance k's edges are
  *                 contiguous, use ids local to the instance, sorted as above.
- *   out_offsets   num_instances+1 int64 (host memory): edge block bounds.
+ *   out_offsets   num_instances+1 int64, host or device memory: edge block
+ *                 bounds.
  * Returns EMST_OK or an emst_status error. */
 int emst_compute_batched(const float *points, const int64_t *offsets, int num_instances, int dim,
                          emst_edge *out_edges, int64_t *out_offsets, void *stream);
+
+/* emst_compute_batched with options and statistics (as emst_compute_ex;
+ * leaf_size, mrd_k, mlp_params and morton_bits other than 0 / 64 do not
+ * apply to the batched form and are ignored: one point per leaf, Euclidean
+ * weights, 64-bit codes with the instance id in the top bits). */
+int emst_compute_batched_ex(const float *points, const int64_t *offsets, int num_instances, int dim,
+                            emst_edge *out_edges, int64_t *out_offsets, void *stream,
+                            const emst_options *options, emst_stats *stats);
 
 /* Squared core distances of the mutual reachability distance (§4.5): for
  * every point, the FP32 squared distance to its k-th nearest neighbour, the

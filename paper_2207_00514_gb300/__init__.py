@@ -28,6 +28,7 @@ __all__ = [
     "emst_compute",
     "emst_compute_ex",
     "emst_compute_batched",
+    "emst_compute_batched_ex",
     "emst_core_distances",
     "EMST_MRD_MAX_K",
     "emst_compute_noalloc",
@@ -124,6 +125,9 @@ def load_library(path: str | None = None):
         lib.emst_compute_ex.restype = I
         lib.emst_compute_batched.argtypes = [V, V, I, I, V, V, V]
         lib.emst_compute_batched.restype = I
+        lib.emst_compute_batched_ex.argtypes = [V, V, I, I, V, V, V, ctypes.POINTER(_Options),
+                                                ctypes.POINTER(_Stats)]
+        lib.emst_compute_batched_ex.restype = I
         lib.emst_build_bvh_ex.argtypes = [V, I64, I, I, I, V, V, V, V, V]
         lib.emst_build_bvh_ex.restype = I
         lib.emst_core_distances.argtypes = [V, I64, I, I, V, V]
@@ -238,14 +242,8 @@ def emst_compute_noalloc(points, out_edges=None, stream=None):
     return out_edges
 
 
-def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_radius=True,
-                    use_graph=False, count_visits=False, leaf_size=0, mlp_params=None, mrd_k=0,
-                    morton_bits=0, traversal=0):
-    """emst_compute with options; returns (edges, stats dict).  mrd_k >= 2:
-    the mutual-reachability MST (squared MRD weights).  traversal: 0 default,
-    1 one thread per point, 2 persistent work queue."""
-    n, dim = _check_points(points)
-    out_edges = _edges_out(n, points, out_edges)
+def _make_options(block_size=0, carried_radius=True, use_graph=False, count_visits=False,
+                  leaf_size=0, mlp_params=None, mrd_k=0, morton_bits=0, traversal=0):
     opt = _Options()
     opt.struct_size = ctypes.sizeof(_Options)
     opt.block_size = int(block_size)
@@ -260,27 +258,47 @@ def emst_compute_ex(points, out_edges=None, stream=None, block_size=0, carried_r
         if mlp_params.dtype != _torch().float32 or mlp_params.numel() != EMST_MLP_PARAMS:
             raise ValueError(f"mlp_params must hold {EMST_MLP_PARAMS} float32 values")
         opt.mlp_params = mlp_params.data_ptr()
+    return opt
+
+
+def _new_stats():
     st = _Stats()
     st.struct_size = ctypes.sizeof(_Stats)
+    return st
+
+
+def _stats_dict(st):
+    r = min(st.rounds, 40)
+    return dict(rounds=st.rounds, kernel_launches=st.kernel_launches, total_ms=st.total_ms,
+                build_ms=st.build_ms, rounds_ms=st.rounds_ms, output_ms=st.output_ms,
+                node_visits=st.node_visits, traverse_ms=st.traverse_ms,
+                traverse_launches=st.traverse_launches,
+                round_traverse_ms=[float(st.round_traverse_ms[k]) for k in range(r)],
+                components_per_round=[int(st.components_per_round[k]) for k in range(r)],
+                queried_points=st.queried_points, rerun_points=st.rerun_points,
+                learned_search_ms=st.learned_search_ms, core_ms=st.core_ms,
+                morton_bits=st.morton_bits, code_collisions=st.code_collisions,
+                round_visits=[int(st.round_visits[k]) for k in range(r)],
+                round_queries=[int(st.round_queries[k]) for k in range(r)],
+                round_distinct_nodes=[int(st.round_distinct_nodes[k]) for k in range(r)])
+
+
+def emst_compute_ex(points, out_edges=None, stream=None, **options):
+    """emst_compute with options (keywords of emst_options: block_size,
+    carried_radius, count_visits, leaf_size, mlp_params, mrd_k, morton_bits,
+    traversal); returns (edges, stats dict).  mrd_k >= 2: the
+    mutual-reachability MST (squared MRD weights).  traversal: 0 default,
+    1 one thread per point, 2 persistent work queue."""
+    n, dim = _check_points(points)
+    out_edges = _edges_out(n, points, out_edges)
+    opt = _make_options(**options)
+    st = _new_stats()
     rc = load_library().emst_compute_ex(_ptr(points), n, dim, _ptr(out_edges),
                                         _stream_ptr(stream, points.device), ctypes.byref(opt),
                                         ctypes.byref(st))
     if rc != 0:
         raise EmstError(rc, "emst_compute_ex")
-    stats = dict(rounds=st.rounds, kernel_launches=st.kernel_launches, total_ms=st.total_ms,
-                 build_ms=st.build_ms, rounds_ms=st.rounds_ms, output_ms=st.output_ms,
-                 node_visits=st.node_visits, traverse_ms=st.traverse_ms,
-                 traverse_launches=st.traverse_launches,
-                 round_traverse_ms=[float(st.round_traverse_ms[k]) for k in range(min(st.rounds, 40))],
-                 components_per_round=[int(st.components_per_round[k]) for k in range(min(st.rounds, 40))],
-                 queried_points=st.queried_points, rerun_points=st.rerun_points,
-                 learned_search_ms=st.learned_search_ms, core_ms=st.core_ms,
-                 morton_bits=st.morton_bits, code_collisions=st.code_collisions,
-                 round_visits=[int(st.round_visits[k]) for k in range(min(st.rounds, 40))],
-                 round_queries=[int(st.round_queries[k]) for k in range(min(st.rounds, 40))],
-                 round_distinct_nodes=[int(st.round_distinct_nodes[k])
-                                       for k in range(min(st.rounds, 40))])
-    return out_edges, stats
+    return out_edges, _stats_dict(st)
 
 
 def emst_core_distances(points, k, out=None, stream=None):
@@ -300,25 +318,56 @@ def emst_core_distances(points, k, out=None, stream=None):
 
 def emst_compute_batched(points, offsets, out_edges=None, stream=None):
     """Independent EMSTs of the row blocks [offsets[k], offsets[k+1]).
-    Returns (edges, edge_offsets) with instance-local ids."""
+    Returns (edges, edge_offsets) with instance-local ids.  ``offsets`` may be
+    a CUDA int64 tensor: then the library reads it from device memory and the
+    edge offsets come back as a CUDA tensor too."""
+    e, eo, _ = _batched(points, offsets, out_edges, stream, None)
+    return e, eo
+
+
+def emst_compute_batched_ex(points, offsets, out_edges=None, stream=None, **options):
+    """emst_compute_batched with options (see emst_compute_ex); returns
+    (edges, edge_offsets, stats dict)."""
+    return _batched(points, offsets, out_edges, stream, _make_options(**options))
+
+
+def _batched(points, offsets, out_edges, stream, opt):
     torch = _torch()
     n, dim = _check_points(points)
-    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
-    if offs.ndim != 1 or len(offs) < 1 or offs[0] != 0 or offs[-1] != n or np.any(np.diff(offs) < 0):
-        raise ValueError("offsets must start at 0, end at n and be non-decreasing")
-    k = len(offs) - 1
-    sizes = np.diff(offs)
-    m = int(np.maximum(sizes - 1, 0).sum())
-    if out_edges is None:
-        pin = points.device.type == "cpu" and torch.cuda.is_available()
-        out_edges = torch.empty((m, 3), dtype=torch.int32, device=points.device, pin_memory=pin)
-    out_offs = np.zeros(k + 1, dtype=np.int64)
-    rc = load_library().emst_compute_batched(_ptr(points), ctypes.c_void_p(offs.ctypes.data), k, dim,
-                                             _ptr(out_edges), ctypes.c_void_p(out_offs.ctypes.data),
-                                             _stream_ptr(stream, points.device))
+    st = _new_stats() if opt is not None else None
+    lib = load_library()
+
+    def call(p_off, p_out_off, k):
+        if opt is None:
+            return lib.emst_compute_batched(_ptr(points), p_off, k, dim, _ptr(out_edges), p_out_off,
+                                            _stream_ptr(stream, points.device))
+        return lib.emst_compute_batched_ex(_ptr(points), p_off, k, dim, _ptr(out_edges), p_out_off,
+                                           _stream_ptr(stream, points.device), ctypes.byref(opt),
+                                           ctypes.byref(st))
+
+    if isinstance(offsets, torch.Tensor) and offsets.is_cuda:
+        if offsets.dtype != torch.int64 or offsets.dim() != 1 or not offsets.is_contiguous():
+            raise ValueError("device offsets must be a contiguous 1-D int64 tensor")
+        k = offsets.numel() - 1
+        m = int((offsets[1:] - offsets[:-1] - 1).clamp(min=0).sum()) if k > 0 else 0
+        if out_edges is None:
+            out_edges = torch.empty((m, 3), dtype=torch.int32, device=points.device)
+        out_offs = torch.empty(k + 1, dtype=torch.int64, device=offsets.device)
+        rc = call(_ptr(offsets), _ptr(out_offs), k)
+    else:
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        if offs.ndim != 1 or len(offs) < 1 or offs[0] != 0 or offs[-1] != n or np.any(np.diff(offs) < 0):
+            raise ValueError("offsets must start at 0, end at n and be non-decreasing")
+        k = len(offs) - 1
+        m = int(np.maximum(np.diff(offs) - 1, 0).sum())
+        if out_edges is None:
+            pin = points.device.type == "cpu" and torch.cuda.is_available()
+            out_edges = torch.empty((m, 3), dtype=torch.int32, device=points.device, pin_memory=pin)
+        out_offs = np.zeros(k + 1, dtype=np.int64)
+        rc = call(ctypes.c_void_p(offs.ctypes.data), ctypes.c_void_p(out_offs.ctypes.data), k)
     if rc != 0:
         raise EmstError(rc, "emst_compute_batched")
-    return out_edges, out_offs
+    return out_edges, out_offs, (_stats_dict(st) if st is not None else None)
 
 
 def emst_build_bvh(points, leaf_size=1, stream=None, morton_bits=64):

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -412,6 +413,11 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     leaf_req = opt->leaf_size;
     mlp_params = opt->mlp_params;
     mrd_k = opt->mrd_k;
+    if (offsets) {  // the batched form: Euclidean weights, plain cutoffs, one point per leaf
+      mlp_params = nullptr;
+      mrd_k = 0;
+      leaf_req = 0;
+    }
     if (mrd_k < 0 || mrd_k > EMST_MRD_MAX_K || (mrd_k >= 2 && (mlp_params || n < mrd_k)))
       return EMST_ERR_INVALID_ARG;
     morton_bits = opt->morton_bits;
@@ -453,7 +459,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   P.want_mrd = mrd_k >= 2 && !offsets && n >= 2;
   P.wide = morton_bits == 128 && !offsets;
   P.auto_wide = morton_bits == 0 && !offsets;
-  P.persistent = traversal != 1;
+  P.persistent = traversal == 2;
   P.want_count = count != 0;
   if (logging) {
     P.log_feat = ex->log_feat;
@@ -740,14 +746,54 @@ int emst_compute_ex(const float *points, int64_t n, int dim, emst_edge *out_edge
 
 int emst_compute_batched(const float *points, const int64_t *offsets, int num_instances, int dim,
                          emst_edge *out_edges, int64_t *out_offsets, void *stream) {
+  return emst_compute_batched_ex(points, offsets, num_instances, dim, out_edges, out_offsets, stream,
+                                 nullptr, nullptr);
+}
+
+int emst_compute_batched_ex(const float *points, const int64_t *offsets, int num_instances, int dim,
+                            emst_edge *out_edges, int64_t *out_offsets, void *stream,
+                            const emst_options *options, emst_stats *stats) {
   if (num_instances < 0 || !offsets || !out_offsets || (dim != 2 && dim != 3))
     return EMST_ERR_INVALID_ARG;
-  if (num_instances == 0) {
-    out_offsets[0] = 0;
-    return offsets[0] == 0 ? EMST_OK : EMST_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // offsets / out_offsets may live in device memory: the bounds are read to
+  // the host once (they size the problem) and the edge bounds written back
+  const bool offs_dev = device_accessible(offsets);
+  const bool outoffs_dev = device_accessible(out_offsets);
+  std::vector<int64_t> h_offs, h_out;
+  const int64_t *offs = offsets;
+  if (offs_dev) {
+    h_offs.resize((size_t)num_instances + 1);
+    if (cudaMemcpyAsync(h_offs.data(), offsets, sizeof(int64_t) * h_offs.size(),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      return EMST_ERR_CUDA;
+    }
+    offs = h_offs.data();
   }
-  return compute_impl(points, offsets[num_instances], dim, offsets, num_instances, out_edges,
-                      out_offsets, (cudaStream_t)stream, nullptr, nullptr);
+  int64_t *oo = out_offsets;
+  if (outoffs_dev) {
+    h_out.resize((size_t)num_instances + 1);
+    oo = h_out.data();
+  }
+  int rc;
+  if (num_instances == 0) {
+    oo[0] = 0;
+    rc = offs[0] == 0 ? EMST_OK : EMST_ERR_INVALID_ARG;
+  } else {
+    rc = compute_impl(points, offs[num_instances], dim, offs, num_instances, out_edges, oo, s,
+                      options, stats);
+  }
+  if (outoffs_dev && (rc == EMST_OK || rc == EMST_ERR_INVALID_ARG)) {
+    if (cudaMemcpyAsync(out_offsets, oo, sizeof(int64_t) * h_out.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      return EMST_ERR_CUDA;
+    }
+  }
+  return rc;
 }
 
 int emst_learned_samples(const float *points, int64_t n, int dim, int every, float *out_features,

@@ -514,10 +514,10 @@ __global__ void __launch_bounds__(128) k_log_samples(FeatArgs F, TravArgs T, int
   q.best = q.radius;
   q.bj = kInvalid;
   q.bid = kInvalid;
-  LocalStack stk;
-  stk.init(nullptr, 0);
+  uint32_t st_node[kStackDepth];
+  float st_dist[kStackDepth];
   unsigned long long nv = 0;
-  if (!explore<false, false, false>(q, start, T.nodes, T.nlabels, T.pts, T.labels, 1, F.n, stk, nv)) {
+  if (!explore<false, false, false>(q, start, T.nodes, T.nlabels, T.pts, T.labels, 1, F.n, st_node, st_dist, nv)) {
     atomicOr(T.status, kErrStack);
     return;
   }

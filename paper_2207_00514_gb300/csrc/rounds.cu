@@ -244,21 +244,18 @@ void launch_upper_bounds(Problem &P) {
 }
 
 // One thread per point, or (list != nullptr) a grid-stride pass over the
-// listed points (the certification reruns of the learned radius).  Dynamic
-// shared memory: the stack rings, kRingSlots 8-byte slots per thread.
+// listed points (the certification reruns of the learned radius).
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
           bool FIRST, bool MRD, bool TIES = true>
 __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
-  extern __shared__ uint2 s_ring[];
-  uint2 *ring = s_ring + threadIdx.x;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (list) {
     const int64_t count = *list_count;
     for (int64_t t = gid; t < count; t += (int64_t)gridDim.x * blockDim.x)
-      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, __ldg(list + t), ring);
+      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, __ldg(list + t));
   } else if (gid < A.n) {
-    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, gid, ring);
+    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, gid);
   }
 }
 
@@ -279,7 +276,7 @@ __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k
 #define EMST_QUEUE_CHUNK 64
 #endif
 #ifndef EMST_REFILL_LANES
-#define EMST_REFILL_LANES 8
+#define EMST_REFILL_LANES 16
 #endif
 #ifndef EMST_PERSIST_BLOCK
 #define EMST_PERSIST_BLOCK 128
@@ -287,24 +284,20 @@ __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k
 #ifndef EMST_PERSIST_MIN_BLOCKS
 #define EMST_PERSIST_MIN_BLOCKS 12
 #endif
-#ifndef EMST_PERSIST_RING
-#define EMST_PERSIST_RING 8
-#endif
+
 constexpr int kQueueChunk = EMST_QUEUE_CHUNK;
 static_assert(kQueueChunk >= 32, "a refill takes at most 32 positions, from at most two chunks");
 constexpr int kRefillLanes = EMST_REFILL_LANES;
 constexpr int kPersistBlock = EMST_PERSIST_BLOCK;
-using PersistStack = StackOf<EMST_PERSIST_RING>::type;
 
 template <bool CARRIED, bool FIRST, bool TIES, bool COUNT>
 __global__ void __launch_bounds__(kPersistBlock, EMST_PERSIST_MIN_BLOCKS)
     k_traverse_queue(TravArgs A, unsigned long long *queue) {
-  extern __shared__ uint2 s_ring[];
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t n = A.n;
-  PersistStack stk;
-  stk.init(s_ring + threadIdx.x, blockDim.x);
+  LocalStack stk;
+  stk.init();
   Query q;
   uint32_t node = 0, i = 0;
   float r0 = 0.0f;
@@ -333,7 +326,7 @@ __global__ void __launch_bounds__(kPersistBlock, EMST_PERSIST_MIN_BLOCKS)
           live = start_query<CARRIED, false, true, false, false>(A, t, q, start, r0);
           if (live) {
             node = start;
-            stk.init(s_ring + threadIdx.x, blockDim.x);
+            stk.init();
             if (COUNT) ++nq;
           }
         }
@@ -381,7 +374,7 @@ static void queue_launch(Problem &P, const TravArgs &A) {
   static int blocks_per_sm[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  const size_t sm = sizeof(uint2) * (size_t)EMST_PERSIST_RING * kPersistBlock;
+  const size_t sm = 0;
   auto kern = k_traverse_queue<CARRIED, FIRST, TIES, COUNT>;
   if (dev >= 0 && dev < 64 && blocks_per_sm[dev] == 0) {
     int b = 0;
@@ -453,7 +446,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   const uint32_t *list = learned_pass == 2 ? P.rerun_list : nullptr;
   const uint32_t *list_count = learned_pass == 2 ? P.counters + 13 : nullptr;
   const int g = learned_pass == 2 ? sm_count() * 8 : grid_for(P.n, block);
-  const size_t sm = sizeof(uint2) * (size_t)kRingSlots * (size_t)block;
+  const size_t sm = 0;
   cudaStream_t s = P.stream;
 #define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L, false, false><<<g, block, sm, s>>>(A, list, list_count)
 #define EMST_TRAV_FIRST(K, H) k_traverse<false, false, K, true, H, false, true, false><<<g, block, sm, s>>>(A, list, list_count)

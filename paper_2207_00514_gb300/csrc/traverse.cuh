@@ -89,22 +89,16 @@ __device__ __forceinline__ void load_record(const NodeRec *rec, float4 &a, float
 }
 
 // ---------------------------------------------------------------------------
-// The search stack of one query (Algorithm 2's stack of nodes still to
-// examine, each with the weight bound of its box, re-tested when popped).
-// An entry is one 8-byte (node, bound bits) pair.
-//  - LocalStack: every entry in a per-thread local array.
-//  - RingStack<K>: the top K entries in shared memory, a ring of K slots per
-//    thread stored slot-major (slot s of thread t at ring[s * stride + t]), so
-//    the lanes of a warp touch distinct banks whatever their depths and one
-//    warp-wide push or pop is one or two shared wavefronts instead of one L1
-//    sector per lane; deeper entries are spilled to the local array.
-// Both hold kStackDepth entries in all (the deepest possible path, see
-// traverse_one); push reports an overflow instead of writing past it.
+// The search stack of one query of the persistent kernel (Algorithm 2's
+// stack of nodes still to examine, each with the weight bound of its box,
+// re-tested when popped): one 8-byte (node, bound bits) entry per level in a
+// per-thread local array of kStackDepth entries (the deepest possible path,
+// see traverse_one); push reports an overflow instead of writing past it.
 // ---------------------------------------------------------------------------
 struct LocalStack {
   uint2 e[kStackDepth];
   int sp;
-  __device__ __forceinline__ void init(uint2 *, int) { sp = 0; }
+  __device__ __forceinline__ void init() { sp = 0; }
   __device__ __forceinline__ bool push(uint32_t node, float d) {
     if (sp >= kStackDepth) return false;
     e[sp++] = make_uint2(node, __float_as_uint(d));
@@ -116,52 +110,6 @@ struct LocalStack {
     return true;
   }
 };
-
-template <int K>
-struct RingStack {
-  static_assert(K > 0 && (K & (K - 1)) == 0, "ring size: a power of two");
-  uint2 *ring;   // this thread's slot 0 in shared memory
-  int stride;    // threads of the CTA
-  int sp;        // entries in all
-  int cnt;       // of those, in the ring (the newest cnt)
-  uint2 spill[kStackDepth];
-  __device__ __forceinline__ void init(uint2 *mine, int stride_) {
-    ring = mine;
-    stride = stride_;
-    sp = 0;
-    cnt = 0;
-  }
-  __device__ __forceinline__ bool push(uint32_t node, float d) {
-    if (sp >= kStackDepth) return false;
-    uint2 *slot = ring + (sp & (K - 1)) * stride;
-    if (cnt == K) spill[sp - K] = *slot;  // the oldest ring entry moves to local memory
-    else ++cnt;
-    *slot = make_uint2(node, __float_as_uint(d));
-    ++sp;
-    return true;
-  }
-  __device__ __forceinline__ bool pop(uint2 &x) {
-    if (sp == 0) return false;
-    --sp;
-    if (cnt > 0) {
-      --cnt;
-      x = ring[(sp & (K - 1)) * stride];
-    } else {
-      x = spill[sp];
-    }
-    return true;
-  }
-};
-
-// Shared-memory ring slots per thread of the classic traversal kernel (0 =
-// local stack only).
-#ifndef EMST_RING_SLOTS
-#define EMST_RING_SLOTS 8
-#endif
-constexpr int kRingSlots = EMST_RING_SLOTS;
-template <int K> struct StackOf { using type = RingStack<K>; };
-template <> struct StackOf<0> { using type = LocalStack; };
-using TravStack = StackOf<kRingSlots>::type;
 
 // One visit of internal node `node` of Algorithm 2, whose own box the caller
 // has already accepted: test both children from the node's record, scan
@@ -249,30 +197,94 @@ __device__ __forceinline__ uint32_t pop_next(const Query &q, Stack &stk) {
 }
 
 // Depth-first search of the subtree of internal node `node`, whose own box
-// the caller has already accepted (Algorithm 2): visit, descend into the
-// nearer accepted child, pop when none.  COUNT: count the visits (nvis) and,
-// with a bitmap `seen` of the internal nodes, mark each node visited.
-// Returns false on a stack overflow.
-template <bool COUNT, bool CHUNKS, bool FIRST, bool MRD = false, bool TIES = true, class Stack>
+// the caller has already accepted: test both children of every visited
+// record, scan accepted leaf chunks, descend into the nearer accepted
+// internal child and stack the farther one with its box distance (re-tested
+// when popped).  The same steps as visit() + pop_next(), in one loop with the
+// stack in two local arrays (node, bound): the form the one-thread-per-point
+// kernel measured fastest.  COUNT: count the visits (nvis) and, with a
+// bitmap `seen` of the internal nodes, mark each node visited.
+// FIRST: the first round, where every label is the point's own curve index,
+// so no internal child is single-component and the only one-point leaf to
+// skip is the query itself: no label load.
+// MRD: mutual reachability weights (§4.5).  The boxes prune exactly as for
+// the plain weight: the caller only searches with a cutoff at or above the
+// query's core distance, and every weight from the query is at least that,
+// so max(core, box distance) <= cutoff  <=>  box distance <= cutoff.
+// TIES = false: the input has no large group of identical points (see the
+// tie rule below), so that check is compiled out.
+template <bool COUNT, bool CHUNKS, bool FIRST, bool MRD = false, bool TIES = true>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
                                         const uint2 *__restrict__ nlabels,
                                         const float4 *__restrict__ pts,
                                         const uint32_t *__restrict__ labels, int leaf, int64_t n,
-                                        Stack &stk, unsigned long long &nvis,
+                                        uint32_t *st_node, float *st_dist,
+                                        unsigned long long &nvis,
                                         const float *__restrict__ core2 = nullptr,
                                         bool ties = true, uint32_t *seen = nullptr) {
-  bool overflow = false;
+  int sp = 0;
   while (true) {
     if (COUNT) {
       ++nvis;
       if (seen) atomicOr(seen + (node >> 5), 1u << (node & 31));
     }
-    uint32_t nxt = visit<CHUNKS, FIRST, MRD, TIES>(q, node, nodes, nlabels, pts, labels, leaf, n,
-                                                   stk, overflow, core2, ties);
-    if (overflow) return false;
-    if (nxt == kInvalid) nxt = pop_next(q, stk);
-    if (nxt == kInvalid) return true;
-    node = nxt;
+    float4 a, b, c;
+    uint4 dd;
+    load_record(nodes + node, a, b, c, dd);
+    uint2 lab;
+    if (FIRST) {
+      lab.x = (!CHUNKS && (dd.x & kLeafBit)) ? (dd.x & ~kLeafBit) : kInvalid;
+      lab.y = (!CHUNKS && (dd.y & kLeafBit)) ? (dd.y & ~kLeafBit) : kInvalid;
+    } else {
+      lab = __ldg(nlabels + node);
+    }
+    const float dL = box_dist(q.px, q.py, q.pz, a.x, a.y, a.z, a.w, b.x, b.y);
+    const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
+    bool okL = (lab.x != q.me) && (dL <= q.radius);
+    bool okR = (lab.y != q.me) && (dR <= q.radius);
+    if (okL && (dd.x & kLeafBit)) {
+      scan_chunk<CHUNKS, MRD>(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels, core2);
+      okL = false;
+    }
+    if (okR && (dd.y & kLeafBit)) {
+      if (dR <= q.radius) scan_chunk<CHUNKS, MRD>(q, dd.y & ~kLeafBit, dR, leaf, n, pts, labels, core2);
+      okR = false;
+    }
+    okL = okL && dL <= q.radius;
+    okR = okR && dR <= q.radius;
+    // An internal child whose weight bound only ties the cutoff holds nothing
+    // better than the best so far unless it has a point with a smaller
+    // original id (dd.z / dd.w hold each child's smallest).  Without this a
+    // group of m identical points costs each of its queries a visit to all m,
+    // and so does a group at one equal distance from the query.  (Checked
+    // only when a tie occurs; a leaf resolves its own ties.)
+    // (the ids are read again in the rare tie case: kept live through the
+    // leaf scans above they cost the hot loop a register it does not have)
+    // Only when the input has a run of more than 32 equal codes (`ties`):
+    // otherwise no group of identical points is larger than that, a tie
+    // involves a few points at most and the check would only cost time.
+    const float lbL = MRD ? fmaxf(q.core, dL) : dL, lbR = MRD ? fmaxf(q.core, dR) : dR;
+    if (TIES && ties && q.bj != kInvalid && ((okL && lbL == q.radius) || (okR && lbR == q.radius))) {
+      if (q.bid == kInvalid) q.bid = __float_as_uint(pts[q.bj].w);  // loaded lazily
+      const uint2 mn = __ldg(reinterpret_cast<const uint2 *>(nodes + node) + 7);  // dd.z, dd.w
+      if (lbL == q.radius && mn.x >= q.bid) okL = false;
+      if (lbR == q.radius && mn.y >= q.bid) okR = false;
+    }
+    if (okL && okR) {
+      if (sp >= kStackDepth) return false;
+      if (dL <= dR) { st_node[sp] = dd.y; st_dist[sp] = dR; node = dd.x; }
+      else { st_node[sp] = dd.x; st_dist[sp] = dL; node = dd.y; }
+      ++sp;
+      continue;
+    }
+    if (okL) { node = dd.x; continue; }
+    if (okR) { node = dd.y; continue; }
+    bool found = false;
+    while (sp > 0) {
+      --sp;
+      if (st_dist[sp] <= q.radius) { node = st_node[sp]; found = true; break; }
+    }
+    if (!found) return true;
   }
 }
 
@@ -425,22 +437,72 @@ __device__ __forceinline__ void finish_query(const TravArgs &A, int64_t i, Query
   }
 }
 
-// One query, start to finish (the classic one-thread-per-point form).
-// `ring`: this thread's slot 0 of the shared-memory stack ring (unused with
-// the local stack).
+// One query, start to finish (the one-thread-per-point form): the same
+// steps as start_query + explore + finish_query, kept in one piece so the
+// point's record stays in registers through the search.
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
           bool FIRST = false, bool MRD = false, bool TIES = true>
-__device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i, uint2 *ring) {
+__device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
+  const float kInf = __int_as_float(0x7f800000);
+  const int64_t n = A.n;
+  // Batched form: search only this point's instance (its subtree).
+  uint32_t start = 0u;
+  if (A.inst_of) {
+    const uint32_t I = __ldg(A.inst_of + i);
+    start = __ldg(A.inst_root + I);
+    if (start == kInvalid) {  // a one-point instance: nothing to find
+      A.res[i] = make_uint2(0u, kInvalid);
+      if (LEARNED) A.r_used[i] = kInf;
+      return;
+    }
+  }
+  const float4 p = A.pts[i];
   Query q;
-  uint32_t start;
-  float r0;
-  if (!start_query<CARRIED, RADIUS_IN, SEEDED, LEARNED, MRD>(A, i, q, start, r0)) return;
-  TravStack stk;
-  stk.init(ring, blockDim.x);
+  q.px = p.x;
+  q.py = p.y;
+  q.pz = p.z;
+  q.core = MRD ? __ldg(A.core2 + i) : 0.0f;
+  q.me = A.labels[i];
+  q.best = kInf;
+  q.bj = kInvalid;
+  q.bid = kInvalid;
+  if (RADIUS_IN) q.radius = A.radius_in[i];
+  else q.radius = bound_to_radius(A.bound[q.me]);
+  uint2 prev = make_uint2(0u, kInvalid);
+  if (CARRIED) prev = A.res[i];
+  if (SEEDED) {
+    // The component's best weight found so far this round: a real cross edge
+    // of the component, so never below its minimum.
+    const uint32_t cw =
+        (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(A.comp_key + q.me)) >> 32);
+    q.radius = fminf(q.radius, bound_to_radius(cw));
+    // prev.x is a lower bound of this point's nearest other-component weight
+    // (components only grow, so that weight never decreases).  Above the
+    // component-level cutoff, this point cannot be an endpoint of the
+    // component's minimum edge: skip the query.
+    if (CARRIED && __uint_as_float(prev.x) > q.radius) {
+      A.res[i] = make_uint2(prev.x, kInvalid);
+      if (LEARNED) A.r_used[i] = kInf;
+      return;
+    }
+  }
+  // The previous round's neighbour, if still in another component, is a real
+  // cross edge of this point: a per-point cutoff.
+  if (CARRIED && prev.y != kInvalid && A.labels[prev.y] != q.me)
+    q.radius = fminf(q.radius, __uint_as_float(prev.x));
+  if (LEARNED) q.radius = fminf(q.radius, __ldg(A.pred_r + i));
+  const float r0 = q.radius;  // the search is exact within this cutoff
+  if (LEARNED) A.r_used[i] = r0;
+  if (MRD && q.core > r0) {  // every weight from this point is at least its core distance
+    A.res[i] = make_uint2(__float_as_uint(q.core), kInvalid);
+    return;
+  }
+  uint32_t st_node[kStackDepth];
+  float st_dist[kStackDepth];
   unsigned long long nvis = 0;
-  const bool ok = explore<COUNT, CHUNKS, FIRST, MRD, TIES>(q, start, A.nodes, A.nlabels, A.pts,
-                                                           A.labels, A.leaf, A.n, stk, nvis, A.core2,
-                                                           A.ties, COUNT ? A.seen : nullptr);
+  const bool ok = explore<COUNT, CHUNKS, FIRST, MRD, TIES>(q, start, A.nodes, A.nlabels, A.pts, A.labels,
+                                                     A.leaf, n, st_node, st_dist, nvis, A.core2,
+                                                     A.ties, COUNT ? A.seen : nullptr);
   if (!ok) atomicOr(A.status, kErrStack);
   if (COUNT) {
     // one atomic per warp: sum the active lanes' counts first
@@ -451,7 +513,26 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i, uint2
       atomicAdd(A.queries, (unsigned long long)__popc(mask));
     }
   }
-  finish_query<SEEDED>(A, i, q, r0);
+  if (SEEDED) {
+    // Report only the exact nearest neighbour within r0 (a seed beyond r0 is
+    // dropped); keep in res.x a lower bound for the next round: the found
+    // weight, or r0 when nothing lies within it.
+    const bool found = q.bj != kInvalid && q.best <= r0;
+    if (!found) q.bj = kInvalid;
+    const float lb = found ? q.best : (r0 < kInf ? r0 : 0.0f);
+    A.res[i] = make_uint2(__float_as_uint(lb), q.bj);
+  } else {
+    A.res[i] = make_uint2(__float_as_uint(q.best), q.bj);
+  }
+  if (q.bj != kInvalid) {
+    const uint32_t oi = __float_as_uint(p.w);
+    const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(A.pts[q.bj].w);
+    const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
+    // (many points of a large component find edges: only one that improves
+    // on the value seen now needs the atomic)
+    unsigned long long *ck = reinterpret_cast<unsigned long long *>(A.comp_key + q.me);
+    if ((unsigned long long)key < __ldcg(ck)) atomicMin(ck, (unsigned long long)key);
+  }
 }
 
 }  // namespace emst

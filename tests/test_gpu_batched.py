@@ -124,3 +124,20 @@ def test_full_config4_batch_vs_oracle(pkg):
         results = list(ex.map(check, sorted(picked.tolist(), key=lambda k: -sizes[k])))
     bad = [k for k, ok in results if not ok]
     assert len(results) == 256 and not bad, f"instances differing from the oracle: {bad[:10]}"
+
+
+def test_batched_device_offsets(pkg):
+    """Offsets in device memory (and the edge offsets written back there) give
+    the same result as host offsets; a bad device offsets array is refused."""
+    sizes = [300, 0, 2, 1, 700, 45]
+    pts, offsets = synth.batched_instances(sizes, seed=10)
+    host_e, host_eo = run_batched(pkg, pts, offsets)
+    dev_offs = torch.from_numpy(offsets).cuda()
+    e, eo = pkg.emst_compute_batched(torch.from_numpy(pts).cuda(), dev_offs)
+    torch.cuda.synchronize()
+    assert eo.is_cuda and np.array_equal(eo.cpu().numpy(), host_eo)
+    assert same(pkg.edges_numpy(e), host_e)
+    bad = torch.tensor([0, 5, 4, len(pts)], dtype=torch.int64, device="cuda")
+    with pytest.raises(pkg.EmstError) as ei:
+        pkg.emst_compute_batched(torch.from_numpy(pts).cuda(), bad)
+    assert ei.value.status == -1

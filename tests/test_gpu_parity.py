@@ -353,3 +353,37 @@ def test_massive_duplicate_group(pkg):
     want = oracle.kd_boruvka(pts, threads=os.cpu_count() or 4)
     assert_same_edges(got, want, "duplicates")
     assert np.count_nonzero(got["w"] == 0) == 19_999
+
+
+@pytest.mark.parametrize("case", ["halos3", "blobs2", "lattice_dups", "uniform3_ragged"])
+def test_persistent_traversal_matches_oracle(pkg, case):
+    """The persistent work-queue form of Algorithm 2 (traversal = 2: warps
+    refill lanes from a global queue of curve positions) gives the oracle's
+    tree, as the one-thread-per-point form does; with counting on, the
+    per-round counts add up."""
+    pts = {"halos3": lambda: synth.halos(120_000, 31),
+           "blobs2": lambda: synth.blobs(90_001, 2, 32),
+           "lattice_dups": lambda: synth.lattice_ties(n_sites=40_000, n_dup=2_000, side=40, seed=33),
+           "uniform3_ragged": lambda: synth.uniform(70_003, 3, 34)}[case]()
+    want = oracle.kd_boruvka(pts, threads=os.cpu_count() or 4)
+    t = dev_pts(pts)
+    for count in (False, True):
+        e, st = pkg.emst_compute_ex(t, traversal=2, count_visits=count)
+        assert_same_edges(pkg.edges_numpy(e), want, f"persistent {case}")
+        if count:
+            assert sum(st["round_visits"]) == st["node_visits"]
+            assert st["round_queries"][0] == len(pts)  # the first round searches every point
+            assert all(0 < d <= len(pts) - 1 for d in st["round_distinct_nodes"][:2])
+
+
+def test_batched_persistent_matches_oracle(pkg):
+    sizes = [0, 1, 2, 3, 700, 2500, 3073, 17, 4000]
+    parts = [synth.blobs(s, 3, 700 + k, n_blobs=3) if s > 0 else np.zeros((0, 3), np.float32)
+             for k, s in enumerate(sizes)]
+    pts = np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    e, eo, st = pkg.emst_compute_batched_ex(dev_pts(pts), offsets, traversal=2)
+    got = pkg.edges_numpy(e)
+    for k, s in enumerate(sizes):
+        if s >= 2:
+            assert_same_edges(got[eo[k]:eo[k + 1]], oracle.prim(parts[k]), f"instance {k}")
