@@ -101,8 +101,25 @@ typedef struct emst_options {
                                  queue and refill lanes as searches end (plain rounds on
                                  one-point leaves; other forms use one thread per point).
                                  The tree is the same either way. */
-  int32_t reserved[5];
+  int32_t refill_lanes;       /* traversal 2: idle lanes that trigger a refill, 1..32
+                                 (0 = tuned or default 16) */
+  int32_t queue_chunk;        /* traversal 2: curve positions a warp takes from the queue at
+                                 a time, >= 32 (0 = tuned or default 64) */
+  int32_t ignore_tuning;      /* 1 = do not read the tuning file (see below); 0 = block_size,
+                                 leaf_size, traversal, refill_lanes and queue_chunk left at 0
+                                 take the tuned values for this GPU, dimension and size */
+  int32_t reserved[2];
 } emst_options;
+
+/* Tuning file.  emst_compute_ex / emst_compute_batched_ex (and the calls
+ * without options) read, once per process, the file named by the
+ * environment variable EMST_TUNING_FILE, else emst_tuning.txt beside
+ * libemst.so.  Each line "gpu=<name> dim=<2|3> form=<single|batched>
+ * nmin=<n> nmax=<n> traversal=<1|2> block=<b> leaf=<l> refill=<r> chunk=<c>"
+ * (other keys ignored, '#' starts a comment) gives the parameters of calls on
+ * a device of that name with nmin <= n < nmax points.  A missing or
+ * unreadable file means defaults.  The file only chooses among exact
+ * variants: the tree is the same whatever it says. */
 
 #define EMST_MRD_MAX_K 32
 
@@ -138,6 +155,11 @@ typedef struct emst_stats {
   int64_t round_queries[40];  /* queries that searched (the others were skipped by their
                                  lower bound before any node visit) */
   int64_t round_distinct_nodes[40]; /* distinct internal nodes those searches visited */
+  int32_t traversal_used;  /* the Algorithm 2 kernel that ran: 1 one thread per point, 2
+                              persistent work queue */
+  int32_t block_used;      /* its CTA size */
+  int32_t leaf_used;       /* points per leaf of the hierarchy */
+  int32_t tuned;           /* 1 when the tuning file chose parameters of this call */
 } emst_stats;
 
 /* EMST of n points (§3, Fig. 3 end to end).

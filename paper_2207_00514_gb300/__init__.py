@@ -79,7 +79,8 @@ class _Options(ctypes.Structure):
                 ("count_visits", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("mlp_params", ctypes.c_void_p), ("mrd_k", ctypes.c_int32),
                 ("morton_bits", ctypes.c_int32), ("traversal", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("refill_lanes", ctypes.c_int32), ("queue_chunk", ctypes.c_int32),
+                ("ignore_tuning", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Stats(ctypes.Structure):
@@ -94,7 +95,9 @@ class _Stats(ctypes.Structure):
                 ("learned_search_ms", ctypes.c_double), ("core_ms", ctypes.c_double),
                 ("code_collisions", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1),
                 ("round_visits", ctypes.c_int64 * 40), ("round_queries", ctypes.c_int64 * 40),
-                ("round_distinct_nodes", ctypes.c_int64 * 40)]
+                ("round_distinct_nodes", ctypes.c_int64 * 40),
+                ("traversal_used", ctypes.c_int32), ("block_used", ctypes.c_int32),
+                ("leaf_used", ctypes.c_int32), ("tuned", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -243,7 +246,8 @@ def emst_compute_noalloc(points, out_edges=None, stream=None):
 
 
 def _make_options(block_size=0, carried_radius=True, use_graph=False, count_visits=False,
-                  leaf_size=0, mlp_params=None, mrd_k=0, morton_bits=0, traversal=0):
+                  leaf_size=0, mlp_params=None, mrd_k=0, morton_bits=0, traversal=0,
+                  refill_lanes=0, queue_chunk=0, ignore_tuning=False):
     opt = _Options()
     opt.struct_size = ctypes.sizeof(_Options)
     opt.block_size = int(block_size)
@@ -254,6 +258,9 @@ def _make_options(block_size=0, carried_radius=True, use_graph=False, count_visi
     opt.mrd_k = int(mrd_k)
     opt.morton_bits = int(morton_bits)
     opt.traversal = int(traversal)
+    opt.refill_lanes = int(refill_lanes)
+    opt.queue_chunk = int(queue_chunk)
+    opt.ignore_tuning = 1 if ignore_tuning else 0
     if mlp_params is not None:
         if mlp_params.dtype != _torch().float32 or mlp_params.numel() != EMST_MLP_PARAMS:
             raise ValueError(f"mlp_params must hold {EMST_MLP_PARAMS} float32 values")
@@ -280,7 +287,9 @@ def _stats_dict(st):
                 morton_bits=st.morton_bits, code_collisions=st.code_collisions,
                 round_visits=[int(st.round_visits[k]) for k in range(r)],
                 round_queries=[int(st.round_queries[k]) for k in range(r)],
-                round_distinct_nodes=[int(st.round_distinct_nodes[k]) for k in range(r)])
+                round_distinct_nodes=[int(st.round_distinct_nodes[k]) for k in range(r)],
+                traversal_used=st.traversal_used, block_used=st.block_used,
+                leaf_used=st.leaf_used, tuned=bool(st.tuned))
 
 
 def emst_compute_ex(points, out_edges=None, stream=None, **options):

@@ -405,6 +405,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   }
   if (n == 0) return EMST_OK;
   int block = 0, carried = 1, count = 0, leaf_req = 0, mrd_k = 0, morton_bits = 0, traversal = 0;
+  int refill = 0, chunk = 0, ignore_tuning = 0;
   const float *mlp_params = nullptr;
   if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
     block = opt->block_size;
@@ -423,12 +424,34 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
     morton_bits = opt->morton_bits;
     traversal = opt->traversal;
     if (traversal < 0 || traversal > 2) return EMST_ERR_INVALID_ARG;
+    refill = opt->refill_lanes;
+    chunk = opt->queue_chunk;
+    ignore_tuning = opt->ignore_tuning;
+    if (refill < 0 || refill > 32 || (chunk != 0 && (chunk < 32 || chunk > (1 << 20))))
+      return EMST_ERR_INVALID_ARG;
     if (morton_bits != 0 && morton_bits != 64 && morton_bits != 128) return EMST_ERR_INVALID_ARG;
     if (leaf_req < 0 || leaf_req > 16 || (leaf_req & (leaf_req - 1)) != 0) return EMST_ERR_INVALID_ARG;
     if (block != 0 && (block < 64 || block > kTraverseMaxBlock || block % 32 != 0))
       return EMST_ERR_INVALID_ARG;
   } else if (opt && opt->struct_size != 0) {
     return EMST_ERR_INVALID_ARG;
+  }
+
+  // parameters the caller left to the library: the tuning file's choice for
+  // this GPU, dimension, form and size, if it has one
+  TuneChoice tuned;
+  bool was_tuned = false;
+  if (!ignore_tuning && lookup_tuning(dim, offsets != nullptr, n, &tuned)) {
+    was_tuned = true;
+    if (traversal == 0) traversal = tuned.traversal;
+    if (block == 0 && tuned.block >= 64 && tuned.block <= kTraverseMaxBlock && tuned.block % 32 == 0)
+      block = tuned.block;
+    if (leaf_req == 0 && !offsets && tuned.leaf >= 1 && tuned.leaf <= 16 &&
+        (tuned.leaf & (tuned.leaf - 1)) == 0 && !mlp_params && mrd_k < 2)
+      leaf_req = tuned.leaf;
+    if (refill == 0 && tuned.refill >= 1 && tuned.refill <= 32) refill = tuned.refill;
+    if (chunk == 0 && tuned.chunk >= 32) chunk = tuned.chunk;
+    if (traversal < 0 || traversal > 2) traversal = 0;
   }
 
   int dev = 0;
@@ -460,6 +483,9 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   P.wide = morton_bits == 128 && !offsets;
   P.auto_wide = morton_bits == 0 && !offsets;
   P.persistent = traversal == 2;
+  P.refill_lanes = refill;
+  P.queue_chunk = chunk;
+  P.block = block;
   P.want_count = count != 0;
   if (logging) {
     P.log_feat = ex->log_feat;
@@ -608,6 +634,10 @@ done:
     cudaStreamSynchronize(stream);
     stats->rounds = rounds;
     stats->kernel_launches = P.launches;
+    stats->traversal_used = P.persistent && !learned && !P.core2 && P.leaf == 1 ? 2 : 1;
+    stats->block_used = stats->traversal_used == 2 ? kPersistBlock : (block ? block : kTraverseBlock);
+    stats->leaf_used = P.leaf;
+    stats->tuned = was_tuned ? 1 : 0;
     stats->morton_bits = P.wide ? 128 : 64;
     stats->code_collisions = P.code_collisions;
     stats->build_ms = tm.ms(0, 1);

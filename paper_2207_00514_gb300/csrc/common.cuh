@@ -187,6 +187,9 @@ struct Problem {
                                      // than n/64 distinct points sharing a code (then 128)
   int64_t code_collisions = 0;       // that count, when measured
   bool persistent = false;           // A7 by the persistent work-queue kernel
+  int refill_lanes = 0;              // its refill threshold (0: default)
+  int queue_chunk = 0;               // its queue chunk per warp (0: default)
+  int block = 0;                     // one-thread-per-point traversal CTA size (0: default)
   bool want_count = false;           // set before layout(): carve the visited-node bitmap
   uint32_t *seen = nullptr;          // count runs: bitmap of the internal nodes visited this round
   bool ties = true;                  // the search needs its tie rule (a run of > 32 equal
@@ -305,6 +308,10 @@ int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int 
 #endif
 constexpr int kTraverseBlock = 128;     // default traversal CTA size (measured best)
 constexpr int kTraverseMaxBlock = 256;  // largest the traversal kernels are compiled for
+#ifndef EMST_PERSIST_BLOCK
+#define EMST_PERSIST_BLOCK 128
+#endif
+constexpr int kPersistBlock = EMST_PERSIST_BLOCK;  // CTA size of the persistent traversal
 int64_t scan_tiles_for(int64_t n);
 void launch_label_runs(Problem &P);
 void launch_node_labels(Problem &P);
@@ -335,6 +342,13 @@ void launch_predict(Problem &P, bool carried);
 void launch_rerun_mark(Problem &P);
 void launch_log_samples(Problem &P, int round, bool carried);
 void launch_edge_gather(Problem &P, int64_t m, const uint32_t *order, emst_edge *out);
+
+// tuning.cu: the tuned traversal parameters for this device, dimension, form
+// and size (0 in a field: no choice); false when the tuning file has none.
+struct TuneChoice {
+  int traversal = 0, block = 0, leaf = 0, refill = 0, chunk = 0;
+};
+bool lookup_tuning(int dim, bool batched, int64_t n, TuneChoice *out);
 
 // api.cu: helpers of the orchestration
 bool device_accessible(const void *p);

@@ -262,37 +262,25 @@ __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k
 // ---------------------------------------------------------------------------
 // A7, persistent form: a resident grid whose warps take queries from a
 // global work queue (the curve positions in order, handed out in chunks of
-// kQueueChunk consecutive positions per warp, so the queries a warp holds
-// stay close on the curve and share node records in L1) and refill a lane as
-// soon as its search ends, instead of holding 32 queries until the longest
-// one finishes.  Each loop iteration: when at least kRefillLanes lanes are
-// idle (or all are), they take the next positions of the warp's chunk and
-// start them (a query skipped by its lower bound finishes at once and leaves
-// its lane idle); then every lane with a search in progress makes one node
-// visit (or pops).  Same per-query arithmetic as traverse_one, so the same
-// results.  One-point leaves, no learned cutoff, no mutual reachability.
+// `chunk` consecutive positions per warp, so the queries a warp holds stay
+// close on the curve and share node records in L1) and refill a lane as soon
+// as its search ends, instead of holding 32 queries until the longest one
+// finishes.  Each loop iteration: when at least `refill` lanes are idle (or
+// all are), they take the next positions of the warp's chunk and start them
+// (a query skipped by its lower bound finishes at once and leaves its lane
+// idle); then every lane with a search in progress makes one node visit (or
+// pops).  Same per-query arithmetic as traverse_one, so the same results.
+// One-point leaves, no learned cutoff, no mutual reachability.
 // ---------------------------------------------------------------------------
-#ifndef EMST_QUEUE_CHUNK
-#define EMST_QUEUE_CHUNK 64
-#endif
-#ifndef EMST_REFILL_LANES
-#define EMST_REFILL_LANES 16
-#endif
-#ifndef EMST_PERSIST_BLOCK
-#define EMST_PERSIST_BLOCK 128
-#endif
 #ifndef EMST_PERSIST_MIN_BLOCKS
 #define EMST_PERSIST_MIN_BLOCKS 12
 #endif
-
-constexpr int kQueueChunk = EMST_QUEUE_CHUNK;
-static_assert(kQueueChunk >= 32, "a refill takes at most 32 positions, from at most two chunks");
-constexpr int kRefillLanes = EMST_REFILL_LANES;
-constexpr int kPersistBlock = EMST_PERSIST_BLOCK;
+constexpr int kDefaultRefill = 16;   // measured best of 4 / 8 / 16 at 37M halo points
+constexpr int kDefaultChunk = 64;    // measured best of 32 / 64 / 128
 
 template <bool CARRIED, bool FIRST, bool TIES, bool COUNT>
 __global__ void __launch_bounds__(kPersistBlock, EMST_PERSIST_MIN_BLOCKS)
-    k_traverse_queue(TravArgs A, unsigned long long *queue) {
+    k_traverse_queue(TravArgs A, unsigned long long *queue, int refill, int chunk) {
   const unsigned lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t n = A.n;
@@ -309,12 +297,12 @@ __global__ void __launch_bounds__(kPersistBlock, EMST_PERSIST_MIN_BLOCKS)
   while (true) {
     const unsigned idle = __ballot_sync(0xffffffffu, !live);
     if (idle == 0xffffffffu && drained) break;
-    if (!drained && __popc(idle) >= (idle == 0xffffffffu ? 1 : kRefillLanes)) {
+    if (!drained && __popc(idle) >= (idle == 0xffffffffu ? 1 : refill)) {
       const int need = __popc(idle);
       const int64_t avail = end - next;
       int64_t fresh = 0;
       if (avail < need) {
-        if (lane == 0) fresh = (int64_t)atomicAdd(queue, (unsigned long long)kQueueChunk);
+        if (lane == 0) fresh = (int64_t)atomicAdd(queue, (unsigned long long)chunk);
         fresh = __shfl_sync(0xffffffffu, fresh, 0);
       }
       if (!live) {
@@ -333,7 +321,7 @@ __global__ void __launch_bounds__(kPersistBlock, EMST_PERSIST_MIN_BLOCKS)
       }
       if (avail < need) {
         next = fresh + (need - avail);
-        end = fresh + kQueueChunk;
+        end = fresh + chunk;
       } else {
         next += need;
       }
@@ -371,6 +359,9 @@ __global__ void __launch_bounds__(kPersistBlock, EMST_PERSIST_MIN_BLOCKS)
 
 template <bool CARRIED, bool FIRST, bool TIES, bool COUNT>
 static void queue_launch(Problem &P, const TravArgs &A) {
+  // chunk >= 32: a refill takes at most 32 positions, from at most two chunks
+  const int chunk = P.queue_chunk >= 32 ? P.queue_chunk : kDefaultChunk;
+  const int refill = P.refill_lanes >= 1 && P.refill_lanes <= 32 ? P.refill_lanes : kDefaultRefill;
   static int blocks_per_sm[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -386,12 +377,13 @@ static void queue_launch(Problem &P, const TravArgs &A) {
   }
   const int per_sm = (dev >= 0 && dev < 64) ? blocks_per_sm[dev] : 1;
   // no more warps than there are chunks of queries
-  const int64_t warps_needed = (A.n + kQueueChunk - 1) / kQueueChunk;
+  const int64_t warps_needed = (A.n + chunk - 1) / chunk;
   int64_t g = (int64_t)sm_count() * per_sm;
   const int64_t g_need = (warps_needed + kPersistBlock / 32 - 1) / (kPersistBlock / 32);
   if (g > g_need) g = g_need;
   if (g < 1) g = 1;
-  kern<<<(unsigned)g, kPersistBlock, sm, P.stream>>>(A, reinterpret_cast<unsigned long long *>(P.counters + 36));
+  kern<<<(unsigned)g, kPersistBlock, sm, P.stream>>>(A, reinterpret_cast<unsigned long long *>(P.counters + 36),
+                                                     refill, chunk);
 }
 
 static void launch_traverse_queue(Problem &P, const TravArgs &A, bool carried, bool first, bool count) {
