@@ -32,11 +32,15 @@ sys.path.insert(0, ROOT)
 METRIC = "EMST Mpoints/s at 37M 3D clustered, plain vs learned-radius; % HBM roofline"
 WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member counts m^-1.9 on "
             "[10, 1e5], c = 5, r_vir = 0.01 (m/1e5)^(1/3)), 20% uniform, unit box, seed 2")
-# DRAM bytes (read + write) per launch of the traversal kernel on this
-# workload, averaged over one call's launches, from an ncu capture
-# (--metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none);
-# None until a capture of the kernel as it is now exists.
-TRAVERSE_DRAM_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) of each round's traversal launch on this workload
+# (37M halo points, seed 2), from one ncu capture of one whole call of the
+# kernel as it is now:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#       --cache-control none -k regex:k_traverse -c 11 --csv
+#       python <one emst_compute call on these points>
+# (one pass per launch).  Set back to None whenever the traversal kernel changes.
+TRAVERSE_DRAM_BYTES_PER_ROUND = [4519.8e6, 5671.5e6, 4655.0e6, 3146.4e6, 2021.5e6, 1655.1e6,
+                                 1515.2e6, 1436.0e6, 1390.1e6, 1360.9e6, 1339.7e6]
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")
 
@@ -632,8 +636,13 @@ def main():
         "distinct_nodes": vis["round_distinct_nodes"][:rr],
         "visits": vis["round_visits"][:rr],
     }
-    traffic = TRAVERSE_DRAM_BYTES_PER_LAUNCH if n == 37_000_000 else None
-    roofline = {"bound": "hbm", "kernel": "k_traverse_queue (Algorithm 2 queries, persistent work queue)",
+    measured = (TRAVERSE_DRAM_BYTES_PER_ROUND if n == 37_000_000 and seed == 2
+                and TRAVERSE_DRAM_BYTES_PER_ROUND and len(TRAVERSE_DRAM_BYTES_PER_ROUND) == rr else None)
+    traffic = sum(measured) / rr if measured else None
+    if measured:
+        per_round["dram_bytes"] = measured
+        per_round["dram_over_algorithmic"] = [round(d / b, 3) for d, b in zip(measured, rb)]
+    roofline = {"bound": "hbm", "kernel": "k_traverse (Algorithm 2 queries, one thread per point)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "peak_kind": (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs copy)" if peak_kind == "measured"

@@ -311,9 +311,21 @@ int run_output(Problem &P, emst_edge *out, uint32_t w_bits) {
   if (m <= 0) return EMST_OK;
   const int L = bits_for(P.n - 1);
   const int wb = w_bits ? 32 - __builtin_clz(w_bits) : 0;
-  if (P.num_inst == 1) {
-    launch_edge_keys_wi(P, m, L);
-    const int s = radix_sort_pairs(P, m, 0, (L + wb + 7) / 8, 0);
+  // fast path: one sort of a 64-bit key, then the runs of equal keys (the
+  // edges of one point at one weight) put in j order in place -- unless such
+  // a run is long (exact ties: many identical points), then the full path
+  const int Lloc = P.num_inst > 1 ? bits_for(P.largest > 1 ? P.largest - 1 : 1) : L;
+  const bool fast = P.num_inst == 1 || P.inst_bits + wb + Lloc <= 64;
+  if (fast) {
+    int digits;
+    if (P.num_inst == 1) {
+      launch_edge_keys_wi(P, m, L);
+      digits = (L + wb + 7) / 8;
+    } else {
+      launch_edge_keys_inst_wi(P, m, wb + Lloc, Lloc);
+      digits = (P.inst_bits + wb + Lloc + 7) / 8;
+    }
+    const int s = radix_sort_pairs(P, m, 0, digits, 0);
     cudaMemsetAsync(P.counters + 10, 0, sizeof(uint32_t), P.stream);
     launch_edge_ties(P, m, s);
     uint32_t long_runs = 0;
@@ -322,7 +334,7 @@ int run_output(Problem &P, emst_edge *out, uint32_t w_bits) {
         cudaStreamSynchronize(P.stream) != cudaSuccess)
       return EMST_ERR_CUDA;
     if (long_runs == 0) {
-      launch_edge_from_keys(P, m, s, L, out);
+      launch_edge_from_keys(P, m, s, Lloc, wb, out);
       return EMST_OK;
     }
   }
@@ -475,6 +487,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   P.num_inst = num_inst;
   P.inst_bits = num_inst > 1 ? bits_for(num_inst - 1) : 0;
   P.edges_expected = expected;
+  P.largest = largest;
   // (a batched problem keeps one point per leaf: chunks would mix instances)
   P.leaf = num_inst > 1 ? 1 : effective_leaf(n, leaf_req);
   P.want_learned = learned;

@@ -175,6 +175,7 @@ struct Problem {
   uint32_t *inst_of = nullptr;      // n: instance of each curve position
   uint32_t *inst_root = nullptr;    // num_inst: root node of each instance's subtree
   int64_t edges_expected = 0;       // sum over instances of max(n_I - 1, 0)
+  int64_t largest = 0;              // points of the largest instance
 
   // Learned radius (optional): network parameters (device, EMST_MLP_PARAMS
   // floats), proposed cutoffs, the cutoffs used, component sizes and the
@@ -332,7 +333,9 @@ void launch_count_seen(Problem &P);
 // output
 void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i);
 void launch_edge_ties(Problem &P, int64_t m, int src);
-void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, emst_edge *out);
+void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, int w_bits_used,
+                           emst_edge *out);
+void launch_edge_keys_inst_wi(Problem &P, int64_t m, int shift_w, int shift_i);
 void launch_edge_keys_j(Problem &P, int64_t m);
 void launch_edge_keys_wi_of(Problem &P, int64_t m, int src, int shift_i);
 void launch_edge_keys_inst(Problem &P, int64_t m, int src);

@@ -3,6 +3,10 @@
 //   (Optimization 2), A7 nearest-other-component traversal (Algorithm 2),
 //   A8 per-component minimum, A9 merge (§3 "Merging components together"),
 // plus the final ordering of the edges (A12).
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "traverse.cuh"
 
 namespace emst {
@@ -403,6 +407,28 @@ static void launch_traverse_queue(Problem &P, const TravArgs &A, bool carried, b
   P.launches += 1;
 }
 
+// Shared-memory carve-out preferred for the one-thread-per-point traversal
+// (percent of the unified L1 / shared storage; -1 = the driver's choice).
+// The search needs no shared memory and lives on L1 hits of node records.
+#ifndef EMST_L1_CARVEOUT
+#define EMST_L1_CARVEOUT -1
+#endif
+using TravKernel = void (*)(TravArgs, const uint32_t *, const uint32_t *);
+
+static void launch_trav(TravKernel k, int g, int block, cudaStream_t s, const TravArgs &A,
+                        const uint32_t *list, const uint32_t *list_count) {
+  if (EMST_L1_CARVEOUT >= 0) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.insert({dev, reinterpret_cast<const void *>(k)}).second)
+      cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, EMST_L1_CARVEOUT);
+  }
+  k<<<g, block, 0, s>>>(A, list, list_count);
+}
+
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
                      bool seeded, int learned_pass, bool first) {
   if (block <= 0) block = kTraverseBlock;
@@ -438,12 +464,11 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   const uint32_t *list = learned_pass == 2 ? P.rerun_list : nullptr;
   const uint32_t *list_count = learned_pass == 2 ? P.counters + 13 : nullptr;
   const int g = learned_pass == 2 ? sm_count() * 8 : grid_for(P.n, block);
-  const size_t sm = 0;
   cudaStream_t s = P.stream;
-#define EMST_TRAV2(C, R, K, S, H, L) k_traverse<C, R, K, S, H, L, false, false><<<g, block, sm, s>>>(A, list, list_count)
-#define EMST_TRAV_FIRST(K, H) k_traverse<false, false, K, true, H, false, true, false><<<g, block, sm, s>>>(A, list, list_count)
-#define EMST_TRAV_MRD(C, K, H) k_traverse<C, false, K, true, H, false, false, true><<<g, block, sm, s>>>(A, list, list_count)
-#define EMST_TRAV_NOTIES(C, F, H) k_traverse<C, false, false, true, H, false, F, false, false><<<g, block, sm, s>>>(A, list, list_count)
+#define EMST_TRAV2(C, R, K, S, H, L) launch_trav(k_traverse<C, R, K, S, H, L, false, false>, g, block, s, A, list, list_count)
+#define EMST_TRAV_FIRST(K, H) launch_trav(k_traverse<false, false, K, true, H, false, true, false>, g, block, s, A, list, list_count)
+#define EMST_TRAV_MRD(C, K, H) launch_trav(k_traverse<C, false, K, true, H, false, false, true>, g, block, s, A, list, list_count)
+#define EMST_TRAV_NOTIES(C, F, H) launch_trav(k_traverse<C, false, false, true, H, false, F, false, false>, g, block, s, A, list, list_count)
 #define EMST_TRAV(C, R, K, S, L)                       \
   do {                                                 \
     if (P.leaf > 1) EMST_TRAV2(C, R, K, S, true, L);   \
@@ -737,18 +762,39 @@ __global__ void k_edge_ties(const uint64_t *__restrict__ keys, uint32_t *__restr
   }
 }
 
-// One instance: edge e of the output from its sorted key ((w << L) | i) and j.
+// Edge e of the output from its sorted key ((w << L) | i, with the instance
+// above w in the batched form) and j; w_mask keeps w's bits.
 __global__ void k_edge_from_keys(const uint64_t *__restrict__ keys,
                                  const uint32_t *__restrict__ vals, int64_t m, int shift_i,
-                                 emst_edge *__restrict__ out) {
+                                 uint32_t w_mask, emst_edge *__restrict__ out) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   const uint64_t k = keys[e];
   emst_edge E;
   E.i = (uint32_t)(k & ((1ull << shift_i) - 1ull));
   E.j = vals[e];
-  E.w = __uint_as_float((uint32_t)(k >> shift_i));
+  E.w = __uint_as_float((uint32_t)(k >> shift_i) & w_mask);
   out[e] = E;
+}
+
+// Batched fast path: one key per edge, (instance, w, local i), with the
+// local j as the value, when the three fit in 64 bits.  Sorting it puts every
+// instance's edges together in (w, i, j) order (local ids keep the order of
+// the global ones: one offset per instance), with the same tie fix for runs
+// of equal (w, i) as one instance.
+__global__ void k_edge_keys_inst_wi(const emst_edge *__restrict__ edges, int64_t m,
+                                    uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                    const uint32_t *__restrict__ inst_in,
+                                    const int64_t *__restrict__ offsets, int shift_w,
+                                    int shift_i) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const emst_edge E = edges[e];
+  const uint32_t I = __ldg(inst_in + E.i);
+  const uint32_t base = (uint32_t)__ldg(offsets + I);
+  keys[e] = ((uint64_t)I << shift_w) | ((uint64_t)__float_as_uint(E.w) << shift_i) |
+            (uint64_t)(E.i - base);
+  vals[e] = E.j - base;
 }
 
 // Full path: keys by j with the edge index as the value, then keys by
@@ -804,9 +850,16 @@ void launch_edge_ties(Problem &P, int64_t m, int src) {
                                                             P.counters + 10);
   P.launches += 1;
 }
-void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, emst_edge *out) {
+void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, int w_bits_used,
+                           emst_edge *out) {
+  const uint32_t w_mask = w_bits_used >= 32 ? 0xFFFFFFFFu : ((1u << w_bits_used) - 1u);
   k_edge_from_keys<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], m,
-                                                                 shift_i, out);
+                                                                 shift_i, w_mask, out);
+  P.launches += 1;
+}
+void launch_edge_keys_inst_wi(Problem &P, int64_t m, int shift_w, int shift_i) {
+  k_edge_keys_inst_wi<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(
+      P.edges, m, P.keys[0], P.vals[0], P.inst_in, P.offsets, shift_w, shift_i);
   P.launches += 1;
 }
 void launch_edge_keys_j(Problem &P, int64_t m) {
