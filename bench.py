@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="halos37M",
-                    choices=["halos37M", "batched", "sweep", "mrd", "dense", "dendrogram"],
+                    choices=["halos37M", "batched", "sweep", "mrd", "dense", "dendrogram", "once"],
                     help="batched: 4,096 independent 3D instances (sizes log-uniform in [100, 1e6]) "
                          "in one emst_compute_batched call, against one emst_compute per instance")
     ap.add_argument("--instances", type=int, default=4096)
@@ -509,9 +509,27 @@ def run_dendrogram(args, rank, world, local):
         del edges
 
 
+def run_once(args, rank, world, local):
+    """One emst_compute call on the halo workload (--n, --seed) and nothing
+    else: the command the profiler captures."""
+    if rank != 0:
+        return
+    import torch
+    import paper_2207_00514_gb300 as pkg
+    pkg.load_library()
+    torch.cuda.set_device(local)
+    pts = torch.from_numpy(make_points(args.n, args.seed)).cuda()
+    e = pkg.emst_compute(pts)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": workload_name(args.n, args.seed), "edges": int(e.shape[0])}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "once":
+        run_once(args, rank, world, local)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

@@ -3,10 +3,6 @@
 //   (Optimization 2), A7 nearest-other-component traversal (Algorithm 2),
 //   A8 per-component minimum, A9 merge (§3 "Merging components together"),
 // plus the final ordering of the edges (A12).
-#include <mutex>
-#include <set>
-#include <utility>
-
 #include "traverse.cuh"
 
 namespace emst {
@@ -407,25 +403,10 @@ static void launch_traverse_queue(Problem &P, const TravArgs &A, bool carried, b
   P.launches += 1;
 }
 
-// Shared-memory carve-out preferred for the one-thread-per-point traversal
-// (percent of the unified L1 / shared storage; -1 = the driver's choice).
-// The search needs no shared memory and lives on L1 hits of node records.
-#ifndef EMST_L1_CARVEOUT
-#define EMST_L1_CARVEOUT -1
-#endif
 using TravKernel = void (*)(TravArgs, const uint32_t *, const uint32_t *);
 
 static void launch_trav(TravKernel k, int g, int block, cudaStream_t s, const TravArgs &A,
                         const uint32_t *list, const uint32_t *list_count) {
-  if (EMST_L1_CARVEOUT >= 0) {
-    static std::mutex mu;
-    static std::set<std::pair<int, const void *>> done;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> lock(mu);
-    if (done.insert({dev, reinterpret_cast<const void *>(k)}).second)
-      cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, EMST_L1_CARVEOUT);
-  }
   k<<<g, block, 0, s>>>(A, list, list_count);
 }
 
