@@ -61,6 +61,75 @@ __global__ void __launch_bounds__(kBlock) k_scene_box(const float *__restrict__ 
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kErrNonFinite);
 }
 
+// The COPY form reading 16 bytes per load (the host input through its
+// mapping): the flat coordinate array as float4s, element e of dimension
+// e % DIM; `tail` (< 4) trailing elements read one by one by thread 0.
+// src and copy 16-byte aligned.
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_scene_box_copy4(const float4 *__restrict__ src,
+                                                            int64_t nv, int tail,
+                                                            uint32_t *__restrict__ box,
+                                                            uint32_t *__restrict__ status,
+                                                            float4 *__restrict__ copy) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY};
+  float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool bad = false;
+  auto take = [&](float x, int d) {
+    if (!isfinite(x)) { bad = true; return; }
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) {
+      if (q == d) {
+        lo[q] = fminf(lo[q], x);
+        hi[q] = fmaxf(hi[q], x);
+      }
+    }
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  auto use = [&](const float4 &a, int64_t v) {
+    copy[v] = a;
+    const int d0 = (int)((4 * v) % DIM);
+    take(a.x, d0);
+    take(a.y, (d0 + 1) % DIM);
+    take(a.z, (d0 + 2) % DIM);
+    take(a.w, (d0 + 3) % DIM);
+  };
+  // four independent loads in flight per thread (the link's latency is long)
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; v + 3 * stride < nv; v += 4 * stride) {
+    const float4 a0 = src[v], a1 = src[v + stride], a2 = src[v + 2 * stride], a3 = src[v + 3 * stride];
+    use(a0, v);
+    use(a1, v + stride);
+    use(a2, v + 2 * stride);
+    use(a3, v + 3 * stride);
+  }
+  for (; v < nv; v += stride) use(src[v], v);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const float *s1 = reinterpret_cast<const float *>(src + nv);
+    float *c1 = reinterpret_cast<float *>(copy + nv);
+    for (int t = 0; t < tail; ++t) {
+      c1[t] = s1[t];
+      take(s1[t], (int)((4 * nv + t) % DIM));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[q] = fminf(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+      hi[q] = fmaxf(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) {
+      if (lo[q] <= hi[q]) {
+        atomicMin(&box[q], float_to_ordered(lo[q]));
+        atomicMax(&box[3 + q], float_to_ordered(hi[q]));
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kErrNonFinite);
+}
+
 __global__ void k_box_init(uint32_t *box) {
   int t = threadIdx.x;
   if (t < 3) box[t] = 0xFFFFFFFFu;
@@ -74,7 +143,20 @@ void launch_scene_box(Problem &P) {
   int64_t need = (P.n + kBlock - 1) / kBlock;
   if (need < grid) grid = (int)(need < 1 ? 1 : need);
   float *copy = const_cast<float *>(P.points);
-  if (P.points_mapped) {  // read the host input through its mapping, keep a device copy
+  if (P.points_mapped && (reinterpret_cast<uintptr_t>(P.points_mapped) & 15u) == 0 &&
+      (reinterpret_cast<uintptr_t>(copy) & 15u) == 0) {
+    // read the host input through its mapping 16 bytes at a time, keep a device copy
+    const int64_t elems = P.n * P.dim, nv = elems / 4;
+    const int tail = (int)(elems - 4 * nv);
+    int g4 = sm_count() * 4;
+    if ((nv + kBlock - 1) / kBlock < g4) g4 = (int)((nv + kBlock - 1) / kBlock < 1 ? 1 : (nv + kBlock - 1) / kBlock);
+    const float4 *src = reinterpret_cast<const float4 *>(P.points_mapped);
+    float4 *dst = reinterpret_cast<float4 *>(copy);
+    if (P.dim == 3)
+      k_scene_box_copy4<3><<<g4, kBlock, 0, P.stream>>>(src, nv, tail, box, P.counters + 1, dst);
+    else
+      k_scene_box_copy4<2><<<g4, kBlock, 0, P.stream>>>(src, nv, tail, box, P.counters + 1, dst);
+  } else if (P.points_mapped) {  // read the host input through its mapping, keep a device copy
     if (P.dim == 3)
       k_scene_box<3, true><<<grid, kBlock, 0, P.stream>>>(P.points_mapped, P.n, box, P.counters + 1, copy);
     else

@@ -758,6 +758,37 @@ __global__ void k_edge_from_keys(const uint64_t *__restrict__ keys,
   out[e] = E;
 }
 
+// The same with 16-byte stores that consecutive lanes make to consecutive
+// addresses (the output may be pinned host memory written over the
+// chip-to-chip link, where whole coalesced lines matter): thread c writes
+// 16-byte chunk c of the output, i.e. words 4c..4c+3 of the flat array of
+// (i, j, w) words, rebuilt from the (at most two) edges they belong to.
+// `out` 16-byte aligned; chunks = floor(3m / 4) whole chunks.
+__global__ void k_edge_from_keys16(const uint64_t *__restrict__ keys,
+                                   const uint32_t *__restrict__ vals, int64_t chunks, int shift_i,
+                                   uint32_t w_mask, uint4 *__restrict__ out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= chunks) return;
+  const uint64_t imask = (1ull << shift_i) - 1ull;
+  uint32_t w[4];
+  const int64_t w0 = 4 * c;
+  int64_t e = w0 / 3;
+  int f = (int)(w0 - 3 * e);
+  uint64_t k = __ldg(keys + e);
+  uint32_t j = __ldg(vals + e);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    w[q] = f == 0 ? (uint32_t)(k & imask) : f == 1 ? j : ((uint32_t)(k >> shift_i) & w_mask);
+    if (++f == 3 && q < 3) {
+      f = 0;
+      ++e;
+      k = __ldg(keys + e);
+      j = __ldg(vals + e);
+    }
+  }
+  out[c] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // Batched fast path: one key per edge, (instance, w, local i), with the
 // local j as the value, when the three fit in 64 bits.  Sorting it puts every
 // instance's edges together in (w, i, j) order (local ids keep the order of
@@ -834,9 +865,21 @@ void launch_edge_ties(Problem &P, int64_t m, int src) {
 void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, int w_bits_used,
                            emst_edge *out) {
   const uint32_t w_mask = w_bits_used >= 32 ? 0xFFFFFFFFu : ((1u << w_bits_used) - 1u);
-  k_edge_from_keys<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], m,
-                                                                 shift_i, w_mask, out);
-  P.launches += 1;
+  // whole 16-byte chunks of the output by coalesced wide stores when it is
+  // 16-byte aligned, the edges after the last whole chunk one by one
+  const int64_t chunks = (reinterpret_cast<uintptr_t>(out) & 15u) == 0 ? (3 * m) / 4 : 0;
+  const int64_t covered = (4 * chunks) / 3;  // edges wholly inside those chunks (the next one,
+                                             // if split, is rewritten whole below)
+  if (chunks > 0) {
+    k_edge_from_keys16<<<grid_for(chunks, kBlock), kBlock, 0, P.stream>>>(
+        P.keys[src], P.vals[src], chunks, shift_i, w_mask, reinterpret_cast<uint4 *>(out));
+    P.launches += 1;
+  }
+  if (m - covered > 0) {
+    k_edge_from_keys<<<grid_for(m - covered, kBlock), kBlock, 0, P.stream>>>(
+        P.keys[src] + covered, P.vals[src] + covered, m - covered, shift_i, w_mask, out + covered);
+    P.launches += 1;
+  }
 }
 void launch_edge_keys_inst_wi(Problem &P, int64_t m, int shift_w, int shift_i) {
   k_edge_keys_inst_wi<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(

@@ -387,3 +387,23 @@ def test_batched_persistent_matches_oracle(pkg):
     for k, s in enumerate(sizes):
         if s >= 2:
             assert_same_edges(got[eo[k]:eo[k + 1]], oracle.prim(parts[k]), f"instance {k}")
+
+
+@pytest.mark.parametrize("n,dim", [(70_001, 3), (50_002, 2), (4, 3), (2, 2)])
+def test_pinned_host_buffers_match_oracle(pkg, n, dim):
+    """Pinned host input and output are read and written in place (the
+    scene-box pass reads the points through their device mapping, 16 bytes
+    at a time with a ragged tail; the last output kernel writes four edges
+    per thread straight into the host buffer, the rest one by one): the tree
+    is the oracle's, and pageable host buffers give the same."""
+    pts = synth.halos(n, 41) if dim == 3 else synth.blobs(n, 2, 42)
+    want = oracle.kd_boruvka(pts, threads=os.cpu_count() or 4) if n > 10 else oracle.prim(pts)
+    hp = torch.from_numpy(pts).pin_memory()
+    ho = torch.empty((n - 1, 3), dtype=torch.int32).pin_memory()
+    pkg.emst_compute(hp, out_edges=ho)
+    torch.cuda.synchronize()
+    assert_same_edges(pkg.edges_numpy(ho), want, f"pinned n={n} dim={dim}")
+    po = torch.empty((n - 1, 3), dtype=torch.int32)  # pageable
+    pkg.emst_compute(torch.from_numpy(pts.copy()), out_edges=po)
+    torch.cuda.synchronize()
+    assert_same_edges(pkg.edges_numpy(po), want, f"pageable n={n} dim={dim}")
