@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--cpu-full", type=int, default=1,
                     help="cpu_baseline: 1 = the oracle on the whole workload (all host threads)")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--traversal", type=int, default=0,
+                    help="once workload: the traversal kernel (0 default, 1 one thread per point, "
+                         "2 persistent work queue)")
     ap.add_argument("--no-batched-summary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -519,7 +522,7 @@ def run_once(args, rank, world, local):
     pkg.load_library()
     torch.cuda.set_device(local)
     pts = torch.from_numpy(make_points(args.n, args.seed)).cuda()
-    e = pkg.emst_compute(pts)
+    e = pkg.emst_compute_ex(pts, traversal=args.traversal)[0]
     torch.cuda.synchronize()
     print(json.dumps({"workload": workload_name(args.n, args.seed), "edges": int(e.shape[0])}), flush=True)
 

@@ -225,6 +225,8 @@ int emst_core_distances(const float *points, int64_t n, int dim, int k, float *o
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before any
  *     stream capture on the device.
+ *   - The call waits on its stream: it reads a status word back after the
+ *     build and after every round, like emst_compute.
  *   - Every call on a device shares the array and it keeps the last call's
  *     contents (each call clears what must start at zero).  Calls whose GPU
  *     work overlaps (other streams or threads, same device) race on it and

@@ -158,12 +158,9 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.next_list = P.list_buf[0];
   P.n_active = n;
   P.res = c.take<uint2>(n);
-  P.comp_key_buf[0] = c.take<uint64_t>(n);
-  P.comp_key_buf[1] = c.take<uint64_t>(n);
-  P.comp_max_buf[0] = c.take<uint64_t>(n);
-  P.comp_max_buf[1] = c.take<uint64_t>(n);
-  P.comp_key = P.comp_key_buf[0];
-  P.comp_max = P.comp_max_buf[0];
+  P.comp_buf[0] = c.take<CompBest>(n);
+  P.comp_buf[1] = c.take<CompBest>(n);
+  P.comp = P.comp_buf[0];
   P.root = c.take<uint32_t>(n);
   P.edges = c.take<emst_edge>(n);
   if (P.num_inst > 1) {
@@ -197,7 +194,7 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
 int status_from_bits(uint32_t bits) {
   if (bits & kErrBadInput) return EMST_ERR_INVALID_ARG;
   if (bits & kErrNonFinite) return EMST_ERR_NONFINITE;
-  if (bits & (kErrStack | kErrSpin | kErrChain)) return EMST_ERR_INTERNAL;
+  if (bits & (kErrStack | kErrSpin | kErrChain | kErrCas)) return EMST_ERR_INTERNAL;
   return EMST_OK;
 }
 
@@ -292,15 +289,13 @@ void run_round(Problem &P, int round, bool carried, int block, bool count) {
   if (round > 0) launch_node_labels(P);
   else launch_upper_bounds(P);
   launch_traverse(P, round > 0 && carried, nullptr, block, count, true, 0, round == 0);
-  launch_reduce(P);
   launch_merge(P);
 }
 
 void reset_round_state(Problem &P) {
   cudaMemsetAsync(P.bound, 0xFF, sizeof(uint32_t) * (size_t)P.n, P.stream);
   // (the other buffer is cleared by the first round's merge)
-  cudaMemsetAsync(P.comp_key, 0xFF, sizeof(uint64_t) * (size_t)P.n, P.stream);
-  cudaMemsetAsync(P.comp_max, 0xFF, sizeof(uint64_t) * (size_t)P.n, P.stream);
+  cudaMemsetAsync(P.comp, 0xFF, sizeof(CompBest) * (size_t)P.n, P.stream);
 }
 
 // A12: the n-1 edges in (w, i, j) order into `out` (device).  w_bits: the
@@ -597,7 +592,6 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
         n_tev = rounds + 1;
       }
       if (count) launch_count_seen(P);
-      launch_reduce(P);
       launch_merge(P);
       CU(cudaPeekAtLastError());  // a launch that failed must not read as a round without edges
       CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(host_counters), cudaMemcpyDeviceToHost,
@@ -941,7 +935,6 @@ int emst_round_step(const float *points, int64_t n, int dim, int leaf_size,
     k_bound_to_float<<<grid_for(n, 256), 256, 0, s>>>(P.bound, out_upper_bound, n);
   launch_traverse(P, false, radius_in, 0, false, false);
   if (out_nn_w || out_nn_j) k_split_res<<<grid_for(n, 256), 256, 0, s>>>(P.res, out_nn_w, out_nn_j, n);
-  launch_reduce(P);
   launch_merge(P);
   if (out_labels)
     cudaMemcpyAsync(out_labels, P.labels_buf[P.cur ^ 1], 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);

@@ -14,6 +14,18 @@ constexpr uint32_t kLeafBit = 0x80000000u;   // child reference of a leaf
 constexpr uint32_t kNoBound = 0xFFFFFFFFu;   // "+inf" in the u32 radius arrays
 constexpr uint64_t kEmptyKey = ~0ull;        // empty per-component minimum
 
+// The minimum outgoing edge of a component (A8) as one 128-bit key, ordered
+// as the pair (key, mx): key = (w bits << 32) | min original id (w >= 0, so
+// float bits order as unsigned), mx = (max original id << 32) | the label of
+// the edge's endpoint outside the component (fixed by the edge, so it never
+// decides the order).  Its lexicographic minimum is the (w, min id, max id)
+// minimum of §2's tie-break.  All ones = no edge yet.
+struct __align__(16) CompBest {
+  uint64_t mx;
+  uint64_t key;
+};
+static_assert(sizeof(CompBest) == 16, "one 128-bit key per component");
+
 // Error bits of the device status word.
 enum : uint32_t {
   kErrNonFinite = 1u << 0,
@@ -21,6 +33,7 @@ enum : uint32_t {
   kErrSpin = 1u << 2,
   kErrChain = 1u << 3,
   kErrBadInput = 1u << 4,  // an input found invalid on the device (dendrogram)
+  kErrCas = 1u << 5,       // a compare-and-swap loop gave up (bounded retries)
 };
 
 // One internal node of the hierarchy, 64 bytes.  The boxes of both children
@@ -245,13 +258,11 @@ struct Problem {
   uint2 *res = nullptr;              // n: (w bits, neighbour curve index)
   float *core2 = nullptr;            // n: mutual reachability -- squared core distances in
                                      //    curve order (nullptr: the Euclidean weight)
-  // Per-component minimum edge, in two stages (A8), ping-pong by round: the
-  // merge of round r clears the other buffer's entries of its active labels.
-  uint64_t *comp_key_buf[2] = {nullptr, nullptr};  // n: (w bits << 32) | min original id
-  uint64_t *comp_max_buf[2] = {nullptr, nullptr};  // n: (max original id << 32) | label of the
-                                                   //    edge's endpoint outside the component
-  uint64_t *comp_key = nullptr;      // = comp_key_buf[cur]
-  uint64_t *comp_max = nullptr;      // = comp_max_buf[cur]
+  // Per-component minimum edge (A8), indexed by label, ping-pong by round:
+  // the merge of round r clears the other buffer's entries of its active
+  // labels.
+  CompBest *comp_buf[2] = {nullptr, nullptr};  // n
+  CompBest *comp = nullptr;          // = comp_buf[cur]
   uint32_t *root = nullptr;          // n: new label of a component
   emst_edge *edges = nullptr;        // n: edges in emission order
   emst_edge *out_stage = nullptr;    // n-1: device staging of host outputs
@@ -324,7 +335,6 @@ void launch_core_to_input(Problem &P, float *out);
 // first: the first round of the plain form (labels = curve indices)
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
                      bool seeded, int learned_pass = 0, bool first = false);
-void launch_reduce(Problem &P);
 void launch_merge(Problem &P);
 void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
 // count runs: adds the bits of the visited-node bitmap to counters[38..39]

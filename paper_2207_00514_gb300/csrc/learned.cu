@@ -54,7 +54,7 @@ struct FeatArgs {
   const float4 *pts;
   const uint32_t *labels;
   const uint32_t *bound;
-  const uint64_t *comp_key;
+  const CompBest *comp;
   const uint2 *res;
   const uint32_t *comp_size;
   const uint32_t *box;  // ordered scene box
@@ -105,7 +105,7 @@ __device__ __forceinline__ void point_features(const FeatArgs &A, int64_t i, flo
   const uint32_t me = A.labels[i];
   U = bound_to_radius(A.bound[me]);
   const uint32_t cw =
-      (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(A.comp_key + me)) >> 32);
+      (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(&A.comp[me].key)) >> 32);
   U = fminf(U, bound_to_radius(cw));
   lb = A.carried ? __uint_as_float(A.res[i].x) : 0.f;
   f[3] = safe_log2(wmin);
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256) k_predict(FeatArgs A, const float *__rest
       const uint32_t me = A.labels[i];
       float U = bound_to_radius(A.bound[me]);
       const uint32_t cw =
-          (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(A.comp_key + me)) >> 32);
+          (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(&A.comp[me].key)) >> 32);
       U = fminf(U, bound_to_radius(cw));
       skip = __uint_as_float(A.res[i].x) > U;
     }
@@ -536,14 +536,14 @@ __global__ void __launch_bounds__(128) k_log_samples(FeatArgs F, TravArgs T, int
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_rerun_mark(const float *__restrict__ r_used,
                                                     const uint32_t *__restrict__ labels,
-                                                    const uint64_t *__restrict__ comp_key,
+                                                    const CompBest *__restrict__ comp,
                                                     int64_t n, uint32_t *__restrict__ list,
                                                     uint32_t *counters) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float r = r_used[i];
   if (r == __int_as_float(0x7f800000)) return;  // skipped or unbounded: nothing to certify
-  const uint32_t wc = (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(comp_key + labels[i])) >> 32);
+  const uint32_t wc = (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(&comp[labels[i]].key)) >> 32);
   const bool rerun = r < bound_to_radius(wc);
   const unsigned mask = __ballot_sync(__activemask(), true);
   const unsigned mine = __ballot_sync(mask, rerun);
@@ -565,7 +565,7 @@ static FeatArgs feat_args(Problem &P, bool carried) {
   F.pts = P.pts;
   F.labels = P.labels;
   F.bound = P.bound;
-  F.comp_key = P.comp_key;
+  F.comp = P.comp;
   F.res = P.res;
   F.comp_size = P.comp_size;
   F.box = P.counters + 4;
@@ -605,7 +605,7 @@ void launch_predict(Problem &P, bool carried) {
 }
 
 void launch_rerun_mark(Problem &P) {
-  k_rerun_mark<<<grid_for(P.n, 256), 256, 0, P.stream>>>(P.r_used, P.labels, P.comp_key, P.n,
+  k_rerun_mark<<<grid_for(P.n, 256), 256, 0, P.stream>>>(P.r_used, P.labels, P.comp, P.n,
                                                           P.rerun_list, P.counters);
   P.launches += 1;
 }
@@ -626,7 +626,7 @@ void launch_log_samples(Problem &P, int round, bool carried) {
   T.inst_root = P.inst_root;
   T.offsets = P.offsets;
   T.res = P.res;
-  T.comp_key = P.comp_key;
+  T.comp = P.comp;
   T.n = P.n;
   T.status = P.counters + 1;
   T.visits = nullptr;

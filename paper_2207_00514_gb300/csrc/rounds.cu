@@ -1,7 +1,8 @@
 // rounds.cu -- one Boruvka round of the method (§3, Fig. 3 loop body):
 //   A5 node labels (Optimization 1, Fig. 4), A6 component upper bounds
 //   (Optimization 2), A7 nearest-other-component traversal (Algorithm 2),
-//   A8 per-component minimum, A9 merge (§3 "Merging components together"),
+//   A9 merge (§3 "Merging components together"; the A8 minimum itself is
+//   taken at the end of every query, offer_best in traverse.cuh),
 // plus the final ordering of the edges (A12).
 #include "traverse.cuh"
 
@@ -427,7 +428,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   A.inst_root = P.inst_root;
   A.offsets = P.offsets;
   A.res = P.res;
-  A.comp_key = P.comp_key;
+  A.comp = P.comp;
   A.n = P.n;
   A.status = P.counters + 1;
   A.visits = reinterpret_cast<unsigned long long *>(P.counters + 2);
@@ -500,38 +501,6 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
 }
 
 // ---------------------------------------------------------------------------
-// A8 (second half). Among the points whose (w, min id) equals the component's
-// winner, the smallest max id: together the exact minimum of the key
-// (w, min id, max id) of §2 over the component.  The stage-B value carries
-// the label of the edge's endpoint outside the component (the neighbour's
-// label: one pair, one label), which is the merge's target.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_reduce_max(const float4 *__restrict__ pts,
-                                                       const uint32_t *__restrict__ labels,
-                                                       const uint2 *__restrict__ res,
-                                                       const uint64_t *__restrict__ comp_key,
-                                                       unsigned long long *comp_max,
-                                                       int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint2 r = res[i];
-  if (r.y == kInvalid) return;
-  const uint32_t me = labels[i];
-  const uint64_t ck = __ldg(reinterpret_cast<const unsigned long long *>(comp_key + me));
-  if (r.x != (uint32_t)(ck >> 32)) return;  // not the component's minimum weight
-  const uint32_t oi = __float_as_uint(pts[i].w), oj = __float_as_uint(__ldg(&pts[r.y].w));
-  if ((oi < oj ? oi : oj) != (uint32_t)ck) return;
-  const uint64_t v = ((uint64_t)(oi < oj ? oj : oi) << 32) | (uint64_t)__ldg(labels + r.y);
-  atomicMin(comp_max + me, (unsigned long long)v);
-}
-
-void launch_reduce(Problem &P) {
-  k_reduce_max<<<grid_for(P.n, kBlock), kBlock, 0, P.stream>>>(
-      P.pts, P.labels, P.res, P.comp_key, reinterpret_cast<unsigned long long *>(P.comp_max), P.n);
-  P.launches += 1;
-}
-
-// ---------------------------------------------------------------------------
 // A9. Merge.  (a) every component C with an edge points to T(C), the label of
 // the edge's outside endpoint; (b) following the chain C -> T(C) -> ... ends
 // in a mutual pair X <-> T(X) (edge weights strictly decrease along a chain
@@ -545,25 +514,21 @@ void launch_reduce(Problem &P) {
 // in the same pass, prepare the next round: its curve-pair upper bounds (A6)
 // and the label-boundary prefix scan the node labels (A5) need.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t merge_target(const uint64_t *comp_key,
-                                                 const uint64_t *comp_max, uint32_t x) {
-  if (comp_key[x] == kEmptyKey) return kInvalid;
-  const uint64_t mx = comp_max[x];
-  return mx == kEmptyKey ? kInvalid : (uint32_t)mx;
+__device__ __forceinline__ uint32_t merge_target(const CompBest *comp, uint32_t x) {
+  const CompBest b = comp[x];
+  return b.key == kEmptyKey ? kInvalid : (uint32_t)b.mx;
 }
 
 // One thread per listed component.  The edges and the next round's list are
 // appended through one atomic per CTA (their order carries no meaning: the
-// output is sorted, the list is a set).  key_clear / max_clear: the other
-// round's buffers, cleared for the listed labels; bound_next: the next
+// output is sorted, the list is a set).  comp_clear: the other round's
+// minima, cleared for the listed labels; bound_next: the next
 // round's bounds, cleared for the new roots (the only labels it reads) before
 // the relabel pass lowers them.
 __global__ void __launch_bounds__(kBlock) k_merge_roots(const uint32_t *__restrict__ list,
                                                         int64_t count,
-                                                        const uint64_t *__restrict__ comp_key,
-                                                        const uint64_t *__restrict__ comp_max,
-                                                        uint64_t *__restrict__ key_clear,
-                                                        uint64_t *__restrict__ max_clear,
+                                                        const CompBest *__restrict__ comp,
+                                                        CompBest *__restrict__ comp_clear,
                                                         uint32_t *__restrict__ bound_next,
                                                         uint32_t *__restrict__ root,
                                                         emst_edge *__restrict__ edges,
@@ -579,31 +544,29 @@ __global__ void __launch_bounds__(kBlock) k_merge_roots(const uint32_t *__restri
   emst_edge E = {0u, 0u, 0.0f};
   if (t64 < count) {
     c = list ? list[t64] : (uint32_t)t64;
-    const uint64_t key = comp_key[c];
-    const uint64_t mx = comp_max[c];
-    // (a key without a stage-B winner cannot happen: the winner of the first
-    // half always matches its own key in the second; guarded so no index is
-    // ever wild)
-    if (key != kEmptyKey && mx == kEmptyKey) atomicOr(&counters[1], kErrChain);
-    const uint32_t t = (key == kEmptyKey || mx == kEmptyKey) ? kInvalid : (uint32_t)mx;
+    const CompBest b = comp[c];
+    const uint64_t key = b.key, mx = b.mx;
+    const uint32_t t = key == kEmptyKey ? kInvalid : (uint32_t)mx;
     uint32_t r = c;
     if (t != kInvalid) {
-      emit = !(merge_target(comp_key, comp_max, t) == c) || c < t;
+      emit = !(merge_target(comp, t) == c) || c < t;
       E.i = (uint32_t)key;
       E.j = (uint32_t)(mx >> 32);
       E.w = __uint_as_float((uint32_t)(key >> 32));
       uint32_t x = c, y = t;
       for (int64_t steps = 0;; ++steps) {
         if (y == kInvalid) { r = x; break; }  // chain ends at a component without an edge
-        const uint32_t z = merge_target(comp_key, comp_max, y);
+        const uint32_t z = merge_target(comp, y);
         if (z == x) { r = x < y ? x : y; break; }
         x = y;
         y = z;
         if (steps > n) { atomicOr(&counters[1], kErrChain); r = x; break; }
       }
     }
-    key_clear[c] = kEmptyKey;
-    max_clear[c] = kEmptyKey;
+    CompBest empty;
+    empty.key = kEmptyKey;
+    empty.mx = kEmptyKey;
+    comp_clear[c] = empty;
     root[c] = r;
     is_root = r == c;
     if (is_root) bound_next[c] = kNoBound;
@@ -640,8 +603,7 @@ void launch_merge(Problem &P) {
   const int64_t count = P.active_list ? P.n_active : P.n;
   const int g = grid_for(count, kBlock);
   cudaMemsetAsync(P.counters + 12, 0, sizeof(uint32_t), P.stream);
-  k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.active_list, count, P.comp_key, P.comp_max,
-                                            P.comp_key_buf[P.cur ^ 1], P.comp_max_buf[P.cur ^ 1],
+  k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.active_list, count, P.comp, P.comp_buf[P.cur ^ 1],
                                             P.bound_buf[P.cur ^ 1], P.root, P.edges, P.next_list, P.counters, P.n);
   P.launches += 1;
   launch_runs(P, true);
@@ -653,8 +615,7 @@ void advance_round(Problem &P, int64_t n_active) {
   P.cur ^= 1;
   P.labels = P.labels_buf[P.cur];
   P.bound = P.bound_buf[P.cur];
-  P.comp_key = P.comp_key_buf[P.cur];
-  P.comp_max = P.comp_max_buf[P.cur];
+  P.comp = P.comp_buf[P.cur];
   uint32_t *t = P.list_buf[0] == P.next_list ? P.list_buf[1] : P.list_buf[0];
   P.active_list = P.next_list;
   P.next_list = t;

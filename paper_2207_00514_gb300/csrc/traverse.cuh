@@ -305,8 +305,8 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
 // later bit of the augmented key (code + 32-bit index: 96 bits with 64-bit
 // codes, 160 with 128-bit codes), so a root-to-leaf path has at most 160
 // internal nodes and at most one stacked sibling per level.
-// Ends with the first half of the per-component minimum (A8): an atomicMin of
-// (w bits << 32 | min original id) per component.
+// Ends with the per-component minimum (A8): the found edge is offered to its
+// component's 128-bit (w, min id, max id, outside label) key.
 // SEEDED (the emst_compute path) also tightens each cutoff with the
 // component's best weight found so far (a real cross edge, so never below
 // the component minimum), reports the exact nearest neighbour within that cutoff
@@ -317,6 +317,34 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
 // Unseeded, each point reports exactly its nearest other-component point
 // within its cutoff (what the inspection entry point exposes).
 // ---------------------------------------------------------------------------
+// A8: offer the edge (w, oi, oj) found by a query of component `c` (its
+// neighbour j in curve order) to the component's 128-bit minimum.  Many
+// points of a large component find edges, but only one that improves on the
+// value seen now needs the compare-and-swap; the outside endpoint's label is
+// loaded only then.  Values only decrease, so a failed swap returns a
+// smaller value and the loop re-checks it (bounded; a status bit if not).
+__device__ __forceinline__ void offer_best(CompBest *c, uint32_t w_bits, uint32_t oi, uint32_t oj,
+                                           const uint32_t *__restrict__ labels, uint32_t j,
+                                           uint32_t *status) {
+  const uint64_t key = ((uint64_t)w_bits << 32) | (uint64_t)(oi < oj ? oi : oj);
+  const uint64_t mx_hi = (uint64_t)(oi < oj ? oj : oi) << 32;
+  CompBest cur;
+  cur.key = __ldcg(reinterpret_cast<const unsigned long long *>(&c->key));
+  if (key > cur.key) return;
+  cur.mx = __ldcg(reinterpret_cast<const unsigned long long *>(&c->mx));
+  if (key == cur.key && mx_hi >= (cur.mx & 0xFFFFFFFF00000000ull)) return;  // same or later edge
+  CompBest want;
+  want.key = key;
+  want.mx = mx_hi | (uint64_t)__ldg(labels + j);
+  for (int it = 0; it < (1 << 20); ++it) {
+    const CompBest old = atomicCAS(c, cur, want);
+    if (old.key == cur.key && old.mx == cur.mx) return;
+    cur = old;
+    if (want.key > cur.key || (want.key == cur.key && want.mx >= cur.mx)) return;
+  }
+  atomicOr(status, kErrCas);
+}
+
 struct TravArgs {
   const float4 *pts;
   const NodeRec *nodes;
@@ -331,7 +359,7 @@ struct TravArgs {
   const uint32_t *inst_root;
   const int64_t *offsets;
   uint2 *res;
-  uint64_t *comp_key;
+  CompBest *comp;
   int64_t n;
   uint32_t *status;
   unsigned long long *visits;   // COUNT: node visits
@@ -384,7 +412,7 @@ __device__ __forceinline__ bool start_query(const TravArgs &A, int64_t i, Query 
     // The component's best weight found so far this round: a real cross edge
     // of the component, so never below its minimum.
     const uint32_t cw =
-        (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(A.comp_key + q.me)) >> 32);
+        (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(&A.comp[q.me].key)) >> 32);
     q.radius = fminf(q.radius, bound_to_radius(cw));
     // prev.x is a lower bound of this point's nearest other-component weight
     // (components only grow, so that weight never decreases).  Above the
@@ -410,8 +438,8 @@ __device__ __forceinline__ bool start_query(const TravArgs &A, int64_t i, Query 
   return true;
 }
 
-// The second half: the query's result and the first stage of its
-// component's minimum (A8): an atomicMin of (w bits << 32 | min original id).
+// The second half: the query's result, and its edge offered to its
+// component's minimum (A8, offer_best).
 // SEEDED reports only the exact nearest neighbour within r0 (a seed beyond r0
 // is dropped) and keeps in res.x a lower bound for the next round: the found
 // weight, or r0 when nothing lies within it.
@@ -429,11 +457,7 @@ __device__ __forceinline__ void finish_query(const TravArgs &A, int64_t i, Query
   if (q.bj != kInvalid) {
     const uint32_t oi = __float_as_uint(__ldg(&A.pts[i].w));
     const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(__ldg(&A.pts[q.bj].w));
-    const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
-    // (many points of a large component find edges: only one that improves
-    // on the value seen now needs the atomic)
-    unsigned long long *ck = reinterpret_cast<unsigned long long *>(A.comp_key + q.me);
-    if ((unsigned long long)key < __ldcg(ck)) atomicMin(ck, (unsigned long long)key);
+    offer_best(A.comp + q.me, __float_as_uint(q.best), oi, oj, A.labels, q.bj, A.status);
   }
 }
 
@@ -474,7 +498,7 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
     // The component's best weight found so far this round: a real cross edge
     // of the component, so never below its minimum.
     const uint32_t cw =
-        (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(A.comp_key + q.me)) >> 32);
+        (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(&A.comp[q.me].key)) >> 32);
     q.radius = fminf(q.radius, bound_to_radius(cw));
     // prev.x is a lower bound of this point's nearest other-component weight
     // (components only grow, so that weight never decreases).  Above the
@@ -527,11 +551,7 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   if (q.bj != kInvalid) {
     const uint32_t oi = __float_as_uint(p.w);
     const uint32_t oj = q.bid != kInvalid ? q.bid : __float_as_uint(A.pts[q.bj].w);
-    const uint64_t key = ((uint64_t)__float_as_uint(q.best) << 32) | (uint64_t)(oi < oj ? oi : oj);
-    // (many points of a large component find edges: only one that improves
-    // on the value seen now needs the atomic)
-    unsigned long long *ck = reinterpret_cast<unsigned long long *>(A.comp_key + q.me);
-    if ((unsigned long long)key < __ldcg(ck)) atomicMin(ck, (unsigned long long)key);
+    offer_best(A.comp + q.me, __float_as_uint(q.best), oi, oj, A.labels, q.bj, A.status);
   }
 }
 
