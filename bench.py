@@ -39,8 +39,7 @@ WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member count
 #       --cache-control none -k regex:k_traverse -c 11 --csv
 #       python <one emst_compute call on these points>
 # (one pass per launch).  Set back to None whenever the traversal kernel changes.
-TRAVERSE_DRAM_BYTES_PER_ROUND = [4519.3e6, 5664.3e6, 4655.1e6, 3144.1e6, 2019.7e6, 1655.8e6,
-                                 1515.4e6, 1435.7e6, 1389.6e6, 1360.5e6, 1339.4e6]
+TRAVERSE_DRAM_BYTES_PER_ROUND = None
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")
 

@@ -70,9 +70,16 @@ typedef struct emst_options {
   int32_t block_size;         /* traversal CTA size: 0 = default (128), else 64..256, multiple of 32 */
   int32_t carried_radius;     /* 1 (default if struct_size==0) = seed each query with the previous
                                  round's neighbour when it is still in another component */
-  int32_t use_graph;          /* accepted and ignored: the rounds run from a host loop with one
-                                 synchronisation per round (the host gaps of a whole call are
-                                 about 1 % of its device time at 37M points) */
+  int32_t use_graph;          /* 1 = graph rounds: after the first round (run and checked from
+                                 the host), every later round runs inside one CUDA graph whose
+                                 while node repeats a two-round body until a one-thread kernel
+                                 finds, on the device, all edges emitted, an error bit set or
+                                 the round limit reached -- no host round trip per round.
+                                 Captured on streams the library creates, launched on `stream`,
+                                 instantiated per call.  Not with mlp_params or count_visits
+                                 (those run the host loop); per-round traversal times then
+                                 cover the first round only.  0 (default) = the host loop,
+                                 one status read per round.  The tree is the same either way. */
   int32_t count_visits;       /* 1 = count node visits per round into emst_stats */
   int32_t leaf_size;          /* points per leaf chunk of the hierarchy: 0 = default (1, one
                                  point per leaf as in the paper), else 1, 2, 4, 8 or 16 (halved

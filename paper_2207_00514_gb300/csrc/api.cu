@@ -292,6 +292,142 @@ void run_round(Problem &P, int round, bool carried, int block, bool count) {
   launch_merge(P);
 }
 
+// ---------------------------------------------------------------------------
+// Graph rounds (emst_options.use_graph): rounds 1, 2, ... as one CUDA graph
+// whose while node repeats them until a device-side flag says the method is
+// done -- no host round trip between rounds.  The round's buffers alternate
+// (ping-pong), so the loop body holds two rounds, the second under an if
+// node; after each round a one-thread kernel reads the edge count, the status
+// word and the round count on the device and sets the conditions: continue
+// while edges < expected, no error bit is set and fewer than `limit` rounds
+// have run (the same bound as the host loop, so the loop always ends).
+// ---------------------------------------------------------------------------
+enum : int { kCondInit = 0, kCondBoth = 1, kCondLoop = 2 };
+
+__global__ void k_rounds_cond(cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_if,
+                              int mode, uint32_t *counters, uint32_t expected, uint32_t limit,
+                              uint32_t rounds_before) {
+  uint32_t done_rounds;
+  if (mode == kCondInit) {
+    done_rounds = rounds_before;
+  } else {
+    done_rounds = counters[41] + 1u;
+  }
+  counters[41] = done_rounds;
+  const unsigned go = counters[0] < expected && counters[1] == 0u && done_rounds < limit ? 1u : 0u;
+  cudaGraphSetConditional(h_loop, go);
+  if (mode == kCondBoth) cudaGraphSetConditional(h_if, go);
+}
+
+// Captures and runs the rounds after round 0 (which the caller ran and
+// checked: P holds its state, P.n_active the components it left, the cap of
+// every later round's list).  Returns the status of the capture and launch;
+// the rounds' own results are in P.counters ([41] = rounds done in all).
+// `kernels` receives the kernels one round body launches.
+static cudaError_t run_rounds_graph(Problem &P, int64_t expected, int limit, bool carried,
+                                    int block, int rounds_before, int *kernels) {
+  cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  const cudaStream_t caller = P.stream;
+  int capturing = 0;
+  cudaError_t e = cudaSuccess;
+  for (auto &x : cs)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+  P.count_dev = P.counters + 40;
+  cudaStreamCaptureStatus st;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  cudaGraphConditionalHandle h_loop = 0, h_if = 0;
+  cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};
+  cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+  cudaGraphNode_t wn = nullptr, in = nullptr;
+  int launches0 = 0;
+#define GR(call)                        \
+  do {                                  \
+    if (e == cudaSuccess) e = (call);   \
+  } while (0)
+  // outer graph: set the loop condition, then the while node
+  GR(cudaStreamBeginCapture(cs[0], cudaStreamCaptureModeThreadLocal));
+  if (e == cudaSuccess) capturing = 1;
+  GR(cudaStreamGetCaptureInfo(cs[0], &st, nullptr, &cg, &deps, nullptr, &nd));
+  GR(cudaGraphConditionalHandleCreate(&h_loop, cg, 0, 0));
+  if (e == cudaSuccess) {
+    k_rounds_cond<<<1, 1, 0, cs[0]>>>(h_loop, h_loop, kCondInit, P.counters, (uint32_t)expected,
+                                      (uint32_t)limit, (uint32_t)rounds_before);
+    e = cudaPeekAtLastError();
+  }
+  GR(cudaStreamGetCaptureInfo(cs[0], &st, nullptr, &cg, &deps, nullptr, &nd));
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = h_loop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  GR(cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &wp));
+  GR(cudaStreamUpdateCaptureDependencies(cs[0], &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  // the loop body: one round, its conditions, then the other parity's round
+  // under the if node
+  GR(cudaStreamBeginCaptureToGraph(cs[1], e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr,
+                                   nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  if (e == cudaSuccess) capturing = 2;
+  GR(cudaGraphConditionalHandleCreate(&h_if, wp.conditional.phGraph_out[0], 0, 0));
+  if (e == cudaSuccess) {
+    P.stream = cs[1];
+    launches0 = P.launches;
+    run_round(P, 1, carried, block, false);
+    *kernels = P.launches - launches0 + 1;
+    k_rounds_cond<<<1, 1, 0, cs[1]>>>(h_loop, h_if, kCondBoth, P.counters, (uint32_t)expected,
+                                      (uint32_t)limit, 0u);
+    e = cudaPeekAtLastError();
+  }
+  GR(cudaStreamGetCaptureInfo(cs[1], &st, nullptr, &cg, &deps, nullptr, &nd));
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = h_if;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  GR(cudaGraphAddNode(&in, cg, deps, nullptr, nd, &ip));
+  GR(cudaStreamUpdateCaptureDependencies(cs[1], &in, nullptr, 1, cudaStreamSetCaptureDependencies));
+  GR(cudaStreamBeginCaptureToGraph(cs[2], e == cudaSuccess ? ip.conditional.phGraph_out[0] : nullptr,
+                                   nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  if (e == cudaSuccess) {
+    capturing = 3;
+    advance_round(P, P.n_active);  // the other parity (same cap)
+    P.stream = cs[2];
+    run_round(P, 2, carried, block, false);
+    k_rounds_cond<<<1, 1, 0, cs[2]>>>(h_loop, h_if, kCondLoop, P.counters, (uint32_t)expected,
+                                      (uint32_t)limit, 0u);
+    e = cudaPeekAtLastError();
+    advance_round(P, P.n_active);  // back: two swaps restore the first parity
+  }
+  P.stream = caller;
+  // end every capture that began, whatever happened
+  if (capturing >= 3) {
+    cudaGraph_t x = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs[2], &x);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (capturing >= 2) {
+    cudaGraph_t x = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs[1], &x);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (capturing >= 1) {
+    const cudaError_t e2 = cudaStreamEndCapture(cs[0], &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  GR(cudaGraphInstantiate(&ge, g, 0));
+  GR(cudaGraphLaunch(ge, caller));
+  GR(cudaStreamSynchronize(caller));
+#undef GR
+  P.count_dev = nullptr;
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  for (auto &x : cs)
+    if (x) cudaStreamDestroy(x);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
+}
+
 void reset_round_state(Problem &P) {
   cudaMemsetAsync(P.bound, 0xFF, sizeof(uint32_t) * (size_t)P.n, P.stream);
   // (the other buffer is cleared by the first round's merge)
@@ -412,11 +548,12 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   }
   if (n == 0) return EMST_OK;
   int block = 0, carried = 1, count = 0, leaf_req = 0, mrd_k = 0, morton_bits = 0, traversal = 0;
-  int refill = 0, chunk = 0, ignore_tuning = 0;
+  int refill = 0, chunk = 0, ignore_tuning = 0, use_graph = 0;
   const float *mlp_params = nullptr;
   if (opt && opt->struct_size >= (int32_t)sizeof(emst_options)) {
     block = opt->block_size;
     carried = opt->carried_radius;
+    use_graph = opt->use_graph;
     count = opt->count_visits;
     leaf_req = opt->leaf_size;
     mlp_params = opt->mlp_params;
@@ -504,7 +641,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
   int64_t reruns = 0;
   const size_t need = layout(P, nullptr, !pts_dev, !out_dev && !out_map);
   char *base = nullptr;
-  uint32_t host_counters[40] = {0};
+  uint32_t host_counters[48] = {0};
   uint64_t prev_visits = 0, prev_queries = 0, prev_distinct = 0;
   Timer tm;
   int rounds = 0;
@@ -610,6 +747,20 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
       }
       advance_round(P, (int64_t)host_counters[12]);
       if ((int64_t)host_counters[0] >= expected) { ++rounds; break; }
+      if (rounds == 0 && use_graph == 1 && !learned && !logging && !count) {
+        // the remaining rounds as one graph ended on the device
+        int kernels = 0;
+        const int before = P.launches;
+        CU(run_rounds_graph(P, expected, limit, carried != 0, block, 1, &kernels));
+        CU(cudaMemcpyAsync(host_counters, P.counters, sizeof(host_counters),
+                           cudaMemcpyDeviceToHost, stream));
+        CU(cudaStreamSynchronize(stream));
+        rounds = (int)host_counters[41];
+        P.launches = before + 1 + (rounds - 1) * kernels;
+        if (host_counters[1] != 0) { rc = status_from_bits(host_counters[1]); goto done; }
+        if ((int64_t)host_counters[0] < expected) { rc = EMST_ERR_ROUND_LIMIT; goto done; }
+        break;
+      }
     }
     tm.mark(2, stream);
     if ((int64_t)host_counters[0] != expected) { rc = EMST_ERR_INTERNAL; goto done; }

@@ -274,7 +274,9 @@ struct Problem {
                                      // [24] scan tiles finished, [34..35] queries that
                                      // searched (u64), [36..37] the work queue of the
                                      // persistent traversal (u64), [38..39] distinct internal
-                                     // nodes visited (u64)
+                                     // nodes visited (u64), [40] this round's active
+                                     // components and [41] rounds done (graph rounds)
+  uint32_t *count_dev = nullptr;     // graph rounds: counters + 40 (else nullptr)
   uint32_t *sort_hist = nullptr;     // 8 x 256
   uint32_t *sort_lookback = nullptr; // tiles x 256
   int64_t sort_tiles = 0;

@@ -524,9 +524,11 @@ __device__ __forceinline__ uint32_t merge_target(const CompBest *comp, uint32_t 
 // output is sorted, the list is a set).  comp_clear: the other round's
 // minima, cleared for the listed labels; bound_next: the next
 // round's bounds, cleared for the new roots (the only labels it reads) before
-// the relabel pass lowers them.
+// the relabel pass lowers them.  count_dev (graph rounds): the list's length
+// on the device, at most `count` (the grid covers `count`).
 __global__ void __launch_bounds__(kBlock) k_merge_roots(const uint32_t *__restrict__ list,
                                                         int64_t count,
+                                                        const uint32_t *__restrict__ count_dev,
                                                         const CompBest *__restrict__ comp,
                                                         CompBest *__restrict__ comp_clear,
                                                         uint32_t *__restrict__ bound_next,
@@ -539,6 +541,10 @@ __global__ void __launch_bounds__(kBlock) k_merge_roots(const uint32_t *__restri
   __shared__ uint32_t s_base[2];
   const int64_t t64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (count_dev) {
+    const int64_t c = (int64_t)*count_dev;
+    if (c < count) count = c;
+  }
   bool emit = false, is_root = false;
   uint32_t c = 0;
   emst_edge E = {0u, 0u, 0.0f};
@@ -602,8 +608,13 @@ __global__ void __launch_bounds__(kBlock) k_merge_roots(const uint32_t *__restri
 void launch_merge(Problem &P) {
   const int64_t count = P.active_list ? P.n_active : P.n;
   const int g = grid_for(count, kBlock);
+  // graph rounds: this round's list length exists only on the device
+  const uint32_t *count_dev = P.active_list ? P.count_dev : nullptr;
+  if (count_dev)
+    cudaMemcpyAsync(P.count_dev, P.counters + 12, sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                    P.stream);
   cudaMemsetAsync(P.counters + 12, 0, sizeof(uint32_t), P.stream);
-  k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.active_list, count, P.comp, P.comp_buf[P.cur ^ 1],
+  k_merge_roots<<<g, kBlock, 0, P.stream>>>(P.active_list, count, count_dev, P.comp, P.comp_buf[P.cur ^ 1],
                                             P.bound_buf[P.cur ^ 1], P.root, P.edges, P.next_list, P.counters, P.n);
   P.launches += 1;
   launch_runs(P, true);
