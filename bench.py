@@ -39,7 +39,8 @@ WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member count
 #       --cache-control none -k regex:k_traverse -c 11 --csv
 #       python <one emst_compute call on these points>
 # (one pass per launch).  Set back to None whenever the traversal kernel changes.
-TRAVERSE_DRAM_BYTES_PER_ROUND = None
+TRAVERSE_DRAM_BYTES_PER_ROUND = [5245.9e6, 6230.5e6, 4761.5e6, 3146.2e6, 2022.4e6, 1655.2e6,
+                                 1515.1e6, 1435.7e6, 1389.7e6, 1360.2e6, 1339.3e6]
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")
 
@@ -152,18 +153,19 @@ def measured_peaks():
 # Algorithmic bytes of one traversal launch (Algorithm 2 over every point), by
 # what the method must read or write at least once:
 #  round 0 (every label is the point's own index, every query searches):
-#    per query 48 B -- its point (16), label (4), component bound (4), the
-#    component's best so far (8), its result (8), the component-minimum
-#    atomic (8) -- and per distinct internal node visited its 64-B record;
+#    per query 56 B -- its point (16), label (4), component bound (4), the
+#    component's best so far (8), its result (8), the update of the
+#    component's 16-byte (w, min id, max id, outside label) minimum (16) --
+#    and per distinct internal node visited its 64-B record;
 #  later rounds: per point 32 B to decide whether to search at all -- label
 #    (4), component bound (4) and best so far (8), its previous result (8),
-#    its new result (8) -- plus per query that searches 28 B -- its point
-#    (16), its previous neighbour's label (4), the atomic (8) -- and per
-#    distinct internal node visited 72 B: the record (64) and its child
-#    labels (8).
-BYTES_FIRST_QUERY = 48
+#    its new result (8) -- plus per query that searches 36 B -- its point
+#    (16), its previous neighbour's label (4), the minimum's update (16) --
+#    and per distinct internal node visited 72 B: the record (64) and its
+#    child labels (8).
+BYTES_FIRST_QUERY = 56
 BYTES_POINT = 32
-BYTES_SEARCH = 28
+BYTES_SEARCH = 36
 BYTES_RECORD_FIRST = 64
 BYTES_RECORD = 72
 

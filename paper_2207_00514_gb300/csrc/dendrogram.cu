@@ -34,8 +34,14 @@
 namespace emst {
 namespace {
 
-constexpr int kLocalEdges = 2048;   // edges per block of the shared-memory levels
-constexpr int kLocalThreads = 512;
+#ifndef EMST_DG_LOCAL_EDGES
+#define EMST_DG_LOCAL_EDGES 2048
+#endif
+#ifndef EMST_DG_LOCAL_THREADS
+#define EMST_DG_LOCAL_THREADS 512
+#endif
+constexpr int kLocalEdges = EMST_DG_LOCAL_EDGES;   // edges per block of the shared-memory levels
+constexpr int kLocalThreads = EMST_DG_LOCAL_THREADS;
 constexpr int kSerialEdges = 32;    // edges per serial finish (one thread each)
 constexpr int kDgBlock = 256;
 constexpr size_t kLocalSmem = (size_t)2 * kLocalEdges * (5 * 4 + 2);
@@ -366,12 +372,13 @@ __global__ void __launch_bounds__(kLocalThreads)
     __syncthreads();
   }
   // Serial finish: thread j merges local edges [j * kSerialEdges, ...).  Its
-  // slots are laid out transposed (slot o of sub-block j at o * kSubSlots +
+  // slots are laid out transposed (slot o of sub-block j at o * kSubs +
   // j), so the lanes of a warp, at the same step of their own sub-blocks,
   // touch 32 different banks.  pn holds each slot's name, transposed too.
   constexpr int kSubSlots = 2 * kSerialEdges;
   constexpr int kSubs = SL / kSubSlots;
-  static_assert(kSubs == kSubSlots, "square transposition");
+  static_assert(kSubs % 32 == 0 && kSubs * kSubSlots == SL, "one sub-block per bank, a bijection");
+  static_assert(kSubs <= kLocalThreads, "one thread per sub-block");
   uint32_t *pn = minh;
   for (int l = tid; l < 2 * cnt; l += kLocalThreads) {
     const uint32_t r = lrep[l];
