@@ -35,10 +35,10 @@ namespace emst {
 namespace {
 
 #ifndef EMST_DG_LOCAL_EDGES
-#define EMST_DG_LOCAL_EDGES 2048
+#define EMST_DG_LOCAL_EDGES 4096
 #endif
 #ifndef EMST_DG_LOCAL_THREADS
-#define EMST_DG_LOCAL_THREADS 512
+#define EMST_DG_LOCAL_THREADS 1024
 #endif
 constexpr int kLocalEdges = EMST_DG_LOCAL_EDGES;   // edges per block of the shared-memory levels
 constexpr int kLocalThreads = EMST_DG_LOCAL_THREADS;
