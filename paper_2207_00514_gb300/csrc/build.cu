@@ -473,11 +473,12 @@ void launch_hierarchy(Problem &P) {
 // A node whose leaf range lies inside this CTA's chunks has both arrivals
 // from this CTA (and its index inside the CTA's range, one end of its range),
 // so both child boxes meet in shared memory and the arrivals are counted
-// there with block-scope fences; only nodes spanning CTAs (about 2 per CTA
-// per level above it) pass the box through their global record and use the
-// global counters.  The global counters are never reset: each
-// pass adds exactly two arrivals per node, so the parity of the count before
-// the add tells first from second.
+// there with block-scope acquire-release adds; only nodes spanning CTAs
+// (about 2 per CTA per level above it) pass the box through their global
+// record and use the global counters (device-scope acquire-release adds).
+// The global counters are never reset: each pass adds exactly two arrivals
+// per node, so the parity of the count before the add tells first from
+// second.
 // Each record also carries the smallest original id of each child's points
 // (the traversal's tie pruning).
 // The child labels are the round-0 ones (a one-point chunk k: label k;
@@ -494,6 +495,21 @@ __device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, const flo
   f[0] = make_float2(bx[0], bx[1]);
   f[1] = make_float2(bx[2], bx[3]);
   f[2] = make_float2(bx[4], bx[5]);
+}
+
+// Arrival counters of the refit with acquire-release order: the first
+// arriver's box stores are released by its add, and the second arriver's add
+// acquires them, so no separate fences are needed around the add.
+__device__ __forceinline__ uint32_t add_acq_rel_gpu(uint32_t *p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ uint32_t add_acq_rel_cta_shared(uint32_t *p, uint32_t v) {
+  uint32_t old;
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
+  return old;
 }
 
 __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
@@ -536,19 +552,15 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
 #pragma unroll
       for (int t = 0; t < 6; ++t) s_box[node - first][slot][t] = box[t];
       s_min[node - first][slot] = idmin;
-      __threadfence_block();
-      if (atomicAdd(&s_arrive[node - first], 1u) == 0u) return;  // first: the sibling carries on
-      __threadfence_block();
+      if (add_acq_rel_cta_shared(&s_arrive[node - first], 1u) == 0u) return;  // first: the sibling carries on
 #pragma unroll
       for (int t = 0; t < 6; ++t) sib[t] = s_box[node - first][slot ^ 1][t];
       sibmin = s_min[node - first][slot ^ 1];
     } else {
       store_slot_box(&nodes[node], slot, box);
       reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = idmin;
-      __threadfence();
-      const uint32_t before = atomicAdd(&arrivals[node], 1u);
+      const uint32_t before = add_acq_rel_gpu(&arrivals[node], 1u);
       if ((before & 1u) == 0u) return;
-      __threadfence();
       const float2 *f = reinterpret_cast<const float2 *>(&nodes[node]) + 3 * (slot ^ 1);
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
