@@ -142,7 +142,7 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.parent_leaf = c.take<uint32_t>(nc);
   P.up_delta = c.take<uint2>(nc - 1);
   P.arrivals = c.take<uint32_t>(nc - 1);
-  P.range = c.take<uint4>(nc - 1);
+  P.range = c.take<uint2>(nc - 1);
   P.runs = c.take<uint32_t>(n);
   P.scan_tiles = c.take<uint32_t>(2 * scan_tiles_for(n));
   P.labels_buf[0] = c.take<uint32_t>(n);

@@ -303,7 +303,7 @@ void launch_instance_ids(Problem &P) {
 // instance with fewer than two chunks... of points (nothing to search).
 __global__ void __launch_bounds__(kBlock) k_instance_roots(const int64_t *__restrict__ offsets,
                                                            int64_t num_inst, int64_t nc, int leaf,
-                                                           const uint4 *__restrict__ range,
+                                                           const uint2 *__restrict__ range,
                                                            uint32_t *__restrict__ inst_root,
                                                            uint32_t *status) {
   int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -316,12 +316,12 @@ __global__ void __launch_bounds__(kBlock) k_instance_roots(const int64_t *__rest
     root = kInvalid;  // inside one leaf chunk: cannot happen with leaf 1 (a < b)
   } else {
     if (ca < nc - 1) {
-      const uint4 r = __ldg(range + ca);
-      if (r.x == (uint32_t)ca && r.z == (uint32_t)cb) root = (uint32_t)ca;
+      const NodeRange r = unpack_range((uint32_t)ca, __ldg(range + ca));
+      if (r.first == (uint32_t)ca && r.last == (uint32_t)cb) root = (uint32_t)ca;
     }
     if (root == kInvalid && cb < nc - 1) {
-      const uint4 r = __ldg(range + cb);
-      if (r.x == (uint32_t)ca && r.z == (uint32_t)cb) root = (uint32_t)cb;
+      const NodeRange r = unpack_range((uint32_t)cb, __ldg(range + cb));
+      if (r.first == (uint32_t)ca && r.last == (uint32_t)cb) root = (uint32_t)cb;
     }
   }
   if (root == kInvalid) atomicOr(status, kErrChain);
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
                                                       int64_t nc, int leaf,
                                                       uint32_t *__restrict__ parent_leaf,
                                                       uint2 *__restrict__ up_delta,
-                                                      uint4 *__restrict__ range) {
+                                                      uint2 *__restrict__ range) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc - 1) return;
   int d = (prefix_delta(keys, keys_hi, nc, leaf, i, i + 1) - prefix_delta(keys, keys_hi, nc, leaf, i, i - 1)) > 0 ? 1 : -1;
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict
   int64_t lo = i < j ? i : j, hi = i < j ? j : i;
   uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
   uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
-  range[i] = make_uint4((uint32_t)lo, (uint32_t)gamma, (uint32_t)hi, 0u);
+  range[i] = pack_range((uint32_t)i, (uint32_t)lo, (uint32_t)gamma, (uint32_t)hi);
   reinterpret_cast<uint32_t *>(up_delta + i)[1] = (uint32_t)dnode;
   uint32_t up = (uint32_t)i << 1;
   if (left & kLeafBit) parent_leaf[left & ~kLeafBit] = up;
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
                                                   uint2 *__restrict__ nlabels,
                                                   const uint32_t *__restrict__ parent_leaf,
                                                   const uint2 *__restrict__ up_delta,
-                                                  const uint4 *__restrict__ range,
+                                                  const uint2 *__restrict__ range,
                                                   uint32_t *arrivals) {
   __shared__ float s_box[kRefitBlock][2][6];  // both child boxes of each local node
   __shared__ uint32_t s_min[kRefitBlock][2];  // and their smallest original ids
@@ -543,9 +543,9 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
     const uint32_t node = up >> 1;
     const int slot = (int)(up & 1u);
     // both depend on the node only: one round trip per level
-    const uint4 r = __ldg(range + node);
+    const NodeRange r = unpack_range(node, __ldg(range + node));
     const uint32_t up_next = __ldg(&up_delta[node].x);
-    const bool local = (int64_t)r.x >= first && (int64_t)r.z <= last;
+    const bool local = (int64_t)r.first >= first && (int64_t)r.last <= last;
     float sib[6];
     uint32_t sibmin;
     if (local) {
@@ -574,8 +574,8 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
     const float *R = slot == 0 ? sib : box;
     // the whole record: boxes, references (leaves where the range ends at the
     // split), round-0 child labels
-    const uint32_t g = r.y;
-    const bool lleaf = r.x == g, rleaf = r.z == g + 1u;
+    const uint32_t g = r.split;
+    const bool lleaf = r.first == g, rleaf = r.last == g + 1u;
     // a chunk of exactly one point is its own component in round 0
     auto one_point = [&](int64_t c) { return n - c * leaf == 1 || leaf == 1; };
     NodeRec rec;

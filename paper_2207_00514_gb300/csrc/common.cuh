@@ -170,6 +170,28 @@ __device__ __forceinline__ uint64_t interleave(uint32_t qx, uint32_t qy, uint32_
 // ---------------------------------------------------------------------------
 // Scratch layout of one EMST problem (carved from one allocation).
 // ---------------------------------------------------------------------------
+// An internal node's leaf-chunk range [first, last] and split, in 8 bytes.
+// In the hierarchy's numbering one end of a node's range is the node's own
+// index, so only the other end is stored, with bit 31 set when that other
+// end is `first` (the node is the range's last chunk).  Chunk indices are
+// below 2^31.
+struct NodeRange {
+  uint32_t first, split, last;
+};
+__host__ __device__ __forceinline__ uint2 pack_range(uint32_t node, uint32_t first, uint32_t split,
+                                                     uint32_t last) {
+  return make_uint2(first == node ? last : (first | 0x80000000u), split);
+}
+__host__ __device__ __forceinline__ NodeRange unpack_range(uint32_t node, uint2 e) {
+  NodeRange r;
+  const uint32_t other = e.x & 0x7FFFFFFFu;
+  const bool node_is_last = (e.x >> 31) != 0u;
+  r.first = node_is_last ? other : node;
+  r.last = node_is_last ? node : other;
+  r.split = e.y;
+  return r;
+}
+
 struct Problem {
   int64_t n = 0;
   int dim = 3;
@@ -240,8 +262,9 @@ struct Problem {
                                      //      position) keys; y < 64 means the node holds
                                      //      exactly the points of one Morton cell
   uint32_t *arrivals = nullptr;      // n-1 arrival counters (parity = who is second)
-  uint4 *range = nullptr;            // nc-1: (first, split, last, 0) of each internal node: its
-                                     //      leaf-chunk range and the last chunk of its left child
+  uint2 *range = nullptr;            // nc-1: each internal node's leaf-chunk range [first, last]
+                                     //      and split (the last chunk of its left child), packed
+                                     //      by pack_range (one end of the range is the node itself)
   uint32_t *runs = nullptr;          // n: label boundaries before each curve position within
                                      //    its scan tile (plus the tile's entry of tile_prefix)
   uint32_t *scan_tiles = nullptr;    // 2 x scan tiles: boundary total of each tile, then the

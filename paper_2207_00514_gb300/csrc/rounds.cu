@@ -191,17 +191,17 @@ void launch_label_runs(Problem &P) { launch_runs(P, false); }
 __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restrict__ labels,
                                                         const uint32_t *__restrict__ runs_local,
                                                         const uint32_t *__restrict__ tile_prefix,
-                                                        const uint4 *__restrict__ range,
+                                                        const uint2 *__restrict__ range,
                                                         int64_t n, int64_t nc, int leaf,
                                                         uint2 *__restrict__ nlabels) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc - 1) return;
   // the children split the node's chunk range [first, last] after `split`
-  const uint4 r = __ldg(range + i);
-  const int64_t a0 = (int64_t)r.x * leaf;
-  const int64_t b0 = ((int64_t)r.y + 1) * leaf - 1;
+  const NodeRange r = unpack_range((uint32_t)i, __ldg(range + i));
+  const int64_t a0 = (int64_t)r.first * leaf;
+  const int64_t b0 = ((int64_t)r.split + 1) * leaf - 1;
   const int64_t a1 = b0 + 1;
-  const int64_t b1 = ((int64_t)r.z + 1) * leaf < n ? ((int64_t)r.z + 1) * leaf - 1 : n - 1;
+  const int64_t b1 = ((int64_t)r.last + 1) * leaf < n ? ((int64_t)r.last + 1) * leaf - 1 : n - 1;
   const uint32_t l0 = __ldg(labels + a0), l1 = __ldg(labels + a1);
   const uint32_t lab0 =
       runs_at(runs_local, tile_prefix, b0) == runs_at(runs_local, tile_prefix, a0) ? l0 : kInvalid;
