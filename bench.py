@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=3_000_000,
                     help="reference arm: points per step in the oracle's spatial-window sample")
+    ap.add_argument("--cpu-single-sample", type=int, default=500_000,
+                    help="cpu_baseline: also time the oracle on one thread on a spatial window of "
+                         "about this many points (0: skip)")
     ap.add_argument("--cpu-full", type=int, default=1,
                     help="cpu_baseline: 1 = the oracle on the whole workload (all host threads)")
     ap.add_argument("--no-learned", action="store_true")
@@ -698,6 +701,14 @@ def main():
             dt = cpu_oracle_run(sample, threads)
             cpu = {"value": len(sample) / dt / 1e6, "unit": "Mpoints/s", "cores": threads, "kind": "oracle",
                    "sample": f"a spatial window of {len(sample):,} points, k-d tree Boruvka, {threads} threads, {dt:.1f} s"}
+        if args.cpu_single_sample > 0:
+            g = np.random.default_rng(54321)
+            sample = window_sample(pts_np, args.cpu_single_sample, g)
+            dt1 = cpu_oracle_run(sample, 1)
+            cpu["single_thread"] = {
+                "value": len(sample) / dt1 / 1e6, "unit": "Mpoints/s", "cores": 1,
+                "sample": f"a spatial window of {len(sample):,} points (same density and clustering), "
+                          f"k-d tree Boruvka, 1 thread, {dt1:.1f} s"}
 
     if rank == 0:
         line = {
