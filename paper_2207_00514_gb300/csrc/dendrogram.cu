@@ -235,7 +235,11 @@ __global__ void k_dg_classify(Level L) {
   warp_update<0>(L.top, x0, k + 1, act && light);
   warp_update<1>(L.minh, x0, s0, act && !light);
   warp_update<1>(L.minh, x1, s0 + 1, act && !light);
-  const bool self0 = act && r0 == s0, self1 = act && r1 == s0 + 1;
+  // sizes are summed for light components only: a slot of the heavy half
+  // that names its vertex names one that touches no light edge (a vertex's
+  // name is its lowest slot in the block, and light slots come first), a
+  // component of its own whose sum the stitch never reads
+  const bool self0 = act && light && r0 == s0, self1 = act && light && r1 == s0 + 1;
   warp_update<2>(L.csz, x0, self0 ? L.sz[s0] : 0u, self0);
   warp_update<2>(L.csz, x1, self1 ? L.sz[s0 + 1] : 0u, self1);
 }
@@ -347,9 +351,7 @@ __global__ void __launch_bounds__(kLocalThreads)
       } else {
         const uint32_t x1 = uf_find<true>(vuf, r1);
         atomicMin(minh + x0, s0);
-        atomicMin(minh + x1, s0 + 1);
-        if (r0 == s0) atomicAdd(csz + x0, szl[s0]);
-        if (r1 == s0 + 1) atomicAdd(csz + x1, szl[s0 + 1]);
+        atomicMin(minh + x1, s0 + 1);  // (no sizes: as in k_dg_classify)
       }
     }
     __syncthreads();
