@@ -225,16 +225,29 @@ __global__ void k_dg_classify(Level L) {
     k = start + L.half - 1 - (k - start);
   }
   const uint32_t s0 = 2 * k;
+  // A vertex named by a slot of the heavy half touches no light edge (its
+  // name is its lowest slot in the block, and light slots come first): a
+  // component of its own whose lowest heavy slot is its name, so it needs no
+  // find and no minimum here, and the stitch keeps its name.
+  const uint32_t hs = 2 * ((k & ~L.mask) + L.half);  // the block's first heavy slot
   uint32_t r0 = 0, r1 = 0, x0 = 0, x1 = 0;
+  bool m0 = false, m1 = false;
   if (act) {
     r0 = L.rep[s0];
     r1 = L.rep[s0 + 1];
-    x0 = uf_find<true>(L.uf, r0);
-    x1 = light ? x0 : uf_find<true>(L.uf, r1);  // a light edge's ends share a root
+    if (light) {
+      x0 = uf_find<true>(L.uf, r0);
+      x1 = x0;  // a light edge's ends share a root
+    } else {
+      m0 = r0 < hs;
+      m1 = r1 < hs;
+      if (m0) x0 = uf_find<true>(L.uf, r0);
+      if (m1) x1 = uf_find<true>(L.uf, r1);
+    }
   }
   warp_update<0>(L.top, x0, k + 1, act && light);
-  warp_update<1>(L.minh, x0, s0, act && !light);
-  warp_update<1>(L.minh, x1, s0 + 1, act && !light);
+  warp_update<1>(L.minh, x0, s0, m0);
+  warp_update<1>(L.minh, x1, s0 + 1, m1);
   // sizes are summed for light components only: a slot of the heavy half
   // that names its vertex names one that touches no light edge (a vertex's
   // name is its lowest slot in the block, and light slots come first), a
@@ -263,10 +276,10 @@ __global__ void k_dg_stitch(Level L) {
       L.sz[h] = L.csz[r];
     }
   } else if (split) {
-    r0 = L.minh[uf_find<false>(L.uf, r0)];
-    r1 = L.minh[uf_find<false>(L.uf, r1)];
-    L.rep[s0] = r0;
-    L.rep[s0 + 1] = r1;
+    // (names in the heavy half stay: see k_dg_classify)
+    const uint32_t hs = 2 * (((uint32_t)k & ~L.mask) + L.half);
+    if (r0 < hs) L.rep[s0] = L.minh[uf_find<false>(L.uf, r0)];
+    if (r1 < hs) L.rep[s0 + 1] = L.minh[uf_find<false>(L.uf, r1)];
   }
   clear_pair(L, s0);
 }
@@ -348,10 +361,10 @@ __global__ void __launch_bounds__(kLocalThreads)
         atomicMax(top + x0, (uint32_t)t + 1);
         if (r0 == s0) atomicAdd(csz + x0, szl[s0]);
         if (r1 == s0 + 1) atomicAdd(csz + x0, szl[s0 + 1]);
-      } else {
-        const uint32_t x1 = uf_find<true>(vuf, r1);
-        atomicMin(minh + x0, s0);
-        atomicMin(minh + x1, s0 + 1);  // (no sizes: as in k_dg_classify)
+      } else {  // (no sizes, and no minimum for names in the heavy half: as in k_dg_classify)
+        const uint32_t hs = 2 * (uint32_t)(start + half);
+        if (r0 < hs) atomicMin(minh + x0, s0);
+        if (r1 < hs) atomicMin(minh + uf_find<true>(vuf, r1), s0 + 1);
       }
     }
     __syncthreads();
@@ -367,8 +380,9 @@ __global__ void __launch_bounds__(kLocalThreads)
           szl[h] = csz[r];
         }
       } else {
-        lrep[s0] = (uint16_t)minh[uf_find<false>(vuf, lrep[s0])];
-        lrep[s0 + 1] = (uint16_t)minh[uf_find<false>(vuf, lrep[s0 + 1])];
+        const uint32_t hs = 2 * (uint32_t)(start + half);
+        if (lrep[s0] < hs) lrep[s0] = (uint16_t)minh[uf_find<false>(vuf, lrep[s0])];
+        if (lrep[s0 + 1] < hs) lrep[s0 + 1] = (uint16_t)minh[uf_find<false>(vuf, lrep[s0 + 1])];
       }
     }
     __syncthreads();
