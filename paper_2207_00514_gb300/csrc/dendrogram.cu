@@ -44,6 +44,11 @@ constexpr int kLocalEdges = EMST_DG_LOCAL_EDGES;   // edges per block of the sha
 constexpr int kLocalThreads = EMST_DG_LOCAL_THREADS;
 constexpr int kSerialEdges = 32;    // edges per serial finish (one thread each)
 constexpr int kDgBlock = 256;
+#ifndef EMST_DG_MID_EDGES
+#define EMST_DG_MID_EDGES 32768
+#endif
+constexpr int64_t kMidEdges = EMST_DG_MID_EDGES;  // blocks of the CTA-level kernel (0: none)
+constexpr int kMidThreads = 1024;
 constexpr size_t kLocalSmem = (size_t)2 * kLocalEdges * (5 * 4 + 2);
 
 // A bijective mix of a slot name (the MurmurHash3 32-bit finaliser): the
@@ -202,21 +207,22 @@ __global__ void k_dg_init(Level L, const emst_edge *__restrict__ e,
 }
 
 // Light components: unite the two vertices of every light edge.
-__global__ void k_dg_unite(Level L) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void dg_unite(const Level &L, int64_t k) {
   if (k >= L.m) return;
   bool light;
   if (!block_split(L, (uint32_t)k, light) || !light) return;
   if (!uf_unite(L.uf, L.rep[2 * k], L.rep[2 * k + 1])) atomicOr(L.status, kErrSpin);
 }
 
+__global__ void k_dg_unite(Level L) { dg_unite(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
+
 // Per light component (by root): its top edge (rank + 1), its size (the sum
 // over its vertices, each counted at the slot that names it) and the lowest
 // heavy slot touching it.  A warp covers 32 edges of one half.  Light halves
 // are visited from the top rank down, so the first value to reach a
 // component's top is usually its maximum and later lanes skip the atomic.
-__global__ void k_dg_classify(Level L) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// (every lane of a warp calls it: warp_update combines across the warp)
+__device__ __forceinline__ void dg_classify(const Level &L, int64_t t) {
   bool light = false;
   const bool act = t < L.m && block_split(L, (uint32_t)t, light);
   uint32_t k = (uint32_t)t;
@@ -257,12 +263,13 @@ __global__ void k_dg_classify(Level L) {
   warp_update<2>(L.csz, x1, self1 ? L.sz[s0 + 1] : 0u, self1);
 }
 
+__global__ void k_dg_classify(Level L) { dg_classify(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
+
 // The top edge of each light component takes the lowest heavy slot touching
 // it as its parent (2p + side: edge p, on that side), and hands the
 // component's size to that slot, which names the component in the heavy
 // half; heavy slots are renamed to it.
-__global__ void k_dg_stitch(Level L) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void dg_stitch(const Level &L, int64_t k) {
   if (k >= L.m) return;
   bool light;
   const bool split = block_split(L, (uint32_t)k, light);
@@ -282,6 +289,34 @@ __global__ void k_dg_stitch(Level L) {
     if (r1 < hs) L.rep[s0 + 1] = L.minh[uf_find<false>(L.uf, r1)];
   }
   clear_pair(L, s0);
+}
+
+__global__ void k_dg_stitch(Level L) { dg_stitch(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
+
+// The levels of blocks from kMidEdges edges down to 2 * kLocalEdges, one CTA
+// per block of kMidEdges edges: the same three steps per level as the global
+// kernels, separated by barriers of the CTA instead of kernel boundaries, on
+// the same global arrays, which stay in L2 while the CTA works on its
+// block's slots (no other CTA touches them).  `L` arrives with the set of
+// the first of these levels current (cleared by the level before); the
+// levels alternate the sets as the host loop does.
+__global__ void __launch_bounds__(kMidThreads) k_dg_mid(Level L, int64_t top) {
+  const int64_t b0 = (int64_t)blockIdx.x * top;
+  for (int64_t S = top; S > kLocalEdges; S >>= 1) {
+    L.mask = (uint32_t)(S - 1);
+    L.half = (uint32_t)(S >> 1);
+    for (int64_t j = threadIdx.x; j < top; j += kMidThreads) dg_unite(L, b0 + j);
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < top; j += kMidThreads) dg_classify(L, b0 + j);
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < top; j += kMidThreads) dg_stitch(L, b0 + j);
+    __syncthreads();
+    uint32_t *t;
+    t = L.uf; L.uf = L.nuf; L.nuf = t;
+    t = L.top; L.top = L.ntop; L.ntop = t;
+    t = L.minh; L.minh = L.nminh; L.nminh = t;
+    t = L.csz; L.csz = L.ncsz; L.ncsz = t;
+  }
 }
 
 // The levels of blocks of kLocalEdges edges and less, in shared memory, one
@@ -548,7 +583,8 @@ int dendrogram_impl(const emst_edge *edges, int64_t n, uint4 *out_link, uint32_t
     std::swap(L.top, L.ntop);
     std::swap(L.minh, L.nminh);
     std::swap(L.csz, L.ncsz);
-    for (; S > kLocalEdges; S /= 2) {
+    const int64_t mid = kMidEdges > kLocalEdges ? kMidEdges : 0;
+    for (; S > kLocalEdges && (mid == 0 || S > mid); S /= 2) {
       L.mask = (uint32_t)(S - 1);
       L.half = (uint32_t)(S / 2);
       k_dg_unite<<<gm, kDgBlock, 0, s>>>(L);
@@ -559,6 +595,8 @@ int dendrogram_impl(const emst_edge *edges, int64_t n, uint4 *out_link, uint32_t
       std::swap(L.minh, L.nminh);
       std::swap(L.csz, L.ncsz);
     }
+    if (S > kLocalEdges)  // the remaining levels, S down to 2 * kLocalEdges, one CTA per block
+      k_dg_mid<<<(unsigned)((m + S - 1) / S), kMidThreads, 0, s>>>(L, S);
     cudaFuncSetAttribute(k_dg_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLocalSmem);
     k_dg_local<<<grid_for(m, kLocalEdges), kLocalThreads, kLocalSmem, s>>>(m, L.rep, L.sz, eparent,
                                                                            size, status);
