@@ -81,6 +81,31 @@ __device__ __forceinline__ uint32_t uf_find(T *uf, uint32_t x) {
   }
 }
 
+// The roots of a and b, the two walks advanced together so that their
+// loads are in flight at once (each walk as in uf_find; `wa` / `wb` false:
+// that walk is not needed and its result is the input).
+template <bool HALVE, class T>
+__device__ __forceinline__ void uf_find2(T *uf, uint32_t &a, uint32_t &b, bool wa = true,
+                                         bool wb = true) {
+  bool da = !wa, db = !wb;
+  while (!(da && db)) {
+    const uint32_t pa = da ? a : uf[a];
+    const uint32_t pb = db ? b : uf[b];
+    if (!da && pa == a) da = true;
+    if (!db && pb == b) db = true;
+    const uint32_t ga = da ? a : uf[pa];
+    const uint32_t gb = db ? b : uf[pb];
+    if (!da) {
+      if (ga == pa) { a = pa; da = true; }
+      else { if (HALVE) uf[a] = ga; a = ga; }
+    }
+    if (!db) {
+      if (gb == pb) { b = pb; db = true; }
+      else { if (HALVE) uf[b] = gb; b = gb; }
+    }
+  }
+}
+
 // Joins the sets of a and b, lock-free.  A failed hook returns the hooked
 // root's actual parent, and the walk resumes there, so each retry climbs the
 // real chain.  Hooking the higher-priority root under the other cannot close
@@ -88,8 +113,7 @@ __device__ __forceinline__ uint32_t uf_find(T *uf, uint32_t x) {
 // priority.  False only if the retry bound runs out.
 template <class T>
 __device__ __forceinline__ bool uf_unite(T *uf, uint32_t a, uint32_t b) {
-  a = uf_find<true>(uf, a);
-  b = uf_find<true>(uf, b);
+  uf_find2<true>(uf, a, b);
   for (int it = 0; it < (1 << 22); ++it) {
     if (a == b) return true;
     const bool ah = prio(a) > prio(b);
@@ -247,8 +271,9 @@ __device__ __forceinline__ void dg_classify(const Level &L, int64_t t) {
     } else {
       m0 = r0 < hs;
       m1 = r1 < hs;
-      if (m0) x0 = uf_find<true>(L.uf, r0);
-      if (m1) x1 = uf_find<true>(L.uf, r1);
+      x0 = r0;
+      x1 = r1;
+      uf_find2<true>(L.uf, x0, x1, m0, m1);
     }
   }
   warp_update<0>(L.top, x0, k + 1, act && light);
@@ -285,8 +310,10 @@ __device__ __forceinline__ void dg_stitch(const Level &L, int64_t k) {
   } else if (split) {
     // (names in the heavy half stay: see k_dg_classify)
     const uint32_t hs = 2 * (((uint32_t)k & ~L.mask) + L.half);
-    if (r0 < hs) L.rep[s0] = L.minh[uf_find<false>(L.uf, r0)];
-    if (r1 < hs) L.rep[s0 + 1] = L.minh[uf_find<false>(L.uf, r1)];
+    uint32_t x0 = r0, x1 = r1;
+    uf_find2<false>(L.uf, x0, x1, r0 < hs, r1 < hs);
+    if (r0 < hs) L.rep[s0] = L.minh[x0];
+    if (r1 < hs) L.rep[s0 + 1] = L.minh[x1];
   }
   clear_pair(L, s0);
 }
