@@ -27,6 +27,7 @@
 // lowest-ranked edge of its block that touches it.  The blocks of one level
 // own disjoint slot ranges, so one union-find over all 2m slots serves every
 // block of a level at once.
+#include <cstdlib>
 #include <utility>
 
 #include "common.cuh"
@@ -64,19 +65,54 @@ __device__ __forceinline__ uint32_t prio(uint32_t x) {
   return x;
 }
 
+// How a level reads and writes its per-slot entries.  Plain (TAG false):
+// an entry holds its value, and every level starts from cleared entries.
+// Tagged (TAG true, trees below 2^26 edges): an entry also carries, in its
+// top 5 bits, the number of the level that wrote it, so an entry of an
+// earlier level reads as never written and nothing needs clearing: a
+// union-find entry is (level, parent) -- any other level's entry makes its
+// slot a root; a component's top edge is (level, rank + 1), which any
+// earlier level's entry is below (atomicMax); its lowest heavy slot is
+// (31 - level, slot), which any earlier level's entry (and the initial all
+// ones) is above (atomicMin).
+template <bool TAG>
+struct Codec {
+  uint32_t cur = 0;  // this level's number, 1..30 (TAG)
+  static constexpr uint32_t kV = 0x07FFFFFFu;
+  __device__ __forceinline__ uint32_t parent(uint32_t raw, uint32_t x) const {
+    if (!TAG) return raw;
+    return (raw >> 27) == cur ? (raw & kV) : x;
+  }
+  __device__ __forceinline__ uint32_t link(uint32_t p) const { return TAG ? ((cur << 27) | p) : p; }
+  __device__ __forceinline__ uint32_t top_val(uint32_t rank1) const {
+    return TAG ? ((cur << 27) | rank1) : rank1;
+  }
+  __device__ __forceinline__ uint32_t top_of(uint32_t raw) const {
+    if (!TAG) return raw;
+    return (raw >> 27) == cur ? (raw & kV) : 0u;
+  }
+  __device__ __forceinline__ uint32_t minh_val(uint32_t slot) const {
+    return TAG ? (((31u - cur) << 27) | slot) : slot;
+  }
+  __device__ __forceinline__ uint32_t minh_of(uint32_t raw) const {
+    if (!TAG) return raw;
+    return (raw >> 27) == 31u - cur ? (raw & kV) : kInvalid;
+  }
+};
+
 // Root of x, optionally halving the path.  Every parent has a lower
 // priority than its child and a parent is only ever replaced by an
 // ancestor, so a walk is strictly descending and ends even when it reads
 // stale (cached) entries: a stale entry is still an ancestor.  A stale root
 // is caught by the hook's compare-and-swap in uf_unite.
-template <bool HALVE, class T>
-__device__ __forceinline__ uint32_t uf_find(T *uf, uint32_t x) {
+template <bool HALVE, bool TAG = false, class T>
+__device__ __forceinline__ uint32_t uf_find(T *uf, uint32_t x, Codec<TAG> C = Codec<TAG>()) {
   for (;;) {
-    const uint32_t p = uf[x];
+    const uint32_t p = C.parent(uf[x], x);
     if (p == x) return x;
-    const uint32_t g = uf[p];
+    const uint32_t g = C.parent(uf[p], p);
     if (g == p) return p;
-    if (HALVE) uf[x] = g;
+    if (HALVE) uf[x] = C.link(g);
     x = g;
   }
 }
@@ -84,24 +120,24 @@ __device__ __forceinline__ uint32_t uf_find(T *uf, uint32_t x) {
 // The roots of a and b, the two walks advanced together so that their
 // loads are in flight at once (each walk as in uf_find; `wa` / `wb` false:
 // that walk is not needed and its result is the input).
-template <bool HALVE, class T>
+template <bool HALVE, bool TAG = false, class T>
 __device__ __forceinline__ void uf_find2(T *uf, uint32_t &a, uint32_t &b, bool wa = true,
-                                         bool wb = true) {
+                                         bool wb = true, Codec<TAG> C = Codec<TAG>()) {
   bool da = !wa, db = !wb;
   while (!(da && db)) {
-    const uint32_t pa = da ? a : uf[a];
-    const uint32_t pb = db ? b : uf[b];
+    const uint32_t pa = da ? a : C.parent(uf[a], a);
+    const uint32_t pb = db ? b : C.parent(uf[b], b);
     if (!da && pa == a) da = true;
     if (!db && pb == b) db = true;
-    const uint32_t ga = da ? a : uf[pa];
-    const uint32_t gb = db ? b : uf[pb];
+    const uint32_t ga = da ? a : C.parent(uf[pa], pa);
+    const uint32_t gb = db ? b : C.parent(uf[pb], pb);
     if (!da) {
       if (ga == pa) { a = pa; da = true; }
-      else { if (HALVE) uf[a] = ga; a = ga; }
+      else { if (HALVE) uf[a] = C.link(ga); a = ga; }
     }
     if (!db) {
       if (gb == pb) { b = pb; db = true; }
-      else { if (HALVE) uf[b] = gb; b = gb; }
+      else { if (HALVE) uf[b] = C.link(gb); b = gb; }
     }
   }
 }
@@ -110,18 +146,32 @@ __device__ __forceinline__ void uf_find2(T *uf, uint32_t &a, uint32_t &b, bool w
 // root's actual parent, and the walk resumes there, so each retry climbs the
 // real chain.  Hooking the higher-priority root under the other cannot close
 // a cycle even when the other is stale: its actual root has a still lower
-// priority.  False only if the retry bound runs out.
-template <class T>
-__device__ __forceinline__ bool uf_unite(T *uf, uint32_t a, uint32_t b) {
-  uf_find2<true>(uf, a, b);
+// priority.  False only if the retry bound runs out.  Tagged entries: the
+// hook swaps the root's entry as read (whatever earlier level wrote it) for
+// the link; a changed entry that still reads as a root is retried.
+template <bool TAG = false, class T>
+__device__ __forceinline__ bool uf_unite(T *uf, uint32_t a, uint32_t b, Codec<TAG> C = Codec<TAG>()) {
+  uf_find2<true, TAG>(uf, a, b, true, true, C);
   for (int it = 0; it < (1 << 22); ++it) {
     if (a == b) return true;
     const bool ah = prio(a) > prio(b);
     const uint32_t hi = ah ? a : b, lo = ah ? b : a;
-    const uint32_t old = atomicCAS((uint32_t *)uf + hi, hi, lo);
-    if (old == hi) return true;
-    if (ah) a = uf_find<true>(uf, old);
-    else b = uf_find<true>(uf, old);
+    uint32_t expect = hi;
+    if constexpr (TAG) {  // (read in L2, where the swap compares: a cached copy may be old)
+      expect = __ldcg(reinterpret_cast<const unsigned int *>(uf) + hi);
+      const uint32_t p = C.parent(expect, hi);
+      if (p != hi) {  // no longer a root
+        if (ah) a = uf_find<true, TAG>(uf, p, C);
+        else b = uf_find<true, TAG>(uf, p, C);
+        continue;
+      }
+    }
+    const uint32_t old = atomicCAS((uint32_t *)uf + hi, expect, C.link(lo));
+    if (old == expect) return true;
+    const uint32_t p = C.parent(old, hi);
+    if (p == hi) continue;  // (TAG: the entry read was not the current one)
+    if (ah) a = uf_find<true, TAG>(uf, p, C);
+    else b = uf_find<true, TAG>(uf, p, C);
   }
   return false;
 }
@@ -192,20 +242,46 @@ __global__ void k_dg_first_slot(const emst_edge *__restrict__ e, int64_t m2,
 // starts at a name and hooks join names), but every slot is cleared: whole
 // coalesced sectors, where clearing the scattered names alone made each
 // sector a partial write that DRAM had to fill first (measured 4.2 GB per
-// stitch launch at 37M points, HBM-bound).
+// stitch launch at 37M points, HBM-bound).  With tagged entries (Codec)
+// only the sizes alternate and are cleared; one set of union-find, top and
+// lowest-heavy entries serves every level.
 struct Level {
   uint32_t *rep, *sz, *uf, *top, *minh, *csz, *parent;
   uint32_t *nuf, *ntop, *nminh, *ncsz;  // the next level's set
   int64_t m;
   uint32_t mask, half;  // block size - 1, half the block size
+  uint32_t cur;         // this level's number (tagged entries)
   uint32_t *status;
 };
 
+template <bool TAG>
+__device__ __forceinline__ Codec<TAG> codec(const Level &L) {
+  Codec<TAG> C;
+  C.cur = L.cur;
+  return C;
+}
+
+template <bool TAG>
 __device__ __forceinline__ void clear_pair(const Level &L, uint32_t s0) {
-  reinterpret_cast<uint2 *>(L.nuf)[s0 >> 1] = make_uint2(s0, s0 + 1);
-  reinterpret_cast<uint2 *>(L.ntop)[s0 >> 1] = make_uint2(0u, 0u);
-  reinterpret_cast<uint2 *>(L.nminh)[s0 >> 1] = make_uint2(kInvalid, kInvalid);
+  if (!TAG) {
+    reinterpret_cast<uint2 *>(L.nuf)[s0 >> 1] = make_uint2(s0, s0 + 1);
+    reinterpret_cast<uint2 *>(L.ntop)[s0 >> 1] = make_uint2(0u, 0u);
+    reinterpret_cast<uint2 *>(L.nminh)[s0 >> 1] = make_uint2(kInvalid, kInvalid);
+  }
   reinterpret_cast<uint2 *>(L.ncsz)[s0 >> 1] = make_uint2(0u, 0u);
+}
+
+// The host's and the CTA-level kernel's step from one level to the next.
+template <bool TAG>
+__host__ __device__ __forceinline__ void next_level(Level &L) {
+  uint32_t *t;
+  if (!TAG) {
+    t = L.uf; L.uf = L.nuf; L.nuf = t;
+    t = L.top; L.top = L.ntop; L.ntop = t;
+    t = L.minh; L.minh = L.nminh; L.nminh = t;
+  }
+  t = L.csz; L.csz = L.ncsz; L.ncsz = t;
+  L.cur += 1;
 }
 
 __device__ __forceinline__ bool block_split(const Level &L, uint32_t k, bool &light) {
@@ -218,6 +294,7 @@ __device__ __forceinline__ bool block_split(const Level &L, uint32_t k, bool &li
 // The slot that names point v also records v as the child on that side of
 // its edge (the cluster a point starts in); the even slot of each edge
 // clears the first level's set for the edge's two slots.
+template <bool TAG>
 __global__ void k_dg_init(Level L, const emst_edge *__restrict__ e,
                           const uint32_t *__restrict__ vslot, uint32_t *__restrict__ child) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,19 +303,21 @@ __global__ void k_dg_init(Level L, const emst_edge *__restrict__ e,
   const uint32_t r = vslot[v];
   L.rep[s] = r;
   L.sz[s] = 1;
-  if ((s & 1) == 0) clear_pair(L, (uint32_t)s);
+  if ((s & 1) == 0) clear_pair<TAG>(L, (uint32_t)s);
   if (child) child[s] = r == (uint32_t)s ? v : kInvalid;  // the rest come from k_dg_children
 }
 
 // Light components: unite the two vertices of every light edge.
+template <bool TAG>
 __device__ __forceinline__ void dg_unite(const Level &L, int64_t k) {
   if (k >= L.m) return;
   bool light;
   if (!block_split(L, (uint32_t)k, light) || !light) return;
-  if (!uf_unite(L.uf, L.rep[2 * k], L.rep[2 * k + 1])) atomicOr(L.status, kErrSpin);
+  if (!uf_unite<TAG>(L.uf, L.rep[2 * k], L.rep[2 * k + 1], codec<TAG>(L))) atomicOr(L.status, kErrSpin);
 }
 
-__global__ void k_dg_unite(Level L) { dg_unite(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
+template <bool TAG>
+__global__ void k_dg_unite(Level L) { dg_unite<TAG>(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
 
 // Per light component (by root): its top edge (rank + 1), its size (the sum
 // over its vertices, each counted at the slot that names it) and the lowest
@@ -246,7 +325,9 @@ __global__ void k_dg_unite(Level L) { dg_unite(L, (int64_t)blockIdx.x * blockDim
 // are visited from the top rank down, so the first value to reach a
 // component's top is usually its maximum and later lanes skip the atomic.
 // (every lane of a warp calls it: warp_update combines across the warp)
+template <bool TAG>
 __device__ __forceinline__ void dg_classify(const Level &L, int64_t t) {
+  const Codec<TAG> C = codec<TAG>(L);
   bool light = false;
   const bool act = t < L.m && block_split(L, (uint32_t)t, light);
   uint32_t k = (uint32_t)t;
@@ -266,19 +347,19 @@ __device__ __forceinline__ void dg_classify(const Level &L, int64_t t) {
     r0 = L.rep[s0];
     r1 = L.rep[s0 + 1];
     if (light) {
-      x0 = uf_find<true>(L.uf, r0);
+      x0 = uf_find<true, TAG>(L.uf, r0, C);
       x1 = x0;  // a light edge's ends share a root
     } else {
       m0 = r0 < hs;
       m1 = r1 < hs;
       x0 = r0;
       x1 = r1;
-      uf_find2<true>(L.uf, x0, x1, m0, m1);
+      uf_find2<true, TAG>(L.uf, x0, x1, m0, m1, C);
     }
   }
-  warp_update<0>(L.top, x0, k + 1, act && light);
-  warp_update<1>(L.minh, x0, s0, m0);
-  warp_update<1>(L.minh, x1, s0 + 1, m1);
+  warp_update<0>(L.top, x0, C.top_val(k + 1), act && light);
+  warp_update<1>(L.minh, x0, C.minh_val(s0), m0);
+  warp_update<1>(L.minh, x1, C.minh_val(s0 + 1), m1);
   // sizes are summed for light components only: a slot of the heavy half
   // that names its vertex names one that touches no light edge (a vertex's
   // name is its lowest slot in the block, and light slots come first), a
@@ -288,22 +369,25 @@ __device__ __forceinline__ void dg_classify(const Level &L, int64_t t) {
   warp_update<2>(L.csz, x1, self1 ? L.sz[s0 + 1] : 0u, self1);
 }
 
-__global__ void k_dg_classify(Level L) { dg_classify(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
+template <bool TAG>
+__global__ void k_dg_classify(Level L) { dg_classify<TAG>(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
 
 // The top edge of each light component takes the lowest heavy slot touching
 // it as its parent (2p + side: edge p, on that side), and hands the
 // component's size to that slot, which names the component in the heavy
 // half; heavy slots are renamed to it.
+template <bool TAG>
 __device__ __forceinline__ void dg_stitch(const Level &L, int64_t k) {
   if (k >= L.m) return;
+  const Codec<TAG> C = codec<TAG>(L);
   bool light;
   const bool split = block_split(L, (uint32_t)k, light);
   const uint32_t s0 = 2 * (uint32_t)k;
   uint32_t r0 = L.rep[s0], r1 = L.rep[s0 + 1];
   if (split && light) {
-    const uint32_t r = uf_find<false>(L.uf, r0);
-    const uint32_t h = L.minh[r];
-    if (L.top[r] == (uint32_t)k + 1 && h != kInvalid) {
+    const uint32_t r = uf_find<false, TAG>(L.uf, r0, C);
+    const uint32_t h = C.minh_of(L.minh[r]);
+    if (C.top_of(L.top[r]) == (uint32_t)k + 1 && h != kInvalid) {
       L.parent[k] = h;
       L.sz[h] = L.csz[r];
     }
@@ -311,14 +395,15 @@ __device__ __forceinline__ void dg_stitch(const Level &L, int64_t k) {
     // (names in the heavy half stay: see k_dg_classify)
     const uint32_t hs = 2 * (((uint32_t)k & ~L.mask) + L.half);
     uint32_t x0 = r0, x1 = r1;
-    uf_find2<false>(L.uf, x0, x1, r0 < hs, r1 < hs);
-    if (r0 < hs) L.rep[s0] = L.minh[x0];
-    if (r1 < hs) L.rep[s0 + 1] = L.minh[x1];
+    uf_find2<false, TAG>(L.uf, x0, x1, r0 < hs, r1 < hs, C);
+    if (r0 < hs) L.rep[s0] = C.minh_of(L.minh[x0]);
+    if (r1 < hs) L.rep[s0 + 1] = C.minh_of(L.minh[x1]);
   }
-  clear_pair(L, s0);
+  clear_pair<TAG>(L, s0);
 }
 
-__global__ void k_dg_stitch(Level L) { dg_stitch(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
+template <bool TAG>
+__global__ void k_dg_stitch(Level L) { dg_stitch<TAG>(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
 
 // The levels of blocks from kMidEdges edges down to 2 * kLocalEdges, one CTA
 // per block of kMidEdges edges: the same three steps per level as the global
@@ -327,22 +412,19 @@ __global__ void k_dg_stitch(Level L) { dg_stitch(L, (int64_t)blockIdx.x * blockD
 // block's slots (no other CTA touches them).  `L` arrives with the set of
 // the first of these levels current (cleared by the level before); the
 // levels alternate the sets as the host loop does.
+template <bool TAG>
 __global__ void __launch_bounds__(kMidThreads) k_dg_mid(Level L, int64_t top) {
   const int64_t b0 = (int64_t)blockIdx.x * top;
   for (int64_t S = top; S > kLocalEdges; S >>= 1) {
     L.mask = (uint32_t)(S - 1);
     L.half = (uint32_t)(S >> 1);
-    for (int64_t j = threadIdx.x; j < top; j += kMidThreads) dg_unite(L, b0 + j);
+    for (int64_t j = threadIdx.x; j < top; j += kMidThreads) dg_unite<TAG>(L, b0 + j);
     __syncthreads();
-    for (int64_t j = threadIdx.x; j < top; j += kMidThreads) dg_classify(L, b0 + j);
+    for (int64_t j = threadIdx.x; j < top; j += kMidThreads) dg_classify<TAG>(L, b0 + j);
     __syncthreads();
-    for (int64_t j = threadIdx.x; j < top; j += kMidThreads) dg_stitch(L, b0 + j);
+    for (int64_t j = threadIdx.x; j < top; j += kMidThreads) dg_stitch<TAG>(L, b0 + j);
     __syncthreads();
-    uint32_t *t;
-    t = L.uf; L.uf = L.nuf; L.nuf = t;
-    t = L.top; L.top = L.ntop; L.ntop = t;
-    t = L.minh; L.minh = L.nminh; L.nminh = t;
-    t = L.csz; L.csz = L.ncsz; L.ncsz = t;
+    next_level<TAG>(L);
   }
 }
 
@@ -600,30 +682,46 @@ int dendrogram_impl(const emst_edge *edges, int64_t n, uint4 *out_link, uint32_t
     uint32_t *child = link ? U(o_slot[10]) : nullptr;
     int64_t S = kLocalEdges;
     while (S < m) S *= 2;
+    // Tagged entries when slot numbers fit their 27 value bits (the level
+    // numbers, at most log2(2^26 / kLocalEdges) + 1, fit the 5 tag bits):
+    // the union-find, top and lowest-heavy entries are set once here and
+    // never cleared again.
+    // (EMST_DENDROGRAM_UNTAGGED=1 in the environment selects the cleared
+    // entries at any size: the tests run both forms)
+    const char *force_plain = getenv("EMST_DENDROGRAM_UNTAGGED");
+    const bool tagged = m2 < ((int64_t)1 << 27) && !(force_plain && force_plain[0] == '1');
+    L.cur = 1;
+    if (tagged) {
+      cudaMemsetAsync(L.uf, 0, 4 * (size_t)m2, s);
+      cudaMemsetAsync(L.top, 0, 4 * (size_t)m2, s);
+      cudaMemsetAsync(L.minh, 0xff, 4 * (size_t)m2, s);
+    }
     // the first level reads the set k_dg_init clears (the "next" one here)
-    std::swap(L.uf, L.nuf);
-    std::swap(L.top, L.ntop);
-    std::swap(L.minh, L.nminh);
-    std::swap(L.csz, L.ncsz);
-    k_dg_init<<<gs, kDgBlock, 0, s>>>(L, e, vslot, child);
-    std::swap(L.uf, L.nuf);
-    std::swap(L.top, L.ntop);
-    std::swap(L.minh, L.nminh);
-    std::swap(L.csz, L.ncsz);
+    next_level<false>(L);
+    if (tagged) k_dg_init<true><<<gs, kDgBlock, 0, s>>>(L, e, vslot, child);
+    else k_dg_init<false><<<gs, kDgBlock, 0, s>>>(L, e, vslot, child);
+    next_level<false>(L);
+    L.cur = 1;
     const int64_t mid = kMidEdges > kLocalEdges ? kMidEdges : 0;
     for (; S > kLocalEdges && (mid == 0 || S > mid); S /= 2) {
       L.mask = (uint32_t)(S - 1);
       L.half = (uint32_t)(S / 2);
-      k_dg_unite<<<gm, kDgBlock, 0, s>>>(L);
-      k_dg_classify<<<gm, kDgBlock, 0, s>>>(L);
-      k_dg_stitch<<<gm, kDgBlock, 0, s>>>(L);
-      std::swap(L.uf, L.nuf);
-      std::swap(L.top, L.ntop);
-      std::swap(L.minh, L.nminh);
-      std::swap(L.csz, L.ncsz);
+      if (tagged) {
+        k_dg_unite<true><<<gm, kDgBlock, 0, s>>>(L);
+        k_dg_classify<true><<<gm, kDgBlock, 0, s>>>(L);
+        k_dg_stitch<true><<<gm, kDgBlock, 0, s>>>(L);
+        next_level<true>(L);
+      } else {
+        k_dg_unite<false><<<gm, kDgBlock, 0, s>>>(L);
+        k_dg_classify<false><<<gm, kDgBlock, 0, s>>>(L);
+        k_dg_stitch<false><<<gm, kDgBlock, 0, s>>>(L);
+        next_level<false>(L);
+      }
     }
-    if (S > kLocalEdges)  // the remaining levels, S down to 2 * kLocalEdges, one CTA per block
-      k_dg_mid<<<(unsigned)((m + S - 1) / S), kMidThreads, 0, s>>>(L, S);
+    if (S > kLocalEdges) {  // the remaining levels, S down to 2 * kLocalEdges, one CTA per block
+      if (tagged) k_dg_mid<true><<<(unsigned)((m + S - 1) / S), kMidThreads, 0, s>>>(L, S);
+      else k_dg_mid<false><<<(unsigned)((m + S - 1) / S), kMidThreads, 0, s>>>(L, S);
+    }
     cudaFuncSetAttribute(k_dg_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLocalSmem);
     k_dg_local<<<grid_for(m, kLocalEdges), kLocalThreads, kLocalSmem, s>>>(m, L.rep, L.sz, eparent,
                                                                            size, status);

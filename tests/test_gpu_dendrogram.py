@@ -72,6 +72,20 @@ def test_deep_and_wide_trees_large(pkg):
         assert_same(pkg, got, oracle.dendrogram(e, n), shape)
 
 
+def test_untagged_levels(pkg, monkeypatch):
+    # Trees below 2^26 edges keep the level number in each union-find, top
+    # and lowest-heavy entry, so no level clears them; larger trees clear
+    # them every level.  The environment switch selects the cleared form at
+    # any size: both must give the oracle's hierarchy.
+    monkeypatch.setenv("EMST_DENDROGRAM_UNTAGGED", "1")
+    for shape in ("random", "path_sorted", "star", "caterpillar"):
+        for ties in (0, 5):
+            for idx, n in enumerate((257, 4097, 100_003, 1_000_000)):
+                e = synth.tree_edges(n, 500 + 10 * idx + ties, shape, ties=ties)
+                got = gpu_dendrogram(pkg, edges_tensor(e), n)
+                assert_same(pkg, got, oracle.dendrogram(e, n), f"untagged {shape} ties={ties} n={n}")
+
+
 @pytest.mark.parametrize("name,make", [
     ("blobs2", lambda: synth.blobs(300_000, 2, 1)),
     ("halos3", lambda: synth.halos(1_000_000, 2)),
