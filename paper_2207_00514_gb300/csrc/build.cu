@@ -464,18 +464,23 @@ void launch_hierarchy(Problem &P) {
 }
 
 // ---------------------------------------------------------------------------
-// A4 (c). Refit: bottom-up boxes.  One thread per leaf chunk computes the box
-// of its points and climbs: at every node the first arriver leaves its box
-// for its sibling and stops; the second merges the two child boxes, writes
-// the node's whole record once (both boxes and the child references from the
-// node's range) and its child labels, and carries the union one level up.
-// Wait-free.
-// A node whose leaf range lies inside this CTA's chunks has both arrivals
-// from this CTA (and its index inside the CTA's range, one end of its range),
-// so both child boxes meet in shared memory and the arrivals are counted
-// there with block-scope acquire-release adds; only nodes spanning CTAs
-// (about 2 per CTA per level above it) pass the box through their global
-// record and use the global counters (device-scope acquire-release adds).
+// A4 (c). Refit: bottom-up boxes, in two launches.
+// k_refit: one thread per leaf chunk computes the box of its points and
+// climbs the nodes whose leaf range lies inside its CTA's chunks: both
+// arrivals at such a node come from this CTA, so both child boxes meet in
+// shared memory and the arrivals are counted there with block-scope
+// acquire-release adds; at every node the first arriver stops, the second
+// merges the two child boxes, writes the node's whole record once (both
+// boxes and the child references from the node's range) and its child
+// labels, and carries the union one level up.  The first node spanning
+// CTAs ends the climb: the thread leaves its box in its slot of that node's
+// global record and adds a device-scope acquire-release arrival; the second
+// arriver lists the node for the next launch.
+// k_refit_up: one thread per listed node (both child boxes in its record)
+// writes it and climbs on in global memory, first arriver stopping, as
+// above.  (In one launch the threads that climb above their CTA's nodes --
+// one or two per CTA, up to the root's depth -- would hold their CTA's
+// slot while its other threads are long done.)
 // The global counters are never reset: each pass adds exactly two arrivals
 // per node, so the parity of the count before the add tells first from
 // second.
@@ -489,12 +494,24 @@ void launch_hierarchy(Problem &P) {
 #define EMST_REFIT_BLOCK 128
 #endif
 constexpr int kRefitBlock = EMST_REFIT_BLOCK;  // leaf chunks per refit CTA
+constexpr int kRefitUpBlock = 128;
+constexpr uint32_t kRefitReadyCounter = 48;  // P.counters slot: nodes listed by k_refit
 
 __device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, const float *bx) {
   float2 *f = reinterpret_cast<float2 *>(rec) + 3 * slot;
   f[0] = make_float2(bx[0], bx[1]);
   f[1] = make_float2(bx[2], bx[3]);
   f[2] = make_float2(bx[4], bx[5]);
+}
+
+__device__ __forceinline__ void load_slot_box(const NodeRec *rec, int slot, float *bx) {
+  const float2 *f = reinterpret_cast<const float2 *>(rec) + 3 * slot;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const float2 v = __ldcg(f + t);
+    bx[2 * t] = v.x;
+    bx[2 * t + 1] = v.y;
+  }
 }
 
 // Arrival counters of the refit with acquire-release order: the first
@@ -512,13 +529,43 @@ __device__ __forceinline__ uint32_t add_acq_rel_cta_shared(uint32_t *p, uint32_t
   return old;
 }
 
+// Node `node` with range r and both child boxes L, R (and their smallest
+// original ids): its whole record (boxes, references -- leaves where the
+// range ends at the split -- and the round-0 child labels); returns the
+// union in `box` / `idmin`.
+__device__ __forceinline__ void write_node(NodeRec *nodes, uint2 *__restrict__ nlabels, uint32_t node,
+                                           const NodeRange &r, const float *L, const float *R,
+                                           uint32_t minL, uint32_t minR, int64_t n, int leaf,
+                                           float *box, uint32_t &idmin) {
+  const uint32_t g = r.split;
+  const bool lleaf = r.first == g, rleaf = r.last == g + 1u;
+  // a chunk of exactly one point is its own component in round 0
+  auto one_point = [&](int64_t c) { return n - c * leaf == 1 || leaf == 1; };
+  NodeRec rec;
+  rec.a = make_float4(L[0], L[1], L[2], L[3]);
+  rec.b = make_float4(L[4], L[5], R[0], R[1]);
+  rec.c = make_float4(R[2], R[3], R[4], R[5]);
+  rec.d = make_uint4(lleaf ? (kLeafBit | g) : g, rleaf ? (kLeafBit | (g + 1u)) : g + 1u, minL, minR);
+  nodes[node] = rec;
+  nlabels[node] = make_uint2(lleaf && one_point(g) ? (uint32_t)((int64_t)g * leaf) : kInvalid,
+                             rleaf && one_point(g + 1) ? (uint32_t)((int64_t)(g + 1) * leaf) : kInvalid);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    box[t] = fminf(L[t], R[t]);
+    box[3 + t] = fmaxf(L[3 + t], R[3 + t]);
+  }
+  idmin = min(minL, minR);
+}
+
 __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
                                                   int64_t nc, int leaf, NodeRec *nodes,
                                                   uint2 *__restrict__ nlabels,
                                                   const uint32_t *__restrict__ parent_leaf,
                                                   const uint2 *__restrict__ up_delta,
                                                   const uint2 *__restrict__ range,
-                                                  uint32_t *arrivals) {
+                                                  uint32_t *arrivals, uint32_t *__restrict__ ready,
+                                                  uint32_t *ready_count, uint32_t capacity,
+                                                  uint32_t *status) {
   __shared__ float s_box[kRefitBlock][2][6];  // both child boxes of each local node
   __shared__ uint32_t s_min[kRefitBlock][2];  // and their smallest original ids
   __shared__ uint32_t s_arrive[kRefitBlock];
@@ -545,64 +592,86 @@ __global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict_
     // both depend on the node only: one round trip per level
     const NodeRange r = unpack_range(node, __ldg(range + node));
     const uint32_t up_next = __ldg(&up_delta[node].x);
-    const bool local = (int64_t)r.first >= first && (int64_t)r.last <= last;
-    float sib[6];
-    uint32_t sibmin;
-    if (local) {
-#pragma unroll
-      for (int t = 0; t < 6; ++t) s_box[node - first][slot][t] = box[t];
-      s_min[node - first][slot] = idmin;
-      if (add_acq_rel_cta_shared(&s_arrive[node - first], 1u) == 0u) return;  // first: the sibling carries on
-#pragma unroll
-      for (int t = 0; t < 6; ++t) sib[t] = s_box[node - first][slot ^ 1][t];
-      sibmin = s_min[node - first][slot ^ 1];
-    } else {
+    if ((int64_t)r.first < first || (int64_t)r.last > last) {
+      // spans CTAs: leave the box for the sibling or for k_refit_up
       store_slot_box(&nodes[node], slot, box);
       reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = idmin;
       const uint32_t before = add_acq_rel_gpu(&arrivals[node], 1u);
-      if ((before & 1u) == 0u) return;
-      const float2 *f = reinterpret_cast<const float2 *>(&nodes[node]) + 3 * (slot ^ 1);
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const float2 v = __ldcg(f + t);
-        sib[2 * t] = v.x;
-        sib[2 * t + 1] = v.y;
+      if ((before & 1u) != 0u) {
+        const uint32_t at = atomicAdd(ready_count, 1u);
+        if (at < capacity) ready[at] = node;
+        else atomicOr(status, kErrChain);  // cannot happen (see launch_refit)
       }
-      sibmin = __ldcg(reinterpret_cast<const uint32_t *>(&nodes[node].d) + 2 + (slot ^ 1));
+      return;
     }
-    const float *L = slot == 0 ? box : sib;
-    const float *R = slot == 0 ? sib : box;
-    // the whole record: boxes, references (leaves where the range ends at the
-    // split), round-0 child labels
-    const uint32_t g = r.split;
-    const bool lleaf = r.first == g, rleaf = r.last == g + 1u;
-    // a chunk of exactly one point is its own component in round 0
-    auto one_point = [&](int64_t c) { return n - c * leaf == 1 || leaf == 1; };
-    NodeRec rec;
-    rec.a = make_float4(L[0], L[1], L[2], L[3]);
-    rec.b = make_float4(L[4], L[5], R[0], R[1]);
-    rec.c = make_float4(R[2], R[3], R[4], R[5]);
-    rec.d = make_uint4(lleaf ? (kLeafBit | g) : g, rleaf ? (kLeafBit | (g + 1u)) : g + 1u,
-                       slot == 0 ? idmin : sibmin, slot == 0 ? sibmin : idmin);
-    nodes[node] = rec;
-    nlabels[node] = make_uint2(lleaf && one_point(g) ? (uint32_t)((int64_t)g * leaf) : kInvalid,
-                               rleaf && one_point(g + 1) ? (uint32_t)((int64_t)(g + 1) * leaf) : kInvalid);
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      box[t] = fminf(L[t], R[t]);
-      box[3 + t] = fmaxf(L[3 + t], R[3 + t]);
-    }
-    idmin = min(idmin, sibmin);
+    for (int t = 0; t < 6; ++t) s_box[node - first][slot][t] = box[t];
+    s_min[node - first][slot] = idmin;
+    if (add_acq_rel_cta_shared(&s_arrive[node - first], 1u) == 0u) return;  // first: the sibling carries on
+    float sib[6];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) sib[t] = s_box[node - first][slot ^ 1][t];
+    const uint32_t sibmin = s_min[node - first][slot ^ 1];
+    if (slot == 0) write_node(nodes, nlabels, node, r, box, sib, idmin, sibmin, n, leaf, box, idmin);
+    else write_node(nodes, nlabels, node, r, sib, box, sibmin, idmin, n, leaf, box, idmin);
     if (node == 0) return;
     up = up_next;
   }
 }
 
+__global__ void __launch_bounds__(kRefitUpBlock) k_refit_up(int64_t n, int leaf, NodeRec *nodes,
+                                                       uint2 *__restrict__ nlabels,
+                                                       const uint2 *__restrict__ up_delta,
+                                                       const uint2 *__restrict__ range,
+                                                       uint32_t *arrivals,
+                                                       const uint32_t *__restrict__ ready,
+                                                       const uint32_t *ready_count, uint32_t capacity) {
+  const uint32_t count = min(*ready_count, capacity);
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+    uint32_t node = __ldg(ready + t);
+    float box[6], sib[6];
+    uint32_t idmin, sibmin;
+    // both children arrived in k_refit: both boxes are in the record
+    load_slot_box(&nodes[node], 0, box);
+    load_slot_box(&nodes[node], 1, sib);
+    idmin = __ldcg(reinterpret_cast<const uint32_t *>(&nodes[node].d) + 2);
+    sibmin = __ldcg(reinterpret_cast<const uint32_t *>(&nodes[node].d) + 3);
+    int slot = 0;
+    while (true) {
+      const NodeRange r = unpack_range(node, __ldg(range + node));
+      if (slot == 0) write_node(nodes, nlabels, node, r, box, sib, idmin, sibmin, n, leaf, box, idmin);
+      else write_node(nodes, nlabels, node, r, sib, box, sibmin, idmin, n, leaf, box, idmin);
+      if (node == 0) break;
+      const uint32_t up = __ldg(&up_delta[node].x);
+      node = up >> 1;
+      slot = (int)(up & 1u);
+      store_slot_box(&nodes[node], slot, box);
+      reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = idmin;
+      const uint32_t before = add_acq_rel_gpu(&arrivals[node], 1u);
+      if ((before & 1u) == 0u) break;  // first: the sibling carries on
+      load_slot_box(&nodes[node], slot ^ 1, sib);
+      sibmin = __ldcg(reinterpret_cast<const uint32_t *>(&nodes[node].d) + 2 + (slot ^ 1));
+    }
+  }
+}
+
 void launch_refit(Problem &P) {
+  // A listed node has both children inside CTAs of k_refit but spans two,
+  // so it splits at the boundary between them: fewer listed nodes than
+  // k_refit has CTAs.  list_buf[1] (n entries) is free until the rounds.
+  uint32_t *ready = P.list_buf[1];
+  uint32_t *ready_count = P.counters + kRefitReadyCounter;
+  cudaMemsetAsync(ready_count, 0, sizeof(uint32_t), P.stream);
   k_refit<<<grid_for(P.nc, kRefitBlock), kRefitBlock, 0, P.stream>>>(P.pts, P.n, P.nc, P.leaf, P.nodes,
                                                           P.nlabels, P.parent_leaf, P.up_delta, P.range,
-                                                          P.arrivals);
-  P.launches += 1;
+                                                          P.arrivals, ready, ready_count,
+                                                          (uint32_t)P.n, P.counters + 1);
+  int64_t g = grid_for(P.nc, kRefitBlock) / kRefitUpBlock + 1;
+  if (g > (int64_t)sm_count() * 16) g = (int64_t)sm_count() * 16;
+  k_refit_up<<<(unsigned)g, kRefitUpBlock, 0, P.stream>>>(P.n, P.leaf, P.nodes, P.nlabels, P.up_delta,
+                                                          P.range, P.arrivals, ready, ready_count,
+                                                          (uint32_t)P.n);
+  P.launches += 2;
 }
 
 }  // namespace emst

@@ -49,14 +49,23 @@ __device__ __forceinline__ uint32_t runs_at(const uint32_t *__restrict__ runs_lo
 
 // Exclusive scan of count values by one CTA of kScanThreads threads, each
 // summing a contiguous chunk (the values come from other CTAs of the same
-// launch: read through L2).
+// launch: read through L2).  Chunks are a multiple of 8 values and read 8 at
+// a time with all 8 loads in flight: this runs on one CTA at the end of the
+// launch, so its L2 round trips are the launch's tail.
 __device__ void block_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t count) {
   __shared__ uint32_t s_part[kScanThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t chunk = (count + kScanThreads - 1) / kScanThreads;
-  const int64_t lo = (int64_t)tid * chunk, hi = lo + chunk < count ? lo + chunk : count;
+  const int64_t chunk = ((count + kScanThreads - 1) / kScanThreads + 7) & ~(int64_t)7;
+  const int64_t lo = (int64_t)tid * chunk < count ? (int64_t)tid * chunk : count;
+  const int64_t hi = lo + chunk < count ? lo + chunk : count;
   uint32_t sum = 0;
-  for (int64_t t = lo; t < hi; ++t) sum += __ldcg(in + t);
+  for (int64_t t = lo; t < hi; t += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = t + u < hi ? __ldcg(in + t + u) : 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sum += v[u];
+  }
   uint32_t x = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -68,10 +77,15 @@ __device__ void block_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t 
   uint32_t base = 0;
   for (int w = 0; w < warp; ++w) base += s_part[w];
   uint32_t run = base + x - sum;
-  for (int64_t t = lo; t < hi; ++t) {
-    const uint32_t v = __ldcg(in + t);
-    out[t] = run;
-    run += v;
+  for (int64_t t = lo; t < hi; t += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = t + u < hi ? __ldcg(in + t + u) : 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (t + u < hi) out[t + u] = run;
+      run += v[u];
+    }
   }
 }
 
