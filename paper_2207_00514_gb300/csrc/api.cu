@@ -288,7 +288,8 @@ void run_build(Problem &P) {
 void run_round(Problem &P, int round, bool carried, int block, bool count) {
   if (round > 0) launch_node_labels(P);
   else launch_upper_bounds(P);
-  launch_traverse(P, round > 0 && carried, nullptr, block, count, true, 0, round == 0);
+  launch_traverse(P, round > 0 && carried, nullptr, block, count, true, 0, round == 0,
+                  P.graph_round ? -1 : round);
   launch_merge(P);
 }
 
@@ -374,6 +375,7 @@ static cudaError_t run_rounds_graph(Problem &P, int64_t expected, int limit, boo
   if (e == cudaSuccess) {
     P.stream = cs[1];
     launches0 = P.launches;
+    P.graph_round = true;  // (the body serves every later round: numbers unknown)
     run_round(P, 1, carried, block, false);
     *kernels = P.launches - launches0 + 1;
     k_rounds_cond<<<1, 1, 0, cs[1]>>>(h_loop, h_if, kCondBoth, P.counters, (uint32_t)expected,
@@ -400,6 +402,7 @@ static cudaError_t run_rounds_graph(Problem &P, int64_t expected, int limit, boo
     advance_round(P, P.n_active);  // back: two swaps restore the first parity
   }
   P.stream = caller;
+  P.graph_round = false;
   // end every capture that began, whatever happened
   if (capturing >= 3) {
     cudaGraph_t x = nullptr;
@@ -722,7 +725,7 @@ int compute_impl(const float *points, int64_t n, int dim, const int64_t *offsets
         launch_rerun_mark(P);
         launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, 2);
       } else {
-        launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, 0, rounds == 0);
+        launch_traverse(P, rounds > 0 && carried, nullptr, block, count != 0, true, 0, rounds == 0, rounds);
       }
       if (stats && rounds < 40) {
         cudaEventRecord(tev[2 * rounds + 1], stream);

@@ -226,6 +226,7 @@ struct Problem {
   int refill_lanes = 0;              // its refill threshold (0: default)
   int queue_chunk = 0;               // its queue chunk per warp (0: default)
   int block = 0;                     // one-thread-per-point traversal CTA size (0: default)
+  bool graph_round = false;          // run_round is being captured as a graph body
   bool want_count = false;           // set before layout(): carve the visited-node bitmap
   uint32_t *seen = nullptr;          // count runs: bitmap of the internal nodes visited this round
   bool ties = true;                  // the search needs its tie rule (a run of > 32 equal
@@ -357,9 +358,10 @@ void launch_upper_bounds(Problem &P);
 // mrd.cu: squared core distances (k-th nearest neighbour, §4.5) into P.core2
 void launch_core_knn(Problem &P, int k);
 void launch_core_to_input(Problem &P, float *out);
-// first: the first round of the plain form (labels = curve indices)
+// first: the first round of the plain form (labels = curve indices);
+// round: the round's number (-1: not known, as in graph rounds)
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded, int learned_pass = 0, bool first = false);
+                     bool seeded, int learned_pass = 0, bool first = false, int round = -1);
 void launch_merge(Problem &P);
 void launch_fill_u32(Problem &P, uint32_t *p, uint32_t v, int64_t count);
 // count runs: adds the bits of the visited-node bitmap to counters[38..39]

@@ -261,16 +261,16 @@ void launch_upper_bounds(Problem &P) {
 // One thread per point, or (list != nullptr) a grid-stride pass over the
 // listed points (the certification reruns of the learned radius).
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
-          bool FIRST, bool MRD, bool TIES = true>
+          bool FIRST, bool MRD, bool TIES = true, bool LBT = true>
 __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (list) {
     const int64_t count = *list_count;
     for (int64_t t = gid; t < count; t += (int64_t)gridDim.x * blockDim.x)
-      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, __ldg(list + t));
+      traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES, LBT>(A, __ldg(list + t));
   } else if (gid < A.n) {
-    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES>(A, gid);
+    traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES, LBT>(A, gid);
   }
 }
 
@@ -425,8 +425,14 @@ static void launch_trav(TravKernel k, int g, int block, cudaStream_t s, const Tr
   k<<<g, block, 0, s>>>(A, list, list_count);
 }
 
+// The tighter lower bound of empty searches (traverse_one's LB) is tracked
+// from the second round after the first on: the round after the first still
+// searches nearly every point, so its bounds would cost it more than they
+// save the rounds after it.
+static bool track_lower_bounds(int round) { return round < 0 || round >= 2; }
+
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
-                     bool seeded, int learned_pass, bool first) {
+                     bool seeded, int learned_pass, bool first, int round) {
   if (block <= 0) block = kTraverseBlock;
   TravArgs A;
   A.pts = P.pts;
@@ -465,6 +471,9 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
 #define EMST_TRAV_FIRST(K, H) launch_trav(k_traverse<false, false, K, true, H, false, true, false>, g, block, s, A, list, list_count)
 #define EMST_TRAV_MRD(C, K, H) launch_trav(k_traverse<C, false, K, true, H, false, false, true>, g, block, s, A, list, list_count)
 #define EMST_TRAV_NOTIES(C, F, H) launch_trav(k_traverse<C, false, false, true, H, false, F, false, false>, g, block, s, A, list, list_count)
+#define EMST_TRAV_NOTIES_NOLB() launch_trav(k_traverse<true, false, false, true, false, false, false, false, false, false>, g, block, s, A, list, list_count)
+#define EMST_TRAV_NOLB(K) launch_trav(k_traverse<true, false, K, true, false, false, false, false, true, false>, g, block, s, A, list, list_count)
+  const bool lbt = track_lower_bounds(round);
 #define EMST_TRAV(C, R, K, S, L)                       \
   do {                                                 \
     if (P.leaf > 1) EMST_TRAV2(C, R, K, S, true, L);   \
@@ -473,7 +482,11 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   if (!P.ties && !count && seeded && !radius_in && learned_pass == 0 && !P.core2) {
     // the plain form on input without large groups of identical points
     const bool h = P.leaf > 1;
-    if (carried) { if (h) EMST_TRAV_NOTIES(true, false, true); else EMST_TRAV_NOTIES(true, false, false); }
+    if (carried) {
+      if (h) EMST_TRAV_NOTIES(true, false, true);
+      else if (lbt) EMST_TRAV_NOTIES(true, false, false);
+      else EMST_TRAV_NOTIES_NOLB();
+    }
     else if (first) { if (h) EMST_TRAV_NOTIES(false, true, true); else EMST_TRAV_NOTIES(false, true, false); }
     else { if (h) EMST_TRAV_NOTIES(false, false, true); else EMST_TRAV_NOTIES(false, false, false); }
   } else if (radius_in) {
@@ -496,7 +509,11 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
       else { if (h) EMST_TRAV_MRD(false, false, true); else EMST_TRAV_MRD(false, false, false); }
     }
   } else if (carried) {
-    if (count) EMST_TRAV(true, false, true, true, false); else EMST_TRAV(true, false, false, true, false);
+    if (!lbt && P.leaf == 1) {
+      if (count) EMST_TRAV_NOLB(true); else EMST_TRAV_NOLB(false);
+    } else {
+      if (count) EMST_TRAV(true, false, true, true, false); else EMST_TRAV(true, false, false, true, false);
+    }
   } else if (first) {  // the first round of the plain form: labels are the curve indices
     if (P.leaf > 1) {
       if (count) EMST_TRAV_FIRST(true, true); else EMST_TRAV_FIRST(false, true);

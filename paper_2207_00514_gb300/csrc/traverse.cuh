@@ -213,7 +213,7 @@ __device__ __forceinline__ uint32_t pop_next(const Query &q, Stack &stk) {
 // so max(core, box distance) <= cutoff  <=>  box distance <= cutoff.
 // TIES = false: the input has no large group of identical points (see the
 // tie rule below), so that check is compiled out.
-template <bool COUNT, bool CHUNKS, bool FIRST, bool MRD = false, bool TIES = true>
+template <bool COUNT, bool CHUNKS, bool FIRST, bool MRD = false, bool TIES = true, bool LB = false>
 __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *__restrict__ nodes,
                                         const uint2 *__restrict__ nlabels,
                                         const float4 *__restrict__ pts,
@@ -242,6 +242,15 @@ __device__ __forceinline__ bool explore(Query &q, uint32_t node, const NodeRec *
     const float dR = box_dist(q.px, q.py, q.pz, b.z, b.w, c.x, c.y, c.z, c.w);
     bool okL = (lab.x != q.me) && (dL <= q.radius);
     bool okR = (lab.y != q.me) && (dR <= q.radius);
+    // LB: while nothing is found, q.best keeps the smallest weight bound of a
+    // child of another component rejected by its distance (see traverse_one)
+    // (once something is found, q.best <= the cutoff < any rejected bound,
+    // so the update leaves it alone)
+    if (LB) {
+      const float rl = (lab.x != q.me && !okL) ? dL : __int_as_float(0x7f800000);
+      const float rr = (lab.y != q.me && !okR) ? dR : __int_as_float(0x7f800000);
+      q.best = fminf(q.best, fminf(rl, rr));
+    }
     if (okL && (dd.x & kLeafBit)) {
       scan_chunk<CHUNKS, MRD>(q, dd.x & ~kLeafBit, dL, leaf, n, pts, labels, core2);
       okL = false;
@@ -465,7 +474,7 @@ __device__ __forceinline__ void finish_query(const TravArgs &A, int64_t i, Query
 // steps as start_query + explore + finish_query, kept in one piece so the
 // point's record stays in registers through the search.
 template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bool LEARNED,
-          bool FIRST = false, bool MRD = false, bool TIES = true>
+          bool FIRST = false, bool MRD = false, bool TIES = true, bool LBT = true>
 __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   const float kInf = __int_as_float(0x7f800000);
   const int64_t n = A.n;
@@ -505,7 +514,8 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
     // component-level cutoff, this point cannot be an endpoint of the
     // component's minimum edge: skip the query.
     if (CARRIED && __uint_as_float(prev.x) > q.radius) {
-      A.res[i] = make_uint2(prev.x, kInvalid);
+      // (the entry already reads so when it holds no neighbour: no write)
+      if (prev.y != kInvalid) A.res[i] = make_uint2(prev.x, kInvalid);
       if (LEARNED) A.r_used[i] = kInf;
       return;
     }
@@ -524,7 +534,17 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
   uint32_t st_node[kStackDepth];
   float st_dist[kStackDepth];
   unsigned long long nvis = 0;
-  const bool ok = explore<COUNT, CHUNKS, FIRST, MRD, TIES>(q, start, A.nodes, A.nlabels, A.pts, A.labels,
+  // A search that finds nothing within r0 leaves a lower bound of this
+  // point's nearest other-component weight for the next round's skip test.
+  // LB: the smallest weight bound of the children of other components that
+  // the search rejected by distance (each above r0; every point of another
+  // component lies in such a child, or in a leaf the search saw), instead of
+  // r0 itself.  One-point leaves and the Euclidean weight only: there every
+  // rejected candidate is a child rejected by its box distance.  (LBT false:
+  // not tracked, where the tracking costs the searches more than the skips
+  // it buys later.)
+  constexpr bool LB = LBT && SEEDED && CARRIED && !CHUNKS && !LEARNED && !FIRST && !MRD;
+  const bool ok = explore<COUNT, CHUNKS, FIRST, MRD, TIES, LB>(q, start, A.nodes, A.nlabels, A.pts, A.labels,
                                                      A.leaf, n, st_node, st_dist, nvis, A.core2,
                                                      A.ties, COUNT ? A.seen : nullptr);
   if (!ok) atomicOr(A.status, kErrStack);
@@ -543,7 +563,10 @@ __device__ __forceinline__ void traverse_one(const TravArgs &A, int64_t i) {
     // weight, or r0 when nothing lies within it.
     const bool found = q.bj != kInvalid && q.best <= r0;
     if (!found) q.bj = kInvalid;
-    const float lb = found ? q.best : (r0 < kInf ? r0 : 0.0f);
+    float lb = found ? q.best : (r0 < kInf ? r0 : 0.0f);
+    // (LB, nothing found: q.best is that bound, above r0, or +inf when the
+    // search met no other component at all; r0 is kept then)
+    if (LB && !found && r0 < kInf && q.best < kInf) lb = q.best;
     A.res[i] = make_uint2(__float_as_uint(lb), q.bj);
   } else {
     A.res[i] = make_uint2(__float_as_uint(q.best), q.bj);
