@@ -450,6 +450,27 @@ int run_output(Problem &P, emst_edge *out, uint32_t w_bits) {
   // a run is long (exact ties: many identical points), then the full path
   const int Lloc = P.num_inst > 1 ? bits_for(P.largest > 1 ? P.largest - 1 : 1) : L;
   const bool fast = P.num_inst == 1 || P.inst_bits + wb + Lloc <= 64;
+  auto long_run_count = [&](uint32_t &c) {
+    return cudaMemcpyAsync(&c, P.counters + 10, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                           P.stream) == cudaSuccess &&
+           cudaStreamSynchronize(P.stream) == cudaSuccess;
+  };
+  // fastest path (one instance, no group of identical points): the same key
+  // sorted on w's bits only, stable, then every run of equal w (a handful of
+  // edges in general position) put in (i, j) order in place -- unless such
+  // a run is long (a lattice, many equal distances), then the next path
+  if (P.num_inst == 1 && !P.ties && wb > 0) {
+    launch_edge_keys_wi(P, m, L);
+    const int s = radix_sort_pairs(P, m, 0, (wb + 7) / 8, 0, L);
+    cudaMemsetAsync(P.counters + 10, 0, sizeof(uint32_t), P.stream);
+    launch_edge_ties_w(P, m, s, L);
+    uint32_t long_runs = 0;
+    if (!long_run_count(long_runs)) return EMST_ERR_CUDA;
+    if (long_runs == 0) {
+      launch_edge_from_keys(P, m, s, Lloc, wb, out);
+      return EMST_OK;
+    }
+  }
   if (fast) {
     int digits;
     if (P.num_inst == 1) {

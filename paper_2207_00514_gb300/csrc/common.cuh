@@ -339,7 +339,10 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 int64_t sort_tiles_for(int64_t n);
 // Stable LSD radix sort of (keys, vals) pairs on digits [digit_begin, digit_end)
 // (8-bit digits).  Returns the index (0/1) of the buffers holding the result.
-int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int src);
+// Stable sort of (keys[src], vals[src]) by the bits [bit0 + 8 digit_begin,
+// bit0 + 8 digit_end) of the keys (digit d of the key >> bit0 per pass);
+// returns the buffer index holding the result.
+int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int src, int bit0 = 0);
 // rounds.cu
 #ifndef EMST_TRAVERSE_MIN_BLOCKS
 #define EMST_TRAVERSE_MIN_BLOCKS 8      // resident 256-thread CTAs the traversal's registers must allow (32 registers: measured best)
@@ -370,6 +373,7 @@ void launch_count_seen(Problem &P);
 // output
 void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i);
 void launch_edge_ties(Problem &P, int64_t m, int src);
+void launch_edge_ties_w(Problem &P, int64_t m, int src, int shift_i);
 void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, int w_bits_used,
                            emst_edge *out);
 void launch_edge_keys_inst_wi(Problem &P, int64_t m, int shift_w, int shift_i);

@@ -746,6 +746,36 @@ __global__ void k_edge_ties(const uint64_t *__restrict__ keys, uint32_t *__restr
   }
 }
 
+// The same after a sort by w alone ((w << L) | i sorted on w's bits, stable,
+// so a run of equal w holds its edges in emission order): the first thread
+// of each run of equal w orders the run by (i, j) -- by (key, j), the key's
+// w bits being equal -- or counts it when it is longer than kTieRunMax.
+__global__ void k_edge_ties_w(uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, int64_t m,
+                              int shift_i, uint32_t *long_runs) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e + 1 >= m) return;
+  const uint64_t w = keys[e] >> shift_i;
+  if ((keys[e + 1] >> shift_i) != w || (e > 0 && (keys[e - 1] >> shift_i) == w)) return;
+  int64_t end = e + 2;
+  while (end < m && end - e <= kTieRunMax && (keys[end] >> shift_i) == w) ++end;
+  if (end - e > kTieRunMax) {
+    atomicAdd(long_runs, 1u);
+    return;
+  }
+  for (int64_t a = e + 1; a < end; ++a) {
+    const uint64_t k = keys[a];
+    const uint32_t v = vals[a];
+    int64_t b = a;
+    while (b > e && (keys[b - 1] > k || (keys[b - 1] == k && vals[b - 1] > v))) {
+      keys[b] = keys[b - 1];
+      vals[b] = vals[b - 1];
+      --b;
+    }
+    keys[b] = k;
+    vals[b] = v;
+  }
+}
+
 // Edge e of the output from its sorted key ((w << L) | i, with the instance
 // above w in the batched form) and j; w_mask keeps w's bits.
 __global__ void k_edge_from_keys(const uint64_t *__restrict__ keys,
@@ -863,6 +893,11 @@ void launch_edge_keys_wi(Problem &P, int64_t m, int shift_i) {
 void launch_edge_ties(Problem &P, int64_t m, int src) {
   k_edge_ties<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], m,
                                                             P.counters + 10);
+  P.launches += 1;
+}
+void launch_edge_ties_w(Problem &P, int64_t m, int src, int shift_i) {
+  k_edge_ties_w<<<grid_for(m, kBlock), kBlock, 0, P.stream>>>(P.keys[src], P.vals[src], m, shift_i,
+                                                              P.counters + 10);
   P.launches += 1;
 }
 void launch_edge_from_keys(Problem &P, int64_t m, int src, int shift_i, int w_bits_used,

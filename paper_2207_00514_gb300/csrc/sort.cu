@@ -24,14 +24,14 @@ int64_t sort_tiles_for(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 
 // Histograms of all digits in [digit_begin, digit_end) in one pass.
 __global__ void __launch_bounds__(512) k_sort_hist(const uint64_t *__restrict__ keys, int64_t n,
-                                                   int digit_begin, int digit_end,
+                                                   int digit_begin, int digit_end, int bit0,
                                                    uint32_t *__restrict__ hist) {
   __shared__ uint32_t sh[8][kRadix];
   for (int t = threadIdx.x; t < 8 * kRadix; t += blockDim.x) (&sh[0][0])[t] = 0;
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-    uint64_t key = __ldg(keys + k);
+    uint64_t key = __ldg(keys + k) >> bit0;
     for (int d = digit_begin; d < digit_end; ++d)
       atomicAdd(&sh[d][(uint32_t)(key >> (8 * d)) & 0xffu], 1u);
   }
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kSortThreads, EMST_SORT_MIN_BLOCKS) k_sort_pas
 
 static bool g_sort_attr_set[64] = {false};
 
-int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int src) {
+int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int src, int bit0) {
   if (n <= 1 || digit_begin >= digit_end) return src;
   cudaStream_t s = P.stream;
   int dev = 0;
@@ -231,14 +231,14 @@ int radix_sort_pairs(Problem &P, int64_t n, int digit_begin, int digit_end, int 
   cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t) * 8, s);
   int hgrid = (int)((n + 511) / 512);
   if (hgrid > sm_count() * 4) hgrid = sm_count() * 4;
-  k_sort_hist<<<hgrid, 512, 0, s>>>(P.keys[src], n, digit_begin, digit_end, hist);
+  k_sort_hist<<<hgrid, 512, 0, s>>>(P.keys[src], n, digit_begin, digit_end, bit0, hist);
   k_sort_scan<<<8, kRadix, 0, s>>>(hist);
   P.launches += 2;
   const int64_t tiles = sort_tiles_for(n);
   for (int d = digit_begin; d < digit_end; ++d) {
     cudaMemsetAsync(P.sort_lookback, 0, sizeof(uint32_t) * kRadix * tiles, s);
     k_sort_pass<<<(unsigned)tiles, kSortThreads, smem, s>>>(
-        P.keys[src], P.vals[src], P.keys[src ^ 1], P.vals[src ^ 1], n, 8 * d, hist + d * kRadix,
+        P.keys[src], P.vals[src], P.keys[src ^ 1], P.vals[src ^ 1], n, bit0 + 8 * d, hist + d * kRadix,
         P.sort_lookback, tile_ctr + d, P.counters + 1);
     P.launches += 1;
     src ^= 1;

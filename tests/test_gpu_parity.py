@@ -211,6 +211,35 @@ EMST_CASES = [
 ]
 
 
+def equal_weight_pairs(n=20_000, pairs=40, triples=3, seed=12):
+    """Uniform points plus `pairs` pairs (a, a + d) and `triples` triples
+    (p - d, p, p + d), d = 2^-14 along x, all in [0.5, 1)^3 where both
+    endpoints and their difference are exact in FP32: many MST edges of one
+    exactly equal weight d^2 between different points (one run of equal
+    weights the output must put in (i, j) order), far shorter than the
+    uniform points' spacing."""
+    g = np.random.default_rng(seed)
+    d = np.float32(2.0 ** -14)
+    base = synth.uniform(n, 3, seed)
+    a = (0.5 + 0.45 * g.random((pairs, 3))).astype(np.float32)
+    b = a.copy()
+    b[:, 0] += d
+    p = (0.5 + 0.45 * g.random((triples, 3))).astype(np.float32)
+    lo, hi = p.copy(), p.copy()
+    lo[:, 0] -= d
+    hi[:, 0] += d
+    pts = np.concatenate([base, a, b, lo, p, hi])
+    return np.ascontiguousarray(pts[g.permutation(len(pts))])
+
+
+EMST_CASES += [
+    ("equal_weight_run", equal_weight_pairs),
+    # equal weights by the million and no identical points: the output's
+    # sort by weight alone meets runs too long to fix in place and falls back
+    ("lattice_no_duplicates", lambda: synth.lattice_ties(n_sites=12_000, n_dup=0, side=30, seed=6)),
+]
+
+
 @pytest.mark.parametrize("name,make", EMST_CASES, ids=[c[0] for c in EMST_CASES])
 def test_emst_matches_oracle(pkg, name, make):
     pts = np.ascontiguousarray(make(), dtype=np.float32)
