@@ -266,8 +266,10 @@ struct Problem {
   uint2 *range = nullptr;            // nc-1: each internal node's leaf-chunk range [first, last]
                                      //      and split (the last chunk of its left child), packed
                                      //      by pack_range (one end of the range is the node itself)
-  uint32_t *runs = nullptr;          // n: label boundaries before each curve position within
-                                     //    its scan tile (plus the tile's entry of tile_prefix)
+  uint32_t *runs = nullptr;          // n: per 32 curve positions, the bitmap of their label
+                                     //    boundaries and the count of boundaries before them
+                                     //    within their scan tile (plus the tile's entry of
+                                     //    tile_prefix): 8 bytes, 256-B aligned
   uint32_t *scan_tiles = nullptr;    // 2 x scan tiles: boundary total of each tile, then the
                                      //    exclusive prefix of those totals
   uint32_t *labels = nullptr;        // n, current round (= labels_buf[cur])

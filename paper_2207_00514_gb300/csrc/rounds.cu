@@ -29,8 +29,11 @@ __device__ __forceinline__ float pair_weight(const float4 &p, const float4 &q,
 // result equals the bottom-up combination of the paper (equal child labels ->
 // that label, else invalid) without its atomics and climbing threads.
 //
-// runs[k] is kept in two parts, so no tile waits on another: the count
-// within k's tile of kScanTile positions (runs_local) plus the count of all
+// runs[k] is kept in three parts, so no tile waits on another and the node
+// pass reads a small array that stays in L2: per word w of 32 positions, a
+// bitmap of its boundaries (bit b: positions 32w + b and 32w + b + 1 differ)
+// beside the count of boundaries before it within its tile of kScanTile
+// positions (one 8-byte entry, carved from P.runs), and the count of all
 // earlier tiles (tile_prefix, an exclusive scan of the tile totals done by
 // the last tile to finish).
 // ---------------------------------------------------------------------------
@@ -42,9 +45,11 @@ static_assert(kScanTile == kScanThreads * kScanItems, "scan tile shape");
 
 int64_t scan_tiles_for(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
-__device__ __forceinline__ uint32_t runs_at(const uint32_t *__restrict__ runs_local,
+__device__ __forceinline__ uint32_t runs_at(const uint2 *__restrict__ words,
                                             const uint32_t *__restrict__ tile_prefix, int64_t k) {
-  return __ldg(runs_local + k) + __ldg(tile_prefix + (k >> kScanTileShift));
+  const uint2 wd = __ldg(words + (k >> 5));  // (bitmap, boundaries before it in the tile)
+  const uint32_t below = wd.x & ((1u << (k & 31)) - 1u);
+  return __ldg(tile_prefix + (k >> kScanTileShift)) + wd.y + (uint32_t)__popc(below);
 }
 
 // Exclusive scan of count values by one CTA of kScanThreads threads, each
@@ -89,10 +94,11 @@ __device__ void block_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t 
   }
 }
 
-// The local boundary counts (runs_local) and tile totals, one tile of
-// kScanTile positions per CTA.  Warp-striped: warp w of the tile owns
-// kScanItems rows of 32 consecutive positions, so every load and store is one
-// coalesced 128-byte row, and the row's flags rank by one ballot.  RELABEL:
+// The boundary bitmap with its per-word counts, and the tile totals,
+// one tile of kScanTile positions per CTA.  Warp-striped: warp w of the tile
+// owns kScanItems rows of 32 consecutive positions, so every load and store
+// is one coalesced 128-byte row, and a row's boundaries are one ballot: its
+// word of the bitmap.  RELABEL:
 // the labels are first mapped through root (the merge's new labels, written
 // to labels_new), and every boundary between two curve neighbours of one
 // instance lowers both components' bounds for the next round (A6) -- one
@@ -103,8 +109,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_runs(
     const float4 *__restrict__ pts, const uint32_t *__restrict__ inst_of,
     const float *__restrict__ core2, int64_t n,
     uint32_t *__restrict__ labels_new, uint32_t *__restrict__ bound_next,
-    uint32_t *__restrict__ runs_local, uint32_t *tile_total, uint32_t *tile_prefix,
-    uint32_t *done) {
+    uint2 *__restrict__ words, uint32_t *tile_total, uint32_t *tile_prefix, uint32_t *done) {
   __shared__ uint32_t s_warp[kScanThreads / 32];
   __shared__ uint32_t s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -162,15 +167,15 @@ __global__ void __launch_bounds__(kScanThreads, 6) k_runs(
     run += w < warp ? v : 0u;
     total += v;
   }
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t *out = runs_local + seg;
+  // lane q writes row q's word and the tile's boundaries before it
+  uint32_t my_bits = 0, my_prefix = 0;
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
-    const int k = q * 32 + lane;
     const uint32_t b = __ballot_sync(0xffffffffu, (flags >> q) & 1u);
-    if (k < rem) out[k] = run + __popc(b & lt);
+    if (lane == q) { my_bits = b; my_prefix = run; }
     run += __popc(b);
   }
+  if (lane < kScanItems && lane * 32 < rem) words[(seg >> 5) + lane] = make_uint2(my_bits, my_prefix);
   // the last tile to finish scans the tile totals
   if (tid == 0) {
     tile_total[tile] = total;
@@ -188,14 +193,15 @@ static void launch_runs(Problem &P, bool relabel) {
   const int64_t tiles = scan_tiles_for(P.n);
   uint32_t *done = P.counters + 24;
   uint32_t *tile_total = P.scan_tiles, *tile_prefix = P.scan_tiles + tiles;
+  uint2 *words = reinterpret_cast<uint2 *>(P.runs);
   cudaMemsetAsync(done, 0, sizeof(uint32_t), P.stream);
   if (relabel)
     k_runs<true><<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(
         P.labels, P.root, P.pts, P.inst_of, P.core2, P.n, P.labels_buf[P.cur ^ 1],
-        P.bound_buf[P.cur ^ 1], P.runs, tile_total, tile_prefix, done);
+        P.bound_buf[P.cur ^ 1], words, tile_total, tile_prefix, done);
   else
     k_runs<false><<<(unsigned)tiles, kScanThreads, 0, P.stream>>>(
-        P.labels, nullptr, P.pts, P.inst_of, nullptr, P.n, nullptr, nullptr, P.runs, tile_total,
+        P.labels, nullptr, P.pts, P.inst_of, nullptr, P.n, nullptr, nullptr, words, tile_total,
         tile_prefix, done);
   P.launches += 1;
 }
@@ -203,7 +209,7 @@ static void launch_runs(Problem &P, bool relabel) {
 void launch_label_runs(Problem &P) { launch_runs(P, false); }
 
 __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restrict__ labels,
-                                                        const uint32_t *__restrict__ runs_local,
+                                                        const uint2 *__restrict__ words,
                                                         const uint32_t *__restrict__ tile_prefix,
                                                         const uint2 *__restrict__ range,
                                                         int64_t n, int64_t nc, int leaf,
@@ -218,15 +224,16 @@ __global__ void __launch_bounds__(kBlock) k_node_labels(const uint32_t *__restri
   const int64_t b1 = ((int64_t)r.last + 1) * leaf < n ? ((int64_t)r.last + 1) * leaf - 1 : n - 1;
   const uint32_t l0 = __ldg(labels + a0), l1 = __ldg(labels + a1);
   const uint32_t lab0 =
-      runs_at(runs_local, tile_prefix, b0) == runs_at(runs_local, tile_prefix, a0) ? l0 : kInvalid;
+      runs_at(words, tile_prefix, b0) == runs_at(words, tile_prefix, a0) ? l0 : kInvalid;
   const uint32_t lab1 =
-      runs_at(runs_local, tile_prefix, b1) == runs_at(runs_local, tile_prefix, a1) ? l1 : kInvalid;
+      runs_at(words, tile_prefix, b1) == runs_at(words, tile_prefix, a1) ? l1 : kInvalid;
   nlabels[i] = make_uint2(lab0, lab1);
 }
 
 void launch_node_labels(Problem &P) {
   k_node_labels<<<grid_for(P.nc - 1, kBlock), kBlock, 0, P.stream>>>(
-      P.labels, P.runs, P.scan_tiles + scan_tiles_for(P.n), P.range, P.n, P.nc, P.leaf, P.nlabels);
+      P.labels, reinterpret_cast<const uint2 *>(P.runs), P.scan_tiles + scan_tiles_for(P.n), P.range,
+      P.n, P.nc, P.leaf, P.nlabels);
   P.launches += 1;
 }
 
