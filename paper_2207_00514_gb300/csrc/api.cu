@@ -139,8 +139,7 @@ size_t layout(Problem &P, char *base, bool copy_points, bool copy_edges) {
   P.vals[1] = c.take<uint32_t>(n);
   P.nodes = c.take<NodeRec>(nc - 1);
   P.nlabels = c.take<uint2>(nc - 1);
-  P.parent_leaf = c.take<uint32_t>(nc);
-  P.up_delta = c.take<uint2>(nc - 1);
+  P.split_far = c.take<uint2>(nc - 1);
   P.arrivals = c.take<uint32_t>(nc - 1);
   P.range = c.take<uint2>(nc - 1);
   P.runs = c.take<uint32_t>(n);
@@ -276,8 +275,7 @@ void run_build(Problem &P) {
   }
   if (P.n >= 2) {
     cudaMemsetAsync(P.arrivals, 0, sizeof(uint32_t) * (size_t)(P.nc - 1), P.stream);
-    launch_hierarchy(P);
-    launch_refit(P);
+    launch_build_tree(P);
     if (P.num_inst > 1) launch_instance_roots(P);
   }
 }

@@ -397,19 +397,46 @@ void launch_gather(Problem &P, const uint32_t *perm) {
 }
 
 // ---------------------------------------------------------------------------
-// A4 (b). Hierarchy: Karras's fully parallel binary radix tree.  Its leaves are
-// chunks of `leaf` consecutive sorted points (leaf = 1: one point per leaf);
-// chunk c's key is the code of its first point, augmented by c so equal codes
-// still split.  Internal node i covers a chunk range with one end at i; its
-// split gamma gives the children gamma (left) and gamma+1 (right), leaves when
-// the range ends there.  This is the numbering drawn in Fig. 4.
+// A4 (b, c). Hierarchy and boxes in one bottom-up pass.
+// The hierarchy is Karras's binary radix tree over the leaf chunks (chunks of
+// `leaf` consecutive sorted points; leaf = 1: one point per leaf; chunk c's
+// key is the code of its first point, augmented by c so equal codes still
+// split), numbered as in Fig. 4: internal node i covers a chunk range with
+// one end at i, and its split gamma gives the children gamma (left) and
+// gamma + 1 (right), leaves when the range ends there.
+// Here it is found from the leaves up (the agglomerative form of the same
+// tree): with delta(i) the leading bits shared by the keys of chunks i and
+// i + 1, a node covering chunks [l, r] hangs under the split r (it is the
+// left child) when delta(r) > delta(l - 1), else under the split l - 1 (the
+// right child).  So a left child's index is its right end and a right
+// child's its left end: a node knows its own index once it knows which side
+// it hangs on.  At every split the first child to arrive stops and the
+// second builds the parent: its range from both children's far ends, its
+// box as the union of theirs, its record (both child boxes, the child
+// references, their smallest original ids), range and round-0 child labels,
+// written once at the parent's index; then it carries on upwards.
+// k_build_local: one thread per leaf chunk climbs the splits between two of
+// its CTA's chunks, with the CTA's shared keys' delta values, boxes and
+// arrival counts in shared memory (block-scope acquire-release adds).  A
+// split at the CTA's edge ends the climb in global memory: the thread leaves
+// its far end in split_far, adds a device-scope acquire-release arrival, and
+// the second arriver lists the split.  A split inside the CTA that only one
+// child reached (the other spans CTAs) passes that child's far end to global
+// memory at the end.
+// k_build_up: one thread per listed split builds it and climbs on in global
+// memory; a child's box comes from its record (the union of the record's two
+// child boxes) or from its points (a leaf).
+// Each split gets exactly two arrivals; the counters start at zero.
+// The child labels are the round-0 ones (a one-point chunk k: label k;
+// otherwise several components, kInvalid); a caller with other labels
+// rewrites them (A5).
 // ---------------------------------------------------------------------------
 // kh != nullptr: 128-bit codes, kh their high words (the augmented key is
 // then (high, low, position), 160 bits)
 __device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k,
                                             const uint64_t *__restrict__ kh, int64_t nc, int leaf,
                                             int64_t i, int64_t j) {
-  if (j < 0 || j >= nc) return -1;
+  if (j < 0 || j >= nc || i < 0 || i >= nc) return -1;
   int base = 0;
   if (kh) {
     const uint64_t a = __ldg(kh + i * leaf), b = __ldg(kh + j * leaf);
@@ -421,102 +448,97 @@ __device__ __forceinline__ int prefix_delta(const uint64_t *__restrict__ k,
   return base + 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
 }
 
-__global__ void __launch_bounds__(kBlock) k_hierarchy(const uint64_t *__restrict__ keys,
-                                                      const uint64_t *__restrict__ keys_hi,
-                                                      int64_t nc, int leaf,
-                                                      uint32_t *__restrict__ parent_leaf,
-                                                      uint2 *__restrict__ up_delta,
-                                                      uint2 *__restrict__ range) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nc - 1) return;
-  int d = (prefix_delta(keys, keys_hi, nc, leaf, i, i + 1) - prefix_delta(keys, keys_hi, nc, leaf, i, i - 1)) > 0 ? 1 : -1;
-  int dmin = prefix_delta(keys, keys_hi, nc, leaf, i, i - d);
-  int64_t lmax = 2;
-  while (prefix_delta(keys, keys_hi, nc, leaf, i, i + lmax * d) > dmin) lmax <<= 1;
-  int64_t l = 0;
-  for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-    if (prefix_delta(keys, keys_hi, nc, leaf, i, i + (l + t) * d) > dmin) l += t;
-  int64_t j = i + l * d;
-  int dnode = prefix_delta(keys, keys_hi, nc, leaf, i, j);
-  int64_t s = 0, t = l;
-  do {
-    t = (t + 1) >> 1;
-    if (prefix_delta(keys, keys_hi, nc, leaf, i, i + (s + t) * d) > dnode) s += t;
-  } while (t > 1);
-  int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
-  int64_t lo = i < j ? i : j, hi = i < j ? j : i;
-  uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
-  uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
-  range[i] = pack_range((uint32_t)i, (uint32_t)lo, (uint32_t)gamma, (uint32_t)hi);
-  reinterpret_cast<uint32_t *>(up_delta + i)[1] = (uint32_t)dnode;
-  uint32_t up = (uint32_t)i << 1;
-  if (left & kLeafBit) parent_leaf[left & ~kLeafBit] = up;
-  else reinterpret_cast<uint32_t *>(up_delta + left)[0] = up;
-  if (right & kLeafBit) parent_leaf[right & ~kLeafBit] = up | 1u;
-  else reinterpret_cast<uint32_t *>(up_delta + right)[0] = up | 1u;
-  if (i == 0) reinterpret_cast<uint32_t *>(up_delta)[0] = kInvalid;
-}
-
-void launch_hierarchy(Problem &P) {
-  k_hierarchy<<<grid_for(P.nc - 1, kBlock), kBlock, 0, P.stream>>>(
-      P.keys[0] /*sorted*/, P.code_hi, P.nc, P.leaf, P.parent_leaf, P.up_delta, P.range);
-  P.launches += 1;
-}
-
-// ---------------------------------------------------------------------------
-// A4 (c). Refit: bottom-up boxes, in two launches.
-// k_refit: one thread per leaf chunk computes the box of its points and
-// climbs the nodes whose leaf range lies inside its CTA's chunks: both
-// arrivals at such a node come from this CTA, so both child boxes meet in
-// shared memory and the arrivals are counted there with block-scope
-// acquire-release adds; at every node the first arriver stops, the second
-// merges the two child boxes, writes the node's whole record once (both
-// boxes and the child references from the node's range) and its child
-// labels, and carries the union one level up.  The first node spanning
-// CTAs ends the climb: the thread leaves its box in its slot of that node's
-// global record and adds a device-scope acquire-release arrival; the second
-// arriver lists the node for the next launch.
-// k_refit_up: one thread per listed node (both child boxes in its record)
-// writes it and climbs on in global memory, first arriver stopping, as
-// above.  (In one launch the threads that climb above their CTA's nodes --
-// one or two per CTA, up to the root's depth -- would hold their CTA's
-// slot while its other threads are long done.)
-// The global counters are never reset: each pass adds exactly two arrivals
-// per node, so the parity of the count before the add tells first from
-// second.
-// Each record also carries the smallest original id of each child's points
-// (the traversal's tie pruning).
-// The child labels are the round-0 ones (a one-point chunk k: label k;
-// otherwise several components, kInvalid); a caller with other labels
-// rewrites them (A5).
-// ---------------------------------------------------------------------------
 #ifndef EMST_REFIT_BLOCK
 #define EMST_REFIT_BLOCK 128
 #endif
-constexpr int kRefitBlock = EMST_REFIT_BLOCK;  // leaf chunks per refit CTA
+constexpr int kRefitBlock = EMST_REFIT_BLOCK;  // leaf chunks per k_build_local CTA
 constexpr int kRefitUpBlock = 128;
-constexpr uint32_t kRefitReadyCounter = 48;  // P.counters slot: nodes listed by k_refit
+constexpr uint32_t kRefitReadyCounter = 48;  // P.counters slot: splits listed by k_build_local
 
-__device__ __forceinline__ void store_slot_box(NodeRec *rec, int slot, const float *bx) {
-  float2 *f = reinterpret_cast<float2 *>(rec) + 3 * slot;
-  f[0] = make_float2(bx[0], bx[1]);
-  f[1] = make_float2(bx[2], bx[3]);
-  f[2] = make_float2(bx[4], bx[5]);
+// The split a node [l, r] hangs under and its side (0: left child, the split
+// is r; 1: right child, the split is l - 1), from delta(l - 1) and delta(r);
+// false for the root.
+__device__ __forceinline__ bool parent_split(int64_t l, int64_t r, int64_t nc, int dl, int dr,
+                                             uint32_t &ps, int &side) {
+  if (l == 0 && r == nc - 1) return false;
+  const bool left = l == 0 || (r != nc - 1 && dr > dl);
+  ps = (uint32_t)(left ? r : l - 1);
+  side = left ? 0 : 1;
+  return true;
 }
 
-__device__ __forceinline__ void load_slot_box(const NodeRec *rec, int slot, float *bx) {
-  const float2 *f = reinterpret_cast<const float2 *>(rec) + 3 * slot;
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    const float2 v = __ldcg(f + t);
-    bx[2 * t] = v.x;
-    bx[2 * t + 1] = v.y;
+// The index of node [l, r] (Fig. 4 numbering): 0 for the root, else the end
+// of its range away from the split it hangs under.
+__device__ __forceinline__ uint32_t node_index(int64_t l, int64_t r, bool root, int side) {
+  return root ? 0u : (uint32_t)(side == 0 ? r : l);
+}
+
+__device__ __forceinline__ void chunk_box(const float4 *__restrict__ pts, int64_t n, int leaf,
+                                          int64_t c, float *box, uint32_t &idmin) {
+  const int64_t p0 = c * leaf, p1 = p0 + leaf < n ? p0 + leaf : n;
+  float4 p = __ldg(pts + p0);
+  box[0] = box[3] = p.x;
+  box[1] = box[4] = p.y;
+  box[2] = box[5] = p.z;
+  idmin = __float_as_uint(p.w);
+  for (int64_t m = p0 + 1; m < p1; ++m) {
+    p = __ldg(pts + m);
+    box[0] = fminf(box[0], p.x); box[1] = fminf(box[1], p.y); box[2] = fminf(box[2], p.z);
+    box[3] = fmaxf(box[3], p.x); box[4] = fmaxf(box[4], p.y); box[5] = fmaxf(box[5], p.z);
+    idmin = min(idmin, __float_as_uint(p.w));
   }
 }
 
-// Arrival counters of the refit with acquire-release order: the first
-// arriver's box stores are released by its add, and the second arriver's add
-// acquires them, so no separate fences are needed around the add.
+// A finished child's box and smallest original id: a leaf chunk's from its
+// points, an internal node's from its record (written before its arrival was
+// released, so read through L2).
+__device__ __forceinline__ void child_box(const float4 *__restrict__ pts, int64_t n, int leaf,
+                                          const NodeRec *nodes, uint32_t idx, bool is_leaf,
+                                          float *box, uint32_t &idmin) {
+  if (is_leaf) {
+    chunk_box(pts, n, leaf, idx, box, idmin);
+    return;
+  }
+  const float4 *f = reinterpret_cast<const float4 *>(nodes + idx);
+  const float4 a = __ldcg(f), b = __ldcg(f + 1), c = __ldcg(f + 2);
+  const uint4 d = __ldcg(reinterpret_cast<const uint4 *>(f + 3));
+  box[0] = fminf(a.x, b.z); box[1] = fminf(a.y, b.w); box[2] = fminf(a.z, c.x);
+  box[3] = fmaxf(a.w, c.y); box[4] = fmaxf(b.x, c.z); box[5] = fmaxf(b.y, c.w);
+  idmin = min(d.z, d.w);
+}
+
+// Node `idx` covering chunks [L, R] with split g and child boxes Lb, Rb (and
+// their smallest original ids): its whole record, range and round-0 child
+// labels; returns the union in `box` / `idmin` (which may alias Lb or Rb).
+__device__ __forceinline__ void write_node(NodeRec *nodes, uint2 *__restrict__ nlabels,
+                                           uint2 *__restrict__ range, uint32_t idx, uint32_t L,
+                                           uint32_t g, uint32_t R, const float *Lb, const float *Rb,
+                                           uint32_t minL, uint32_t minR, int64_t n, int leaf,
+                                           float *box, uint32_t &idmin) {
+  const bool lleaf = L == g, rleaf = R == g + 1u;
+  // a chunk of exactly one point is its own component in round 0
+  auto one_point = [&](int64_t c) { return n - c * leaf == 1 || leaf == 1; };
+  NodeRec rec;
+  rec.a = make_float4(Lb[0], Lb[1], Lb[2], Lb[3]);
+  rec.b = make_float4(Lb[4], Lb[5], Rb[0], Rb[1]);
+  rec.c = make_float4(Rb[2], Rb[3], Rb[4], Rb[5]);
+  rec.d = make_uint4(lleaf ? (kLeafBit | g) : g, rleaf ? (kLeafBit | (g + 1u)) : g + 1u, minL, minR);
+  nodes[idx] = rec;
+  range[idx] = pack_range(idx, L, g, R);
+  nlabels[idx] = make_uint2(lleaf && one_point(g) ? (uint32_t)((int64_t)g * leaf) : kInvalid,
+                            rleaf && one_point(g + 1) ? (uint32_t)((int64_t)(g + 1) * leaf) : kInvalid);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const float lo = fminf(Lb[t], Rb[t]), hi = fmaxf(Lb[3 + t], Rb[3 + t]);
+    box[t] = lo;
+    box[3 + t] = hi;
+  }
+  idmin = min(minL, minR);
+}
+
+// Arrival counters with acquire-release order: the first arriver's stores
+// (its box and far end) are released by its add, and the second arriver's
+// add acquires them, so no separate fences are needed around the add.
 __device__ __forceinline__ uint32_t add_acq_rel_gpu(uint32_t *p, uint32_t v) {
   uint32_t old;
   asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -529,148 +551,159 @@ __device__ __forceinline__ uint32_t add_acq_rel_cta_shared(uint32_t *p, uint32_t
   return old;
 }
 
-// Node `node` with range r and both child boxes L, R (and their smallest
-// original ids): its whole record (boxes, references -- leaves where the
-// range ends at the split -- and the round-0 child labels); returns the
-// union in `box` / `idmin`.
-__device__ __forceinline__ void write_node(NodeRec *nodes, uint2 *__restrict__ nlabels, uint32_t node,
-                                           const NodeRange &r, const float *L, const float *R,
-                                           uint32_t minL, uint32_t minR, int64_t n, int leaf,
-                                           float *box, uint32_t &idmin) {
-  const uint32_t g = r.split;
-  const bool lleaf = r.first == g, rleaf = r.last == g + 1u;
-  // a chunk of exactly one point is its own component in round 0
-  auto one_point = [&](int64_t c) { return n - c * leaf == 1 || leaf == 1; };
-  NodeRec rec;
-  rec.a = make_float4(L[0], L[1], L[2], L[3]);
-  rec.b = make_float4(L[4], L[5], R[0], R[1]);
-  rec.c = make_float4(R[2], R[3], R[4], R[5]);
-  rec.d = make_uint4(lleaf ? (kLeafBit | g) : g, rleaf ? (kLeafBit | (g + 1u)) : g + 1u, minL, minR);
-  nodes[node] = rec;
-  nlabels[node] = make_uint2(lleaf && one_point(g) ? (uint32_t)((int64_t)g * leaf) : kInvalid,
-                             rleaf && one_point(g + 1) ? (uint32_t)((int64_t)(g + 1) * leaf) : kInvalid);
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    box[t] = fminf(L[t], R[t]);
-    box[3 + t] = fmaxf(L[3 + t], R[3 + t]);
-  }
-  idmin = min(minL, minR);
-}
-
-__global__ void __launch_bounds__(kRefitBlock) k_refit(const float4 *__restrict__ pts, int64_t n,
-                                                  int64_t nc, int leaf, NodeRec *nodes,
-                                                  uint2 *__restrict__ nlabels,
-                                                  const uint32_t *__restrict__ parent_leaf,
-                                                  const uint2 *__restrict__ up_delta,
-                                                  const uint2 *__restrict__ range,
-                                                  uint32_t *arrivals, uint32_t *__restrict__ ready,
-                                                  uint32_t *ready_count, uint32_t capacity,
-                                                  uint32_t *status) {
-  __shared__ float s_box[kRefitBlock][2][6];  // both child boxes of each local node
-  __shared__ uint32_t s_min[kRefitBlock][2];  // and their smallest original ids
+__global__ void __launch_bounds__(kRefitBlock) k_build_local(
+    const uint64_t *__restrict__ keys, const uint64_t *__restrict__ keys_hi,
+    const float4 *__restrict__ pts, int64_t n, int64_t nc, int leaf, NodeRec *nodes,
+    uint2 *__restrict__ nlabels, uint2 *__restrict__ range, uint2 *split_far, uint32_t *arrivals,
+    uint32_t *__restrict__ ready, uint32_t *ready_count, uint32_t capacity, uint32_t *status) {
+  __shared__ int s_delta[kRefitBlock + 1];     // delta(first - 1 + t)
+  __shared__ float s_box[kRefitBlock][2][6];   // both child boxes of each split inside the CTA
+  __shared__ uint32_t s_min[kRefitBlock][2];   // their smallest original ids
+  __shared__ uint32_t s_far[kRefitBlock][2];   // their far ends (kInvalid: not arrived)
   __shared__ uint32_t s_arrive[kRefitBlock];
   const int64_t first = (int64_t)blockIdx.x * kRefitBlock;
-  const int64_t last = first + kRefitBlock - 1;
+  const int64_t last = first + kRefitBlock - 1 < nc - 1 ? first + kRefitBlock - 1 : nc - 1;
+  for (int t = threadIdx.x; t <= kRefitBlock; t += blockDim.x)
+    s_delta[t] = prefix_delta(keys, keys_hi, nc, leaf, first - 1 + t, first + t);
   s_arrive[threadIdx.x] = 0u;
+  s_far[threadIdx.x][0] = s_far[threadIdx.x][1] = kInvalid;
   __syncthreads();
   const int64_t k = first + threadIdx.x;  // this thread's chunk
-  if (k >= nc) return;
-  const int64_t p0 = k * leaf, p1 = p0 + leaf < n ? p0 + leaf : n;
-  float4 p = pts[p0];
-  float box[6] = {p.x, p.y, p.z, p.x, p.y, p.z};
-  uint32_t idmin = __float_as_uint(p.w);
-  for (int64_t m = p0 + 1; m < p1; ++m) {
-    p = pts[m];
-    box[0] = fminf(box[0], p.x); box[1] = fminf(box[1], p.y); box[2] = fminf(box[2], p.z);
-    box[3] = fmaxf(box[3], p.x); box[4] = fmaxf(box[4], p.y); box[5] = fmaxf(box[5], p.z);
-    idmin = min(idmin, __float_as_uint(p.w));
-  }
-  uint32_t up = parent_leaf[k];
-  while (true) {
-    const uint32_t node = up >> 1;
-    const int slot = (int)(up & 1u);
-    // both depend on the node only: one round trip per level
-    const NodeRange r = unpack_range(node, __ldg(range + node));
-    const uint32_t up_next = __ldg(&up_delta[node].x);
-    if ((int64_t)r.first < first || (int64_t)r.last > last) {
-      // spans CTAs: leave the box for the sibling or for k_refit_up
-      store_slot_box(&nodes[node], slot, box);
-      reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = idmin;
-      const uint32_t before = add_acq_rel_gpu(&arrivals[node], 1u);
-      if ((before & 1u) != 0u) {
-        const uint32_t at = atomicAdd(ready_count, 1u);
-        if (at < capacity) ready[at] = node;
-        else atomicOr(status, kErrChain);  // cannot happen (see launch_refit)
+  if (k <= last) {
+    float box[6];
+    uint32_t idmin;
+    chunk_box(pts, n, leaf, k, box, idmin);
+    int64_t l = k, r = k;
+    uint32_t ps;
+    int side;
+    bool up = parent_split(l, r, nc, s_delta[l - first], s_delta[r - first + 1], ps, side);
+    while (up) {
+      const uint32_t far = side == 0 ? (uint32_t)l : (uint32_t)r;
+      if ((int64_t)ps < first || (int64_t)ps >= last) {
+        // a split at the CTA's edge: its other child lies (partly) in another CTA
+        reinterpret_cast<uint32_t *>(split_far + ps)[side] = far;
+        if ((add_acq_rel_gpu(arrivals + ps, 1u) & 1u) != 0u) {  // second: list it
+          const uint32_t at = atomicAdd(ready_count, 1u);
+          if (at < capacity) ready[at] = ps;
+          else atomicOr(status, kErrChain);  // cannot happen (see launch_build_tree)
+        }
+        break;
       }
-      return;
+      const int j = (int)(ps - first);
+#pragma unroll
+      for (int t = 0; t < 6; ++t) s_box[j][side][t] = box[t];
+      s_min[j][side] = idmin;
+      s_far[j][side] = far;
+      if (add_acq_rel_cta_shared(&s_arrive[j], 1u) == 0u) break;  // first: the sibling carries on
+      float sib[6];
+#pragma unroll
+      for (int t = 0; t < 6; ++t) sib[t] = s_box[j][side ^ 1][t];
+      const uint32_t sibmin = s_min[j][side ^ 1], sibfar = s_far[j][side ^ 1];
+      if (side == 0 ? (sibfar <= ps || (int64_t)sibfar > last) : ((int64_t)sibfar < first || sibfar > ps)) {
+        atomicOr(status, kErrChain);  // cannot happen: the sibling lies in this CTA
+        break;
+      }
+      // the parent covers [L, R] with split ps; which side it hangs on gives its index
+      const int64_t L = side == 0 ? l : (int64_t)sibfar, R = side == 0 ? (int64_t)sibfar : r;
+      uint32_t ps2;
+      int side2;
+      up = parent_split(L, R, nc, s_delta[L - first], s_delta[R - first + 1], ps2, side2);
+      const uint32_t idx = node_index(L, R, !up, side2);
+      if (side == 0)
+        write_node(nodes, nlabels, range, idx, (uint32_t)L, ps, (uint32_t)R, box, sib, idmin, sibmin, n,
+                   leaf, box, idmin);
+      else
+        write_node(nodes, nlabels, range, idx, (uint32_t)L, ps, (uint32_t)R, sib, box, sibmin, idmin, n,
+                   leaf, box, idmin);
+      l = L;
+      r = R;
+      ps = ps2;
+      side = side2;
     }
-#pragma unroll
-    for (int t = 0; t < 6; ++t) s_box[node - first][slot][t] = box[t];
-    s_min[node - first][slot] = idmin;
-    if (add_acq_rel_cta_shared(&s_arrive[node - first], 1u) == 0u) return;  // first: the sibling carries on
-    float sib[6];
-#pragma unroll
-    for (int t = 0; t < 6; ++t) sib[t] = s_box[node - first][slot ^ 1][t];
-    const uint32_t sibmin = s_min[node - first][slot ^ 1];
-    if (slot == 0) write_node(nodes, nlabels, node, r, box, sib, idmin, sibmin, n, leaf, box, idmin);
-    else write_node(nodes, nlabels, node, r, sib, box, sibmin, idmin, n, leaf, box, idmin);
-    if (node == 0) return;
-    up = up_next;
+  }
+  __syncthreads();
+  // a split inside the CTA that one child reached: the other spans CTAs and
+  // arrives in k_build_up, which finds this one's far end in split_far
+  const int64_t s = first + threadIdx.x;
+  if (s < last && s_arrive[threadIdx.x] == 1u) {
+    const int side = s_far[threadIdx.x][0] != kInvalid ? 0 : 1;
+    reinterpret_cast<uint32_t *>(split_far + s)[side] = s_far[threadIdx.x][side];
+    arrivals[s] = 1u;
   }
 }
 
-__global__ void __launch_bounds__(kRefitUpBlock) k_refit_up(int64_t n, int leaf, NodeRec *nodes,
-                                                       uint2 *__restrict__ nlabels,
-                                                       const uint2 *__restrict__ up_delta,
-                                                       const uint2 *__restrict__ range,
-                                                       uint32_t *arrivals,
-                                                       const uint32_t *__restrict__ ready,
-                                                       const uint32_t *ready_count, uint32_t capacity) {
+__global__ void __launch_bounds__(kRefitUpBlock) k_build_up(
+    const uint64_t *__restrict__ keys, const uint64_t *__restrict__ keys_hi,
+    const float4 *__restrict__ pts, int64_t n, int64_t nc, int leaf, NodeRec *nodes,
+    uint2 *__restrict__ nlabels, uint2 *__restrict__ range, uint2 *split_far, uint32_t *arrivals,
+    const uint32_t *__restrict__ ready, const uint32_t *ready_count, uint32_t capacity,
+    uint32_t *status) {
   const uint32_t count = min(*ready_count, capacity);
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
-    uint32_t node = __ldg(ready + t);
+    // a split both of whose children k_build_local finished
+    uint32_t ps = __ldg(ready + t);
+    const uint2 fe = __ldcg(split_far + ps);
+    if (fe.x > ps || fe.y <= ps || (int64_t)fe.y >= nc) {  // cannot happen: both children arrived
+      atomicOr(status, kErrChain);
+      continue;
+    }
     float box[6], sib[6];
     uint32_t idmin, sibmin;
-    // both children arrived in k_refit: both boxes are in the record
-    load_slot_box(&nodes[node], 0, box);
-    load_slot_box(&nodes[node], 1, sib);
-    idmin = __ldcg(reinterpret_cast<const uint32_t *>(&nodes[node].d) + 2);
-    sibmin = __ldcg(reinterpret_cast<const uint32_t *>(&nodes[node].d) + 3);
-    int slot = 0;
+    child_box(pts, n, leaf, nodes, ps, fe.x == ps, box, idmin);
+    child_box(pts, n, leaf, nodes, ps + 1u, fe.y == ps + 1u, sib, sibmin);
+    int64_t L = fe.x, R = fe.y;
+    int side = 0;  // the child whose box is in `box`
     while (true) {
-      const NodeRange r = unpack_range(node, __ldg(range + node));
-      if (slot == 0) write_node(nodes, nlabels, node, r, box, sib, idmin, sibmin, n, leaf, box, idmin);
-      else write_node(nodes, nlabels, node, r, sib, box, sibmin, idmin, n, leaf, box, idmin);
-      if (node == 0) break;
-      const uint32_t up = __ldg(&up_delta[node].x);
-      node = up >> 1;
-      slot = (int)(up & 1u);
-      store_slot_box(&nodes[node], slot, box);
-      reinterpret_cast<uint32_t *>(&nodes[node].d)[2 + slot] = idmin;
-      const uint32_t before = add_acq_rel_gpu(&arrivals[node], 1u);
-      if ((before & 1u) == 0u) break;  // first: the sibling carries on
-      load_slot_box(&nodes[node], slot ^ 1, sib);
-      sibmin = __ldcg(reinterpret_cast<const uint32_t *>(&nodes[node].d) + 2 + (slot ^ 1));
+      uint32_t ps2;
+      int side2;
+      const bool up = parent_split(L, R, nc, prefix_delta(keys, keys_hi, nc, leaf, L - 1, L),
+                                   prefix_delta(keys, keys_hi, nc, leaf, R, R + 1), ps2, side2);
+      const uint32_t idx = node_index(L, R, !up, side2);
+      if (side == 0)
+        write_node(nodes, nlabels, range, idx, (uint32_t)L, ps, (uint32_t)R, box, sib, idmin, sibmin, n,
+                   leaf, box, idmin);
+      else
+        write_node(nodes, nlabels, range, idx, (uint32_t)L, ps, (uint32_t)R, sib, box, sibmin, idmin, n,
+                   leaf, box, idmin);
+      if (!up) break;
+      // arrive at the parent's split; the record just written is released with the add
+      ps = ps2;
+      side = side2;
+      const uint32_t far = side == 0 ? (uint32_t)L : (uint32_t)R;
+      reinterpret_cast<uint32_t *>(split_far + ps)[side] = far;
+      if ((add_acq_rel_gpu(arrivals + ps, 1u) & 1u) == 0u) break;  // first: the sibling carries on
+      const uint32_t sibfar = __ldcg(reinterpret_cast<const uint32_t *>(split_far + ps) + (side ^ 1));
+      if (side == 0 ? (sibfar <= ps || (int64_t)sibfar >= nc) : sibfar > ps) {  // cannot happen
+        atomicOr(status, kErrChain);
+        break;
+      }
+      const uint32_t sidx = side == 0 ? ps + 1u : ps;  // the sibling's index or leaf chunk
+      const bool sleaf = side == 0 ? sibfar == ps + 1u : sibfar == ps;
+      child_box(pts, n, leaf, nodes, sidx, sleaf, sib, sibmin);
+      if (side == 0) R = sibfar;
+      else L = sibfar;
     }
   }
 }
 
-void launch_refit(Problem &P) {
-  // A listed node has both children inside CTAs of k_refit but spans two,
-  // so it splits at the boundary between them: fewer listed nodes than
-  // k_refit has CTAs.  list_buf[1] (n entries) is free until the rounds.
+void launch_build_tree(Problem &P) {
+  // A listed split has both children inside CTAs of k_build_local but lies at
+  // the edge of one, so it is the boundary between two: fewer listed splits
+  // than k_build_local has CTAs.  list_buf[1] (n entries) is free until the
+  // rounds.
   uint32_t *ready = P.list_buf[1];
   uint32_t *ready_count = P.counters + kRefitReadyCounter;
+  uint2 *split_far = P.split_far;
   cudaMemsetAsync(ready_count, 0, sizeof(uint32_t), P.stream);
-  k_refit<<<grid_for(P.nc, kRefitBlock), kRefitBlock, 0, P.stream>>>(P.pts, P.n, P.nc, P.leaf, P.nodes,
-                                                          P.nlabels, P.parent_leaf, P.up_delta, P.range,
-                                                          P.arrivals, ready, ready_count,
-                                                          (uint32_t)P.n, P.counters + 1);
-  int64_t g = grid_for(P.nc, kRefitBlock) / kRefitUpBlock + 1;
+  const int64_t ctas = grid_for(P.nc, kRefitBlock);
+  k_build_local<<<(unsigned)ctas, kRefitBlock, 0, P.stream>>>(
+      P.keys[0] /*sorted*/, P.code_hi, P.pts, P.n, P.nc, P.leaf, P.nodes, P.nlabels, P.range, split_far,
+      P.arrivals, ready, ready_count, (uint32_t)P.n, P.counters + 1);
+  int64_t g = ctas / kRefitUpBlock + 1;
   if (g > (int64_t)sm_count() * 16) g = (int64_t)sm_count() * 16;
-  k_refit_up<<<(unsigned)g, kRefitUpBlock, 0, P.stream>>>(P.n, P.leaf, P.nodes, P.nlabels, P.up_delta,
-                                                          P.range, P.arrivals, ready, ready_count,
-                                                          (uint32_t)P.n);
+  k_build_up<<<(unsigned)g, kRefitUpBlock, 0, P.stream>>>(
+      P.keys[0], P.code_hi, P.pts, P.n, P.nc, P.leaf, P.nodes, P.nlabels, P.range, split_far,
+      P.arrivals, ready, ready_count, (uint32_t)P.n, P.counters + 1);
   P.launches += 2;
 }
 

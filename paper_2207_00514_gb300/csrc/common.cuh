@@ -257,12 +257,9 @@ struct Problem {
                                       // else nullptr; the sorted low words are keys[0]
   NodeRec *nodes = nullptr;       // nc-1 internal nodes
   uint2 *nlabels = nullptr;       // nc-1: child labels of each internal node (A5)
-  uint32_t *parent_leaf = nullptr;   // nc: (parent << 1) | slot of each leaf chunk
-  uint2 *up_delta = nullptr;         // n-1: x = (parent << 1) | slot (root: kInvalid),
-                                     //      y = leading bits shared by the node's (code,
-                                     //      position) keys; y < 64 means the node holds
-                                     //      exactly the points of one Morton cell
-  uint32_t *arrivals = nullptr;      // n-1 arrival counters (parity = who is second)
+  uint2 *split_far = nullptr;        // nc-1: per split of the build, the far end of the left
+                                     //      and of the right child that reached it
+  uint32_t *arrivals = nullptr;      // nc-1 arrival counters of the splits (parity = who is second)
   uint2 *range = nullptr;            // nc-1: each internal node's leaf-chunk range [first, last]
                                      //      and split (the last chunk of its left child), packed
                                      //      by pack_range (one end of the range is the node itself)
@@ -322,8 +319,9 @@ void launch_gather_u64(Problem &P, const uint64_t *src, const uint32_t *idx, uin
 void launch_gather(Problem &P, const uint32_t *perm);
 void launch_instance_ids(Problem &P);
 void launch_instance_roots(Problem &P);
-void launch_hierarchy(Problem &P);
-void launch_refit(Problem &P);
+// A4: hierarchy, boxes, records, ranges and round-0 child labels in one
+// bottom-up pass (P.arrivals zeroed first)
+void launch_build_tree(Problem &P);
 // sort.cu
 // Tile shape of one sort pass (compile-time knobs; the defaults are the measured best).
 #ifndef EMST_SORT_THREADS

@@ -38,8 +38,17 @@ __device__ __forceinline__ float pair_weight(const float4 &p, const float4 &q,
 // the last tile to finish).
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;  // rows of 32 positions per warp
-constexpr int kScanTileShift = 12;
+// Tile shape of the relabel pass (build knobs): 8 rows of 32 positions per
+// warp at 8 CTAs per SM measured best at 37M halo points (rounds 40.90 ms;
+// 16 rows at 6 CTAs 40.99, 16 at 8 40.92, 4 at 8 41.48).
+#ifndef EMST_SCAN_ROWS_LOG2
+#define EMST_SCAN_ROWS_LOG2 3
+#endif
+#ifndef EMST_SCAN_MIN_BLOCKS
+#define EMST_SCAN_MIN_BLOCKS 8
+#endif
+constexpr int kScanItems = 1 << EMST_SCAN_ROWS_LOG2;  // rows of 32 positions per warp
+constexpr int kScanTileShift = EMST_SCAN_ROWS_LOG2 + 8;
 constexpr int kScanTile = 1 << kScanTileShift;
 static_assert(kScanTile == kScanThreads * kScanItems, "scan tile shape");
 
@@ -104,7 +113,7 @@ __device__ void block_exclusive_scan(const uint32_t *in, uint32_t *out, int64_t 
 // instance lowers both components' bounds for the next round (A6) -- one
 // pass for A9's relabel, A6 and A5's counts.
 template <bool RELABEL>
-__global__ void __launch_bounds__(kScanThreads, 6) k_runs(
+__global__ void __launch_bounds__(kScanThreads, EMST_SCAN_MIN_BLOCKS) k_runs(
     const uint32_t *__restrict__ labels_old, const uint32_t *__restrict__ root,
     const float4 *__restrict__ pts, const uint32_t *__restrict__ inst_of,
     const float *__restrict__ core2, int64_t n,
