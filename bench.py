@@ -35,12 +35,12 @@ WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member count
 # DRAM bytes (read + write) of each round's traversal launch on this workload
 # (37M halo points, seed 2), from one ncu capture of one whole call of the
 # kernel as it is now:
-#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
-#       --cache-control none -k regex:k_traverse -c 11 --csv
-#       python <one emst_compute call on these points>
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:k_traverse -c 11 --csv
+#       python bench.py --workload once
 # (one pass per launch).  Set back to None whenever the traversal kernel changes.
-TRAVERSE_DRAM_BYTES_PER_ROUND = [5245.9e6, 6230.5e6, 4761.5e6, 3146.2e6, 2022.4e6, 1655.2e6,
-                                 1515.1e6, 1435.7e6, 1389.7e6, 1360.2e6, 1339.3e6]
+TRAVERSE_DRAM_BYTES_PER_ROUND = [5228.9e6, 6226.2e6, 4670.4e6, 3008.7e6, 1810.5e6, 1423.6e6,
+                                 1217.5e6, 1121.2e6, 1067.6e6, 1046.8e6, 1037.3e6]
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")
 
@@ -160,15 +160,16 @@ def measured_peaks():
 #    component's best so far (8), its result (8), the update of the
 #    component's 16-byte (w, min id, max id, outside label) minimum (16) --
 #    and per distinct internal node visited its 64-B record;
-#  later rounds: per point 32 B to decide whether to search at all -- label
-#    (4), component bound (4) and best so far (8), its previous result (8),
-#    its new result (8) -- plus per query that searches 36 B -- its point
-#    (16), its previous neighbour's label (4), the minimum's update (16) --
-#    and per distinct internal node visited 72 B: the record (64) and its
-#    child labels (8).
+#  later rounds: per point 24 B to decide whether to search at all -- label
+#    (4), component bound (4) and best so far (8), its previous result (8)
+#    (a skipped query rewrites its result only when it held a neighbour,
+#    not counted) -- plus per query that searches 44 B -- its point (16),
+#    its previous neighbour's label (4), its new result (8), the minimum's
+#    update (16) -- and per distinct internal node visited 72 B: the record
+#    (64) and its child labels (8).
 BYTES_FIRST_QUERY = 56
-BYTES_POINT = 32
-BYTES_SEARCH = 36
+BYTES_POINT = 24
+BYTES_SEARCH = 44
 BYTES_RECORD_FIRST = 64
 BYTES_RECORD = 72
 
