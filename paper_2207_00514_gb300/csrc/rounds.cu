@@ -434,6 +434,78 @@ static void launch_traverse_queue(Problem &P, const TravArgs &A, bool carried, b
   P.launches += 1;
 }
 
+// ---------------------------------------------------------------------------
+// The queries of a round that need a search (rounds from kCompactFromRound
+// on, where most points skip theirs): a point whose lower bound exceeds its
+// component's cutoff as the round starts (upper bound, best so far) is
+// finished here exactly as traverse_one would finish it; the others are
+// listed, four curve positions per thread, in curve order within each warp's
+// 128 positions (one atomic per warp), for the traversal, which tests them
+// again against the cutoff as it has shrunk by then.  The list is a subset of
+// what the one-thread-per-point launch would search, so the result is the
+// same; its searches fill whole warps instead of a third of each.
+// ---------------------------------------------------------------------------
+#ifndef EMST_COMPACT_FROM_ROUND
+#define EMST_COMPACT_FROM_ROUND 3
+#endif
+constexpr int kCompactFromRound = EMST_COMPACT_FROM_ROUND;
+constexpr uint32_t kActiveCounter = 50;  // P.counters slot: listed queries
+
+__global__ void __launch_bounds__(256) k_active(const uint32_t *__restrict__ labels,
+                                                const uint32_t *__restrict__ bound,
+                                                const CompBest *comp, uint2 *__restrict__ res,
+                                                int64_t n, uint32_t *__restrict__ list,
+                                                uint32_t *count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  uint32_t act = 0;
+  if (i0 < n) {
+    uint32_t lab[4];
+    uint2 prev[4];
+    if (i0 + 4 <= n) {  // 16-byte loads (i0 is a multiple of 4; the arrays are 256-B aligned)
+      const uint4 l4 = *reinterpret_cast<const uint4 *>(labels + i0);
+      const uint4 ra = reinterpret_cast<const uint4 *>(res + i0)[0];
+      const uint4 rb = reinterpret_cast<const uint4 *>(res + i0)[1];
+      lab[0] = l4.x; lab[1] = l4.y; lab[2] = l4.z; lab[3] = l4.w;
+      prev[0] = make_uint2(ra.x, ra.y); prev[1] = make_uint2(ra.z, ra.w);
+      prev[2] = make_uint2(rb.x, rb.y); prev[3] = make_uint2(rb.z, rb.w);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        lab[j] = i0 + j < n ? labels[i0 + j] : 0u;
+        prev[j] = i0 + j < n ? res[i0 + j] : make_uint2(0u, kInvalid);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (i0 + j >= n) continue;
+      float r = bound_to_radius(__ldg(bound + lab[j]));
+      const uint32_t cw =
+          (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(&comp[lab[j]].key)) >> 32);
+      r = fminf(r, bound_to_radius(cw));
+      if (__uint_as_float(prev[j].x) > r) {
+        if (prev[j].y != kInvalid) res[i0 + j] = make_uint2(prev[j].x, kInvalid);
+      } else {
+        act |= 1u << j;
+      }
+    }
+  }
+  const uint32_t c = (uint32_t)__popc(act);
+  uint32_t x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  uint32_t base = 0;
+  if (lane == 31 && x) base = atomicAdd(count, x);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  uint32_t at = base + x - c;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if ((act >> j) & 1u) list[at++] = (uint32_t)(i0 + j);
+}
+
 using TravKernel = void (*)(TravArgs, const uint32_t *, const uint32_t *);
 
 static void launch_trav(TravKernel k, int g, int block, cudaStream_t s, const TravArgs &A,
@@ -481,8 +553,20 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   }
   const uint32_t *list = learned_pass == 2 ? P.rerun_list : nullptr;
   const uint32_t *list_count = learned_pass == 2 ? P.counters + 13 : nullptr;
-  const int g = learned_pass == 2 ? sm_count() * 8 : grid_for(P.n, block);
+  int g = learned_pass == 2 ? sm_count() * 8 : grid_for(P.n, block);
   cudaStream_t s = P.stream;
+  if (carried && seeded && !radius_in && learned_pass == 0 && round >= kCompactFromRound) {
+    // the queries that need a search, listed (vals[1] is free during the rounds)
+    uint32_t *active = P.vals[1];
+    uint32_t *active_count = P.counters + kActiveCounter;
+    cudaMemsetAsync(active_count, 0, sizeof(uint32_t), s);
+    k_active<<<(unsigned)grid_for((P.n + 3) / 4, 256), 256, 0, s>>>(P.labels, P.bound, P.comp, P.res,
+                                                                     P.n, active, active_count);
+    P.launches += 1;
+    list = active;
+    list_count = active_count;
+    g = sm_count() * (2048 / block);  // one resident wave, each thread walking the list
+  }
 #define EMST_TRAV2(C, R, K, S, H, L) launch_trav(k_traverse<C, R, K, S, H, L, false, false>, g, block, s, A, list, list_count)
 #define EMST_TRAV_FIRST(K, H) launch_trav(k_traverse<false, false, K, true, H, false, true, false>, g, block, s, A, list, list_count)
 #define EMST_TRAV_MRD(C, K, H) launch_trav(k_traverse<C, false, K, true, H, false, false, true>, g, block, s, A, list, list_count)
