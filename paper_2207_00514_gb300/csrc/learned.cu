@@ -629,6 +629,7 @@ void launch_log_samples(Problem &P, int round, bool carried) {
   T.comp = P.comp;
   T.n = P.n;
   T.status = P.counters + 1;
+  T.queue = nullptr;
   T.visits = nullptr;
   T.queries = nullptr;
   T.seen = nullptr;

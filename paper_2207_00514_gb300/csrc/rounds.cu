@@ -281,7 +281,22 @@ template <bool CARRIED, bool RADIUS_IN, bool COUNT, bool SEEDED, bool CHUNKS, bo
 __global__ void __launch_bounds__(kTraverseMaxBlock, EMST_TRAVERSE_MIN_BLOCKS) k_traverse(TravArgs A, const uint32_t *__restrict__ list,
                                                      const uint32_t *__restrict__ list_count) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (list) {
+  if (list && A.queue) {
+    // the next 32 entries for this warp, in list order, so the queries in
+    // flight stay a window of the list (and of the curve) that L2 holds
+    const uint32_t count = *list_count;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(A.queue, 32u);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= count) break;
+      if (base + lane < count)
+        traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES, LBT>(
+            A, __ldg(list + base + lane));
+      __syncwarp();
+    }
+  } else if (list) {
     const int64_t count = *list_count;
     for (int64_t t = gid; t < count; t += (int64_t)gridDim.x * blockDim.x)
       traverse_one<CARRIED, RADIUS_IN, COUNT, SEEDED, CHUNKS, LEARNED, FIRST, MRD, TIES, LBT>(A, __ldg(list + t));
@@ -436,20 +451,31 @@ static void launch_traverse_queue(Problem &P, const TravArgs &A, bool carried, b
 
 // ---------------------------------------------------------------------------
 // The queries of a round that need a search (rounds from kCompactFromRound
-// on, where most points skip theirs): a point whose lower bound exceeds its
+// on, where many points skip theirs): a point whose lower bound exceeds its
 // component's cutoff as the round starts (upper bound, best so far) is
 // finished here exactly as traverse_one would finish it; the others are
 // listed, four curve positions per thread, in curve order within each warp's
 // 128 positions (one atomic per warp), for the traversal, which tests them
 // again against the cutoff as it has shrunk by then.  The list is a subset of
 // what the one-thread-per-point launch would search, so the result is the
-// same; its searches fill whole warps instead of a third of each.
+// same; its searches fill whole warps instead of a third of each.  The
+// traversal's warps take the list 32 entries at a time from a counter, in
+// list order, so the queries in flight stay one window of the curve whose
+// node records L2 holds (a grid-stride walk spread them: round 3 read twice
+// the DRAM bytes).  Measured at 37M halo points, ms per call: first listed
+// round 1 / 2 / 3 with the ordered warps 45.48 / 45.31 / 46.40, with the
+// grid-stride walk 2 / 3 / 4 / 5 48.46 / 48.24 / 49.43 / 49.71, no list
+// 50.41.
 // ---------------------------------------------------------------------------
 #ifndef EMST_COMPACT_FROM_ROUND
-#define EMST_COMPACT_FROM_ROUND 3
+#define EMST_COMPACT_FROM_ROUND 2
 #endif
 constexpr int kCompactFromRound = EMST_COMPACT_FROM_ROUND;
 constexpr uint32_t kActiveCounter = 50;  // P.counters slot: listed queries
+constexpr uint32_t kActiveQueue = 51;    // P.counters slot: list entries handed out
+#ifndef EMST_LIST_QUEUE
+#define EMST_LIST_QUEUE 1
+#endif
 
 __global__ void __launch_bounds__(256) k_active(const uint32_t *__restrict__ labels,
                                                 const uint32_t *__restrict__ bound,
@@ -517,7 +543,10 @@ static void launch_trav(TravKernel k, int g, int block, cudaStream_t s, const Tr
 // from the second round after the first on: the round after the first still
 // searches nearly every point, so its bounds would cost it more than they
 // save the rounds after it.
-static bool track_lower_bounds(int round) { return round < 0 || round >= 2; }
+#ifndef EMST_LB_FROM_ROUND
+#define EMST_LB_FROM_ROUND 2
+#endif
+static bool track_lower_bounds(int round) { return round < 0 || round >= EMST_LB_FROM_ROUND; }
 
 void launch_traverse(Problem &P, bool carried, const float *radius_in, int block, bool count,
                      bool seeded, int learned_pass, bool first, int round) {
@@ -544,6 +573,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   A.seen = P.seen;
   A.pred_r = P.pred_r;
   A.r_used = P.r_used;
+  A.queue = nullptr;
   // learned_pass: 0 = plain, 1 = with the proposed radii, 2 = rerun of the
   // listed points with the plain cutoff
   // the persistent work-queue form serves the plain rounds on one-point leaves
@@ -565,7 +595,11 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
     P.launches += 1;
     list = active;
     list_count = active_count;
-    g = sm_count() * (2048 / block);  // one resident wave, each thread walking the list
+    g = sm_count() * (2048 / block);  // one resident wave
+#if EMST_LIST_QUEUE
+    A.queue = P.counters + kActiveQueue;  // warps take the list in order
+    cudaMemsetAsync(A.queue, 0, sizeof(uint32_t), s);
+#endif
   }
 #define EMST_TRAV2(C, R, K, S, H, L) launch_trav(k_traverse<C, R, K, S, H, L, false, false>, g, block, s, A, list, list_count)
 #define EMST_TRAV_FIRST(K, H) launch_trav(k_traverse<false, false, K, true, H, false, true, false>, g, block, s, A, list, list_count)

@@ -376,6 +376,8 @@ struct TravArgs {
   uint32_t *seen;               // COUNT: bitmap of the internal nodes visited
   const float *pred_r;  // LEARNED: proposed cutoff of each point
   float *r_used;        // LEARNED: cutoff each query was exact within (+inf: skipped)
+  uint32_t *queue;      // a listed launch: warps take 32 list entries at a time, in list
+                        // order, from this counter (null: a grid-stride walk of the list)
 };
 
 // The first half of a query: its cutoff, and whether it needs a search at all.
