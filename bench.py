@@ -32,15 +32,17 @@ sys.path.insert(0, ROOT)
 METRIC = "EMST Mpoints/s at 37M 3D clustered, plain vs learned-radius; % HBM roofline"
 WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member counts m^-1.9 on "
             "[10, 1e5], c = 5, r_vir = 0.01 (m/1e5)^(1/3)), 20% uniform, unit box, seed 2")
-# DRAM bytes (read + write) of each round's traversal launch on this workload
-# (37M halo points, seed 2), from one ncu capture of one whole call of the
-# kernel as it is now:
+# DRAM bytes (read + write) of each round's traversal on this workload (37M
+# halo points, seed 2): its k_traverse launch, plus from round 2 on the
+# k_active launch that lists the queries to search (inside the round's CUDA
+# events), from one ncu capture of one whole call of the kernels as they are
+# now:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-#       --clock-control none -k regex:k_traverse -c 11 --csv
+#       --clock-control none -k regex:"k_traverse|k_active" -c 20 --csv
 #       python bench.py --workload once
-# (one pass per launch).  Set back to None whenever the traversal kernel changes.
-TRAVERSE_DRAM_BYTES_PER_ROUND = [5228.9e6, 6226.2e6, 4670.4e6, 3008.7e6, 1810.5e6, 1423.6e6,
-                                 1217.5e6, 1121.2e6, 1067.6e6, 1046.8e6, 1037.3e6]
+# (one pass per launch).  Set back to None whenever those kernels change.
+TRAVERSE_DRAM_BYTES_PER_ROUND = [5220.1e6, 6215.8e6, 8873.7e6, 4307.6e6, 1962.2e6, 1446.0e6,
+                                 834.1e6, 541.9e6, 474.1e6, 455.6e6, 444.7e6]
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")
 

@@ -506,8 +506,11 @@ __global__ void __launch_bounds__(256) k_active(const uint32_t *__restrict__ lab
     for (int j = 0; j < 4; ++j) {
       if (i0 + j >= n) continue;
       float r = bound_to_radius(__ldg(bound + lab[j]));
+      // (no query of the round has run yet, so the entries are fixed during
+      // this kernel and may come through L1: in the last rounds every point
+      // reads one of a handful of them)
       const uint32_t cw =
-          (uint32_t)(__ldcg(reinterpret_cast<const unsigned long long *>(&comp[lab[j]].key)) >> 32);
+          (uint32_t)(__ldg(reinterpret_cast<const unsigned long long *>(&comp[lab[j]].key)) >> 32);
       r = fminf(r, bound_to_radius(cw));
       if (__uint_as_float(prev[j].x) > r) {
         if (prev[j].y != kInvalid) res[i0 + j] = make_uint2(prev[j].x, kInvalid);
