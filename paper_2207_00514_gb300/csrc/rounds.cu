@@ -454,9 +454,10 @@ static void launch_traverse_queue(Problem &P, const TravArgs &A, bool carried, b
 // on, where many points skip theirs): a point whose lower bound exceeds its
 // component's cutoff as the round starts (upper bound, best so far) is
 // finished here exactly as traverse_one would finish it; the others are
-// listed, four curve positions per thread, in curve order within each warp's
-// 128 positions (one atomic per warp), for the traversal, which tests them
-// again against the cutoff as it has shrunk by then.  The list is a subset of
+// listed in curve order (k_active_count flags them and counts them per tile,
+// its last CTA scans the tile counts, k_active_write writes the list) for
+// the traversal, which tests them again against the cutoff as it has shrunk
+// by then.  The list is a subset of
 // what the one-thread-per-point launch would search, so the result is the
 // same; its searches fill whole warps instead of a third of each.  The
 // traversal's warps take the list 32 entries at a time from a counter, in
@@ -473,10 +474,19 @@ static void launch_traverse_queue(Problem &P, const TravArgs &A, bool carried, b
 constexpr int kCompactFromRound = EMST_COMPACT_FROM_ROUND;
 constexpr uint32_t kActiveCounter = 50;  // P.counters slot: listed queries
 constexpr uint32_t kActiveQueue = 51;    // P.counters slot: list entries handed out
+constexpr uint32_t kActiveDone = 52;     // P.counters slot: tiles of k_active_count finished
+#ifndef EMST_ORDERED_UNTIL_ROUND
+#define EMST_ORDERED_UNTIL_ROUND 6
+#endif
+constexpr int kOrderedUntilRound = EMST_ORDERED_UNTIL_ROUND;  // exact curve order before this round
 #ifndef EMST_LIST_QUEUE
 #define EMST_LIST_QUEUE 1
 #endif
 
+// The same with one atomic per warp of 128 positions (four per thread):
+// the list is in curve order only within each warp's positions, which costs
+// the traversal locality while many queries are listed but saves the count
+// pass's scan when few are (rounds from kOrderedUntilRound on).
 __global__ void __launch_bounds__(256) k_active(const uint32_t *__restrict__ labels,
                                                 const uint32_t *__restrict__ bound,
                                                 const CompBest *comp, uint2 *__restrict__ res,
@@ -535,6 +545,111 @@ __global__ void __launch_bounds__(256) k_active(const uint32_t *__restrict__ lab
     if ((act >> j) & 1u) list[at++] = (uint32_t)(i0 + j);
 }
 
+// Eight curve positions per thread, 2,048 per CTA (one scan tile): the skip
+// test, the positions to search as one byte of flags per thread, the tile's
+// count of them, and (last CTA to finish) the exclusive scan of the tile
+// counts and the list's length.
+constexpr int kActiveThreads = 256;
+constexpr int kActiveTile = kActiveThreads * 8;
+static_assert(kActiveTile == kScanTile, "one scan tile per CTA of k_active_count");
+
+__global__ void __launch_bounds__(kActiveThreads) k_active_count(
+    const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound, const CompBest *comp,
+    uint2 *__restrict__ res, int64_t n, uint8_t *__restrict__ flags, uint32_t *tile_total,
+    uint32_t *tile_prefix, uint32_t *done, uint32_t *count) {
+  __shared__ uint32_t s_warp[kActiveThreads / 32];
+  __shared__ uint32_t s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t t = (int64_t)blockIdx.x * kActiveThreads + tid;
+  const int64_t i0 = t * 8;
+  uint32_t act = 0;
+  if (i0 < n) {
+    uint32_t lab[8];
+    uint2 prev[8];
+    if (i0 + 8 <= n) {  // 16-byte loads (i0 is a multiple of 8; the arrays are 256-B aligned)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint4 l4 = reinterpret_cast<const uint4 *>(labels + i0)[h];
+        lab[4 * h] = l4.x; lab[4 * h + 1] = l4.y; lab[4 * h + 2] = l4.z; lab[4 * h + 3] = l4.w;
+      }
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const uint4 r = reinterpret_cast<const uint4 *>(res + i0)[h];
+        prev[2 * h] = make_uint2(r.x, r.y);
+        prev[2 * h + 1] = make_uint2(r.z, r.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        lab[j] = i0 + j < n ? labels[i0 + j] : 0u;
+        prev[j] = i0 + j < n ? res[i0 + j] : make_uint2(0u, kInvalid);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (i0 + j >= n) continue;
+      float r = bound_to_radius(__ldg(bound + lab[j]));
+      // (no query of the round has run yet, so the entries are fixed during
+      // this kernel and may come through L1: in the last rounds every point
+      // reads one of a handful of them)
+      const uint32_t cw =
+          (uint32_t)(__ldg(reinterpret_cast<const unsigned long long *>(&comp[lab[j]].key)) >> 32);
+      r = fminf(r, bound_to_radius(cw));
+      if (__uint_as_float(prev[j].x) > r) {
+        if (prev[j].y != kInvalid) res[i0 + j] = make_uint2(prev[j].x, kInvalid);
+      } else {
+        act |= 1u << j;
+      }
+    }
+    flags[t] = (uint8_t)act;
+  }
+  const uint32_t wsum = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(act));
+  if (lane == 0) s_warp[warp] = wsum;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kActiveThreads / 32; ++w) total += s_warp[w];
+    tile_total[blockIdx.x] = total;
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    block_exclusive_scan(tile_total, tile_prefix, gridDim.x);
+    __syncthreads();
+    if (tid == 0) *count = tile_prefix[gridDim.x - 1] + __ldcg(tile_total + gridDim.x - 1);
+  }
+}
+
+// The list in curve order: each tile's positions after the positions of all
+// earlier tiles, in order within the tile.
+__global__ void __launch_bounds__(kActiveThreads) k_active_write(const uint8_t *__restrict__ flags,
+                                                                 const uint32_t *__restrict__ tile_prefix,
+                                                                 int64_t n, uint32_t *__restrict__ list) {
+  __shared__ uint32_t s_warp[kActiveThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t t = (int64_t)blockIdx.x * kActiveThreads + tid;
+  const int64_t i0 = t * 8;
+  const uint32_t act = i0 < n ? (uint32_t)flags[t] : 0u;
+  const uint32_t c = (uint32_t)__popc(act);
+  uint32_t x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int w = 0; w < warp; ++w) before += s_warp[w];
+  uint32_t at = __ldg(tile_prefix + blockIdx.x) + before + x - c;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if ((act >> j) & 1u) list[at++] = (uint32_t)(i0 + j);
+}
+
 using TravKernel = void (*)(TravArgs, const uint32_t *, const uint32_t *);
 
 static void launch_trav(TravKernel k, int g, int block, cudaStream_t s, const TravArgs &A,
@@ -589,13 +704,28 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
   int g = learned_pass == 2 ? sm_count() * 8 : grid_for(P.n, block);
   cudaStream_t s = P.stream;
   if (carried && seeded && !radius_in && learned_pass == 0 && round >= kCompactFromRound) {
-    // the queries that need a search, listed (vals[1] is free during the rounds)
+    // the queries that need a search, listed in curve order (vals[1] and
+    // keys[1] are free during the rounds: the list, and the flags and tile
+    // counts behind it)
     uint32_t *active = P.vals[1];
     uint32_t *active_count = P.counters + kActiveCounter;
-    cudaMemsetAsync(active_count, 0, sizeof(uint32_t), s);
-    k_active<<<(unsigned)grid_for((P.n + 3) / 4, 256), 256, 0, s>>>(P.labels, P.bound, P.comp, P.res,
-                                                                     P.n, active, active_count);
-    P.launches += 1;
+    const int64_t tiles = (P.n + kActiveTile - 1) / kActiveTile;
+    uint8_t *flags = reinterpret_cast<uint8_t *>(P.keys[1]);
+    uint32_t *tile_total = reinterpret_cast<uint32_t *>(P.keys[1]) + ((P.n + 8 * 256 - 1) / (8 * 256)) * 64;
+    uint32_t *tile_prefix = tile_total + tiles;
+    if (round < kOrderedUntilRound) {
+      cudaMemsetAsync(P.counters + kActiveDone, 0, sizeof(uint32_t), s);
+      k_active_count<<<(unsigned)tiles, kActiveThreads, 0, s>>>(P.labels, P.bound, P.comp, P.res, P.n,
+                                                               flags, tile_total, tile_prefix,
+                                                               P.counters + kActiveDone, active_count);
+      k_active_write<<<(unsigned)tiles, kActiveThreads, 0, s>>>(flags, tile_prefix, P.n, active);
+      P.launches += 2;
+    } else {
+      cudaMemsetAsync(active_count, 0, sizeof(uint32_t), s);
+      k_active<<<(unsigned)grid_for((P.n + 3) / 4, 256), 256, 0, s>>>(P.labels, P.bound, P.comp, P.res,
+                                                                       P.n, active, active_count);
+      P.launches += 1;
+    }
     list = active;
     list_count = active_count;
     g = sm_count() * (2048 / block);  // one resident wave
