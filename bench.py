@@ -34,15 +34,15 @@ WORKLOAD = ("37,000,000 FP32 3D points: 80% in NFW halos (power-law member count
             "[10, 1e5], c = 5, r_vir = 0.01 (m/1e5)^(1/3)), 20% uniform, unit box, seed 2")
 # DRAM bytes (read + write) of each round's traversal on this workload (37M
 # halo points, seed 2): its k_traverse launch, plus from round 2 on the
-# k_active launch that lists the queries to search (inside the round's CUDA
+# k_active launches that list the queries to search (inside the round's CUDA
 # events), from one ncu capture of one whole call of the kernels as they are
 # now:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-#       --clock-control none -k regex:"k_traverse|k_active" -c 20 --csv
+#       --clock-control none -k regex:"k_traverse|k_active" -c 24 --csv
 #       python bench.py --workload once
 # (one pass per launch).  Set back to None whenever those kernels change.
-TRAVERSE_DRAM_BYTES_PER_ROUND = [5220.1e6, 6215.8e6, 8873.7e6, 4307.6e6, 1962.2e6, 1446.0e6,
-                                 834.1e6, 541.9e6, 474.1e6, 455.6e6, 444.7e6]
+TRAVERSE_DRAM_BYTES_PER_ROUND = [5220.5e6, 6216.1e6, 6480.0e6, 3833.9e6, 1894.4e6, 1398.3e6,
+                                 818.0e6, 537.6e6, 472.7e6, 455.1e6, 444.7e6]
 PAPER_CONTEXT = ("paper: Hacc37M (real 37M 3D cosmology points) on one A100 in < 0.5 s, best-case "
                  "270 MFeatures/s ~ 90 Mpoints/s; other data, other GPU: context only")
 
