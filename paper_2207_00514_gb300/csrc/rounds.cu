@@ -545,13 +545,13 @@ __global__ void __launch_bounds__(256) k_active(const uint32_t *__restrict__ lab
     if ((act >> j) & 1u) list[at++] = (uint32_t)(i0 + j);
 }
 
-// Eight curve positions per thread, 2,048 per CTA (one scan tile): the skip
+// Eight curve positions per thread, 2,048 per CTA: the skip
 // test, the positions to search as one byte of flags per thread, the tile's
 // count of them, and (last CTA to finish) the exclusive scan of the tile
 // counts and the list's length.
 constexpr int kActiveThreads = 256;
 constexpr int kActiveTile = kActiveThreads * 8;
-static_assert(kActiveTile == kScanTile, "one scan tile per CTA of k_active_count");
+static_assert(kActiveThreads == kScanThreads, "block_exclusive_scan runs on a CTA of kScanThreads");
 
 __global__ void __launch_bounds__(kActiveThreads) k_active_count(
     const uint32_t *__restrict__ labels, const uint32_t *__restrict__ bound, const CompBest *comp,
@@ -711,7 +711,7 @@ void launch_traverse(Problem &P, bool carried, const float *radius_in, int block
     uint32_t *active_count = P.counters + kActiveCounter;
     const int64_t tiles = (P.n + kActiveTile - 1) / kActiveTile;
     uint8_t *flags = reinterpret_cast<uint8_t *>(P.keys[1]);
-    uint32_t *tile_total = reinterpret_cast<uint32_t *>(P.keys[1]) + ((P.n + 8 * 256 - 1) / (8 * 256)) * 64;
+    uint32_t *tile_total = reinterpret_cast<uint32_t *>(P.keys[1]) + tiles * (kActiveTile / 8 / 4);  // after the flags
     uint32_t *tile_prefix = tile_total + tiles;
     if (round < kOrderedUntilRound) {
       cudaMemsetAsync(P.counters + kActiveDone, 0, sizeof(uint32_t), s);
