@@ -658,9 +658,10 @@ static void launch_trav(TravKernel k, int g, int block, cudaStream_t s, const Tr
 }
 
 // The tighter lower bound of empty searches (traverse_one's LB) is tracked
-// from the second round after the first on: the round after the first still
-// searches nearly every point, so its bounds would cost it more than they
-// save the rounds after it.
+// from round 2 on (rounds count from 0): round 1 still searches nearly every
+// point, so tracking there would cost it more than its bounds save the
+// rounds after it (measured: from round 1 / 2 / 3, 48.36 / 48.35 / 48.56 ms
+// per call at 37M halo points).
 #ifndef EMST_LB_FROM_ROUND
 #define EMST_LB_FROM_ROUND 2
 #endif
